@@ -1,0 +1,76 @@
+"""Many independent chains of surrogate-only DINO-mMALA (oracle driver).
+
+TEST INFRASTRUCTURE ONLY (see `oracle/__init__.py`).
+
+One step is one transition of every chain: Alg. 1 lines 1-6 (reduced proposal,
+surrogate evaluation, first-stage acceptance with rho_r^(1)) with the
+complement drawn as in Prop. 5.1 so that an accepted chain moves its full
+field m to m^dagger (Alg. 1 lines 7-8).  There is no second stage: the target
+is the surrogate posterior.
+
+Random numbers (see `philox`): step j of chain c uses XI(j, c) for the r
+reduced normals, U(j, c) for the accept uniform and Z(j, c) for the N normals
+of the complement prior draw; the initial prior draw uses INIT(0, c).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import mmala, philox, prior
+
+
+class OracleChains:
+    def __init__(self, sur: mmala.Surrogate, E, D, n_grid: int, gamma: float, delta: float,
+                 n_chains: int, dt: float, seed: int, m0=None, chain_ids=None):
+        self.sur, self.E, self.D = sur, np.asarray(E), np.asarray(D)
+        self.n_grid, self.gamma, self.delta = n_grid, gamma, delta
+        self.dt, self.seed = float(dt), int(seed)
+        self.ids = (np.arange(n_chains, dtype=np.uint64) if chain_ids is None
+                    else np.asarray(chain_ids, dtype=np.uint64))
+        C = len(self.ids)
+        N = n_grid * n_grid
+        if m0 is None:
+            z = philox.normals(seed, philox.STREAM_INIT, 0, self.ids, N)
+            m0 = prior.prior_sample(n_grid, gamma, delta, z)
+        self.m = np.array(np.broadcast_to(np.asarray(m0, dtype=np.float64), (C, N)))
+        self.m_r = self.m @ self.E.T                     # m_r = Psi_r^* m (eq:projector)
+        self.geo = mmala.geometry(sur, self.m_r)
+        self.step_index = 0
+        self.accepts = np.zeros(C, dtype=np.int64)
+        self.last = None
+
+    def step(self, n_steps: int = 1):
+        for _ in range(n_steps):
+            self._step()
+
+    def _step(self):
+        j = self.step_index
+        sur, dt, r = self.sur, self.dt, self.sur.r
+        N = self.m.shape[1]
+        xi = philox.normals(self.seed, philox.STREAM_XI, j, self.ids, r)
+        u = philox.uniform(self.seed, philox.STREAM_U, j, self.ids)
+        a, geo_a = self.m_r, self.geo
+        mu, b = mmala.reduced_proposal(a, geo_a, xi, dt)
+        geo_b = mmala.geometry(sur, b)
+        lr = mmala.log_rho(a, geo_a, b, geo_b, dt)
+        log_u = np.log(u)
+        acc = mmala.accept(log_u, lr)
+        z = philox.normals(self.seed, philox.STREAM_Z, j, self.ids, N)
+        M = prior.prior_sample(self.n_grid, self.gamma, self.delta, z)
+        m_new = mmala.field_proposal(self.m, b, M, self.E, self.D, dt)
+        self.last = dict(mu=mu, b=b, log_rho=lr, log_u=log_u, accepted=acc.copy(),
+                         phi_b=geo_b.phi, hld_b=geo_b.hld, J_b=geo_b.J, f_b=geo_b.f,
+                         g_b=geo_b.g, L_b=geo_b.L, m_new=m_new)
+        self.m = np.where(acc[:, None], m_new, self.m)
+        self.m_r = np.where(acc[:, None], b, a)
+        g = self.geo
+        self.geo = mmala.Geometry(
+            f=np.where(acc[:, None], geo_b.f, g.f),
+            J=np.where(acc[:, None, None], geo_b.J, g.J),
+            phi=np.where(acc, geo_b.phi, g.phi),
+            g=np.where(acc[:, None], geo_b.g, g.g),
+            H=np.where(acc[:, None, None], geo_b.H, g.H),
+            L=np.where(acc[:, None, None], geo_b.L, g.L),
+            hld=np.where(acc, geo_b.hld, g.hld))
+        self.accepts += acc
+        self.step_index += 1
