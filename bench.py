@@ -1,0 +1,338 @@
+"""Throughput of the many-chain surrogate mMALA step (proposals/s) on GB300.
+
+One step = one transition of every chain of the workload: reduced proposal,
+tensor-core MLP forward and Jacobian, FP64 Gauss-Newton Cholesky and
+log-acceptance, complement draw and field update.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Default workload: 16384 chains, r = 200 DIS basis, GELU 200-400-400-100,
+65 x 65 grid, dt = 0.5, BF16 slices on tcgen05 with FP64 Cholesky.  The FP64
+plain step (4096 chains, r = 200 KLE) is timed beside it.  With N > 1 (under
+torchrun) every rank runs its own chain shard (weak scaling, no collective on
+the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from workloads import (BASIS_KLE, CONFIGS, SEED_CHAINS, make_data,  # noqa: E402
+                       surrogate_inputs)
+
+METRIC = "mMALA proposals/s at r=200 (BF16/FP32 vs FP64 plain)"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 peak of GB300 from the pool's profiling notes (no measured FP64 figure exists)
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def fp64_flops_geometry(r: int, d_y: int) -> float:
+    """Algorithmic FP64 flops of one geometry/accept launch per chain.
+
+    Cholesky r^3/3, two triangular solves 2 r^2, three triangular matvecs 3 r^2,
+    gradient J^T res 2 r d_y (the Gauss-Newton product J^T J runs in FP32).
+    """
+    return r ** 3 / 3.0 + 5.0 * r * r + 2.0 * r * d_y
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.result = None
+        if self.proc is None:
+            return False
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r.split(",") for r in out.strip().splitlines() if r.count(",") >= 7]
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                mx = float(r[1])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if r[4 + k].strip().lower() == "active":
+                    reasons.add(nm)
+        if sm:
+            loaded = [x for x in sm if x > 0.5 * (mx or max(sm))] or sm
+            self.result = {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx,
+                           "reasons": sorted(reasons), "samples": len(sm)}
+        return False
+
+
+def load_surrogate(dino, ctx, w):
+    inp = surrogate_inputs(w)
+    prec = dino.DINO_PREC_BF16 if w.precision == "bf16" else dino.DINO_PREC_FP64
+    sid = dino.dino_load_surrogate(
+        ctx, n_grid=w.n_grid, prior_gamma=w.prior_gamma, prior_delta=w.prior_delta, r=w.r,
+        widths=w.widths, activation=w.activation, W=inp["Ws"], b=inp["bs"],
+        basis_kind=w.basis_kind, basis_gauss=inp["G"], precision=prec)
+    twin = dino.dino_load_surrogate(
+        ctx, n_grid=w.n_grid, prior_gamma=w.prior_gamma, prior_delta=w.prior_delta, r=w.r,
+        widths=w.widths, activation=w.activation, W=inp["Ws"], b=inp["bs"],
+        basis_kind=BASIS_KLE, precision=dino.DINO_PREC_FP64)
+    f0 = dino.dino_surrogate_eval(ctx, twin, inp["m_true_r"], w.d_y, want_L=False)["f"][0]
+    dino.dino_unload_surrogate(ctx, twin)
+    y, nv = make_data(f0, inp["eps"], w.noise_frac)
+    dino.dino_set_data(ctx, sid, y, nv)
+    return sid
+
+
+def timed_steps(dino, ctx, pool, steps, st, barrier):
+    """Device time of `steps` transitions (CUDA events on the stream the library launches on)."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(st)
+    dino.dino_chains_step(ctx, pool, steps, stats=False)
+    e1.record(st)
+    torch.cuda.synchronize()
+    barrier()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def run_ours(args, rank, world, device):
+    import torch
+    import paper_2403_08220_gb300 as dino
+
+    torch.cuda.set_device(device)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist = dist_mod
+        dist.init_process_group("nccl", device_id=torch.device("cuda", device))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    w = CONFIGS[args.workload]
+    C = args.chains or w.n_chains
+    # a dedicated stream: the library launches every kernel on it and the
+    # CUDA events below are recorded on it
+    stream = torch.cuda.Stream(device=device)
+    assert stream.cuda_stream != 0
+    ctx = dino.dino_init(device, 0, stream.cuda_stream, 0)
+    sid = load_surrogate(dino, ctx, w)
+    base = rank * C                       # weak scaling: each rank owns its chain range
+    pool = dino.dino_chains_create(ctx, sid, C, w.dt, SEED_CHAINS, base)
+    dino.dino_chains_step(ctx, pool, args.warmup, stats=False)
+    dino.dino_sync(ctx)
+    n0 = dino.dino_launch_count(ctx)
+    with ClockSampler(device) as clk:
+        secs = timed_steps(dino, ctx, pool, args.steps, stream, barrier)
+    launches = dino.dino_launch_count(ctx) - n0
+    stats = dino.dino_chains_step(ctx, pool, 1)
+    secs = max_over_ranks(secs)
+    value = world * C * args.steps / secs
+
+    # per-kernel times (CUDA events around each launch) over a second pass
+    ctx_t = dino.dino_init(device, 0, stream.cuda_stream, dino.DINO_FLAG_TIMING)
+    sid_t = load_surrogate(dino, ctx_t, w)
+    pool_t = dino.dino_chains_create(ctx_t, sid_t, C, w.dt, SEED_CHAINS, base)
+    dino.dino_chains_step(ctx_t, pool_t, 1, stats=False)
+    dino.dino_kernel_times(ctx_t, reset=True)
+    dino.dino_chains_step(ctx_t, pool_t, max(2, min(args.steps, 5)), stats=False)
+    kt = dino.dino_kernel_times(ctx_t)
+    dino.dino_chains_destroy(ctx_t, pool_t)
+    ctx_t.close()
+    total = sum(v[0] for v in kt.values()) or 1.0
+    dom = max(kt.items(), key=lambda kv: kv[1][0])
+    geo = kt.get("geometry_accept", dom[1])
+    geo_ms = geo[0] / max(1, geo[1])
+    flops = fp64_flops_geometry(w.r, w.d_y) * C
+    achieved = flops / (geo_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "pipe": "fp64", "kernel": "geometry_accept",
+                "achieved": round(achieved, 4), "peak": FP64_NOMINAL_TFLOPS,
+                "peak_source": "nominal GB300 FP64 (no measured FP64 peak in MEASURED_PEAKS.json)",
+                "unit": "TFLOP/s", "frac": round(achieved / FP64_NOMINAL_TFLOPS, 4),
+                "traffic": None, "share_of_step": round(geo[0] / total, 4),
+                "flops_per_chain": fp64_flops_geometry(w.r, w.d_y)}
+
+    # FP64 plain step beside it (fewer steps: it runs its GEMMs in FP64)
+    fp64_line = None
+    if not args.skip_fp64 and rank == 0:
+        w64 = CONFIGS["r200_kle_fp64"]
+        sid64 = load_surrogate(dino, ctx, w64)
+        p64 = dino.dino_chains_create(ctx, sid64, w64.n_chains, w64.dt, SEED_CHAINS)
+        dino.dino_chains_step(ctx, p64, 1, stats=False)
+        k64 = max(1, min(3, args.steps))
+        s64 = timed_steps(dino, ctx, p64, k64, stream, lambda: None)
+        fp64_line = {"workload": "r200_kle_fp64", "chains": w64.n_chains, "steps": k64,
+                     "proposals_per_s": w64.n_chains * k64 / s64,
+                     "ms_per_step": 1e3 * s64 / k64}
+        dino.dino_chains_destroy(ctx, p64)
+
+    # end to end through the C ABI with host buffers: create from a host m0,
+    # run the steps, read the reduced states and misfits back
+    e2e = None
+    if not args.skip_e2e:
+        rng = np.random.default_rng(rank)
+        m0 = np.ascontiguousarray(0.05 * rng.standard_normal((C, w.N)))
+        barrier()
+        t0 = time.perf_counter()
+        pe = dino.dino_chains_create(ctx, sid, C, w.dt, SEED_CHAINS, base, m0)
+        dino.dino_chains_step(ctx, pe, args.steps, stats=False)
+        st = dino.dino_chains_read(ctx, pe, C, w.r, w.N, field=False)
+        el = max_over_ranks(time.perf_counter() - t0)
+        dino.dino_chains_destroy(ctx, pe)
+        e2e = {"value": world * C * args.steps / el, "unit": "proposals/s",
+               "h2d_bytes_per_step": int(m0.nbytes / args.steps),
+               "d2h_bytes_per_step": int((st["m_r"].nbytes + st["phi"].nbytes +
+                                          st["accepts"].nbytes) / args.steps),
+               "what": f"create {C} chains from host fields + {args.steps} steps + read m_r, phi"}
+    dino.dino_chains_destroy(ctx, pool)
+    ctx.close()
+
+    line = None
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "proposals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f64",
+            "data": "synthetic (seeded weights, DIS basis, data from the surrogate at a seeded truth)",
+            "config": {"workload": f"{args.workload}: {C} chains/GPU, r={w.r} "
+                                   f"{'DIS' if w.basis_kind else 'KLE'}, MLP "
+                                   f"{'-'.join(map(str, w.widths))} GELU, N={w.N}, dt={w.dt}",
+                       "l2": "inputs larger than L2 (Cholesky factors %.1f GB)"
+                             % (C * w.r * (w.r + 1) / 2 * 8 / 1e9),
+                       "parallelism": f"chains sharded over {world} GPU(s)"},
+            "roofline": roofline, "gpu_launches": int(launches),
+            "acceptance_rate": stats["accepts"] / max(1, stats["proposals"]),
+            "kernel_share": {k: round(v[0] / total, 4) for k, v in kt.items()},
+            "fp64_plain": fp64_line, "e2e": e2e,
+            "clocks": clk.result,
+        }
+    if dist is not None:
+        dist.destroy_process_group()
+    return line
+
+
+def cpu_baseline(args, sample_chains=None, sample_steps=None):
+    """The FP64 oracle, untuned, on a bounded sample of the same workload."""
+    from oracle import mlp, mmala, prior
+    from oracle.chains import OracleChains
+    w = CONFIGS[args.workload]
+    inp = surrogate_inputs(w)
+    if w.basis_kind == BASIS_KLE:
+        E, D = prior.kle_basis(w.n_grid, w.prior_gamma, w.prior_delta, w.r)
+    else:
+        E, D = prior.dis_basis(w.n_grid, w.prior_gamma, w.prior_delta, inp["G"])
+    f0, _ = mlp.forward(inp["Ws"], inp["bs"], w.activation, inp["m_true_r"])
+    y, nv = make_data(f0, inp["eps"], w.noise_frac)
+    sur = mmala.Surrogate(Ws=inp["Ws"], bs=inp["bs"], act=w.activation, y=y, noise_var=nv)
+    C = sample_chains or 64
+    K = sample_steps or 2
+    och = OracleChains(sur, E, D, w.n_grid, w.prior_gamma, w.prior_delta, C, w.dt,
+                       seed=SEED_CHAINS)
+    t0 = time.perf_counter()
+    och.step(K)
+    el = time.perf_counter() - t0
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
+    except Exception:
+        cores = os.cpu_count()
+    return {"value": C * K / el, "unit": "proposals/s", "cores": cores, "kind": "oracle",
+            "sample": f"{C} chains x {K} steps of {args.workload} ({el:.1f} s)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="r200_dis_bf16")
+    ap.add_argument("--chains", type=int, default=0)
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--cpu-chains", type=int, default=512)
+    ap.add_argument("--cpu-steps", type=int, default=4)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.warmup < 3:
+        args.warmup = 3
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        w = CONFIGS[args.workload]
+        per_step = []
+        for _ in range(args.warmup):
+            cpu_baseline(args, 8, 1)
+        for _ in range(args.steps):
+            per_step.append(cpu_baseline(args, 8, 1))
+        v = statistics.median([p["value"] for p in per_step])
+        cb = dict(per_step[0])
+        cb["value"] = v
+        cb["sample"] = f"8 chains x 1 step of {args.workload} per timed step"
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": v, "unit": "proposals/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * 8 / v, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: FP64 oracle on host cores",
+                       "chains_per_step": 8, "r": w.r},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "proposals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}))
+        return
+
+    line = run_ours(args, rank, world, local)
+    if rank == 0:
+        if not args.skip_cpu and world == 1:
+            line["cpu_baseline"] = cpu_baseline(args, args.cpu_chains, args.cpu_steps)
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

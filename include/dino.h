@@ -1,0 +1,230 @@
+/*
+ * dino.h -- C ABI of the many-chain surrogate (DINO) mMALA sampler for GB300.
+ *
+ * One transition of C independent chains of surrogate-driven mMALA with
+ * surrogate-only acceptance (Algorithm 1 lines 1-6 of Cao, O'Leary-Roseberry
+ * and Ghattas, "Derivative-informed neural operator acceleration of geometric
+ * MCMC for infinite-dimensional Bayesian inverse problems"), with the
+ * prior-complement draw of Proposition 5.1 (Sec. 5.3) applied to every
+ * proposal so that accepted chains move their full parameter field.
+ *
+ * Conventions for every entry point
+ *   - Every call returns an int status (DINO_OK or a negative error code);
+ *     nothing throws or longjmps across the ABI.
+ *   - Pointers named host_* or documented as "host" are ordinary host memory.
+ *     The library copies what it needs before returning and never retains a
+ *     caller pointer.  Matrices are row-major float64 unless stated otherwise.
+ *   - The library owns all device memory it allocates for a context
+ *     (cudaMalloc on the context's device).  Results are copied into
+ *     caller-owned host buffers; a NULL output pointer skips that output.
+ *   - On error the call leaves the context usable and records a message that
+ *     dino_last_error() returns (valid until the next call on that context).
+ *   - A context is internally serialised: concurrent calls from several host
+ *     threads are safe but run one at a time.
+ *   - Every per-step operation runs in CUDA kernels on the context's stream;
+ *     there is no CPU fallback.  If the device cannot be used, dino_init fails
+ *     with DINO_ECUDA.
+ *
+ * Notation (reduced, whitened coordinates, Sec. 5.1):
+ *   N = n_grid^2 field nodes, r reduced dimension, d_y observations,
+ *   E = Psi_r^* (r x N encoder), D = Psi_r (N x r decoder), E D = I_r,
+ *   f = reduced MLP R^r -> R^{d_y}, J = df/dm_r (d_y x r),
+ *   Gamma = noise_var I,
+ *   Phi(m_r) = |f(m_r) - y|^2 / (2 noise_var),  g = J^T (f - y) / noise_var,
+ *   H = J^T J / noise_var,  L L^T = I + H (lower Cholesky, FP64),
+ *   hld = (1/2) log det(I + H) = sum_j log L_jj,  s = (4 - dt)/(4 + dt).
+ */
+#ifndef DINO_H
+#define DINO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define DINO_OK          0
+#define DINO_PENDING     1   /* serving: request not finished yet */
+#define DINO_EINVAL     (-1) /* invalid argument (shape, range, NULL) */
+#define DINO_ENOMEM     (-2) /* HBM budget or device allocation exceeded */
+#define DINO_ECUDA      (-3) /* a CUDA runtime/driver call failed */
+#define DINO_EBUSY      (-4) /* serving queue full */
+#define DINO_ETIMEOUT   (-5) /* a bounded device or host wait ran out */
+#define DINO_ENOTFOUND  (-6) /* unknown surrogate, pool or ticket id */
+#define DINO_ENUMERIC   (-7) /* non-SPD input or non-finite setup data */
+#define DINO_ESTATE     (-8) /* call not valid in the object's state */
+
+/* ---- enumerations ------------------------------------------------------ */
+#define DINO_ACT_IDENTITY 0
+#define DINO_ACT_TANH     1
+#define DINO_ACT_GELU     2   /* exact x * Phi(x) */
+
+#define DINO_BASIS_KLE      0 /* closed-form Karhunen-Loeve basis (Sec. 4.2) */
+#define DINO_BASIS_DIS      1 /* C_pr^-1-orthonormalised Gaussian vectors (DIS stand-in) */
+#define DINO_BASIS_EXPLICIT 2 /* caller supplies E (r x N) and D (N x r) */
+
+#define DINO_PREC_FP64 0      /* every step in float64 */
+#define DINO_PREC_BF16 1      /* MLP/Jacobian GEMMs on tcgen05 in BF16 (FP32 accum),
+                                 Cholesky, solves and log-acceptance in FP64,
+                                 field update in FP32 */
+
+#define DINO_FLAG_TIMING 1u   /* record per-kernel CUDA-event times */
+
+typedef struct dino_ctx dino_ctx;
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.
+ * hbm_budget_bytes: cap on device memory the context may allocate
+ *   (0 = 90% of the device's free memory at init).
+ * stream: a cudaStream_t (as void*) to launch on, or NULL for a new
+ *   non-blocking stream owned by the context.  A caller stream stays owned by
+ *   the caller and must outlive the context.
+ * flags: DINO_FLAG_* bits.
+ * Errors: EINVAL (out == NULL), ECUDA (no usable device). */
+int dino_init(dino_ctx **out, int device, size_t hbm_budget_bytes, void *stream,
+              unsigned flags);
+
+/* Wait for the stream, free every device allocation, destroy the context. */
+int dino_destroy(dino_ctx *ctx);
+
+/* Last error message of this context ("" if none); owned by the context. */
+const char *dino_last_error(const dino_ctx *ctx);
+
+/* ABI version (major*100 + minor). */
+int dino_version(void);
+
+/* Block until all work issued on the context's stream has finished. */
+int dino_sync(dino_ctx *ctx);
+
+/* ---- surrogate --------------------------------------------------------- */
+
+/* A reduced-basis neural-operator surrogate G~(m) = V f(Psi_r^* m)
+ * (eq:rb_dino, Sec. 4) with its Gaussian prior and data.
+ *
+ * Prior: n_grid x n_grid interior nodes of the unit square, h = 1/(n_grid+1),
+ *   node p = i + n_grid*j; A = prior_delta I - prior_gamma Lap_h (5-point
+ *   Dirichlet stencil / h^2); C_pr = A^-2 (Assumption 2, Sec. 2.2).
+ * MLP: n_layers affine layers; widths[0] = r, widths[n_layers] = d_y;
+ *   W[l] is widths[l+1] x widths[l], b[l] has widths[l+1] entries; the
+ *   activation acts on every hidden layer, the output layer is linear.
+ * Basis: KLE (E, D built from the closed-form eigenpairs; ties in the KLE
+ *   order broken by smaller kx), DIS (basis_gauss = N x r standard normals,
+ *   Q = thin QR with positive diag R, D = A^-1 Q, E = Q^T A), or EXPLICIT
+ *   (E r x N and D N x r given, E D = I_r required to 1e-8).
+ * Data: y (d_y values) and noise_var > 0; y may be NULL and set later with
+ *   dino_set_data (chains cannot be created before data is set).
+ * precision: DINO_PREC_FP64 or DINO_PREC_BF16.
+ * fwd_slices / jac_slices (BF16 only): number of bf16 terms that represent
+ *   each operand of the MLP-forward / Jacobian GEMMs (1..3; 0 = default 3 and
+ *   2).  k terms use the k(k+1)/2 leading cross products, so 2 is the
+ *   "bf16x3" scheme and 3 reaches FP32-level accuracy.
+ * Errors: EINVAL (shapes, r > N, NULL arrays, noise_var <= 0), ENUMERIC
+ *   (E D != I, non-finite data), ENOMEM. */
+typedef struct {
+  int n_grid;
+  double prior_gamma, prior_delta;
+  int r;
+  int n_layers;
+  const int *widths;
+  int activation;
+  const double *const *W;
+  const double *const *b;
+  int basis_kind;
+  const double *basis_gauss;
+  const double *E;
+  const double *D;
+  const double *y;
+  double noise_var;
+  int precision;
+  int fwd_slices;
+  int jac_slices;
+} dino_surrogate_desc;
+
+int dino_load_surrogate(dino_ctx *ctx, const dino_surrogate_desc *desc, int *surrogate_id);
+
+/* Replace the data y (d_y host values) and noise variance of a surrogate.
+ * Pools created later use the new data; existing pools are unaffected
+ * only if they were created before (they keep a reference to the surrogate,
+ * so do not change data while pools of it exist: ESTATE). */
+int dino_set_data(dino_ctx *ctx, int surrogate_id, const double *y, double noise_var);
+
+/* Free a surrogate (ESTATE while chain pools of it exist). */
+int dino_unload_surrogate(dino_ctx *ctx, int surrogate_id);
+
+/* Copy the reduced basis the library built: E (r x N) and D (N x r), host. */
+int dino_read_basis(dino_ctx *ctx, int surrogate_id, double *E, double *D);
+
+/* Evaluate the surrogate and its geometry at n reduced points m_r (n x r,
+ * host) with the surrogate's precision path (Sec. 5.1; Alg. 1 lines 3-4):
+ *   f (n x d_y), J (n x d_y x r), phi (n), g (n x r),
+ *   L (n x r x r, full lower-triangular with zeros above), hld (n).
+ * Any output may be NULL.  With y unset, phi and g are not defined. */
+int dino_surrogate_eval(dino_ctx *ctx, int surrogate_id, int n, const double *m_r,
+                        double *f, double *J, double *phi, double *g, double *L,
+                        double *hld);
+
+/* ---- chain pools ------------------------------------------------------- */
+
+/* Create n_chains chains of surrogate `surrogate_id` with step size dt > 0.
+ * Chain k has global id chain_id_base + k; its random numbers are
+ * Philox4x32-10 with key = seed and counter = (block, step, global id,
+ * stream), stream 0 = reduced noise xi, 1 = accept uniform, 2 = complement
+ * prior draw, 3 = initial prior draw (step 0).  Results therefore do not
+ * depend on how chains are grouped into pools.
+ * m0: n_chains x N host field values, or NULL for prior draws.
+ * The initial state is m_r = E m0 and the surrogate geometry at m_r.
+ * Errors: EINVAL, ENOTFOUND, ESTATE (data unset), ENOMEM. */
+int dino_chains_create(dino_ctx *ctx, int surrogate_id, int n_chains, double dt,
+                       uint64_t seed, uint64_t chain_id_base, const double *m0,
+                       int *pool_id);
+
+typedef struct {
+  uint64_t proposals;   /* chain-steps performed */
+  uint64_t accepts;
+  uint64_t nan_rejects; /* proposals rejected because log rho was not finite */
+  double sum_alpha;     /* sum over proposals of min(1, rho) */
+} dino_step_stats;
+
+/* Advance every chain of the pool by n_steps transitions.  Each transition:
+ * reduced proposal m_r^dagger = mu + sqrt(1-s^2) L^-T xi with
+ * mu = m_r - (1-s)(I+H)^-1 (m_r + g) (eq:reduced_space_sampling in Cholesky
+ * form); surrogate geometry at m_r^dagger; log rho_r^(1) (eq:da_dino_trr_1);
+ * complement draw m^dagger = s m + sqrt(1-s^2) M + D (m_r^dagger - s m_r -
+ * sqrt(1-s^2) E M) with M a prior draw (Prop. 5.1); accept iff
+ * log u <= min(0, log rho) (non-finite log rho rejects).
+ * stats (may be NULL) receives the totals of this call (it synchronises). */
+int dino_chains_step(dino_ctx *ctx, int pool_id, int n_steps, dino_step_stats *stats);
+
+/* Copy the current state to host buffers (any may be NULL):
+ * m (n_chains x N), m_r (n_chains x r), phi (n_chains), accepts (n_chains). */
+int dino_chains_read(dino_ctx *ctx, int pool_id, double *m, double *m_r, double *phi,
+                     uint64_t *accepts);
+
+/* Copy what the last transition computed (any may be NULL): the proposal
+ * m_r^dagger (n_chains x r), the proposal mean mu (n_chains x r), log rho,
+ * log u and the accept flags (0/1) of each chain. */
+int dino_chains_read_last(dino_ctx *ctx, int pool_id, double *b, double *mu,
+                          double *log_rho, double *log_u, int *accepted);
+
+int dino_chains_destroy(dino_ctx *ctx, int pool_id);
+
+/* ---- instrumentation --------------------------------------------------- */
+
+/* Number of kernels this context has launched since creation. */
+uint64_t dino_launch_count(const dino_ctx *ctx);
+
+/* Per-kernel CUDA-event timing collected under DINO_FLAG_TIMING.
+ * Writes up to `cap` entries: name (NUL-terminated, 48 bytes each in
+ * `names`), total milliseconds and launch count.  Returns the number of
+ * entries through *n.  reset != 0 clears the accumulators afterwards. */
+int dino_kernel_times(dino_ctx *ctx, char *names, double *total_ms, uint64_t *launches,
+                      int cap, int *n, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DINO_H */

@@ -53,12 +53,16 @@ class OracleChains:
         mu, b = mmala.reduced_proposal(a, geo_a, xi, dt)
         geo_b = mmala.geometry(sur, b)
         lr = mmala.log_rho(a, geo_a, b, geo_b, dt)
+        # magnitude of the terms log rho sums (the scale its rounding error lives on)
+        lr_scale = (np.abs(geo_a.phi) + np.abs(geo_b.phi)
+                    + np.abs(mmala.log_rho0(a, b, geo_a, dt))
+                    + np.abs(mmala.log_rho0(b, a, geo_b, dt)))
         log_u = np.log(u)
         acc = mmala.accept(log_u, lr)
         z = philox.normals(self.seed, philox.STREAM_Z, j, self.ids, N)
         M = prior.prior_sample(self.n_grid, self.gamma, self.delta, z)
         m_new = mmala.field_proposal(self.m, b, M, self.E, self.D, dt)
-        self.last = dict(mu=mu, b=b, log_rho=lr, log_u=log_u, accepted=acc.copy(),
+        self.last = dict(mu=mu, b=b, log_rho=lr, log_rho_scale=lr_scale, log_u=log_u, accepted=acc.copy(),
                          phi_b=geo_b.phi, hld_b=geo_b.hld, J_b=geo_b.J, f_b=geo_b.f,
                          g_b=geo_b.g, L_b=geo_b.L, m_new=m_new)
         self.m = np.where(acc[:, None], m_new, self.m)

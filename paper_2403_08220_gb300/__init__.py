@@ -1,0 +1,283 @@
+"""Python binding of libdino (the C ABI in include/dino.h).
+
+Thin marshalling only: every function below converts numpy arrays to
+pointers, calls the C entry point of the same name, checks the status and
+copies results into numpy arrays.  All computation happens in the CUDA
+library; if `_build/libdino.so` is missing, every call raises.
+
+    import paper_2403_08220_gb300 as dino
+    ctx = dino.dino_init()
+    sid = dino.dino_load_surrogate(ctx, n_grid=33, prior_gamma=0.1, ...)
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libdino.so")
+
+DINO_OK = 0
+DINO_PENDING = 1
+DINO_EINVAL = -1
+DINO_ENOMEM = -2
+DINO_ECUDA = -3
+DINO_EBUSY = -4
+DINO_ETIMEOUT = -5
+DINO_ENOTFOUND = -6
+DINO_ENUMERIC = -7
+DINO_ESTATE = -8
+
+DINO_ACT_IDENTITY, DINO_ACT_TANH, DINO_ACT_GELU = 0, 1, 2
+DINO_BASIS_KLE, DINO_BASIS_DIS, DINO_BASIS_EXPLICIT = 0, 1, 2
+DINO_PREC_FP64, DINO_PREC_BF16 = 0, 1
+DINO_FLAG_TIMING = 1
+
+_ERRNAMES = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EBUSY", -5: "ETIMEOUT",
+             -6: "ENOTFOUND", -7: "ENUMERIC", -8: "ESTATE"}
+
+
+class DinoError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"dino error {code} ({_ERRNAMES.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class _Desc(ct.Structure):
+    _fields_ = [("n_grid", ct.c_int), ("prior_gamma", ct.c_double), ("prior_delta", ct.c_double),
+                ("r", ct.c_int), ("n_layers", ct.c_int), ("widths", ct.POINTER(ct.c_int)),
+                ("activation", ct.c_int), ("W", ct.POINTER(ct.POINTER(ct.c_double))),
+                ("b", ct.POINTER(ct.POINTER(ct.c_double))), ("basis_kind", ct.c_int),
+                ("basis_gauss", ct.POINTER(ct.c_double)), ("E", ct.POINTER(ct.c_double)),
+                ("D", ct.POINTER(ct.c_double)), ("y", ct.POINTER(ct.c_double)),
+                ("noise_var", ct.c_double), ("precision", ct.c_int), ("fwd_slices", ct.c_int),
+                ("jac_slices", ct.c_int)]
+
+
+class _Stats(ct.Structure):
+    _fields_ = [("proposals", ct.c_uint64), ("accepts", ct.c_uint64),
+                ("nan_rejects", ct.c_uint64), ("sum_alpha", ct.c_double)]
+
+
+_lib = None
+_P = ct.c_void_p
+_D = ct.POINTER(ct.c_double)
+_I = ct.c_int
+
+_SIGNATURES = {
+    "dino_version": ([], ct.c_int),
+    "dino_init": ([ct.POINTER(_P), _I, ct.c_size_t, _P, ct.c_uint], _I),
+    "dino_destroy": ([_P], _I),
+    "dino_last_error": ([_P], ct.c_char_p),
+    "dino_sync": ([_P], _I),
+    "dino_load_surrogate": ([_P, ct.POINTER(_Desc), ct.POINTER(_I)], _I),
+    "dino_set_data": ([_P, _I, _D, ct.c_double], _I),
+    "dino_unload_surrogate": ([_P, _I], _I),
+    "dino_read_basis": ([_P, _I, _D, _D], _I),
+    "dino_surrogate_eval": ([_P, _I, _I, _D, _D, _D, _D, _D, _D, _D], _I),
+    "dino_chains_create": ([_P, _I, _I, ct.c_double, ct.c_uint64, ct.c_uint64, _D,
+                            ct.POINTER(_I)], _I),
+    "dino_chains_step": ([_P, _I, _I, ct.POINTER(_Stats)], _I),
+    "dino_chains_read": ([_P, _I, _D, _D, _D, ct.POINTER(ct.c_uint64)], _I),
+    "dino_chains_read_last": ([_P, _I, _D, _D, _D, _D, ct.POINTER(_I)], _I),
+    "dino_chains_destroy": ([_P, _I], _I),
+    "dino_launch_count": ([_P], ct.c_uint64),
+    "dino_kernel_times": ([_P, ct.c_char_p, _D, ct.POINTER(ct.c_uint64), _I, ct.POINTER(_I), _I],
+                          _I),
+}
+
+
+def lib():
+    """The loaded libdino (raises if the CUDA library has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libdino.so not found at {LIB_PATH}; run "
+                              "`python -m paper_2403_08220_gb300.build` (needs nvcc)")
+        L = ct.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGNATURES)
+
+
+class Ctx:
+    """Handle of a dino_ctx; `close()` (or garbage collection) destroys it."""
+
+    def __init__(self, ptr):
+        self.ptr = ptr
+
+    def close(self):
+        if self.ptr:
+            lib().dino_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _check(ctx: Optional[Ctx], code: int):
+    if code != DINO_OK and code != DINO_PENDING:
+        msg = lib().dino_last_error(ctx.ptr).decode() if ctx is not None and ctx.ptr else ""
+        raise DinoError(code, msg)
+    return code
+
+
+def _dptr(a):
+    return None if a is None else a.ctypes.data_as(_D)
+
+
+def _f64(a, shape=None):
+    x = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if shape is not None and x.shape != tuple(shape):
+        x = x.reshape(shape)
+    return x
+
+
+def dino_version() -> int:
+    return lib().dino_version()
+
+
+def dino_init(device: int = 0, hbm_budget_bytes: int = 0, stream=None, flags: int = 0) -> Ctx:
+    p = _P()
+    code = lib().dino_init(ct.byref(p), device, hbm_budget_bytes,
+                           _P(stream) if stream else None, flags)
+    _check(None, code)
+    return Ctx(p)
+
+
+def dino_destroy(ctx: Ctx):
+    ctx.close()
+
+
+def dino_last_error(ctx: Ctx) -> str:
+    return lib().dino_last_error(ctx.ptr).decode()
+
+
+def dino_sync(ctx: Ctx):
+    _check(ctx, lib().dino_sync(ctx.ptr))
+
+
+def dino_load_surrogate(ctx: Ctx, *, n_grid, prior_gamma, prior_delta, r, widths, activation,
+                        W, b, basis_kind, basis_gauss=None, E=None, D=None, y=None,
+                        noise_var=0.0, precision=DINO_PREC_FP64, fwd_slices=0,
+                        jac_slices=0) -> int:
+    L = len(W)
+    wid = (ct.c_int * (L + 1))(*[int(x) for x in widths])
+    Ws = [_f64(w) for w in W]
+    bs = [_f64(x) for x in b]
+    Wp = (ct.POINTER(ct.c_double) * L)(*[_dptr(w) for w in Ws])
+    bp = (ct.POINTER(ct.c_double) * L)(*[_dptr(x) for x in bs])
+    G = _f64(basis_gauss) if basis_gauss is not None else None
+    Ea = _f64(E) if E is not None else None
+    Da = _f64(D) if D is not None else None
+    ya = _f64(y) if y is not None else None
+    d = _Desc(n_grid, prior_gamma, prior_delta, r, L, wid, activation, Wp, bp, basis_kind,
+              _dptr(G), _dptr(Ea), _dptr(Da), _dptr(ya), float(noise_var), precision,
+              fwd_slices, jac_slices)
+    sid = _I()
+    _check(ctx, lib().dino_load_surrogate(ctx.ptr, ct.byref(d), ct.byref(sid)))
+    return sid.value
+
+
+def dino_set_data(ctx: Ctx, sid: int, y, noise_var: float):
+    ya = _f64(y)
+    _check(ctx, lib().dino_set_data(ctx.ptr, sid, _dptr(ya), float(noise_var)))
+
+
+def dino_unload_surrogate(ctx: Ctx, sid: int):
+    _check(ctx, lib().dino_unload_surrogate(ctx.ptr, sid))
+
+
+def dino_read_basis(ctx: Ctx, sid: int, r: int, N: int):
+    E = np.empty((r, N))
+    D = np.empty((N, r))
+    _check(ctx, lib().dino_read_basis(ctx.ptr, sid, _dptr(E), _dptr(D)))
+    return E, D
+
+
+def dino_surrogate_eval(ctx: Ctx, sid: int, m_r, d_y: int, want_L: bool = True) -> dict:
+    x = _f64(m_r)
+    if x.ndim == 1:
+        x = x[None, :]
+    n, r = x.shape
+    out = dict(f=np.empty((n, d_y)), J=np.empty((n, d_y, r)), phi=np.empty(n),
+               g=np.empty((n, r)), L=np.empty((n, r, r)) if want_L else None, hld=np.empty(n))
+    _check(ctx, lib().dino_surrogate_eval(ctx.ptr, sid, n, _dptr(x), _dptr(out["f"]),
+                                          _dptr(out["J"]), _dptr(out["phi"]), _dptr(out["g"]),
+                                          _dptr(out["L"]), _dptr(out["hld"])))
+    return out
+
+
+def dino_chains_create(ctx: Ctx, sid: int, n_chains: int, dt: float, seed: int,
+                       chain_id_base: int = 0, m0=None) -> int:
+    m = _f64(m0) if m0 is not None else None
+    pid = _I()
+    _check(ctx, lib().dino_chains_create(ctx.ptr, sid, n_chains, float(dt), int(seed),
+                                         int(chain_id_base), _dptr(m), ct.byref(pid)))
+    return pid.value
+
+
+def dino_chains_step(ctx: Ctx, pool: int, n_steps: int, stats: bool = True):
+    st = _Stats()
+    _check(ctx, lib().dino_chains_step(ctx.ptr, pool, n_steps, ct.byref(st) if stats else None))
+    if not stats:
+        return None
+    return dict(proposals=st.proposals, accepts=st.accepts, nan_rejects=st.nan_rejects,
+                sum_alpha=st.sum_alpha)
+
+
+def dino_chains_read(ctx: Ctx, pool: int, C: int, r: int, N: int, field: bool = True) -> dict:
+    out = dict(m=np.empty((C, N)) if field else None, m_r=np.empty((C, r)), phi=np.empty(C),
+               accepts=np.empty(C, dtype=np.uint64))
+    _check(ctx, lib().dino_chains_read(ctx.ptr, pool, _dptr(out["m"]), _dptr(out["m_r"]),
+                                       _dptr(out["phi"]),
+                                       out["accepts"].ctypes.data_as(ct.POINTER(ct.c_uint64))))
+    return out
+
+
+def dino_chains_read_last(ctx: Ctx, pool: int, C: int, r: int) -> dict:
+    out = dict(b=np.empty((C, r)), mu=np.empty((C, r)), log_rho=np.empty(C),
+               log_u=np.empty(C), accepted=np.empty(C, dtype=np.int32))
+    _check(ctx, lib().dino_chains_read_last(ctx.ptr, pool, _dptr(out["b"]), _dptr(out["mu"]),
+                                            _dptr(out["log_rho"]), _dptr(out["log_u"]),
+                                            out["accepted"].ctypes.data_as(ct.POINTER(_I))))
+    out["accepted"] = out["accepted"].astype(bool)
+    return out
+
+
+def dino_chains_destroy(ctx: Ctx, pool: int):
+    _check(ctx, lib().dino_chains_destroy(ctx.ptr, pool))
+
+
+def dino_launch_count(ctx: Ctx) -> int:
+    return int(lib().dino_launch_count(ctx.ptr))
+
+
+def dino_kernel_times(ctx: Ctx, reset: bool = False) -> dict:
+    cap = 64
+    names = ct.create_string_buffer(48 * cap)
+    ms = np.zeros(cap)
+    cnt = np.zeros(cap, dtype=np.uint64)
+    n = _I()
+    _check(ctx, lib().dino_kernel_times(ctx.ptr, names, _dptr(ms),
+                                        cnt.ctypes.data_as(ct.POINTER(ct.c_uint64)), cap,
+                                        ct.byref(n), 1 if reset else 0))
+    out = {}
+    raw = names.raw
+    for k in range(min(n.value, cap)):
+        nm = raw[48 * k:48 * (k + 1)].split(b"\0", 1)[0].decode()
+        out[nm] = (float(ms[k]), int(cnt[k]))
+    return out

@@ -1,0 +1,136 @@
+// Internal interfaces between the host runtime (host.cpp) and the kernels.
+// Every launcher issues exactly one kernel on the given stream.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstddef>
+#include <cstdint>
+
+namespace dino {
+
+// Largest reduced dimension whose packed FP64 Cholesky factor the per-chain
+// kernels keep in shared memory (r (r+1)/2 doubles plus work vectors).
+constexpr int kMaxRSmem = 208;
+
+// Philox streams (counter word 3): reduced noise, accept uniform, complement
+// prior draw, initial prior draw.
+constexpr uint32_t STREAM_XI_ID = 0, STREAM_U_ID = 1, STREAM_Z_ID = 2, STREAM_INIT_ID = 3;
+
+inline __host__ __device__ size_t tri_size(int r) { return (size_t)r * (r + 1) / 2; }
+
+// ---- per-chain reduced-space kernels (FP64) -----------------------------
+struct ReducedArgs {
+  int C = 0, r = 0, d_y = 0;
+  double s = 0, dt = 0, noise_var = 1;
+  uint64_t seed = 0, id_base = 0;
+  uint32_t step = 0;
+  // chain state
+  double *mr = nullptr, *g = nullptr, *phi = nullptr, *hld = nullptr, *L = nullptr;
+  // proposal (written by propose, read by geometry)
+  double *b = nullptr, *mu = nullptr, *lq_fwd = nullptr;
+  // surrogate output at b: J (C x d_y x r) and f (C x d_y), FP64 or FP32
+  const void *J = nullptr;
+  const void *f = nullptr;
+  int jf_f32 = 0;
+  const double *y = nullptr;
+  // accept outputs
+  double *coef = nullptr, *log_rho = nullptr, *log_u = nullptr;
+  int *acc = nullptr;
+  unsigned long long *acc_count = nullptr;
+  unsigned long long *counters = nullptr;  // [0] accepts, [1] nan rejects
+  double *sum_alpha = nullptr;
+  // tensor-core path: the proposal as bf16 slice planes (row pitch b_ld,
+  // plane pitch b_plane elements); nullptr when unused
+  __nv_bfloat16 *b_bf16 = nullptr;
+  int b_slices = 0, b_ld = 0;
+  size_t b_plane = 0;
+};
+
+size_t propose_smem_bytes(int r);
+size_t geometry_smem_bytes(int r, int d_y, int jf_f32);
+cudaError_t launch_propose(const ReducedArgs &a, cudaStream_t st);
+// mode 0: initialise the state at b (no accept); mode 1: MH step
+cudaError_t launch_geometry(const ReducedArgs &a, int mode, cudaStream_t st);
+
+// ---- SIMT GEMMs: out = epilogue(A B^T), A: M x K (lda), B: N x K (ldb) ----
+template <typename T>
+cudaError_t gemm_store(int M, int N, int K, const T *A, int lda, const T *B, int ldb, T *out,
+                       int ldo, cudaStream_t st);
+// out = act(acc + bias[col]); der = act'(acc + bias[col])   (der may be null)
+template <typename T>
+cudaError_t gemm_bias_act(int M, int N, int K, const T *A, int lda, const T *B, int ldb,
+                          const T *bias, int act, T *out, T *der, int ldo, cudaStream_t st);
+// out = acc * scale[(row / group) * lds + col]
+template <typename T>
+cudaError_t gemm_scale_group(int M, int N, int K, const T *A, int lda, const T *B, int ldb,
+                             const T *scale, int lds, int group, T *out, int ldo,
+                             cudaStream_t st);
+// complement coefficient: out[row, col] = coef[row * ldc + col] - c * acc
+template <typename T>
+cudaError_t gemm_coef(int M, int N, int K, const T *A, int lda, const T *B, int ldb,
+                      const double *coef, int ldc, double c, T *out, int ldo, cudaStream_t st);
+// field update: if acc_flag[row]: m[row, col] = s m + c Mf[row, col] + acc
+template <typename T>
+cudaError_t gemm_field(int M, int N, int K, const T *A, int lda, const T *B, int ldb,
+                       const int *acc_flag, double s, double c, T *m, const T *Mf, int ldm,
+                       cudaStream_t st);
+
+// ---- elementwise / per-chain helpers -------------------------------------
+// Prior draw from the full KLE: out[c] = S^T (sqrt(Lambda) .* Z_c) S,
+// Z_c from Philox stream `stream` at `step` for chain id_base + c.
+template <typename T>
+cudaError_t launch_prior_draw(int C, int n, const T *sqrtlam, const T *S, uint64_t seed,
+                              uint64_t id_base, uint32_t stream, uint32_t step, T *out,
+                              int ldo, cudaStream_t st);
+// P[(c d_y + i) w + k] = WL[i w + k] * der[c ldd + k]
+template <typename T>
+cudaError_t launch_jac_init(int C, int d_y, int w, const T *WL, const T *der, int ldd, T *P,
+                            cudaStream_t st);
+// out[c] = W (broadcast of a d_y x r matrix to every chain)
+template <typename T>
+cudaError_t launch_broadcast(int C, size_t n, const T *src, T *out, cudaStream_t st);
+cudaError_t launch_f64_to_f32(size_t n, const double *src, float *dst, cudaStream_t st);
+cudaError_t launch_f32_to_f64(size_t n, const float *src, double *dst, cudaStream_t st);
+
+// ---- tcgen05 BF16 GEMM (sm_103a) -----------------------------------------
+// Operands are bf16 "slice planes": X ~= sum_s X_s, plane s at X + s * plane.
+// D = sum over slice pairs (i, j), i + j < nslice, of A_i B_j^T, FP32 accum.
+// A: M x K (row pitch lda elements), B: N x K (row pitch ldb).
+enum TcEpi : int {
+  TC_EPI_STORE_F32 = 0,   // outf[row, col] = acc
+  TC_EPI_BIAS_F32 = 1,    // outf = acc + bias[col]
+  TC_EPI_BIAS_ACT = 2,    // z = acc + bias; out slices = act(z); der = act'(z) (fp32)
+  TC_EPI_SCALE_GROUP = 3  // out slices = acc * scale[(row/group)*lds + col]
+};
+struct TcGemmArgs {
+  int M = 0, N = 0, K = 0;
+  const __nv_bfloat16 *A = nullptr;
+  int lda = 0;
+  size_t a_plane = 0;
+  const __nv_bfloat16 *B = nullptr;
+  int ldb = 0;
+  size_t b_plane = 0;
+  int nslice = 1;
+  int epi = TC_EPI_STORE_F32;
+  float *outf = nullptr;
+  int ldo = 0;
+  const float *bias = nullptr;
+  int act = 0;
+  __nv_bfloat16 *out_bf = nullptr;  // slice planes of the output
+  size_t out_plane = 0;
+  int out_slices = 1;
+  float *der = nullptr;
+  const float *scale = nullptr;
+  int lds = 0, group = 1;
+};
+cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st);
+// Split FP32/FP64 values into bf16 slice planes (x ~= sum_s slice_s).
+cudaError_t launch_split_bf16_f64(int rows, int cols, const double *src, int lds,
+                                  __nv_bfloat16 *dst, int ldd, size_t plane, int nslice,
+                                  cudaStream_t st);
+// Jacobian start on the tensor path: P = W_L (fp64) .* der (fp32) as bf16 slices
+cudaError_t launch_jac_init_bf16(int C, int d_y, int w, const double *WL, const float *der,
+                                 int ldd, __nv_bfloat16 *P, int ldp, size_t plane, int nslice,
+                                 cudaStream_t st);
+
+}  // namespace dino

@@ -1,0 +1,1289 @@
+// Host runtime behind the C ABI in include/dino.h: contexts, surrogates,
+// chain pools and the per-step launch sequence.  Setup work (building the
+// reduced basis, uploading weights) runs here once per surrogate; every
+// per-step operation is a CUDA kernel launched on the context's stream.
+#include "../../include/dino.h"
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "dino_internal.h"
+
+namespace dino {
+
+struct Error {
+  int code;
+  std::string msg;
+};
+
+[[noreturn]] void fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  throw Error{code, buf};
+}
+
+#define CK(expr)                                                                         \
+  do {                                                                                   \
+    cudaError_t _e = (expr);                                                             \
+    if (_e != cudaSuccess) fail(DINO_ECUDA, "%s: %s", #expr, cudaGetErrorString(_e)); \
+  } while (0)
+
+static inline int pad8(int x) { return (x + 7) & ~7; }
+
+// One device allocation carved into aligned sub-buffers.
+struct Arena {
+  char *base = nullptr;
+  size_t bytes = 0, off = 0;
+  size_t reserve(size_t n) {
+    off = (off + 255) & ~(size_t)255;
+    const size_t at = off;
+    off += n;
+    return at;
+  }
+};
+
+struct Surrogate;
+struct Pool;
+
+}  // namespace dino
+
+struct dino_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  size_t budget = 0, used = 0;
+  unsigned flags = 0;
+  std::recursive_mutex mu;
+  std::string err;
+  int next_id = 1;
+  std::map<int, std::unique_ptr<dino::Surrogate>> surrogates;
+  std::map<int, std::unique_ptr<dino::Pool>> pools;
+  uint64_t launches = 0;
+  struct KTime {
+    double ms = 0;
+    uint64_t n = 0;
+  };
+  std::map<std::string, KTime> ktimes;
+  struct Pending {
+    std::string name;
+    cudaEvent_t e0, e1;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
+};
+
+namespace dino {
+
+// ---------------------------------------------------------------------------
+// device memory accounting
+void *dev_alloc(dino_ctx *ctx, size_t bytes) {
+  if (bytes == 0) return nullptr;
+  if (ctx->used + bytes > ctx->budget)
+    fail(DINO_ENOMEM, "HBM budget exceeded: need %zu more bytes, %zu of %zu used", bytes,
+         ctx->used, ctx->budget);
+  void *p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(DINO_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+  }
+  ctx->used += bytes;
+  return p;
+}
+
+void dev_free(dino_ctx *ctx, void *p, size_t bytes) {
+  if (!p) return;
+  cudaFree(p);
+  ctx->used -= std::min(ctx->used, bytes);
+}
+
+template <typename T>
+T *upload(dino_ctx *ctx, const T *host, size_t n) {
+  T *d = (T *)dev_alloc(ctx, n * sizeof(T));
+  CK(cudaMemcpyAsync(d, host, n * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+  return d;
+}
+
+// ---------------------------------------------------------------------------
+// kernel launch bookkeeping (count + optional CUDA-event timing)
+template <class F>
+void launch(dino_ctx *ctx, const char *name, F &&fn) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const bool timing = (ctx->flags & DINO_FLAG_TIMING) != 0;
+  if (timing) {
+    for (cudaEvent_t *e : {&e0, &e1}) {
+      if (!ctx->event_pool.empty()) {
+        *e = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+      } else {
+        CK(cudaEventCreate(e));
+      }
+    }
+    CK(cudaEventRecord(e0, ctx->stream));
+  }
+  cudaError_t err = fn();
+  ctx->launches += 1;
+  if (err != cudaSuccess) fail(DINO_ECUDA, "kernel %s: %s", name, cudaGetErrorString(err));
+  if (timing) {
+    CK(cudaEventRecord(e1, ctx->stream));
+    ctx->pending.push_back({name, e0, e1});
+  }
+}
+
+void collect_times(dino_ctx *ctx) {
+  if (ctx->pending.empty()) return;
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (auto &p : ctx->pending) {
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, p.e0, p.e1));
+    auto &kt = ctx->ktimes[p.name];
+    kt.ms += ms;
+    kt.n += 1;
+    ctx->event_pool.push_back(p.e0);
+    ctx->event_pool.push_back(p.e1);
+  }
+  ctx->pending.clear();
+}
+
+// ---------------------------------------------------------------------------
+// reduced bases (setup, host)
+
+struct Modes {
+  std::vector<int> kx, ky;
+  std::vector<double> kappa;
+};
+
+static std::vector<double> lap1d_eigs(int n) {
+  const double h = 1.0 / (n + 1);
+  std::vector<double> s(n);
+  for (int k = 1; k <= n; ++k) {
+    const double t = std::sin(k * M_PI * h / 2.0);
+    s[k - 1] = 4.0 / (h * h) * t * t;
+  }
+  return s;
+}
+
+// Sine matrix S[k-1][i] = sqrt(2/(n+1)) sin(k (i+1) pi/(n+1)) (symmetric, orthogonal).
+static std::vector<double> sine_matrix(int n) {
+  std::vector<double> S((size_t)n * n);
+  const double c = std::sqrt(2.0 / (n + 1));
+  for (int k = 1; k <= n; ++k)
+    for (int i = 1; i <= n; ++i) S[(size_t)(k - 1) * n + (i - 1)] = c * std::sin(k * i * M_PI / (n + 1));
+  return S;
+}
+
+// KLE order: increasing kappa (decreasing lambda), ties by smaller kx.
+static Modes kle_modes(int n) {
+  const auto s = lap1d_eigs(n);
+  std::vector<int> idx((size_t)n * n);
+  std::iota(idx.begin(), idx.end(), 0);
+  auto kap = [&](int q) { return s[q % n] + s[q / n]; };  // q = (kx-1) + n (ky-1)
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+    const double ka = kap(a), kb = kap(b);
+    if (ka != kb) return ka < kb;
+    return (a % n) < (b % n);
+  });
+  Modes m;
+  for (int q : idx) {
+    m.kx.push_back(q % n + 1);
+    m.ky.push_back(q / n + 1);
+    m.kappa.push_back(kap(q));
+  }
+  return m;
+}
+
+static void build_kle(int n, double gamma, double delta, int r, std::vector<double> &E,
+                      std::vector<double> &D) {
+  const int N = n * n;
+  const auto S = sine_matrix(n);
+  const Modes md = kle_modes(n);
+  E.assign((size_t)r * N, 0.0);
+  D.assign((size_t)N * r, 0.0);
+  for (int j = 0; j < r; ++j) {
+    const double lam_sqrt = 1.0 / (delta + gamma * md.kappa[j]);  // sqrt(lambda)
+    const double *vx = &S[(size_t)(md.kx[j] - 1) * n];
+    const double *vy = &S[(size_t)(md.ky[j] - 1) * n];
+    for (int jj = 0; jj < n; ++jj)
+      for (int i = 0; i < n; ++i) {
+        const double eta = vx[i] * vy[jj];
+        const int p = i + n * jj;
+        E[(size_t)j * N + p] = eta / lam_sqrt;
+        D[(size_t)p * r + j] = lam_sqrt * eta;
+      }
+  }
+}
+
+// Thin Householder QR of G (N x r, row-major) -> Q with positive diag(R).
+static std::vector<double> thin_q(const double *G, int N, int r) {
+  std::vector<double> A(G, G + (size_t)N * r);  // working copy, column j = A[p*r + j]
+  std::vector<double> vs((size_t)N * r, 0.0), beta(r, 0.0), rdiag(r, 0.0);
+  for (int j = 0; j < r; ++j) {
+    double nrm = 0.0;
+    for (int p = j; p < N; ++p) nrm += A[(size_t)p * r + j] * A[(size_t)p * r + j];
+    nrm = std::sqrt(nrm);
+    const double x0 = A[(size_t)j * r + j];
+    const double alpha = x0 >= 0 ? -nrm : nrm;  // R_jj = alpha
+    double *v = &vs[(size_t)j * N];              // reflector j stored contiguously
+    for (int p = 0; p < N; ++p) v[p] = 0.0;
+    v[j] = x0 - alpha;
+    for (int p = j + 1; p < N; ++p) v[p] = A[(size_t)p * r + j];
+    double vv = 0.0;
+    for (int p = j; p < N; ++p) vv += v[p] * v[p];
+    beta[j] = vv > 0 ? 2.0 / vv : 0.0;
+    rdiag[j] = alpha;
+    for (int k = j; k < r; ++k) {
+      double d = 0.0;
+      for (int p = j; p < N; ++p) d += v[p] * A[(size_t)p * r + k];
+      d *= beta[j];
+      for (int p = j; p < N; ++p) A[(size_t)p * r + k] -= d * v[p];
+    }
+  }
+  // Q = H_0 H_1 ... H_{r-1} [I_r; 0]
+  std::vector<double> Q((size_t)N * r, 0.0);
+  for (int k = 0; k < r; ++k) Q[(size_t)k * r + k] = 1.0;
+  for (int j = r - 1; j >= 0; --j) {
+    const double *v = &vs[(size_t)j * N];
+    for (int k = 0; k < r; ++k) {
+      double d = 0.0;
+      for (int p = j; p < N; ++p) d += v[p] * Q[(size_t)p * r + k];
+      d *= beta[j];
+      for (int p = j; p < N; ++p) Q[(size_t)p * r + k] -= d * v[p];
+    }
+  }
+  for (int k = 0; k < r; ++k)
+    if (rdiag[k] < 0)
+      for (int p = 0; p < N; ++p) Q[(size_t)p * r + k] = -Q[(size_t)p * r + k];
+  return Q;
+}
+
+// y = A^-1 x for one field (n x n) through the sine transform: A^-1 = S diag(1/(delta+gamma kappa)) S.
+static void apply_Ainv(int n, double gamma, double delta, const std::vector<double> &S,
+                       const std::vector<double> &s1, const double *x, double *y,
+                       std::vector<double> &t1, std::vector<double> &t2) {
+  // t1 = S X  (X[j][i] = x[i + n j]); t2 = t1 S = S X S (spectral [ky][kx])
+  for (int a = 0; a < n; ++a)
+    for (int i = 0; i < n; ++i) {
+      double acc = 0;
+      for (int j = 0; j < n; ++j) acc += S[(size_t)a * n + j] * x[i + n * j];
+      t1[(size_t)a * n + i] = acc;
+    }
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) {
+      double acc = 0;
+      for (int i = 0; i < n; ++i) acc += t1[(size_t)a * n + i] * S[(size_t)i * n + b];
+      t2[(size_t)a * n + b] = acc / (delta + gamma * (s1[a] + s1[b]));
+    }
+  for (int a = 0; a < n; ++a)
+    for (int i = 0; i < n; ++i) {
+      double acc = 0;
+      for (int b = 0; b < n; ++b) acc += t2[(size_t)a * n + b] * S[(size_t)b * n + i];
+      t1[(size_t)a * n + i] = acc;
+    }
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i < n; ++i) {
+      double acc = 0;
+      for (int a = 0; a < n; ++a) acc += S[(size_t)a * n + j] * t1[(size_t)a * n + i];
+      y[i + n * j] = acc;
+    }
+}
+
+static void build_dis(int n, double gamma, double delta, int r, const double *G,
+                      std::vector<double> &E, std::vector<double> &D) {
+  const int N = n * n;
+  const double h2 = 1.0 / ((n + 1.0) * (n + 1.0));
+  const auto Q = thin_q(G, N, r);
+  const auto S = sine_matrix(n);
+  const auto s1 = lap1d_eigs(n);
+  E.assign((size_t)r * N, 0.0);
+  D.assign((size_t)N * r, 0.0);
+  std::vector<double> q(N), y(N), t1((size_t)n * n), t2((size_t)n * n);
+  for (int j = 0; j < r; ++j) {
+    for (int p = 0; p < N; ++p) q[p] = Q[(size_t)p * r + j];
+    apply_Ainv(n, gamma, delta, S, s1, q.data(), y.data(), t1, t2);
+    for (int p = 0; p < N; ++p) D[(size_t)p * r + j] = y[p];
+    for (int jj = 0; jj < n; ++jj)
+      for (int i = 0; i < n; ++i) {
+        const int p = i + n * jj;
+        double lap = -4.0 * q[p];
+        if (i > 0) lap += q[p - 1];
+        if (i < n - 1) lap += q[p + 1];
+        if (jj > 0) lap += q[p - n];
+        if (jj < n - 1) lap += q[p + n];
+        E[(size_t)j * N + p] = delta * q[p] - gamma * lap / h2;  // (A q)_p
+      }
+  }
+}
+
+static double max_ed_error(const std::vector<double> &E, const std::vector<double> &D, int r,
+                           int N) {
+  double worst = 0.0;
+  for (int i = 0; i < r; ++i)
+    for (int j = 0; j < r; ++j) {
+      double acc = 0.0;
+      for (int p = 0; p < N; ++p) acc += E[(size_t)i * N + p] * D[(size_t)p * r + j];
+      worst = std::max(worst, std::fabs(acc - (i == j ? 1.0 : 0.0)));
+    }
+  return worst;
+}
+
+// ---------------------------------------------------------------------------
+// surrogate
+
+struct Surrogate {
+  int id = 0;
+  int n_grid = 0, N = 0;
+  double gamma = 0, delta = 0;
+  int r = 0, d_y = 0, L = 0, act = 0, precision = 0, fwd_slices = 1, jac_slices = 1;
+  std::vector<int> widths;
+  std::vector<std::vector<double>> W, b;
+  std::vector<double> E, D, y;
+  double noise_var = 0;
+  bool has_data = false;
+  int pools = 0;
+  // device
+  std::vector<std::pair<void *, size_t>> allocs;
+  double *dE = nullptr, *dD = nullptr, *dS = nullptr, *dSqrtLam = nullptr, *dy = nullptr;
+  float *fE = nullptr, *fD = nullptr, *fS = nullptr, *fSqrtLam = nullptr;
+  std::vector<double *> dW, dWT, db;
+  std::vector<float *> fb;
+  std::vector<__nv_bfloat16 *> bW, bWT;
+  std::vector<int> ldW, ldWT;
+  std::vector<size_t> plW, plWT;
+  int widest = 0;  // max hidden/output width used by the Jacobian buffers
+};
+
+template <typename T>
+static T *sur_alloc(dino_ctx *ctx, Surrogate *s, size_t n) {
+  T *p = (T *)dev_alloc(ctx, n * sizeof(T));
+  s->allocs.push_back({p, n * sizeof(T)});
+  return p;
+}
+
+template <typename T>
+static T *sur_upload(dino_ctx *ctx, Surrogate *s, const T *host, size_t n) {
+  T *p = sur_alloc<T>(ctx, s, n);
+  CK(cudaMemcpyAsync(p, host, n * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+  return p;
+}
+
+static std::vector<float> to_f32(const std::vector<double> &v) {
+  return std::vector<float>(v.begin(), v.end());
+}
+
+// bf16 slice planes of a rows x cols matrix with row pitch ld: plane s holds
+// the s-th term of x ~= sum_s x_s, each the bf16 rounding of what remains.
+static std::vector<__nv_bfloat16> split_planes(const std::vector<double> &x, int rows, int cols,
+                                               int ld, int nslice, size_t &plane) {
+  plane = (size_t)rows * ld;
+  std::vector<__nv_bfloat16> out(plane * nslice, __float2bfloat16(0.0f));
+  for (int i = 0; i < rows; ++i)
+    for (int j = 0; j < cols; ++j) {
+      float rem = (float)x[(size_t)i * cols + j];
+      for (int s = 0; s < nslice; ++s) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(rem);
+        out[s * plane + (size_t)i * ld + j] = h;
+        rem -= __bfloat162float(h);
+      }
+    }
+  return out;
+}
+
+static void upload_data(dino_ctx *ctx, Surrogate *s) {
+  if (!s->dy) s->dy = sur_alloc<double>(ctx, s, std::max(1, s->d_y));
+  CK(cudaMemcpyAsync(s->dy, s->y.data(), s->d_y * sizeof(double), cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+}
+
+static void free_surrogate(dino_ctx *ctx, Surrogate *s) {
+  cudaStreamSynchronize(ctx->stream);
+  for (auto &a : s->allocs) dev_free(ctx, a.first, a.second);
+  s->allocs.clear();
+}
+
+static Surrogate *get_surrogate(dino_ctx *ctx, int id) {
+  auto it = ctx->surrogates.find(id);
+  if (it == ctx->surrogates.end()) fail(DINO_ENOTFOUND, "unknown surrogate id %d", id);
+  return it->second.get();
+}
+
+static int load_surrogate(dino_ctx *ctx, const dino_surrogate_desc *d) {
+  if (!d) fail(DINO_EINVAL, "desc is NULL");
+  if (d->n_grid < 1 || d->r < 1 || d->n_layers < 1 || !d->widths || !d->W || !d->b)
+    fail(DINO_EINVAL, "n_grid, r, n_layers must be >= 1 and widths/W/b non-NULL");
+  if (!(d->prior_delta > 0) || !(d->prior_gamma >= 0))
+    fail(DINO_EINVAL, "prior_delta must be > 0 and prior_gamma >= 0");
+  if (d->precision != DINO_PREC_FP64 && d->precision != DINO_PREC_BF16)
+    fail(DINO_EINVAL, "unknown precision %d", d->precision);
+  if (d->activation < 0 || d->activation > 2) fail(DINO_EINVAL, "unknown activation");
+  auto s = std::make_unique<Surrogate>();
+  s->id = ctx->next_id++;
+  s->n_grid = d->n_grid;
+  s->N = d->n_grid * d->n_grid;
+  s->gamma = d->prior_gamma;
+  s->delta = d->prior_delta;
+  s->r = d->r;
+  s->L = d->n_layers;
+  s->act = d->activation;
+  s->precision = d->precision;
+  s->widths.assign(d->widths, d->widths + d->n_layers + 1);
+  if (s->widths[0] != s->r) fail(DINO_EINVAL, "widths[0]=%d must equal r=%d", s->widths[0], s->r);
+  for (int w : s->widths)
+    if (w < 1) fail(DINO_EINVAL, "every width must be >= 1");
+  s->d_y = s->widths.back();
+  if (s->r > s->N) fail(DINO_EINVAL, "r=%d exceeds N=%d", s->r, s->N);
+  if (s->r > kMaxRSmem) fail(DINO_EINVAL, "r=%d exceeds the supported maximum %d", s->r, kMaxRSmem);
+  if (geometry_smem_bytes(s->r, s->d_y, 1) > 227 * 1024 ||
+      geometry_smem_bytes(s->r, s->d_y, 0) > 227 * 1024)
+    fail(DINO_EINVAL, "r=%d, d_y=%d exceed the per-chain shared-memory budget", s->r, s->d_y);
+  if (d->precision == DINO_PREC_BF16 && s->L < 2)
+    fail(DINO_EINVAL, "the tensor-core path needs at least one hidden layer");
+  if (d->precision == DINO_PREC_BF16) {
+    s->fwd_slices = d->fwd_slices ? d->fwd_slices : 3;
+    s->jac_slices = d->jac_slices ? d->jac_slices : 2;
+    if (s->fwd_slices < 1 || s->fwd_slices > 3 || s->jac_slices < 1 || s->jac_slices > 3)
+      fail(DINO_EINVAL, "fwd_slices/jac_slices must be in 1..3");
+  }
+  for (int l = 0; l < s->L; ++l) {
+    if (!d->W[l] || !d->b[l]) fail(DINO_EINVAL, "W[%d] or b[%d] is NULL", l, l);
+    const size_t nw = (size_t)s->widths[l + 1] * s->widths[l];
+    s->W.emplace_back(d->W[l], d->W[l] + nw);
+    s->b.emplace_back(d->b[l], d->b[l] + s->widths[l + 1]);
+    for (double v : s->W.back())
+      if (!std::isfinite(v)) fail(DINO_ENUMERIC, "non-finite weight in layer %d", l);
+  }
+  // basis
+  const int N = s->N, r = s->r;
+  if (d->basis_kind == DINO_BASIS_KLE) {
+    build_kle(s->n_grid, s->gamma, s->delta, r, s->E, s->D);
+  } else if (d->basis_kind == DINO_BASIS_DIS) {
+    if (!d->basis_gauss) fail(DINO_EINVAL, "DIS basis needs basis_gauss (N x r)");
+    build_dis(s->n_grid, s->gamma, s->delta, r, d->basis_gauss, s->E, s->D);
+  } else if (d->basis_kind == DINO_BASIS_EXPLICIT) {
+    if (!d->E || !d->D) fail(DINO_EINVAL, "EXPLICIT basis needs E and D");
+    s->E.assign(d->E, d->E + (size_t)r * N);
+    s->D.assign(d->D, d->D + (size_t)N * r);
+  } else {
+    fail(DINO_EINVAL, "unknown basis kind %d", d->basis_kind);
+  }
+  const double ed = max_ed_error(s->E, s->D, r, N);
+  if (!(ed <= 1e-8)) fail(DINO_ENUMERIC, "E D differs from I_r by %g", ed);
+
+  // device copies
+  const int n = s->n_grid;
+  const auto S = sine_matrix(n);
+  const auto s1 = lap1d_eigs(n);
+  std::vector<double> sqrtlam((size_t)N);
+  for (int ky = 0; ky < n; ++ky)
+    for (int kx = 0; kx < n; ++kx)
+      sqrtlam[kx + (size_t)n * ky] = 1.0 / (s->delta + s->gamma * (s1[kx] + s1[ky]));
+  s->dE = sur_upload(ctx, s.get(), s->E.data(), s->E.size());
+  s->dD = sur_upload(ctx, s.get(), s->D.data(), s->D.size());
+  s->dS = sur_upload(ctx, s.get(), S.data(), S.size());
+  s->dSqrtLam = sur_upload(ctx, s.get(), sqrtlam.data(), sqrtlam.size());
+  for (int l = 0; l < s->L; ++l) {
+    const int wo = s->widths[l + 1], wi = s->widths[l];
+    std::vector<double> WT((size_t)wi * wo);
+    for (int i = 0; i < wo; ++i)
+      for (int j = 0; j < wi; ++j) WT[(size_t)j * wo + i] = s->W[l][(size_t)i * wi + j];
+    s->dW.push_back(sur_upload(ctx, s.get(), s->W[l].data(), s->W[l].size()));
+    s->dWT.push_back(sur_upload(ctx, s.get(), WT.data(), WT.size()));
+    s->db.push_back(sur_upload(ctx, s.get(), s->b[l].data(), s->b[l].size()));
+    if (l >= 1) s->widest = std::max(s->widest, wi);
+    if (s->precision == DINO_PREC_BF16) {
+      const auto fb = to_f32(s->b[l]);
+      s->fb.push_back(sur_upload(ctx, s.get(), fb.data(), fb.size()));
+      size_t pl = 0, plt = 0;
+      const int ldw = pad8(wi), ldwt = pad8(wo);
+      const auto bw = split_planes(s->W[l], wo, wi, ldw, s->fwd_slices, pl);
+      const auto bwt = split_planes(WT, wi, wo, ldwt, s->jac_slices, plt);
+      s->bW.push_back(sur_upload(ctx, s.get(), bw.data(), bw.size()));
+      s->bWT.push_back(sur_upload(ctx, s.get(), bwt.data(), bwt.size()));
+      s->ldW.push_back(ldw);
+      s->ldWT.push_back(ldwt);
+      s->plW.push_back(pl);
+      s->plWT.push_back(plt);
+    }
+  }
+  if (s->precision == DINO_PREC_BF16) {
+    const auto fE = to_f32(s->E), fD = to_f32(s->D), fS = to_f32(S), fL = to_f32(sqrtlam);
+    s->fE = sur_upload(ctx, s.get(), fE.data(), fE.size());
+    s->fD = sur_upload(ctx, s.get(), fD.data(), fD.size());
+    s->fS = sur_upload(ctx, s.get(), fS.data(), fS.size());
+    s->fSqrtLam = sur_upload(ctx, s.get(), fL.data(), fL.size());
+  }
+  if (d->y) {
+    if (!(d->noise_var > 0)) fail(DINO_EINVAL, "noise_var must be > 0");
+    s->y.assign(d->y, d->y + s->d_y);
+    s->noise_var = d->noise_var;
+    s->has_data = true;
+    upload_data(ctx, s.get());
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  const int id = s->id;
+  ctx->surrogates[id] = std::move(s);
+  return id;
+}
+
+// ---------------------------------------------------------------------------
+// workspace for evaluating the surrogate (forward + Jacobian) at C points
+
+struct Work {
+  int C = 0;
+  // FP64 path
+  std::vector<double *> act64, der64;
+  double *f64 = nullptr, *P64[2] = {nullptr, nullptr}, *J64 = nullptr;
+  // tensor path
+  __nv_bfloat16 *xb = nullptr;
+  int ldx = 0;
+  size_t plx = 0;
+  std::vector<__nv_bfloat16 *> actb;
+  std::vector<int> ldact;
+  std::vector<size_t> plact;
+  std::vector<float *> der32;
+  float *f32 = nullptr, *J32 = nullptr;
+  __nv_bfloat16 *Pb[2] = {nullptr, nullptr};
+  int ldp = 0;
+  size_t plp = 0;
+};
+
+// Lays out (or, with base != nullptr, assigns) the workspace in an arena.
+static void layout_work(const Surrogate *s, int C, Arena &ar, Work &w, bool assign) {
+  auto take = [&](size_t bytes) -> char * {
+    const size_t at = ar.reserve(bytes);
+    return assign ? ar.base + at : nullptr;
+  };
+  w.C = C;
+  const int L = s->L, dy = s->d_y;
+  const size_t rows = (size_t)C * dy;
+  w.act64.assign(L, nullptr);
+  w.der64.assign(L, nullptr);
+  w.der32.assign(L, nullptr);
+  w.actb.assign(L, nullptr);
+  w.ldact.assign(L, 0);
+  w.plact.assign(L, 0);
+  if (s->precision == DINO_PREC_FP64) {
+    for (int l = 0; l + 1 < L; ++l) {
+      w.act64[l] = (double *)take((size_t)C * s->widths[l + 1] * 8);
+      w.der64[l] = (double *)take((size_t)C * s->widths[l + 1] * 8);
+    }
+    w.f64 = (double *)take((size_t)C * dy * 8);
+    if (L >= 2) {
+      w.P64[0] = (double *)take(rows * s->widest * 8);
+      w.P64[1] = (double *)take(rows * s->widest * 8);
+    }
+    w.J64 = (double *)take(rows * s->r * 8);
+  } else {
+    w.ldx = pad8(s->r);
+    w.plx = (size_t)C * w.ldx;
+    w.xb = (__nv_bfloat16 *)take(w.plx * s->fwd_slices * 2);
+    for (int l = 0; l + 1 < L; ++l) {
+      const int wd = s->widths[l + 1];
+      w.ldact[l] = pad8(wd);
+      w.plact[l] = (size_t)C * w.ldact[l];
+      w.actb[l] = (__nv_bfloat16 *)take(w.plact[l] * s->fwd_slices * 2);
+      w.der32[l] = (float *)take((size_t)C * wd * 4);
+    }
+    w.f32 = (float *)take((size_t)C * dy * 4);
+    if (L >= 2) {
+      w.ldp = pad8(s->widest);
+      w.plp = rows * w.ldp;
+      w.Pb[0] = (__nv_bfloat16 *)take(w.plp * s->jac_slices * 2);
+      w.Pb[1] = (__nv_bfloat16 *)take(w.plp * s->jac_slices * 2);
+    }
+    w.J32 = (float *)take(rows * s->r * 4);
+  }
+}
+
+// Forward pass and Jacobian at the C points in `x` (FP64 C x r; the tensor
+// path reads the bf16 planes in w.xb, which the caller has filled).
+static void eval_surrogate(dino_ctx *ctx, const Surrogate *s, Work &w, const double *x) {
+  const int C = w.C, L = s->L, dy = s->d_y, r = s->r;
+  cudaStream_t st = ctx->stream;
+  if (s->precision == DINO_PREC_FP64) {
+    const double *a = x;
+    int lda = r;
+    for (int l = 0; l + 1 < L; ++l) {
+      const int wo = s->widths[l + 1], wi = s->widths[l];
+      launch(ctx, "mlp_f64", [&] {
+        return gemm_bias_act<double>(C, wo, wi, a, lda, s->dW[l], wi, s->db[l], s->act,
+                                     w.act64[l], w.der64[l], wo, st);
+      });
+      a = w.act64[l];
+      lda = wo;
+    }
+    launch(ctx, "mlp_f64", [&] {
+      return gemm_bias_act<double>(C, dy, s->widths[L - 1], a, lda, s->dW[L - 1],
+                                   s->widths[L - 1], s->db[L - 1], 0, w.f64, nullptr, dy, st);
+    });
+    if (L == 1) {
+      launch(ctx, "jac_broadcast", [&] {
+        return launch_broadcast<double>(C, (size_t)dy * r, s->dW[0], w.J64, st);
+      });
+      return;
+    }
+    // reverse mode: P = W_{L-1} .* d_{L-2}; P <- (P W_l) .* d_{l-1}; J = P W_0
+    const int wl = s->widths[L - 1];
+    launch(ctx, "jac_init_f64", [&] {
+      return launch_jac_init<double>(C, dy, wl, s->dW[L - 1], w.der64[L - 2], wl, w.P64[0], st);
+    });
+    int cur = 0;
+    for (int l = L - 2; l >= 1; --l) {
+      const int wi = s->widths[l], wo = s->widths[l + 1];
+      launch(ctx, "jac_gemm_f64", [&] {
+        return gemm_scale_group<double>(C * dy, wi, wo, w.P64[cur], wo, s->dWT[l], wo,
+                                        w.der64[l - 1], wi, dy, w.P64[1 - cur], wi, st);
+      });
+      cur = 1 - cur;
+    }
+    launch(ctx, "jac_gemm_f64", [&] {
+      return gemm_store<double>(C * dy, r, s->widths[1], w.P64[cur], s->widths[1], s->dWT[0],
+                                s->widths[1], w.J64, r, st);
+    });
+    return;
+  }
+  // tensor-core path
+  const __nv_bfloat16 *a = w.xb;
+  int lda = w.ldx;
+  size_t pla = w.plx;
+  for (int l = 0; l + 1 < L; ++l) {
+    TcGemmArgs g;
+    g.M = C;
+    g.N = s->widths[l + 1];
+    g.K = s->widths[l];
+    g.A = a;
+    g.lda = lda;
+    g.a_plane = pla;
+    g.B = s->bW[l];
+    g.ldb = s->ldW[l];
+    g.b_plane = s->plW[l];
+    g.nslice = s->fwd_slices;
+    g.epi = TC_EPI_BIAS_ACT;
+    g.bias = s->fb[l];
+    g.act = s->act;
+    g.out_bf = w.actb[l];
+    g.ldo = w.ldact[l];
+    g.out_plane = w.plact[l];
+    g.out_slices = s->fwd_slices;
+    g.der = w.der32[l];
+    launch(ctx, "mlp_tc", [&] { return launch_tc_gemm(g, st); });
+    a = w.actb[l];
+    lda = w.ldact[l];
+    pla = w.plact[l];
+  }
+  {
+    TcGemmArgs g;
+    g.M = C;
+    g.N = dy;
+    g.K = s->widths[L - 1];
+    g.A = a;
+    g.lda = lda;
+    g.a_plane = pla;
+    g.B = s->bW[L - 1];
+    g.ldb = s->ldW[L - 1];
+    g.b_plane = s->plW[L - 1];
+    g.nslice = s->fwd_slices;
+    g.epi = TC_EPI_BIAS_F32;
+    g.bias = s->fb[L - 1];
+    g.outf = w.f32;
+    g.ldo = dy;
+    launch(ctx, "mlp_tc", [&] { return launch_tc_gemm(g, st); });
+  }
+  const int wl = s->widths[L - 1];
+  launch(ctx, "jac_init_tc", [&] {
+    return launch_jac_init_bf16(C, dy, wl, s->dW[L - 1], w.der32[L - 2], wl, w.Pb[0], w.ldp,
+                                w.plp, s->jac_slices, st);
+  });
+  int cur = 0;
+  for (int l = L - 2; l >= 1; --l) {
+    TcGemmArgs g;
+    g.M = C * dy;
+    g.N = s->widths[l];
+    g.K = s->widths[l + 1];
+    g.A = w.Pb[cur];
+    g.lda = w.ldp;
+    g.a_plane = w.plp;
+    g.B = s->bWT[l];
+    g.ldb = s->ldWT[l];
+    g.b_plane = s->plWT[l];
+    g.nslice = s->jac_slices;
+    g.epi = TC_EPI_SCALE_GROUP;
+    g.scale = w.der32[l - 1];
+    g.lds = s->widths[l];
+    g.group = dy;
+    g.out_bf = w.Pb[1 - cur];
+    g.ldo = w.ldp;
+    g.out_plane = w.plp;
+    g.out_slices = s->jac_slices;
+    launch(ctx, "jac_tc", [&] { return launch_tc_gemm(g, st); });
+    cur = 1 - cur;
+  }
+  TcGemmArgs g;
+  g.M = C * dy;
+  g.N = r;
+  g.K = s->widths[1];
+  g.A = w.Pb[cur];
+  g.lda = w.ldp;
+  g.a_plane = w.plp;
+  g.B = s->bWT[0];
+  g.ldb = s->ldWT[0];
+  g.b_plane = s->plWT[0];
+  g.nslice = s->jac_slices;
+  g.epi = TC_EPI_STORE_F32;
+  g.outf = w.J32;
+  g.ldo = r;
+  launch(ctx, "jac_tc", [&] { return launch_tc_gemm(g, st); });
+}
+
+// ---------------------------------------------------------------------------
+// chain pools
+
+struct Pool {
+  int id = 0;
+  Surrogate *s = nullptr;
+  int C = 0;
+  double dt = 0, sc = 0;
+  uint64_t seed = 0, id_base = 0;
+  uint32_t step = 0;
+  Arena ar;
+  // state
+  double *mr, *g, *phi, *hld, *L;
+  void *m;  // C x N, double (FP64 path) or float (tensor path)
+  double *b, *mu, *lq_fwd, *coef, *log_rho, *log_u;
+  int *acc;
+  unsigned long long *acc_count, *counters;
+  double *sum_alpha;
+  // field scratch
+  void *Mf, *coef2;
+  Work w;
+};
+
+static void layout_pool(Pool &p, bool assign) {
+  const Surrogate *s = p.s;
+  const int C = p.C, r = s->r, N = s->N;
+  const size_t fe = s->precision == DINO_PREC_FP64 ? 8 : 4;
+  Arena &ar = p.ar;
+  ar.off = 0;
+  auto take = [&](size_t bytes) -> char * {
+    const size_t at = ar.reserve(bytes);
+    return assign ? ar.base + at : nullptr;
+  };
+  p.mr = (double *)take((size_t)C * r * 8);
+  p.g = (double *)take((size_t)C * r * 8);
+  p.phi = (double *)take((size_t)C * 8);
+  p.hld = (double *)take((size_t)C * 8);
+  p.L = (double *)take((size_t)C * tri_size(r) * 8);
+  p.m = take((size_t)C * N * fe);
+  p.b = (double *)take((size_t)C * r * 8);
+  p.mu = (double *)take((size_t)C * r * 8);
+  p.lq_fwd = (double *)take((size_t)C * 8);
+  p.coef = (double *)take((size_t)C * r * 8);
+  p.log_rho = (double *)take((size_t)C * 8);
+  p.log_u = (double *)take((size_t)C * 8);
+  p.acc = (int *)take((size_t)C * 4);
+  p.acc_count = (unsigned long long *)take((size_t)C * 8);
+  p.counters = (unsigned long long *)take(2 * 8);
+  p.sum_alpha = (double *)take(8);
+  // FP64 at init even on the FP32 path; also holds a zero data vector in surrogate_eval
+  p.Mf = take(std::max((size_t)C * N, (size_t)s->d_y) * std::max(fe, (size_t)8));
+  p.coef2 = take((size_t)C * r * fe);
+  layout_work(s, C, ar, p.w, assign);
+}
+
+static Pool *get_pool(dino_ctx *ctx, int id) {
+  auto it = ctx->pools.find(id);
+  if (it == ctx->pools.end()) fail(DINO_ENOTFOUND, "unknown pool id %d", id);
+  return it->second.get();
+}
+
+static ReducedArgs reduced_args(const Pool &p) {
+  const Surrogate *s = p.s;
+  ReducedArgs a;
+  a.C = p.C;
+  a.r = s->r;
+  a.d_y = s->d_y;
+  a.s = p.sc;
+  a.dt = p.dt;
+  a.noise_var = s->noise_var;
+  a.seed = p.seed;
+  a.id_base = p.id_base;
+  a.step = p.step;
+  a.mr = p.mr;
+  a.g = p.g;
+  a.phi = p.phi;
+  a.hld = p.hld;
+  a.L = p.L;
+  a.b = p.b;
+  a.mu = p.mu;
+  a.lq_fwd = p.lq_fwd;
+  a.y = s->dy;
+  a.coef = p.coef;
+  a.log_rho = p.log_rho;
+  a.log_u = p.log_u;
+  a.acc = p.acc;
+  a.acc_count = p.acc_count;
+  a.counters = p.counters;
+  a.sum_alpha = p.sum_alpha;
+  if (s->precision == DINO_PREC_FP64) {
+    a.J = p.w.J64;
+    a.f = p.w.f64;
+    a.jf_f32 = 0;
+  } else {
+    a.J = p.w.J32;
+    a.f = p.w.f32;
+    a.jf_f32 = 1;
+    a.b_bf16 = p.w.xb;
+    a.b_slices = s->fwd_slices;
+    a.b_ld = p.w.ldx;
+    a.b_plane = p.w.plx;
+  }
+  return a;
+}
+
+static void split_input(dino_ctx *ctx, const Surrogate *s, Work &w, const double *x) {
+  if (s->precision != DINO_PREC_BF16) return;
+  launch(ctx, "split_bf16", [&] {
+    return launch_split_bf16_f64(w.C, s->r, x, s->r, w.xb, w.ldx, w.plx, s->fwd_slices,
+                                 ctx->stream);
+  });
+}
+
+static int create_pool(dino_ctx *ctx, int sid, int C, double dt, uint64_t seed,
+                       uint64_t id_base, const double *m0) {
+  Surrogate *s = get_surrogate(ctx, sid);
+  if (C < 1) fail(DINO_EINVAL, "n_chains must be >= 1");
+  if (!(dt > 0) || !std::isfinite(dt)) fail(DINO_EINVAL, "dt must be > 0");
+  if (!s->has_data) fail(DINO_ESTATE, "surrogate %d has no data (dino_set_data)", sid);
+  auto p = std::make_unique<Pool>();
+  p->id = ctx->next_id++;
+  p->s = s;
+  p->C = C;
+  p->dt = dt;
+  p->sc = (4.0 - dt) / (4.0 + dt);
+  p->seed = seed;
+  p->id_base = id_base;
+  layout_pool(*p, false);
+  p->ar.bytes = p->ar.off;
+  p->ar.base = (char *)dev_alloc(ctx, p->ar.bytes);
+  try {
+    layout_pool(*p, true);
+    const int r = s->r, N = s->N;
+    cudaStream_t st = ctx->stream;
+    CK(cudaMemsetAsync(p->acc_count, 0, (size_t)C * 8, st));
+    CK(cudaMemsetAsync(p->counters, 0, 16, st));
+    CK(cudaMemsetAsync(p->sum_alpha, 0, 8, st));
+    CK(cudaMemsetAsync(p->acc, 0, (size_t)C * 4, st));
+    double *m64 = (double *)p->Mf;  // FP64 initial field
+    if (m0) {
+      CK(cudaMemcpyAsync(m64, m0, (size_t)C * N * 8, cudaMemcpyHostToDevice, st));
+    } else {
+      launch(ctx, "prior_draw_f64", [&] {
+        return launch_prior_draw<double>(C, s->n_grid, s->dSqrtLam, s->dS, seed, id_base,
+                                         STREAM_INIT_ID, 0, m64, N, st);
+      });
+    }
+    // m_r = E m0 (eq:projector), then the geometry at m_r
+    launch(ctx, "encode_f64", [&] {
+      return gemm_store<double>(C, r, N, m64, N, s->dE, N, p->b, r, st);
+    });
+    if (s->precision == DINO_PREC_FP64) {
+      CK(cudaMemcpyAsync(p->m, m64, (size_t)C * N * 8, cudaMemcpyDeviceToDevice, st));
+    } else {
+      launch(ctx, "convert", [&] {
+        return launch_f64_to_f32((size_t)C * N, m64, (float *)p->m, st);
+      });
+    }
+    split_input(ctx, s, p->w, p->b);
+    eval_surrogate(ctx, s, p->w, p->b);
+    ReducedArgs ra = reduced_args(*p);
+    launch(ctx, "geometry_init", [&] { return launch_geometry(ra, 0, st); });
+    CK(cudaStreamSynchronize(st));
+  } catch (...) {
+    dev_free(ctx, p->ar.base, p->ar.bytes);
+    throw;
+  }
+  s->pools += 1;
+  const int id = p->id;
+  ctx->pools[id] = std::move(p);
+  return id;
+}
+
+// One transition of every chain of the pool.
+static void step_pool(dino_ctx *ctx, Pool &p) {
+  const Surrogate *s = p.s;
+  const int C = p.C, r = s->r, N = s->N;
+  cudaStream_t st = ctx->stream;
+  const double cs = std::sqrt(1.0 - p.sc * p.sc);
+  ReducedArgs ra = reduced_args(p);
+  launch(ctx, "propose", [&] { return launch_propose(ra, st); });
+  eval_surrogate(ctx, s, p.w, p.b);
+  launch(ctx, "geometry_accept", [&] { return launch_geometry(ra, 1, st); });
+  // complement (Prop. 5.1): M prior draw, coef2 = (b - s a) - cs E M, m <- s m + cs M + D coef2
+  if (s->precision == DINO_PREC_FP64) {
+    double *Mf = (double *)p.Mf, *coef2 = (double *)p.coef2, *m = (double *)p.m;
+    launch(ctx, "prior_draw_f64", [&] {
+      return launch_prior_draw<double>(C, s->n_grid, s->dSqrtLam, s->dS, p.seed, p.id_base,
+                                       STREAM_Z_ID, p.step, Mf, N, st);
+    });
+    launch(ctx, "field_coef_f64", [&] {
+      return gemm_coef<double>(C, r, N, Mf, N, s->dE, N, p.coef, r, cs, coef2, r, st);
+    });
+    launch(ctx, "field_update_f64", [&] {
+      return gemm_field<double>(C, N, r, coef2, r, s->dD, r, p.acc, p.sc, cs, m, Mf, N, st);
+    });
+  } else {
+    float *Mf = (float *)p.Mf, *coef2 = (float *)p.coef2, *m = (float *)p.m;
+    launch(ctx, "prior_draw_f32", [&] {
+      return launch_prior_draw<float>(C, s->n_grid, s->fSqrtLam, s->fS, p.seed, p.id_base,
+                                      STREAM_Z_ID, p.step, Mf, N, st);
+    });
+    launch(ctx, "field_coef_f32", [&] {
+      return gemm_coef<float>(C, r, N, Mf, N, s->fE, N, p.coef, r, cs, coef2, r, st);
+    });
+    launch(ctx, "field_update_f32", [&] {
+      return gemm_field<float>(C, N, r, coef2, r, s->fD, r, p.acc, p.sc, cs, m, Mf, N, st);
+    });
+  }
+  p.step += 1;
+}
+
+static void destroy_pool(dino_ctx *ctx, int id) {
+  Pool *p = get_pool(ctx, id);
+  cudaStreamSynchronize(ctx->stream);
+  dev_free(ctx, p->ar.base, p->ar.bytes);
+  p->s->pools -= 1;
+  ctx->pools.erase(id);
+}
+
+// ---------------------------------------------------------------------------
+// surrogate evaluation at caller points (setup / testing entry point)
+
+static void surrogate_eval(dino_ctx *ctx, int sid, int n, const double *x_host, double *f,
+                           double *J, double *phi, double *g, double *Lfull, double *hld) {
+  Surrogate *s = get_surrogate(ctx, sid);
+  if (n < 1 || !x_host) fail(DINO_EINVAL, "need n >= 1 points");
+  const int r = s->r, dy = s->d_y;
+  Pool p;  // scratch pool-shaped workspace; only the geometry fields are used
+  p.s = s;
+  p.C = n;
+  p.dt = 1.0;
+  p.sc = 0.6;
+  layout_pool(p, false);
+  p.ar.bytes = p.ar.off;
+  p.ar.base = (char *)dev_alloc(ctx, p.ar.bytes);
+  std::vector<double> yzero;
+  double *ysave = s->dy;
+  try {
+    layout_pool(p, true);
+    cudaStream_t st = ctx->stream;
+    if (!s->has_data) {
+      // geometry needs some data vector: evaluate against zeros (phi and g then meaningless)
+      yzero.assign(dy, 0.0);
+      s->dy = (double *)p.Mf;
+      CK(cudaMemcpyAsync(s->dy, yzero.data(), dy * 8, cudaMemcpyHostToDevice, st));
+    }
+    CK(cudaMemcpyAsync(p.b, x_host, (size_t)n * r * 8, cudaMemcpyHostToDevice, st));
+    split_input(ctx, s, p.w, p.b);
+    eval_surrogate(ctx, s, p.w, p.b);
+    ReducedArgs ra = reduced_args(p);
+    ra.noise_var = s->has_data ? s->noise_var : 1.0;
+    launch(ctx, "geometry_init", [&] { return launch_geometry(ra, 0, st); });
+    CK(cudaStreamSynchronize(st));
+    std::vector<double> tmp;
+    auto fetch = [&](const void *src, size_t cnt, bool f32, double *dst) {
+      if (!dst) return;
+      if (f32) {
+        std::vector<float> t(cnt);
+        CK(cudaMemcpy(t.data(), src, cnt * 4, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < cnt; ++i) dst[i] = t[i];
+      } else {
+        CK(cudaMemcpy(dst, src, cnt * 8, cudaMemcpyDeviceToHost));
+      }
+    };
+    const bool tc = s->precision == DINO_PREC_BF16;
+    fetch(tc ? (const void *)p.w.f32 : p.w.f64, (size_t)n * dy, tc, f);
+    fetch(tc ? (const void *)p.w.J32 : p.w.J64, (size_t)n * dy * r, tc, J);
+    fetch(p.phi, n, false, phi);
+    fetch(p.g, (size_t)n * r, false, g);
+    fetch(p.hld, n, false, hld);
+    if (Lfull) {
+      const size_t ts = tri_size(r);
+      std::vector<double> packed((size_t)n * ts);
+      CK(cudaMemcpy(packed.data(), p.L, packed.size() * 8, cudaMemcpyDeviceToHost));
+      for (int c = 0; c < n; ++c)
+        for (int i = 0; i < r; ++i)
+          for (int j = 0; j < r; ++j)
+            Lfull[(size_t)c * r * r + (size_t)i * r + j] =
+                j <= i ? packed[(size_t)c * ts + (size_t)i * (i + 1) / 2 + j] : 0.0;
+    }
+  } catch (...) {
+    s->dy = ysave;
+    dev_free(ctx, p.ar.base, p.ar.bytes);
+    throw;
+  }
+  s->dy = ysave;
+  dev_free(ctx, p.ar.base, p.ar.bytes);
+}
+
+}  // namespace dino
+
+// ===========================================================================
+// C ABI
+using namespace dino;
+
+template <class F>
+static int guarded(dino_ctx *ctx, F &&fn) {
+  if (!ctx) return DINO_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  ctx->err.clear();
+  try {
+    fn();
+    return DINO_OK;
+  } catch (const Error &e) {
+    ctx->err = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc &) {
+    ctx->err = "host allocation failed";
+    return DINO_ENOMEM;
+  } catch (...) {
+    ctx->err = "unexpected internal error";
+    return DINO_ECUDA;
+  }
+}
+
+extern "C" {
+
+int dino_version(void) { return 100; }
+
+int dino_init(dino_ctx **out, int device, size_t hbm_budget_bytes, void *stream,
+              unsigned flags) {
+  if (!out) return DINO_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= device || device < 0) {
+    cudaGetLastError();
+    return DINO_ECUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return DINO_ECUDA;
+  auto ctx = new dino_ctx();
+  ctx->device = device;
+  ctx->flags = flags;
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    delete ctx;
+    return DINO_ECUDA;
+  }
+  ctx->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)fr);
+  if (stream) {
+    ctx->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete ctx;
+      return DINO_ECUDA;
+    }
+    ctx->own_stream = true;
+  }
+  *out = ctx;
+  return DINO_OK;
+}
+
+int dino_destroy(dino_ctx *ctx) {
+  if (!ctx) return DINO_EINVAL;
+  {
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto &kv : ctx->pools) dev_free(ctx, kv.second->ar.base, kv.second->ar.bytes);
+    ctx->pools.clear();
+    for (auto &kv : ctx->surrogates) free_surrogate(ctx, kv.second.get());
+    ctx->surrogates.clear();
+    for (auto &p : ctx->pending) {
+      cudaEventDestroy(p.e0);
+      cudaEventDestroy(p.e1);
+    }
+    for (auto e : ctx->event_pool) cudaEventDestroy(e);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  }
+  delete ctx;
+  return DINO_OK;
+}
+
+const char *dino_last_error(const dino_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int dino_sync(dino_ctx *ctx) {
+  return guarded(ctx, [&] {
+    cudaSetDevice(ctx->device);
+    CK(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
+int dino_load_surrogate(dino_ctx *ctx, const dino_surrogate_desc *desc, int *surrogate_id) {
+  return guarded(ctx, [&] {
+    if (!surrogate_id) fail(DINO_EINVAL, "surrogate_id is NULL");
+    cudaSetDevice(ctx->device);
+    *surrogate_id = load_surrogate(ctx, desc);
+  });
+}
+
+int dino_set_data(dino_ctx *ctx, int surrogate_id, const double *y, double noise_var) {
+  return guarded(ctx, [&] {
+    cudaSetDevice(ctx->device);
+    Surrogate *s = get_surrogate(ctx, surrogate_id);
+    if (!y) fail(DINO_EINVAL, "y is NULL");
+    if (!(noise_var > 0) || !std::isfinite(noise_var)) fail(DINO_EINVAL, "noise_var must be > 0");
+    if (s->pools > 0) fail(DINO_ESTATE, "surrogate has live chain pools");
+    for (int i = 0; i < s->d_y; ++i)
+      if (!std::isfinite(y[i])) fail(DINO_ENUMERIC, "non-finite data value");
+    s->y.assign(y, y + s->d_y);
+    s->noise_var = noise_var;
+    s->has_data = true;
+    upload_data(ctx, s);
+  });
+}
+
+int dino_unload_surrogate(dino_ctx *ctx, int surrogate_id) {
+  return guarded(ctx, [&] {
+    cudaSetDevice(ctx->device);
+    Surrogate *s = get_surrogate(ctx, surrogate_id);
+    if (s->pools > 0) fail(DINO_ESTATE, "surrogate has live chain pools");
+    free_surrogate(ctx, s);
+    ctx->surrogates.erase(surrogate_id);
+  });
+}
+
+int dino_read_basis(dino_ctx *ctx, int surrogate_id, double *E, double *D) {
+  return guarded(ctx, [&] {
+    Surrogate *s = get_surrogate(ctx, surrogate_id);
+    if (E) std::memcpy(E, s->E.data(), s->E.size() * 8);
+    if (D) std::memcpy(D, s->D.data(), s->D.size() * 8);
+  });
+}
+
+int dino_surrogate_eval(dino_ctx *ctx, int surrogate_id, int n, const double *m_r, double *f,
+                        double *J, double *phi, double *g, double *L, double *hld) {
+  return guarded(ctx, [&] {
+    cudaSetDevice(ctx->device);
+    surrogate_eval(ctx, surrogate_id, n, m_r, f, J, phi, g, L, hld);
+    collect_times(ctx);
+  });
+}
+
+int dino_chains_create(dino_ctx *ctx, int surrogate_id, int n_chains, double dt, uint64_t seed,
+                       uint64_t chain_id_base, const double *m0, int *pool_id) {
+  return guarded(ctx, [&] {
+    if (!pool_id) fail(DINO_EINVAL, "pool_id is NULL");
+    cudaSetDevice(ctx->device);
+    *pool_id = create_pool(ctx, surrogate_id, n_chains, dt, seed, chain_id_base, m0);
+    collect_times(ctx);
+  });
+}
+
+int dino_chains_step(dino_ctx *ctx, int pool_id, int n_steps, dino_step_stats *stats) {
+  return guarded(ctx, [&] {
+    if (n_steps < 0) fail(DINO_EINVAL, "n_steps must be >= 0");
+    cudaSetDevice(ctx->device);
+    Pool *p = get_pool(ctx, pool_id);
+    unsigned long long c0[2] = {0, 0};
+    double a0 = 0;
+    if (stats) {
+      CK(cudaMemcpyAsync(c0, p->counters, 16, cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaMemcpyAsync(&a0, p->sum_alpha, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    for (int k = 0; k < n_steps; ++k) step_pool(ctx, *p);
+    if (stats) {
+      unsigned long long c1[2];
+      double a1 = 0;
+      CK(cudaMemcpyAsync(c1, p->counters, 16, cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaMemcpyAsync(&a1, p->sum_alpha, 8, cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      stats->proposals = (uint64_t)p->C * (uint64_t)n_steps;
+      stats->accepts = c1[0] - c0[0];
+      stats->nan_rejects = c1[1] - c0[1];
+      stats->sum_alpha = a1 - a0;
+    }
+    collect_times(ctx);
+  });
+}
+
+int dino_chains_read(dino_ctx *ctx, int pool_id, double *m, double *m_r, double *phi,
+                     uint64_t *accepts) {
+  return guarded(ctx, [&] {
+    cudaSetDevice(ctx->device);
+    Pool *p = get_pool(ctx, pool_id);
+    const int C = p->C, r = p->s->r, N = p->s->N;
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (m) {
+      if (p->s->precision == DINO_PREC_FP64) {
+        CK(cudaMemcpy(m, p->m, (size_t)C * N * 8, cudaMemcpyDeviceToHost));
+      } else {
+        std::vector<float> t((size_t)C * N);
+        CK(cudaMemcpy(t.data(), p->m, t.size() * 4, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < t.size(); ++i) m[i] = t[i];
+      }
+    }
+    if (m_r) CK(cudaMemcpy(m_r, p->mr, (size_t)C * r * 8, cudaMemcpyDeviceToHost));
+    if (phi) CK(cudaMemcpy(phi, p->phi, (size_t)C * 8, cudaMemcpyDeviceToHost));
+    if (accepts) CK(cudaMemcpy(accepts, p->acc_count, (size_t)C * 8, cudaMemcpyDeviceToHost));
+  });
+}
+
+int dino_chains_read_last(dino_ctx *ctx, int pool_id, double *b, double *mu, double *log_rho,
+                          double *log_u, int *accepted) {
+  return guarded(ctx, [&] {
+    cudaSetDevice(ctx->device);
+    Pool *p = get_pool(ctx, pool_id);
+    const int C = p->C, r = p->s->r;
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (b) CK(cudaMemcpy(b, p->b, (size_t)C * r * 8, cudaMemcpyDeviceToHost));
+    if (mu) CK(cudaMemcpy(mu, p->mu, (size_t)C * r * 8, cudaMemcpyDeviceToHost));
+    if (log_rho) CK(cudaMemcpy(log_rho, p->log_rho, (size_t)C * 8, cudaMemcpyDeviceToHost));
+    if (log_u) CK(cudaMemcpy(log_u, p->log_u, (size_t)C * 8, cudaMemcpyDeviceToHost));
+    if (accepted) CK(cudaMemcpy(accepted, p->acc, (size_t)C * 4, cudaMemcpyDeviceToHost));
+  });
+}
+
+int dino_chains_destroy(dino_ctx *ctx, int pool_id) {
+  return guarded(ctx, [&] {
+    cudaSetDevice(ctx->device);
+    destroy_pool(ctx, pool_id);
+  });
+}
+
+uint64_t dino_launch_count(const dino_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+int dino_kernel_times(dino_ctx *ctx, char *names, double *total_ms, uint64_t *launches, int cap,
+                      int *n, int reset) {
+  return guarded(ctx, [&] {
+    collect_times(ctx);
+    int k = 0;
+    for (auto &kv : ctx->ktimes) {
+      if (k >= cap) break;
+      if (names) {
+        std::memset(names + 48 * k, 0, 48);
+        std::strncpy(names + 48 * k, kv.first.c_str(), 47);
+      }
+      if (total_ms) total_ms[k] = kv.second.ms;
+      if (launches) launches[k] = kv.second.n;
+      ++k;
+    }
+    if (n) *n = (int)ctx->ktimes.size();
+    if (reset) ctx->ktimes.clear();
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,320 @@
+// SIMT kernels of the sampler: FP64/FP32 tiled GEMMs with fused epilogues
+// (MLP layers, reverse-mode Jacobian products, complement projection and
+// field update), the full-KLE prior draw, and small elementwise helpers.
+//
+// GEMM convention: out = epilogue(A B^T) with A: M x K (row pitch lda) and
+// B: N x K (row pitch ldb), i.e. both operands K-contiguous.
+#include "dino_internal.h"
+#include "philox.cuh"
+
+namespace dino {
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4, kGemmThreads = 256;
+
+template <typename T>
+__device__ __forceinline__ T act_fn(int kind, T z) {
+  if (kind == 1) return tanh(z);
+  if (kind == 2) return T(0.5) * z * (T(1) + erf(z * T(0.70710678118654752440)));
+  return z;
+}
+
+template <typename T>
+__device__ __forceinline__ T act_deriv(int kind, T z) {
+  if (kind == 1) {
+    const T t = tanh(z);
+    return T(1) - t * t;
+  }
+  if (kind == 2)
+    return T(0.5) * (T(1) + erf(z * T(0.70710678118654752440))) +
+           z * exp(T(-0.5) * z * z) * T(0.39894228040143267794);
+  return T(1);
+}
+
+// Tiled GEMM: each thread owns a TM x TN block of outputs, strided by 16 so
+// that the shared-memory reads of a warp fall in distinct banks.
+template <typename T, class Epi>
+__global__ void __launch_bounds__(kGemmThreads)
+    k_gemm(int M, int N, int K, const T *__restrict__ A, int lda, const T *__restrict__ B,
+           int ldb, Epi epi) {
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
+  T acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    for (int e = tid; e < BM * BK; e += kGemmThreads) {
+      const int m = e / BK, k = e % BK, gr = row0 + m, gk = k0 + k;
+      As[k][m] = (gr < M && gk < K) ? A[(size_t)gr * lda + gk] : T(0);
+    }
+    for (int e = tid; e < BN * BK; e += kGemmThreads) {
+      const int n = e / BK, k = e % BK, gc = col0 + n, gk = k0 + k;
+      Bs[k][n] = (gc < N && gk < K) ? B[(size_t)gc * ldb + gk] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < BK; ++k) {
+      T a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[k][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[k][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] += a[i] * b[j];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int r = row0 + ty + 16 * i, c = col0 + tx + 16 * j;
+      if (r < M && c < N) epi(r, c, acc[i][j]);
+    }
+}
+
+template <typename T>
+struct EpiStore {
+  T *out;
+  int ldo;
+  __device__ void operator()(int r, int c, T v) const { out[(size_t)r * ldo + c] = v; }
+};
+
+template <typename T>
+struct EpiBiasAct {
+  const T *bias;
+  int act;
+  T *out, *der;
+  int ldo;
+  __device__ void operator()(int r, int c, T v) const {
+    const T z = v + bias[c];
+    out[(size_t)r * ldo + c] = act_fn(act, z);
+    if (der) der[(size_t)r * ldo + c] = act_deriv(act, z);
+  }
+};
+
+template <typename T>
+struct EpiScaleGroup {
+  const T *scale;
+  int lds, group;
+  T *out;
+  int ldo;
+  __device__ void operator()(int r, int c, T v) const {
+    out[(size_t)r * ldo + c] = v * scale[(size_t)(r / group) * lds + c];
+  }
+};
+
+template <typename T>
+struct EpiCoef {
+  const double *coef;
+  int ldc;
+  double cs;
+  T *out;
+  int ldo;
+  __device__ void operator()(int r, int c, T v) const {
+    out[(size_t)r * ldo + c] = (T)(coef[(size_t)r * ldc + c] - cs * (double)v);
+  }
+};
+
+template <typename T>
+struct EpiField {
+  const int *acc;
+  double s, cs;
+  T *m;
+  const T *Mf;
+  int ldm;
+  __device__ void operator()(int r, int c, T v) const {
+    if (!acc[r]) return;
+    const size_t o = (size_t)r * ldm + c;
+    m[o] = (T)(s * (double)m[o] + cs * (double)Mf[o]) + v;
+  }
+};
+
+template <typename T, class Epi>
+cudaError_t run_gemm(int M, int N, int K, const T *A, int lda, const T *B, int ldb, Epi epi,
+                     cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+  k_gemm<T, Epi><<<grid, kGemmThreads, 0, st>>>(M, N, K, A, lda, B, ldb, epi);
+  return cudaGetLastError();
+}
+
+// Prior draw: one CTA per chain; X = sqrt(Lambda) .* Z (spectral), Y = X S,
+// M = S^T Y, all n x n in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_prior_draw(int n, const T *__restrict__ sqrtlam, const T *__restrict__ S, uint64_t seed,
+                 uint64_t id_base, uint32_t stream, uint32_t step, T *out, int ldo) {
+  extern __shared__ unsigned char smraw[];
+  T *X = reinterpret_cast<T *>(smraw);
+  T *Ss = X + n * n;
+  T *Y = Ss + n * n;
+  const int c = blockIdx.x, N = n * n;
+  const uint32_t chain = (uint32_t)(id_base + (uint64_t)c);
+  for (int blk = threadIdx.x; blk < (N + 3) / 4; blk += blockDim.x) {
+    const uint4 w = philox_block(seed, stream, step, chain, blk);
+    if constexpr (sizeof(T) == 8) {
+      double z[4];
+      normals4_f64(w, z);
+      for (int q = 0; q < 4; ++q)
+        if (4 * blk + q < N) X[4 * blk + q] = sqrtlam[4 * blk + q] * z[q];
+    } else {
+      float z[4];
+      normals4_f32(w, z);
+      for (int q = 0; q < 4; ++q)
+        if (4 * blk + q < N) X[4 * blk + q] = sqrtlam[4 * blk + q] * z[q];
+    }
+  }
+  for (int e = threadIdx.x; e < N; e += blockDim.x) Ss[e] = S[e];
+  __syncthreads();
+  // X is indexed [ky-1][kx-1]; Y[ky][i] = sum_kx X[ky][kx] S[kx][i]
+  for (int e = threadIdx.x; e < N; e += blockDim.x) {
+    const int ky = e / n, i = e % n;
+    T acc = 0;
+    for (int kx = 0; kx < n; ++kx) acc += X[ky * n + kx] * Ss[kx * n + i];
+    Y[e] = acc;
+  }
+  __syncthreads();
+  // M[j][i] = sum_ky S[ky][j] Y[ky][i]; node p = i + n j
+  T *o = out + (size_t)c * ldo;
+  for (int e = threadIdx.x; e < N; e += blockDim.x) {
+    const int j = e / n, i = e % n;
+    T acc = 0;
+    for (int ky = 0; ky < n; ++ky) acc += Ss[ky * n + j] * Y[ky * n + i];
+    o[e] = acc;
+  }
+}
+
+template <typename T>
+__global__ void k_jac_init(int C, int d_y, int w, const T *__restrict__ WL,
+                           const T *__restrict__ der, int ldd, T *__restrict__ P) {
+  const size_t total = (size_t)C * d_y * w;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const size_t row = e / w;
+    const int k = (int)(e % w);
+    const size_t c = row / d_y;
+    const int i = (int)(row % d_y);
+    P[e] = WL[(size_t)i * w + k] * der[c * ldd + k];
+  }
+}
+
+template <typename T>
+__global__ void k_broadcast(int C, size_t n, const T *__restrict__ src, T *__restrict__ out) {
+  const size_t total = (size_t)C * n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x)
+    out[e] = src[e % n];
+}
+
+template <typename S, typename D>
+__global__ void k_convert(size_t n, const S *__restrict__ src, D *__restrict__ dst) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x)
+    dst[e] = (D)src[e];
+}
+
+inline int grid_for(size_t n) {
+  size_t g = (n + 255) / 256;
+  return (int)(g > 152 * 32 ? 152 * 32 : (g ? g : 1));
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t gemm_store(int M, int N, int K, const T *A, int lda, const T *B, int ldb, T *out,
+                       int ldo, cudaStream_t st) {
+  return run_gemm(M, N, K, A, lda, B, ldb, EpiStore<T>{out, ldo}, st);
+}
+
+template <typename T>
+cudaError_t gemm_bias_act(int M, int N, int K, const T *A, int lda, const T *B, int ldb,
+                          const T *bias, int act, T *out, T *der, int ldo, cudaStream_t st) {
+  return run_gemm(M, N, K, A, lda, B, ldb, EpiBiasAct<T>{bias, act, out, der, ldo}, st);
+}
+
+template <typename T>
+cudaError_t gemm_scale_group(int M, int N, int K, const T *A, int lda, const T *B, int ldb,
+                             const T *scale, int lds, int group, T *out, int ldo,
+                             cudaStream_t st) {
+  return run_gemm(M, N, K, A, lda, B, ldb, EpiScaleGroup<T>{scale, lds, group, out, ldo}, st);
+}
+
+template <typename T>
+cudaError_t gemm_coef(int M, int N, int K, const T *A, int lda, const T *B, int ldb,
+                      const double *coef, int ldc, double c, T *out, int ldo, cudaStream_t st) {
+  return run_gemm(M, N, K, A, lda, B, ldb, EpiCoef<T>{coef, ldc, c, out, ldo}, st);
+}
+
+template <typename T>
+cudaError_t gemm_field(int M, int N, int K, const T *A, int lda, const T *B, int ldb,
+                       const int *acc_flag, double s, double c, T *m, const T *Mf, int ldm,
+                       cudaStream_t st) {
+  return run_gemm(M, N, K, A, lda, B, ldb, EpiField<T>{acc_flag, s, c, m, Mf, ldm}, st);
+}
+
+template <typename T>
+cudaError_t launch_prior_draw(int C, int n, const T *sqrtlam, const T *S, uint64_t seed,
+                              uint64_t id_base, uint32_t stream, uint32_t step, T *out, int ldo,
+                              cudaStream_t st) {
+  if (C <= 0) return cudaSuccess;
+  const size_t smem = 3 * (size_t)n * n * sizeof(T);
+  cudaError_t e = cudaFuncSetAttribute(k_prior_draw<T>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_prior_draw<T><<<C, 256, smem, st>>>(n, sqrtlam, S, seed, id_base, stream, step, out, ldo);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_jac_init(int C, int d_y, int w, const T *WL, const T *der, int ldd, T *P,
+                            cudaStream_t st) {
+  k_jac_init<T><<<grid_for((size_t)C * d_y * w), 256, 0, st>>>(C, d_y, w, WL, der, ldd, P);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_broadcast(int C, size_t n, const T *src, T *out, cudaStream_t st) {
+  k_broadcast<T><<<grid_for((size_t)C * n), 256, 0, st>>>(C, n, src, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_f64_to_f32(size_t n, const double *src, float *dst, cudaStream_t st) {
+  k_convert<double, float><<<grid_for(n), 256, 0, st>>>(n, src, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_f32_to_f64(size_t n, const float *src, double *dst, cudaStream_t st) {
+  k_convert<float, double><<<grid_for(n), 256, 0, st>>>(n, src, dst);
+  return cudaGetLastError();
+}
+
+#define DINO_INST(T)                                                                          \
+  template cudaError_t gemm_store<T>(int, int, int, const T *, int, const T *, int, T *, int, \
+                                     cudaStream_t);                                           \
+  template cudaError_t gemm_bias_act<T>(int, int, int, const T *, int, const T *, int,        \
+                                        const T *, int, T *, T *, int, cudaStream_t);         \
+  template cudaError_t gemm_scale_group<T>(int, int, int, const T *, int, const T *, int,     \
+                                           const T *, int, int, T *, int, cudaStream_t);      \
+  template cudaError_t gemm_coef<T>(int, int, int, const T *, int, const T *, int,            \
+                                    const double *, int, double, T *, int, cudaStream_t);     \
+  template cudaError_t gemm_field<T>(int, int, int, const T *, int, const T *, int,           \
+                                     const int *, double, double, T *, const T *, int,        \
+                                     cudaStream_t);                                           \
+  template cudaError_t launch_prior_draw<T>(int, int, const T *, const T *, uint64_t,         \
+                                            uint64_t, uint32_t, uint32_t, T *, int,           \
+                                            cudaStream_t);                                    \
+  template cudaError_t launch_jac_init<T>(int, int, int, const T *, const T *, int, T *,      \
+                                          cudaStream_t);                                      \
+  template cudaError_t launch_broadcast<T>(int, size_t, const T *, T *, cudaStream_t);
+
+DINO_INST(double)
+DINO_INST(float)
+
+}  // namespace dino

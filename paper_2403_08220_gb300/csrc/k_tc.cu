@@ -1,0 +1,447 @@
+// Tensor-core GEMMs of the reduced MLP and its Jacobian on sm_103a (tcgen05).
+//
+//   D[M x N] = sum_{(i,j): i + j < nslice} A_i B_j^T,   FP32 accumulation in TMEM,
+//
+// where X ~= X_0 + X_1 + ... are bf16 "slice planes" of an FP32 value
+// (X_0 = bf16(X), X_1 = bf16(X - X_0), ...).  nslice = 1 is the plain BF16
+// product, 2 the three-product "bf16x3" scheme, 3 six products (FP32-level).
+//
+// One CTA computes a 128 x BN output tile (cta_group::1, M = 128):
+//   warp 0     TMA producer: 3D tiled loads (k, row, slice) of 128 x 64 A and
+//              BN x 64 B boxes, 128-byte swizzle, into a ring of stages;
+//   warp 1     allocates TMEM and issues tcgen05.mma (K = 16 per instruction,
+//              four per 64-wide stage); tcgen05.commit frees each stage;
+//   warps 2-5  epilogue: tcgen05.ld of their 32 TMEM lanes, fused bias /
+//              activation / derivative / per-chain scaling, bf16 re-slicing.
+// Every mbarrier wait is bounded; on timeout the CTA raises a device error
+// flag, lets its copies and MMAs drain (bounded), frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
+#include "dino_internal.h"
+
+namespace dino {
+namespace {
+
+constexpr int kBlockM = 128;
+constexpr int kBlockK = 64;  // 128 bytes of bf16: one swizzle row
+constexpr int kThreads = 192;
+constexpr uint32_t kSpinLimit = 1u << 24;
+constexpr int kMaxStages = 4;
+
+struct TcParams {
+  int M, N, K, BN, nkb, npairs, stages;
+  int pair_a[6], pair_b[6];
+  int epi, ldo, act, out_slices, lds, group;
+  size_t out_plane;
+  float *outf;
+  const float *bias;
+  __nv_bfloat16 *out_bf;
+  float *der;
+  const float *scale;
+  uint32_t tmem_cols;
+  int *err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait; gives up early when another role has aborted.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+  for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if (abort_flag && *abort_flag) return false;
+    if (it > 32) __nanosleep(64);
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *tm, int c0, int c1,
+                                            int c2, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO), descriptor version 1 (bits 46-47).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor of kind::f16: D f32, A and B bf16, both K-major.
+__device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float act_fn(int kind, float z) {
+  if (kind == 1) return tanhf(z);
+  if (kind == 2) return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
+  return z;
+}
+__device__ __forceinline__ float act_deriv(int kind, float z) {
+  if (kind == 1) {
+    const float t = tanhf(z);
+    return 1.0f - t * t;
+  }
+  if (kind == 2)
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) +
+           z * __expf(-0.5f * z * z) * 0.39894228040143267794f;
+  return 1.0f;
+}
+
+__device__ __forceinline__ void store_slices(float x, __nv_bfloat16 *dst, size_t plane,
+                                             int nslice) {
+  float rem = x;
+  for (int s = 0; s < nslice; ++s) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(rem);
+    dst[s * plane] = h;
+    rem -= __bfloat162float(h);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              const TcParams p) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  // 1024-byte aligned stage ring, then barriers
+  const uint32_t raw = smem_u32(smraw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char *gbase = smraw + (base - raw);
+  const uint32_t a_bytes = kBlockM * kBlockK * 2, b_bytes = (uint32_t)p.BN * kBlockK * 2;
+  const uint32_t stage_bytes = a_bytes + b_bytes;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(gbase + p.stages * stage_bytes);
+  // bars[0..S) full, [S..2S) empty, [2S] accumulator ready
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 2 * p.stages + 1);
+  volatile int *consumed = abort_flag + 1;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * p.stages + 2);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kBlockM, n0 = blockIdx.y * p.BN;
+  const int n_iter = p.npairs * p.nkb;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < p.stages; ++s) {
+      mbar_init(smem_u32(&bars[s]), 1);
+      mbar_init(smem_u32(&bars[p.stages + s]), 1);
+    }
+    mbar_init(smem_u32(&bars[2 * p.stages]), 1);
+    *abort_flag = 0;
+    *consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(p.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int it = 0; it < n_iter; ++it) {
+        const int s = it % p.stages;
+        const uint32_t ph = (uint32_t)(it / p.stages) & 1u;
+        if (!mbar_wait(smem_u32(&bars[p.stages + s]), ph ^ 1u, abort_flag)) {
+          *abort_flag = 1;
+          atomicOr(p.err, 1);
+          break;
+        }
+        const int pr = it / p.nkb, kb = it % p.nkb;
+        const uint32_t full = smem_u32(&bars[s]);
+        mbar_expect_tx(full, stage_bytes);
+        const uint32_t sa = base + s * stage_bytes;
+        tma_load_3d(sa, &tmA, kb * kBlockK, m0, p.pair_a[pr], full);
+        tma_load_3d(sa + a_bytes, &tmB, kb * kBlockK, n0, p.pair_b[pr], full);
+        issued = it + 1;
+      }
+      if (*abort_flag) {
+        // let the copies already issued land before the CTA's memory goes away
+        for (int it = *consumed; it < issued; ++it)
+          mbar_wait(smem_u32(&bars[it % p.stages]), (uint32_t)(it / p.stages) & 1u, nullptr);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(kBlockM, p.BN);
+      bool ok = true;
+      for (int it = 0; it < n_iter; ++it) {
+        const int s = it % p.stages;
+        const uint32_t ph = (uint32_t)(it / p.stages) & 1u;
+        if (!mbar_wait(smem_u32(&bars[s]), ph, abort_flag)) {
+          *abort_flag = 1;
+          atomicOr(p.err, 2);
+          ok = false;
+          break;
+        }
+        *consumed = it + 1;
+        fence_after();
+        const uint32_t sa = base + s * stage_bytes;
+        const uint64_t ad = smem_desc_sw128(sa), bd = smem_desc_sw128(sa + a_bytes);
+#pragma unroll
+        for (int k = 0; k < kBlockK / 16; ++k)
+          mma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc, (it > 0 || k > 0) ? 1u : 0u);
+        mma_commit(smem_u32(&bars[p.stages + s]));
+      }
+      mma_commit(smem_u32(&bars[2 * p.stages]));
+      if (!ok) mbar_wait(smem_u32(&bars[2 * p.stages]), 0, nullptr);  // drain issued MMAs
+    }
+  } else {
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31
+    const int quarter = warp & 3;
+    const int row = m0 + quarter * 32 + lane;
+    // one lane waits, the warp follows its verdict (tcgen05.ld is warp-collective)
+    int okl = 0;
+    if (lane == 0) okl = mbar_wait(smem_u32(&bars[2 * p.stages]), 0, abort_flag) ? 1 : 0;
+    const bool ok = __shfl_sync(0xffffffffu, okl, 0) != 0;
+    fence_after();
+    if (ok && n_iter > 0) {
+      const int nvalid = min(p.BN, p.N - n0);
+      for (int c0 = 0; c0 < nvalid; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
+        if (row >= p.M) continue;
+        const int ncols = min(16, nvalid - c0);
+        const int col0 = n0 + c0;
+        if (p.epi == TC_EPI_STORE_F32 || p.epi == TC_EPI_BIAS_F32) {
+          float *o = p.outf + (size_t)row * p.ldo + col0;
+          for (int j = 0; j < ncols; ++j)
+            o[j] = v[j] + (p.epi == TC_EPI_BIAS_F32 ? p.bias[col0 + j] : 0.0f);
+        } else if (p.epi == TC_EPI_BIAS_ACT) {
+          __nv_bfloat16 *o = p.out_bf + (size_t)row * p.ldo + col0;
+          float *d = p.der + (size_t)row * p.N + col0;
+          for (int j = 0; j < ncols; ++j) {
+            const float z = v[j] + p.bias[col0 + j];
+            store_slices(act_fn(p.act, z), o + j, p.out_plane, p.out_slices);
+            d[j] = act_deriv(p.act, z);
+          }
+        } else {
+          __nv_bfloat16 *o = p.out_bf + (size_t)row * p.ldo + col0;
+          const float *sc = p.scale + (size_t)(row / p.group) * p.lds + col0;
+          for (int j = 0; j < ncols; ++j)
+            store_slices(v[j] * sc[j], o + j, p.out_plane, p.out_slices);
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(p.tmem_cols)
+                 : "memory");
+  }
+}
+
+__global__ void k_split_bf16(int rows, int cols, const double *__restrict__ src, int lds,
+                             __nv_bfloat16 *__restrict__ dst, int ldd, size_t plane, int nslice) {
+  const size_t total = (size_t)rows * cols;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = e / cols;
+    const int j = (int)(e % cols);
+    store_slices((float)src[i * lds + j], dst + i * ldd + j, plane, nslice);
+  }
+}
+
+__global__ void k_jac_init_bf16(int C, int d_y, int w, const double *__restrict__ WL,
+                                const float *__restrict__ der, int ldd,
+                                __nv_bfloat16 *__restrict__ P, int ldp, size_t plane,
+                                int nslice) {
+  const size_t total = (size_t)C * d_y * w;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const size_t row = e / w;
+    const int k = (int)(e % w);
+    const size_t c = row / d_y;
+    const int i = (int)(row % d_y);
+    const float v = (float)(WL[(size_t)i * w + k] * (double)der[c * ldd + k]);
+    store_slices(v, P + row * ldp + k, plane, nslice);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+  }
+  return fn;
+}
+
+// 3D map over slice planes: dims (K, rows, slices), box (64, box_rows, 1).
+bool make_map(CUtensorMap *tm, const __nv_bfloat16 *ptr, int K, int rows, int ld, size_t plane,
+              int slices, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)slices};
+  cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)plane * 2};
+  cuuint32_t box[3] = {(cuuint32_t)kBlockK, (cuuint32_t)box_rows, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  return fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void *)ptr, dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int *error_word() {
+  static int *d = nullptr;
+  if (!d && cudaMalloc(&d, sizeof(int)) == cudaSuccess) cudaMemset(d, 0, sizeof(int));
+  return d;
+}
+
+}  // namespace
+
+int tc_error_flag(bool reset) {
+  int *d = error_word();
+  if (!d) return 0;
+  int h = 0;
+  cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost);
+  if (reset) cudaMemset(d, 0, sizeof(int));
+  return h;
+}
+
+cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st) {
+  if (a.M <= 0 || a.N <= 0) return cudaSuccess;
+  if (a.nslice < 1 || a.nslice > 3 || a.K <= 0 || (a.lda & 7) || (a.ldb & 7) ||
+      (a.a_plane & 7) || (a.b_plane & 7) || ((uintptr_t)a.A & 15) || ((uintptr_t)a.B & 15))
+    return cudaErrorInvalidValue;
+  TcParams p{};
+  p.M = a.M;
+  p.N = a.N;
+  p.K = a.K;
+  const int ntiles = (a.N + 255) / 256;
+  p.BN = ((a.N + ntiles - 1) / ntiles + 15) / 16 * 16;
+  p.nkb = (a.K + kBlockK - 1) / kBlockK;
+  static const int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 2, 1, 0};
+  p.npairs = a.nslice == 1 ? 1 : (a.nslice == 2 ? 3 : 6);
+  for (int i = 0; i < 6; ++i) {
+    p.pair_a[i] = pa[i];
+    p.pair_b[i] = pb[i];
+  }
+  const int stage_bytes = kBlockM * kBlockK * 2 + p.BN * kBlockK * 2;
+  p.stages = (110 * 1024) / stage_bytes;
+  if (p.stages > kMaxStages) p.stages = kMaxStages;
+  if (p.stages < 2) p.stages = 2;
+  p.epi = a.epi;
+  p.ldo = a.ldo;
+  p.act = a.act;
+  p.out_slices = a.out_slices;
+  p.lds = a.lds;
+  p.group = a.group > 0 ? a.group : 1;
+  p.out_plane = a.out_plane;
+  p.outf = a.outf;
+  p.bias = a.bias;
+  p.out_bf = a.out_bf;
+  p.der = a.der;
+  p.scale = a.scale;
+  uint32_t cols = 32;
+  while (cols < (uint32_t)p.BN) cols <<= 1;
+  p.tmem_cols = cols;
+  p.err = error_word();
+  if (!p.err) return cudaErrorMemoryAllocation;
+  CUtensorMap tmA, tmB;
+  if (!make_map(&tmA, a.A, a.K, a.M, a.lda, a.a_plane, a.nslice, kBlockM) ||
+      !make_map(&tmB, a.B, a.K, a.N, a.ldb, a.b_plane, a.nslice, p.BN))
+    return cudaErrorInvalidValue;
+  const size_t smem = 1024 + (size_t)p.stages * stage_bytes + (2 * p.stages + 4) * 8;
+  cudaError_t e =
+      cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((a.M + kBlockM - 1) / kBlockM, ntiles);
+  k_tc_gemm<<<grid, kThreads, smem, st>>>(tmA, tmB, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_bf16_f64(int rows, int cols, const double *src, int lds,
+                                  __nv_bfloat16 *dst, int ldd, size_t plane, int nslice,
+                                  cudaStream_t st) {
+  const size_t n = (size_t)rows * cols;
+  const int grid = (int)std::min<size_t>((n + 255) / 256, 152 * 32);
+  k_split_bf16<<<grid > 0 ? grid : 1, 256, 0, st>>>(rows, cols, src, lds, dst, ldd, plane, nslice);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jac_init_bf16(int C, int d_y, int w, const double *WL, const float *der,
+                                 int ldd, __nv_bfloat16 *P, int ldp, size_t plane, int nslice,
+                                 cudaStream_t st) {
+  const size_t n = (size_t)C * d_y * w;
+  const int grid = (int)std::min<size_t>((n + 255) / 256, 152 * 32);
+  k_jac_init_bf16<<<grid > 0 ? grid : 1, 256, 0, st>>>(C, d_y, w, WL, der, ldd, P, ldp, plane,
+                                                       nslice);
+  return cudaGetLastError();
+}
+
+}  // namespace dino

@@ -1,0 +1,138 @@
+"""Parity of the tensor-core (tcgen05, BF16 slices) path with the FP64 oracle (GPU).
+
+Bars (stated for the BF16 path):
+  Jacobian       |J - J64|_F / |J64|_F <= 2e-2 per chain (1e-4 with the 2-slice default)
+  proposal mean  |mu - mu64|_2 / |mu64|_2 <= 1e-3 from the same state
+  accept         decisions identical under shared uniforms unless
+                 |log u - min(0, log rho64)| < 1e-3
+  forward        f with 3 slices: FP32-level, |f - f64| <= 1e-4 max(1, |f64|)
+                 (FP32 accumulation over K = 400 per layer: K u = 2.4e-5, three layers)
+The Cholesky factor, its log-determinant and log rho are computed in FP64
+from the BF16/FP32 Jacobian, so their error is the Jacobian's, propagated.
+"""
+import numpy as np
+import pytest
+
+from helpers import gpu_setup, oracle_setup, rel_err, variant
+from oracle import mmala
+from oracle.chains import OracleChains
+from workloads import BASIS_DIS, CONFIGS, SEED_CHAINS
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dino():
+    import paper_2403_08220_gb300 as d
+    return d
+
+
+@pytest.fixture(scope="module")
+def ctx(dino):
+    c = dino.dino_init(0)
+    yield c
+    c.close()
+
+
+def _jac_rel(J, J64):
+    return np.linalg.norm(J - J64, axis=(-2, -1)) / np.linalg.norm(J64, axis=(-2, -1))
+
+
+SMALL = variant(CONFIGS["small_fp64"], precision="bf16")
+
+
+@pytest.mark.parametrize("fs,js,jtol", [(1, 1, 2e-2), (3, 2, 1e-4), (3, 3, 1e-5)])
+def test_tensor_core_forward_and_jacobian_small(dino, ctx, fs, js, jtol):
+    """16-64-64-49 tanh network, 130 points (a ragged 128-row tile)."""
+    sid = gpu_setup(dino, ctx, SMALL, fwd_slices=fs, jac_slices=js)
+    sur, _, _ = oracle_setup(SMALL)
+    x = np.random.default_rng(5).standard_normal((130, SMALL.r))
+    g = dino.dino_surrogate_eval(ctx, sid, x, SMALL.d_y)
+    o = mmala.geometry(sur, x)
+    assert _jac_rel(g["J"], o.J).max() <= jtol
+    ftol = {1: 3e-2, 2: 1e-4, 3: 1e-4}[fs]
+    assert rel_err(g["f"], o.f) <= ftol
+    dino.dino_unload_surrogate(ctx, sid)
+
+
+def test_tensor_core_geometry_r200(dino, ctx):
+    """r = 200 DIS, GELU 200-400-400-100: default slices (3 forward, 2 Jacobian)."""
+    w = CONFIGS["r200_dis_bf16"]
+    sid = gpu_setup(dino, ctx, w)
+    sur, _, _ = oracle_setup(w)
+    x = np.random.default_rng(6).standard_normal((33, w.r))
+    g = dino.dino_surrogate_eval(ctx, sid, x, w.d_y)
+    o = mmala.geometry(sur, x)
+    assert _jac_rel(g["J"], o.J).max() <= 1e-4
+    assert rel_err(g["f"], o.f) <= 1e-4
+    # geometry in FP64 from the FP32 Jacobian: relative errors of the same order
+    assert np.max(np.abs(g["phi"] - o.phi) / np.abs(o.phi)) <= 1e-4
+    assert np.max(np.abs(g["hld"] - o.hld) / np.abs(o.hld)) <= 1e-4
+    dino.dino_unload_surrogate(ctx, sid)
+
+
+def _precision_run(dino, ctx, w, C, dt, steps, sample=None, fs=0, js=0):
+    sid = gpu_setup(dino, ctx, w, fwd_slices=fs, jac_slices=js)
+    sur, E, D = oracle_setup(w)
+    ids = np.arange(C) if sample is None else np.asarray(sample)
+    pool = dino.dino_chains_create(ctx, sid, C, dt, SEED_CHAINS)
+    och = OracleChains(sur, E, D, w.n_grid, w.prior_gamma, w.prior_delta, len(ids), dt,
+                       seed=SEED_CHAINS, chain_ids=ids)
+    st0 = dino.dino_chains_read(ctx, pool, C, w.r, w.N)
+    assert rel_err(st0["m_r"][ids], och.m_r) <= 1e-12          # FP64 encode at init
+    out = dict(mu=[], dec_bad=0, dec_near=0, n=0, log_rho=[])
+    active = np.ones(len(ids), dtype=bool)
+    for _ in range(steps):
+        dino.dino_chains_step(ctx, pool, 1, stats=False)
+        och.step()
+        last = dino.dino_chains_read_last(ctx, pool, C, w.r)
+        o = och.last
+        a = active
+        mu_g = last["mu"][ids][a]
+        out["mu"].append(np.max(np.linalg.norm(mu_g - o["mu"][a], axis=1) /
+                                np.linalg.norm(o["mu"][a], axis=1)))
+        lr64 = o["log_rho"][a]
+        near = np.abs(o["log_u"][a] - np.minimum(0.0, lr64)) < 1e-3
+        agree = last["accepted"][ids][a] == o["accepted"][a]
+        out["dec_bad"] += int(np.sum(~agree & ~near))
+        out["dec_near"] += int(np.sum(near))
+        out["n"] += int(a.sum())
+        fin = np.isfinite(lr64)
+        out["log_rho"].append(np.max(np.abs(last["log_rho"][ids][a][fin] - lr64[fin]), initial=0))
+        # only chains that took the same decision stay comparable from the same state
+        sub = np.where(a)[0]
+        active[sub[~agree]] = False
+    st = dino.dino_chains_read(ctx, pool, C, w.r, w.N)
+    out["field"] = float(np.max(np.abs(st["m"][ids][active] - och.m[active]), initial=0))
+    dino.dino_chains_destroy(ctx, pool)
+    dino.dino_unload_surrogate(ctx, sid)
+    return out
+
+
+@pytest.mark.parametrize("dt", [0.5, 2e-5])
+def test_bf16_chains_meet_precision_bars(dino, ctx, dt):
+    """r = 200 DIS workload, 130 chains: mean error, decisions, field (FP32)."""
+    w = CONFIGS["r200_dis_bf16"]
+    out = _precision_run(dino, ctx, w, 130, dt, 3)
+    assert max(out["mu"]) <= 1e-3
+    assert out["dec_bad"] == 0
+    assert out["field"] <= 1e-4
+
+
+def test_bf16_small_config_mixing(dino, ctx):
+    """The small workload on the tensor path with dt = 0.002 (about a third accepted)."""
+    out = _precision_run(dino, ctx, SMALL, 64, 0.002, 20)
+    assert max(out["mu"]) <= 1e-3
+    assert out["dec_bad"] == 0
+    assert out["field"] <= 1e-4
+
+
+def test_bf16_full_size_sampled(dino, ctx):
+    """16384 chains at r = 200 (the BF16 workload's launch shape); 8 chains checked."""
+    w = CONFIGS["r200_dis_bf16"]
+    C = w.n_chains
+    sample = [0, 1, 127, 128, 5000, 9999, 16000, C - 1]
+    out = _precision_run(dino, ctx, w, C, w.dt, 2, sample=sample)
+    assert max(out["mu"]) <= 1e-3
+    assert out["dec_bad"] == 0
+    assert out["field"] <= 1e-4
