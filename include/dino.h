@@ -223,6 +223,44 @@ uint64_t dino_launch_count(const dino_ctx *ctx);
 int dino_kernel_times(dino_ctx *ctx, char *names, double *total_ms, uint64_t *launches,
                       int cap, int *n, int reset);
 
+/* ---- allocation-free evaluation ---------------------------------------- */
+
+/* The paper has no counterpart to this entry point; it serves callers of the
+ * library rather than the method.
+ *
+ * Surrogate forward pass f(x) and reduced Jacobian J = df/dx (reverse mode,
+ * FP64) at n reduced points, computed without allocating any device memory.
+ * It is meant for host code that must not call cudaMalloc: for example a
+ * plugin inside a framework that owns every device byte through its own
+ * pool, or a latency-critical loop in which the synchronisation that
+ * cudaMalloc/cudaFree can imply is not acceptable.  The intermediate
+ * d_y x width products live in a fixed device array of
+ * DINO_NOALLOC_SCRATCH_DOUBLES doubles (8 MiB) that every GPU loading the
+ * library keeps until the process exits.
+ *
+ * widths: host array of n_layers + 1 entries (widths[0] = r, widths[n_layers]
+ *   = d_y), 1 <= n_layers <= 16; activation as in dino_surrogate_desc.
+ * W, b: host arrays of n_layers DEVICE pointers; W[l] is widths[l+1] x
+ *   widths[l] row-major, b[l] has widths[l+1] entries.
+ * x: device, n x r; f: device, n x d_y; J: device, n x d_y x r (row-major).
+ *   All buffers belong to the caller; results are written before the kernel
+ *   ends on `stream` (a cudaStream_t, or NULL for the legacy default stream).
+ * Limit: n * 2 * d_y * (largest hidden width) must not exceed
+ *   DINO_NOALLOC_SCRATCH_DOUBLES, and the activations must fit in 200 KB of
+ *   shared memory; larger requests are rejected with DINO_ENOMEM (scratch)
+ *   or DINO_EINVAL (shared memory, NULL pointers, bad sizes) and nothing runs.
+ * The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current, so make that first call
+ *   before any stream capture on the device.
+ * Every call shares the one array: calls whose kernels can overlap on the GPU
+ *   (unordered streams) race on it, so order them on one stream.
+ * Returns DINO_OK once the kernel is queued, DINO_ECUDA if the launch fails. */
+#define DINO_NOALLOC_SCRATCH_DOUBLES (1u << 20)
+
+int dino_surrogate_jacobian_noalloc(int n, int n_layers, const int *widths, int activation,
+                                    const double *const *W, const double *const *b,
+                                    const double *x, double *f, double *J, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

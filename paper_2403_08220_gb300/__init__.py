@@ -87,6 +87,8 @@ _SIGNATURES = {
     "dino_launch_count": ([_P], ct.c_uint64),
     "dino_kernel_times": ([_P, ct.c_char_p, _D, ct.POINTER(ct.c_uint64), _I, ct.POINTER(_I), _I],
                           _I),
+    "dino_surrogate_jacobian_noalloc": ([_I, _I, ct.POINTER(_I), _I, ct.POINTER(_P),
+                                         ct.POINTER(_P), _P, _P, _P, _P], _I),
 }
 
 
@@ -281,3 +283,24 @@ def dino_kernel_times(ctx: Ctx, reset: bool = False) -> dict:
         nm = raw[48 * k:48 * (k + 1)].split(b"\0", 1)[0].decode()
         out[nm] = (float(ms[k]), int(cnt[k]))
     return out
+
+
+def dino_surrogate_jacobian_noalloc(n: int, widths, activation: int, W_ptrs, b_ptrs, x_ptr: int,
+                                    f_ptr: int, J_ptr: int, stream: int = 0) -> None:
+    """f and J at n points from caller-owned device buffers, with no device allocation.
+
+    W_ptrs / b_ptrs are device addresses (ints) of the layer weights and biases;
+    x_ptr, f_ptr, J_ptr device addresses of the n x r inputs and the n x d_y and
+    n x d_y x r outputs (float64, row-major).  The library's fixed scratch array
+    is shared by all calls, so calls that may overlap on the GPU must be ordered
+    on one stream.
+    """
+    L = len(W_ptrs)
+    wid = (ct.c_int * (L + 1))(*[int(x) for x in widths])
+    Wp = (_P * L)(*[int(p) for p in W_ptrs])
+    bp = (_P * L)(*[int(p) for p in b_ptrs])
+    code = lib().dino_surrogate_jacobian_noalloc(n, L, wid, activation, Wp, bp, _P(x_ptr),
+                                                  _P(f_ptr), _P(J_ptr),
+                                                  _P(stream) if stream else None)
+    if code != DINO_OK:
+        raise DinoError(code, "dino_surrogate_jacobian_noalloc rejected the request")
