@@ -17,6 +17,10 @@ constexpr int kMaxRSmem = 208;
 constexpr uint32_t STREAM_XI_ID = 0, STREAM_U_ID = 1, STREAM_Z_ID = 2, STREAM_INIT_ID = 3;
 
 inline __host__ __device__ size_t tri_size(int r) { return (size_t)r * (r + 1) / 2; }
+// Per-chain stride of the packed factor in global memory: rounded up to an
+// even number of doubles so that every chain's factor starts on 16 bytes
+// (the alignment bulk copies need).
+inline __host__ __device__ size_t l_stride(int r) { return (tri_size(r) + 1) & ~(size_t)1; }
 
 // ---- per-chain reduced-space kernels (FP64) -----------------------------
 struct ReducedArgs {
@@ -39,6 +43,7 @@ struct ReducedArgs {
   unsigned long long *acc_count = nullptr;
   unsigned long long *counters = nullptr;  // [0] accepts, [1] nan rejects
   double *sum_alpha = nullptr;
+  int *err = nullptr;  // set (bit 4) when a bounded device wait gives up
   // tensor-core path: the proposal as bf16 slice planes (row pitch b_ld,
   // plane pitch b_plane elements); nullptr when unused
   __nv_bfloat16 *b_bf16 = nullptr;

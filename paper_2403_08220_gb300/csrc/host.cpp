@@ -768,6 +768,7 @@ struct Pool {
   int *acc;
   unsigned long long *acc_count, *counters;
   double *sum_alpha;
+  int *err;  // raised by a kernel whose bounded wait gave up
   // field scratch
   void *Mf, *coef2;
   Work w;
@@ -787,7 +788,7 @@ static void layout_pool(Pool &p, bool assign) {
   p.g = (double *)take((size_t)C * r * 8);
   p.phi = (double *)take((size_t)C * 8);
   p.hld = (double *)take((size_t)C * 8);
-  p.L = (double *)take((size_t)C * tri_size(r) * 8);
+  p.L = (double *)take((size_t)C * l_stride(r) * 8);
   p.m = take((size_t)C * N * fe);
   p.b = (double *)take((size_t)C * r * 8);
   p.mu = (double *)take((size_t)C * r * 8);
@@ -799,6 +800,7 @@ static void layout_pool(Pool &p, bool assign) {
   p.acc_count = (unsigned long long *)take((size_t)C * 8);
   p.counters = (unsigned long long *)take(2 * 8);
   p.sum_alpha = (double *)take(8);
+  p.err = (int *)take(16);
   // FP64 at init even on the FP32 path; also holds a zero data vector in surrogate_eval
   p.Mf = take(std::max((size_t)C * N, (size_t)s->d_y) * std::max(fe, (size_t)8));
   p.coef2 = take((size_t)C * r * fe);
@@ -839,6 +841,7 @@ static ReducedArgs reduced_args(const Pool &p) {
   a.acc_count = p.acc_count;
   a.counters = p.counters;
   a.sum_alpha = p.sum_alpha;
+  a.err = p.err;
   if (s->precision == DINO_PREC_FP64) {
     a.J = p.w.J64;
     a.f = p.w.f64;
@@ -887,6 +890,7 @@ static int create_pool(dino_ctx *ctx, int sid, int C, double dt, uint64_t seed,
     CK(cudaMemsetAsync(p->acc_count, 0, (size_t)C * 8, st));
     CK(cudaMemsetAsync(p->counters, 0, 16, st));
     CK(cudaMemsetAsync(p->sum_alpha, 0, 8, st));
+    CK(cudaMemsetAsync(p->err, 0, 16, st));
     CK(cudaMemsetAsync(p->acc, 0, (size_t)C * 4, st));
     double *m64 = (double *)p->Mf;  // FP64 initial field
     if (m0) {
@@ -991,6 +995,7 @@ static void surrogate_eval(dino_ctx *ctx, int sid, int n, const double *x_host, 
   try {
     layout_pool(p, true);
     cudaStream_t st = ctx->stream;
+    CK(cudaMemsetAsync(p.err, 0, 16, st));
     if (!s->has_data) {
       // geometry needs some data vector: evaluate against zeros (phi and g then meaningless)
       yzero.assign(dy, 0.0);
@@ -1022,7 +1027,7 @@ static void surrogate_eval(dino_ctx *ctx, int sid, int n, const double *x_host, 
     fetch(p.g, (size_t)n * r, false, g);
     fetch(p.hld, n, false, hld);
     if (Lfull) {
-      const size_t ts = tri_size(r);
+      const size_t ts = l_stride(r);
       std::vector<double> packed((size_t)n * ts);
       CK(cudaMemcpy(packed.data(), p.L, packed.size() * 8, cudaMemcpyDeviceToHost));
       for (int c = 0; c < n; ++c)
@@ -1208,9 +1213,12 @@ int dino_chains_step(dino_ctx *ctx, int pool_id, int n_steps, dino_step_stats *s
     if (stats) {
       unsigned long long c1[2];
       double a1 = 0;
+      int err = 0;
       CK(cudaMemcpyAsync(c1, p->counters, 16, cudaMemcpyDeviceToHost, ctx->stream));
       CK(cudaMemcpyAsync(&a1, p->sum_alpha, 8, cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaMemcpyAsync(&err, p->err, 4, cudaMemcpyDeviceToHost, ctx->stream));
       CK(cudaStreamSynchronize(ctx->stream));
+      if (err) fail(DINO_ETIMEOUT, "a device wait gave up (code %d); the pool state is invalid", err);
       stats->proposals = (uint64_t)p->C * (uint64_t)n_steps;
       stats->accepts = c1[0] - c0[0];
       stats->nan_rejects = c1[1] - c0[1];
@@ -1226,7 +1234,10 @@ int dino_chains_read(dino_ctx *ctx, int pool_id, double *m, double *m_r, double 
     cudaSetDevice(ctx->device);
     Pool *p = get_pool(ctx, pool_id);
     const int C = p->C, r = p->s->r, N = p->s->N;
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, p->err, 4, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    if (err) fail(DINO_ETIMEOUT, "a device wait gave up (code %d); the pool state is invalid", err);
     if (m) {
       if (p->s->precision == DINO_PREC_FP64) {
         CK(cudaMemcpy(m, p->m, (size_t)C * N * 8, cudaMemcpyDeviceToHost));

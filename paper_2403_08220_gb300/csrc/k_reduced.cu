@@ -16,17 +16,32 @@
 // Identities used with L L^T = I + H (exact in real arithmetic):
 //   (I+H)^-1 w_a = a - v_a     for w_a = H a - g_a, v_a = (I+H)^-1 (a + g_a),
 //   H x = L (L^T x) - x,       x^T H x = |L^T x|^2 - |x|^2.
+//
+// The FP64 pipe bounds both kernels (1/64 of the FP32 rate on GB300), so the
+// Cholesky is blocked (8-column panels, 3 barriers per panel) to keep the
+// FP64 units fed from shared memory, and on the tensor-core path the product
+// J^T J is formed from the FP32 Jacobian in FP32 register tiles, off the FP64
+// pipe.  Factors move from HBM into shared memory by TMA bulk copies.
 #include "dino_internal.h"
 #include "philox.cuh"
 
 namespace dino {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kJChunk = 16;  // rows of J staged per pass when forming H
+constexpr int kJChunk = 16;    // rows of an FP64 J staged per pass when forming H
+constexpr int kJChunkF = 32;   // rows of an FP32 J staged per pass
+constexpr int kNB = 8;         // Cholesky panel width
+constexpr int kHT = 4;         // FP32 register tile edge for J^T J
+constexpr int kHMaxTiles = 3;  // tiles per thread: ceil(52*53/2 / 512) for r <= 208
+constexpr uint32_t kSpinLimit = 1u << 24;
 
 __device__ __forceinline__ int tri(int i) { return i * (i + 1) / 2; }
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
 
 // Sum over the CTA; `red` holds >= 33 doubles.  Every thread gets the sum.
 __device__ double block_sum(double v, double *red) {
@@ -44,6 +59,60 @@ __device__ double block_sum(double v, double *red) {
   }
   __syncthreads();
   return red[32];
+}
+
+__device__ __forceinline__ bool mbar_try0(uint32_t bar) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(bar)
+      : "memory");
+  return done != 0;
+}
+
+__device__ bool mbar_wait0_bounded(uint32_t bar) {
+  for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    if (mbar_try0(bar)) return true;
+    if (it > 32) __nanosleep(64);
+  }
+  return false;
+}
+
+// TMA bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned)
+// from global to shared memory.  Thread 0 issues and waits with a bounded
+// spin; the verdict is shared through `flag`.  On timeout it raises bit 4 of
+// `err`, waits once more (bounded) for the copies in flight, and every thread
+// gets false.
+__device__ bool cta_bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *mbar,
+                              int *flag, int *err) {
+  if (threadIdx.x == 0) {
+    const uint32_t bar = smem_u32(mbar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+    const char *s = static_cast<const char *>(src);
+    const uint32_t d = smem_u32(dst);
+    for (uint32_t off = 0; off < bytes; off += 65536u) {
+      const uint32_t n = bytes - off < 65536u ? bytes - off : 65536u;
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+          "[%3];" ::"r"(d + off),
+          "l"(s + off), "r"(n), "r"(bar)
+          : "memory");
+    }
+    const bool ok = mbar_wait0_bounded(bar);
+    if (!ok) {
+      atomicOr(err, 4);
+      mbar_wait0_bounded(bar);
+    }
+    *flag = ok ? 1 : 0;
+  }
+  __syncthreads();
+  return *flag != 0;
 }
 
 // x <- L^-1 x.  32-row diagonal blocks are solved by warp 0 with shuffles,
@@ -129,28 +198,86 @@ __device__ __forceinline__ void tri_pos(int e, int &ii, int &jj) {
   jj = e - tri(ii);
 }
 
-// In-place right-looking Cholesky of the packed matrix; inv[k] = 1 / L_kk.
-// A non-positive pivot produces NaN, which the caller turns into a reject.
+// In-place right-looking Cholesky of the packed matrix in 8-column panels:
+// (a) warp 0 factors the 8 x 8 diagonal block, (b) every row below it is
+// solved against that block, (c) the trailing triangle takes the rank-8
+// update.  Per element this is the same sequence of fused multiply-adds as
+// the column-at-a-time algorithm.  inv[k] = 1 / L_kk.  A non-positive pivot
+// produces NaN, which the caller turns into a reject.
 __device__ void cta_cholesky(double *Ls, double *inv, int r) {
-  const int T = blockDim.x;
-  for (int k = 0; k < r; ++k) {
-    const double dkk = sqrt(Ls[tri(k) + k]);
-    const double ik = 1.0 / dkk;
-    for (int i = k + 1 + threadIdx.x; i < r; i += T) Ls[tri(i) + k] *= ik;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      Ls[tri(k) + k] = dkk;
-      inv[k] = ik;
+  const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int kb = 0; kb < r; kb += kNB) {
+    const int nb = min(kNB, r - kb);
+    if (warp == 0) {
+      for (int q = 0; q < nb; ++q) {
+        const int kq = kb + q;
+        // pivot and its inverse from y = x^(-1/2): an FP32 estimate refined by
+        // two Newton-Raphson steps on 1/y^2 - x = 0, y <- y (3 - x y^2) / 2,
+        // so the serial diagonal work stays short on the FP64 pipe
+        const double xkk = Ls[tri(kq) + kq];
+        double id = (double)rsqrtf((float)xkk);
+        id = id * (1.5 - 0.5 * xkk * id * id);
+        id = id * (1.5 - 0.5 * xkk * id * id);
+        const double d = xkk * id;
+        __syncwarp();
+        if (lane == 0) {
+          Ls[tri(kq) + kq] = d;
+          inv[kq] = id;
+        }
+        if (lane > q && lane < nb) Ls[tri(kb + lane) + kq] *= id;
+        __syncwarp();
+        for (int e = lane; e < nb * nb; e += 32) {
+          const int i = e / nb, j = e % nb;
+          if (j > q && j <= i)
+            Ls[tri(kb + i) + kb + j] -= Ls[tri(kb + i) + kq] * Ls[tri(kb + j) + kq];
+        }
+        __syncwarp();
+      }
     }
-    const int n = r - k - 1;
+    __syncthreads();
+    for (int i = kb + nb + tid; i < r; i += T) {
+      double *row = Ls + tri(i) + kb;
+      double x[kNB];
+#pragma unroll
+      for (int q = 0; q < kNB; ++q) {
+        if (q < nb) {
+          double acc = row[q];
+          const double *lq = Ls + tri(kb + q) + kb;
+#pragma unroll
+          for (int p = 0; p < q; ++p) acc -= x[p] * lq[p];
+          x[q] = acc * inv[kb + q];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kNB; ++q)
+        if (q < nb) row[q] = x[q];
+    }
+    __syncthreads();
+    const int n = r - kb - nb;
     const int ntri = n * (n + 1) / 2;
-    if ((int)threadIdx.x < ntri) {
+    if (tid < ntri) {
       int ii, jj;
-      tri_pos(threadIdx.x, ii, jj);
-      for (int e = threadIdx.x; e < ntri; e += T) {
-        const int i = k + 1 + ii, j = k + 1 + jj;
-        const int ti = tri(i);
-        Ls[ti + j] -= Ls[ti + k] * Ls[tri(j) + k];
+      tri_pos(tid, ii, jj);
+      const int base = kb + nb;
+      for (int e = tid; e < ntri; e += T) {
+        const int i = base + ii, j = base + jj;
+        const double *li = Ls + tri(i) + kb;
+        const double *lj = Ls + tri(j) + kb;
+        double *aij = Ls + tri(i) + j;
+        double acc = *aij;
+        if (nb == kNB) {
+          double pa[kNB], pb[kNB];
+#pragma unroll
+          for (int q = 0; q < kNB; ++q) {
+            pa[q] = li[q];
+            pb[q] = lj[q];
+          }
+#pragma unroll
+          for (int q = 0; q < kNB; ++q) acc -= pa[q] * pb[q];
+        } else {
+          for (int q = 0; q < nb; ++q) acc -= li[q] * lj[q];
+        }
+        *aij = acc;
         jj += T;
         while (jj > ii) {
           jj -= ii + 1;
@@ -200,20 +327,40 @@ __device__ __forceinline__ void split_bf16_store(double x, __nv_bfloat16 *dst, s
   }
 }
 
+// Shared-memory layout in doubles:
+//   Ls[ldL] inv[r] six work vectors[r] res[dy] red[34] mbar[1] flag[1] | J chunk
+struct Layout {
+  size_t Ls, inv, v0, res, red, mbar, flag, tail;
+  __host__ __device__ Layout(int r, int dy, size_t ldL) {
+    Ls = 0;
+    inv = ldL;
+    v0 = inv + r;
+    res = v0 + 6 * (size_t)r;
+    red = res + dy;
+    mbar = (red + 34 + 1) & ~(size_t)1;  // 8-byte mbarrier, kept 16-byte aligned
+    flag = mbar + 1;
+    tail = (flag + 1 + 1) & ~(size_t)1;  // 16-byte aligned start of the J chunk
+  }
+};
+
 __global__ void __launch_bounds__(kThreads) k_propose(ReducedArgs a) {
-  extern __shared__ double sm[];
+  extern __shared__ __align__(16) double sm[];
   const int c = blockIdx.x, r = a.r;
-  const size_t lsz = tri_size(r);
-  double *Ls = sm;
-  double *inv = Ls + lsz;
-  double *va = inv + r, *vg = va + r, *vv = vg + r, *vx = vv + r, *vp = vx + r, *vq = vp + r;
-  double *red = vq + r;
-  const double *Lg = a.L + (size_t)c * lsz;
-  for (size_t e = threadIdx.x; e < lsz; e += blockDim.x) Ls[e] = Lg[e];
+  const size_t ldL = l_stride(r);
+  const Layout lay(r, 0, ldL);
+  double *Ls = sm + lay.Ls;
+  double *inv = sm + lay.inv;
+  double *va = sm + lay.v0, *vg = va + r, *vv = vg + r, *vx = vv + r, *vp = vx + r, *vq = vp + r;
+  double *red = sm + lay.red;
+  if (!cta_bulk_load(Ls, a.L + (size_t)c * ldL, (uint32_t)(ldL * 8),
+                     reinterpret_cast<uint64_t *>(sm + lay.mbar),
+                     reinterpret_cast<int *>(sm + lay.flag), a.err))
+    return;
   for (int i = threadIdx.x; i < r; i += blockDim.x) {
     va[i] = a.mr[(size_t)c * r + i];
     vg[i] = a.g[(size_t)c * r + i];
     vv[i] = va[i] + vg[i];
+    inv[i] = 1.0 / Ls[tri(i) + i];
   }
   const uint32_t chain = (uint32_t)(a.id_base + (uint64_t)c);
   for (int blk = threadIdx.x; blk < (r + 3) / 4; blk += blockDim.x) {
@@ -222,8 +369,6 @@ __global__ void __launch_bounds__(kThreads) k_propose(ReducedArgs a) {
     for (int q = 0; q < 4; ++q)
       if (4 * blk + q < r) vx[4 * blk + q] = n4[q];
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < r; i += blockDim.x) inv[i] = 1.0 / Ls[tri(i) + i];
   __syncthreads();
   cta_lower_solve(Ls, inv, r, vv);
   cta_upper_solve(Ls, inv, r, vv);  // vv = (I+H)^-1 (a + g)
@@ -243,17 +388,114 @@ __global__ void __launch_bounds__(kThreads) k_propose(ReducedArgs a) {
   if (threadIdx.x == 0) a.lq_fwd[c] = lq;
 }
 
+// I + J^T J / noise_var into the packed shared matrix, from an FP64 J:
+// chunks of kJChunk rows, FP64 products accumulated in shared memory.
+__device__ void form_h_f64(const double *J, int dy, int r, double inv_nv, double *Ls,
+                           double *Jc) {
+  const int lsz = tri(r);
+  for (int i0 = 0; i0 < dy; i0 += kJChunk) {
+    const int nr = min(kJChunk, dy - i0);
+    for (int e = threadIdx.x; e < nr * r; e += blockDim.x) Jc[e] = J[(size_t)i0 * r + e];
+    __syncthreads();
+    if ((int)threadIdx.x < lsz) {
+      int ii, jj;
+      tri_pos(threadIdx.x, ii, jj);
+      for (int e = threadIdx.x; e < lsz; e += blockDim.x) {
+        double acc = 0.0;
+        for (int k = 0; k < nr; ++k) acc += Jc[k * r + ii] * Jc[k * r + jj];
+        const double h = acc * inv_nv;
+        Ls[e] = (i0 == 0 ? (ii == jj ? 1.0 : 0.0) : Ls[e]) + h;
+        jj += blockDim.x;
+        while (jj > ii) {
+          jj -= ii + 1;
+          ++ii;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// The same from an FP32 J: each thread accumulates up to kHMaxTiles 4 x 4
+// tiles of J^T J in FP32 registers over all d_y rows (chunks of kJChunkF
+// rows staged in shared memory, padded to a multiple of 4 columns), then
+// writes I + H once in FP64.
+__device__ void form_h_f32(const float *J, int dy, int r, double inv_nv, double *Ls,
+                           float *Jc) {
+  const int nt = (r + kHT - 1) / kHT, rp = nt * kHT;
+  const int ntiles = nt * (nt + 1) / 2;
+  int ti[kHMaxTiles], tj[kHMaxTiles];
+  float acc[kHMaxTiles][kHT][kHT];
+#pragma unroll
+  for (int s = 0; s < kHMaxTiles; ++s) {
+    const int t = threadIdx.x + s * blockDim.x;
+    if (t < ntiles) {
+      tri_pos(t, ti[s], tj[s]);
+    } else {
+      ti[s] = -1;
+      tj[s] = 0;
+    }
+#pragma unroll
+    for (int p = 0; p < kHT; ++p)
+#pragma unroll
+      for (int q = 0; q < kHT; ++q) acc[s][p][q] = 0.0f;
+  }
+  for (int i0 = 0; i0 < dy; i0 += kJChunkF) {
+    const int nr = min(kJChunkF, dy - i0);
+    for (int e = threadIdx.x; e < nr * rp; e += blockDim.x) {
+      const int k = e / rp, j = e % rp;
+      Jc[e] = j < r ? J[(size_t)(i0 + k) * r + j] : 0.0f;
+    }
+    __syncthreads();
+    for (int k = 0; k < nr; ++k) {
+      const float *row = Jc + k * rp;
+#pragma unroll
+      for (int s = 0; s < kHMaxTiles; ++s) {
+        if (ti[s] < 0) continue;
+        const float4 x = *reinterpret_cast<const float4 *>(row + kHT * ti[s]);
+        const float4 y = *reinterpret_cast<const float4 *>(row + kHT * tj[s]);
+        const float xa[4] = {x.x, x.y, x.z, x.w}, ya[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+        for (int p = 0; p < kHT; ++p)
+#pragma unroll
+          for (int q = 0; q < kHT; ++q) acc[s][p][q] = fmaf(xa[p], ya[q], acc[s][p][q]);
+      }
+    }
+    __syncthreads();
+  }
+  if (dy == 0) {
+    for (int e = threadIdx.x; e < tri(r); e += blockDim.x) Ls[e] = 0.0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < r; i += blockDim.x) Ls[tri(i) + i] = 1.0;
+    __syncthreads();
+    return;
+  }
+#pragma unroll
+  for (int s = 0; s < kHMaxTiles; ++s) {
+    if (ti[s] < 0) continue;
+#pragma unroll
+    for (int p = 0; p < kHT; ++p)
+#pragma unroll
+      for (int q = 0; q < kHT; ++q) {
+        const int i = kHT * ti[s] + p, j = kHT * tj[s] + q;
+        if (i < r && j <= i)
+          Ls[tri(i) + j] = (i == j ? 1.0 : 0.0) + (double)acc[s][p][q] * inv_nv;
+      }
+  }
+  __syncthreads();
+}
+
 template <typename TJ>
 __global__ void __launch_bounds__(kThreads) k_geometry(ReducedArgs a, int mode) {
-  extern __shared__ double sm[];
+  extern __shared__ __align__(16) double sm[];
   const int c = blockIdx.x, r = a.r, dy = a.d_y;
-  const size_t lsz = tri_size(r);
-  double *Ls = sm;
-  double *inv = Ls + lsz;
-  double *vb = inv + r, *vg = vb + r, *va = vg + r, *vv = va + r, *vp = vv + r, *vq = vp + r;
-  double *res = vq + r;
-  double *red = res + dy;
-  TJ *Jc = reinterpret_cast<TJ *>(red + 34);
+  const size_t ldL = l_stride(r);
+  const Layout lay(r, dy, ldL);
+  double *Ls = sm + lay.Ls;
+  double *inv = sm + lay.inv;
+  double *vb = sm + lay.v0, *vg = vb + r, *va = vg + r, *vv = va + r, *vp = vv + r, *vq = vp + r;
+  double *res = sm + lay.res;
+  double *red = sm + lay.red;
   const TJ *J = reinterpret_cast<const TJ *>(a.J) + (size_t)c * dy * r;
   const TJ *f = reinterpret_cast<const TJ *>(a.f) + (size_t)c * dy;
   const double inv_nv = 1.0 / a.noise_var;
@@ -266,51 +508,33 @@ __global__ void __launch_bounds__(kThreads) k_geometry(ReducedArgs a, int mode) 
     res[i] = rs;
     ph += rs * rs;
   }
-  const double phi_b = 0.5 * block_sum(ph, red) * inv_nv;  // includes a sync
+  const double phi_b = 0.5 * block_sum(ph, red) * inv_nv;  // includes a barrier
   for (int j = threadIdx.x; j < r; j += blockDim.x) {
     double acc = 0.0;
     for (int i = 0; i < dy; ++i) acc += (double)J[(size_t)i * r + j] * res[i];
     vg[j] = acc * inv_nv;  // g = J^T (f - y) / noise_var
   }
-  // I + J^T J / noise_var, accumulated over chunks of kJChunk rows of J
-  for (int i0 = 0; i0 < dy; i0 += kJChunk) {
-    const int nr = min(kJChunk, dy - i0);
-    for (int e = threadIdx.x; e < nr * r; e += blockDim.x) Jc[e] = J[(size_t)i0 * r + e];
-    __syncthreads();
-    if ((int)threadIdx.x < (int)lsz) {
-      int ii, jj;
-      tri_pos(threadIdx.x, ii, jj);
-      for (int e = threadIdx.x; e < (int)lsz; e += blockDim.x) {
-        TJ acc = 0;
-        for (int k = 0; k < nr; ++k) acc += Jc[k * r + ii] * Jc[k * r + jj];
-        const double h = (double)acc * inv_nv;
-        if (i0 == 0)
-          Ls[e] = (ii == jj ? 1.0 : 0.0) + h;
-        else
-          Ls[e] += h;
-        jj += blockDim.x;
-        while (jj > ii) {
-          jj -= ii + 1;
-          ++ii;
-        }
-      }
+  if constexpr (sizeof(TJ) == 4) {
+    form_h_f32(reinterpret_cast<const float *>(J), dy, r, inv_nv, Ls,
+               reinterpret_cast<float *>(sm + lay.tail));
+  } else {
+    form_h_f64(reinterpret_cast<const double *>(J), dy, r, inv_nv, Ls, sm + lay.tail);
+    if (dy == 0) {
+      for (int e = threadIdx.x; e < tri(r); e += blockDim.x) Ls[e] = 0.0;
+      __syncthreads();
+      for (int i = threadIdx.x; i < r; i += blockDim.x) Ls[tri(i) + i] = 1.0;
+      __syncthreads();
     }
-    __syncthreads();
-  }
-  if (dy == 0) {
-    for (size_t e = threadIdx.x; e < lsz; e += blockDim.x) Ls[e] = 0.0;
-    __syncthreads();
-    for (int i = threadIdx.x; i < r; i += blockDim.x) Ls[tri(i) + i] = 1.0;
-    __syncthreads();
   }
   cta_cholesky(Ls, inv, r);
   double ld = 0.0;
   for (int i = threadIdx.x; i < r; i += blockDim.x) ld += log(Ls[tri(i) + i]);
   const double hld_b = block_sum(ld, red);
 
-  double *Lg = a.L + (size_t)c * lsz;
+  double *Lg = a.L + (size_t)c * ldL;
+  const int lsz = tri(r);
   if (mode == 0) {
-    for (size_t e = threadIdx.x; e < lsz; e += blockDim.x) Lg[e] = Ls[e];
+    for (int e = threadIdx.x; e < lsz; e += blockDim.x) Lg[e] = Ls[e];
     for (int i = threadIdx.x; i < r; i += blockDim.x) {
       a.g[(size_t)c * r + i] = vg[i];
       a.mr[(size_t)c * r + i] = vb[i];
@@ -352,7 +576,7 @@ __global__ void __launch_bounds__(kThreads) k_geometry(ReducedArgs a, int mode) 
     atomicAdd(a.sum_alpha, finite ? exp(fmin(0.0, lr)) : 0.0);
   }
   if (accept) {
-    for (size_t e = threadIdx.x; e < lsz; e += blockDim.x) Lg[e] = Ls[e];
+    for (int e = threadIdx.x; e < lsz; e += blockDim.x) Lg[e] = Ls[e];
     for (int i = threadIdx.x; i < r; i += blockDim.x) {
       a.g[(size_t)c * r + i] = vg[i];
       a.mr[(size_t)c * r + i] = vb[i];
@@ -362,11 +586,16 @@ __global__ void __launch_bounds__(kThreads) k_geometry(ReducedArgs a, int mode) 
 
 }  // namespace
 
-size_t propose_smem_bytes(int r) { return (tri_size(r) + 7 * (size_t)r + 40) * sizeof(double); }
+size_t propose_smem_bytes(int r) {
+  const Layout lay(r, 0, l_stride(r));
+  return lay.tail * sizeof(double);
+}
 
 size_t geometry_smem_bytes(int r, int d_y, int jf_f32) {
-  return (tri_size(r) + 7 * (size_t)r + d_y + 34) * sizeof(double) +
-         (size_t)kJChunk * r * (jf_f32 ? sizeof(float) : sizeof(double)) + 16;
+  const Layout lay(r, d_y, l_stride(r));
+  const size_t jc = jf_f32 ? (size_t)kJChunkF * ((r + kHT - 1) / kHT * kHT) * sizeof(float)
+                           : (size_t)kJChunk * r * sizeof(double);
+  return lay.tail * sizeof(double) + jc;
 }
 
 cudaError_t launch_propose(const ReducedArgs &a, cudaStream_t st) {

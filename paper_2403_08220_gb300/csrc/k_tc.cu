@@ -272,22 +272,68 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int ncols = min(16, nvalid - c0);
         const int col0 = n0 + c0;
         if (p.epi == TC_EPI_STORE_F32 || p.epi == TC_EPI_BIAS_F32) {
+          if (p.epi == TC_EPI_BIAS_F32)
+            for (int j = 0; j < ncols; ++j) v[j] += p.bias[col0 + j];
           float *o = p.outf + (size_t)row * p.ldo + col0;
-          for (int j = 0; j < ncols; ++j)
-            o[j] = v[j] + (p.epi == TC_EPI_BIAS_F32 ? p.bias[col0 + j] : 0.0f);
-        } else if (p.epi == TC_EPI_BIAS_ACT) {
-          __nv_bfloat16 *o = p.out_bf + (size_t)row * p.ldo + col0;
-          float *d = p.der + (size_t)row * p.N + col0;
-          for (int j = 0; j < ncols; ++j) {
-            const float z = v[j] + p.bias[col0 + j];
-            store_slices(act_fn(p.act, z), o + j, p.out_plane, p.out_slices);
-            d[j] = act_deriv(p.act, z);
+          if (ncols == 16 && (p.ldo & 3) == 0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              reinterpret_cast<float4 *>(o)[q] =
+                  make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+          } else {
+            for (int j = 0; j < ncols; ++j) o[j] = v[j];
           }
         } else {
+          float x[16];
+          if (p.epi == TC_EPI_BIAS_ACT) {
+            float *d = p.der + (size_t)row * p.N + col0;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const float z = v[j] + (j < ncols ? p.bias[col0 + j] : 0.0f);
+              x[j] = act_fn(p.act, z);
+              v[j] = act_deriv(p.act, z);
+            }
+            if (ncols == 16 && (p.N & 3) == 0) {
+#pragma unroll
+              for (int q = 0; q < 4; ++q)
+                reinterpret_cast<float4 *>(d)[q] =
+                    make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            } else {
+              for (int j = 0; j < ncols; ++j) d[j] = v[j];
+            }
+          } else {
+            const float *sc = p.scale + (size_t)(row / p.group) * p.lds + col0;
+            if (ncols == 16 && (p.lds & 3) == 0) {
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const float4 t = reinterpret_cast<const float4 *>(sc)[q];
+                x[4 * q] = v[4 * q] * t.x;
+                x[4 * q + 1] = v[4 * q + 1] * t.y;
+                x[4 * q + 2] = v[4 * q + 2] * t.z;
+                x[4 * q + 3] = v[4 * q + 3] * t.w;
+              }
+            } else {
+              for (int j = 0; j < 16; ++j) x[j] = j < ncols ? v[j] * sc[j] : 0.0f;
+            }
+          }
+          // x ~= sum of bf16 slices; 16-byte stores of 8 values per slice
           __nv_bfloat16 *o = p.out_bf + (size_t)row * p.ldo + col0;
-          const float *sc = p.scale + (size_t)(row / p.group) * p.lds + col0;
-          for (int j = 0; j < ncols; ++j)
-            store_slices(v[j] * sc[j], o + j, p.out_plane, p.out_slices);
+          const bool vec = ncols == 16 && (p.ldo & 7) == 0;
+          for (int sl = 0; sl < p.out_slices; ++sl) {
+            __nv_bfloat16 h[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              h[j] = __float2bfloat16_rn(x[j]);
+              x[j] -= __bfloat162float(h[j]);
+            }
+            __nv_bfloat16 *os = o + sl * p.out_plane;
+            if (vec) {
+              reinterpret_cast<uint4 *>(os)[0] = *reinterpret_cast<const uint4 *>(h);
+              reinterpret_cast<uint4 *>(os)[1] = *reinterpret_cast<const uint4 *>(h + 8);
+            } else {
+              for (int j = 0; j < ncols; ++j) os[j] = h[j];
+            }
+          }
         }
       }
     }
@@ -317,15 +363,35 @@ __global__ void k_jac_init_bf16(int C, int d_y, int w, const double *__restrict_
                                 const float *__restrict__ der, int ldd,
                                 __nv_bfloat16 *__restrict__ P, int ldp, size_t plane,
                                 int nslice) {
-  const size_t total = (size_t)C * d_y * w;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-       e += (size_t)gridDim.x * blockDim.x) {
-    const size_t row = e / w;
-    const int k = (int)(e % w);
-    const size_t c = row / d_y;
-    const int i = (int)(row % d_y);
-    const float v = (float)(WL[(size_t)i * w + k] * (double)der[c * ldd + k]);
-    store_slices(v, P + row * ldp + k, plane, nslice);
+  // each thread fills 8 consecutive columns of one row: P = W_L .* der (per chain)
+  const int wv = (w + 7) / 8;
+  const long long total = (long long)C * d_y * wv;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long row = e / wv;
+    const int k0 = (int)(e - row * wv) * 8;
+    const int c = (int)(row / d_y), i = (int)(row - (long long)c * d_y);
+    float x[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int k = k0 + q;
+      x[q] = k < w ? (float)(WL[(size_t)i * w + k] * (double)der[(size_t)c * ldd + k]) : 0.0f;
+    }
+    __nv_bfloat16 *o = P + (size_t)row * ldp + k0;
+    const bool vec = (ldp & 7) == 0 && k0 + 8 <= ldp;
+    for (int sl = 0; sl < nslice; ++sl) {
+      __nv_bfloat16 h[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        h[q] = __float2bfloat16_rn(x[q]);
+        x[q] -= __bfloat162float(h[q]);
+      }
+      if (vec) {
+        *reinterpret_cast<uint4 *>(o + sl * plane) = *reinterpret_cast<const uint4 *>(h);
+      } else {
+        for (int q = 0; q < 8 && k0 + q < w; ++q) o[sl * plane + q] = h[q];
+      }
+    }
   }
 }
 
@@ -437,7 +503,7 @@ cudaError_t launch_split_bf16_f64(int rows, int cols, const double *src, int lds
 cudaError_t launch_jac_init_bf16(int C, int d_y, int w, const double *WL, const float *der,
                                  int ldd, __nv_bfloat16 *P, int ldp, size_t plane, int nslice,
                                  cudaStream_t st) {
-  const size_t n = (size_t)C * d_y * w;
+  const size_t n = (size_t)C * d_y * ((w + 7) / 8);
   const int grid = (int)std::min<size_t>((n + 255) / 256, 152 * 32);
   k_jac_init_bf16<<<grid > 0 ? grid : 1, 256, 0, st>>>(C, d_y, w, WL, der, ldd, P, ldp, plane,
                                                        nslice);
