@@ -133,8 +133,8 @@ cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st);
 cudaError_t launch_split_bf16_f64(int rows, int cols, const double *src, int lds,
                                   __nv_bfloat16 *dst, int ldd, size_t plane, int nslice,
                                   cudaStream_t st);
-// Jacobian start on the tensor path: P = W_L (fp64) .* der (fp32) as bf16 slices
-cudaError_t launch_jac_init_bf16(int C, int d_y, int w, const double *WL, const float *der,
+// Jacobian start on the tensor path: P = W_L .* der (both fp32) as bf16 slices
+cudaError_t launch_jac_init_bf16(int C, int d_y, int w, const float *WL, const float *der,
                                  int ldd, __nv_bfloat16 *P, int ldp, size_t plane, int nslice,
                                  cudaStream_t st);
 

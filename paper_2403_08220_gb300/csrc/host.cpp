@@ -360,7 +360,7 @@ struct Surrogate {
   double *dE = nullptr, *dD = nullptr, *dS = nullptr, *dSqrtLam = nullptr, *dy = nullptr;
   float *fE = nullptr, *fD = nullptr, *fS = nullptr, *fSqrtLam = nullptr;
   std::vector<double *> dW, dWT, db;
-  std::vector<float *> fb;
+  std::vector<float *> fb, fW;
   std::vector<__nv_bfloat16 *> bW, bWT;
   std::vector<int> ldW, ldWT;
   std::vector<size_t> plW, plWT;
@@ -508,6 +508,8 @@ static int load_surrogate(dino_ctx *ctx, const dino_surrogate_desc *d) {
     if (s->precision == DINO_PREC_BF16) {
       const auto fb = to_f32(s->b[l]);
       s->fb.push_back(sur_upload(ctx, s.get(), fb.data(), fb.size()));
+      const auto fw = to_f32(s->W[l]);
+      s->fW.push_back(sur_upload(ctx, s.get(), fw.data(), fw.size()));
       size_t pl = 0, plt = 0;
       const int ldw = pad8(wi), ldwt = pad8(wo);
       const auto bw = split_planes(s->W[l], wo, wi, ldw, s->fwd_slices, pl);
@@ -706,7 +708,7 @@ static void eval_surrogate(dino_ctx *ctx, const Surrogate *s, Work &w, const dou
   }
   const int wl = s->widths[L - 1];
   launch(ctx, "jac_init_tc", [&] {
-    return launch_jac_init_bf16(C, dy, wl, s->dW[L - 1], w.der32[L - 2], wl, w.Pb[0], w.ldp,
+    return launch_jac_init_bf16(C, dy, wl, s->fW[L - 1], w.der32[L - 2], wl, w.Pb[0], w.ldp,
                                 w.plp, s->jac_slices, st);
   });
   int cur = 0;

@@ -388,6 +388,204 @@ __global__ void __launch_bounds__(kThreads) k_propose(ReducedArgs a) {
   if (threadIdx.x == 0) a.lq_fwd[c] = lq;
 }
 
+// ---------------------------------------------------------------------------
+// Warp-per-chain reduced proposal.  Each warp owns one chain; vectors live in
+// registers distributed over lanes (element i in lane i % 32, slot i / 32) and
+// L is read from global memory (L1/L2), so an SM keeps 16 chains in flight
+// and the serial parts of the triangular solves of one chain overlap with the
+// FP64 work of the others.
+
+constexpr int kPropWarps = 4;  // chains per CTA
+
+template <int S>
+__device__ __forceinline__ void warp_lower_solve(const double *__restrict__ L, int r,
+                                                 const double (&invd)[S], double (&t)[S]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int b = 0; b < S; ++b) {
+    if (32 * b >= r) break;
+    const int jb = 32 * b, nb = min(32, r - jb);
+    double tb = t[b];
+    const double ib = invd[b];
+    for (int k = 0; k < nb; ++k) {
+      const double yk = __shfl_sync(kFull, tb, k) * __shfl_sync(kFull, ib, k);
+      if (lane == k)
+        tb = yk;
+      else if (lane > k && lane < nb)
+        tb -= L[tri(jb + lane) + jb + k] * yk;
+    }
+    t[b] = tb;
+#pragma unroll
+    for (int b2 = b + 1; b2 < S; ++b2) {
+      if (32 * b2 >= r) break;
+      const int i = 32 * b2 + lane;
+      const double *row = L + tri(i) + jb;
+      double acc = t[b2];
+      for (int k = 0; k < nb; ++k) {
+        const double yk = __shfl_sync(kFull, tb, k);
+        if (i < r) acc -= row[k] * yk;
+      }
+      t[b2] = acc;
+    }
+  }
+}
+
+template <int S>
+__device__ __forceinline__ void warp_upper_solve(const double *__restrict__ L, int r,
+                                                 const double (&invd)[S], double (&t)[S]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int b = S - 1; b >= 0; --b) {
+    if (32 * b >= r) continue;
+    const int jb = 32 * b, nb = min(32, r - jb);
+    double tb = t[b];
+    const double ib = invd[b];
+    for (int k = nb - 1; k >= 0; --k) {
+      const double xk = __shfl_sync(kFull, tb, k) * __shfl_sync(kFull, ib, k);
+      if (lane == k)
+        tb = xk;
+      else if (lane < k)
+        tb -= L[tri(jb + k) + jb + lane] * xk;
+    }
+    t[b] = tb;
+#pragma unroll
+    for (int b2 = 0; b2 < b; ++b2) {
+      const int i = 32 * b2 + lane;
+      double acc = t[b2];
+      for (int k = 0; k < nb; ++k) acc -= L[tri(jb + k) + i] * __shfl_sync(kFull, tb, k);
+      t[b2] = acc;
+    }
+  }
+}
+
+// y = L^T x: for each row i of L (coalesced across lanes j <= i)
+template <int S>
+__device__ __forceinline__ void warp_upper_matvec(const double *__restrict__ L, int r,
+                                                  const double (&x)[S], double (&y)[S]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 0; s < S; ++s) y[s] = 0.0;
+#pragma unroll
+  for (int b = 0; b < S; ++b) {
+    if (32 * b >= r) break;
+    const int nb = min(32, r - 32 * b);
+    for (int k = 0; k < nb; ++k) {
+      const int i = 32 * b + k;
+      const double xi = __shfl_sync(kFull, x[b], k);
+      const double *row = L + tri(i);
+#pragma unroll
+      for (int s = 0; s <= b; ++s) {
+        const int j = 32 * s + lane;
+        if (j <= i) y[s] += row[j] * xi;
+      }
+    }
+  }
+}
+
+// y = L x: each lane its own rows, contiguous along the row
+template <int S>
+__device__ __forceinline__ void warp_lower_matvec(const double *__restrict__ L, int r,
+                                                  const double (&x)[S], double (&y)[S]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    y[s] = 0.0;
+    if (32 * s >= r) continue;
+    const int i = 32 * s + lane;
+    const double *row = L + tri(min(i, r - 1));
+    double acc = 0.0;
+#pragma unroll
+    for (int b = 0; b <= s; ++b) {
+      for (int k = 0; k < 32; ++k) {
+        const int j = 32 * b + k;
+        const double xj = __shfl_sync(kFull, x[b], k);
+        if (i < r && j <= i) acc += row[j] * xj;
+      }
+    }
+    y[s] = acc;
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+template <int S>
+__global__ void __launch_bounds__(32 * kPropWarps) k_propose_warp(ReducedArgs a) {
+  __shared__ double xi_s[kPropWarps][32 * S];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int c = blockIdx.x * kPropWarps + w;
+  if (c >= a.C) return;  // whole warp
+  const int r = a.r;
+  const double *L = a.L + (size_t)c * l_stride(r);
+  const uint32_t chain = (uint32_t)(a.id_base + (uint64_t)c);
+  for (int blk = lane; blk < (r + 3) / 4; blk += 32) {
+    double n4[4];
+    normals4_f64(philox_block(a.seed, STREAM_XI, a.step, chain, blk), n4);
+    for (int q = 0; q < 4; ++q)
+      if (4 * blk + q < r) xi_s[w][4 * blk + q] = n4[q];
+  }
+  __syncwarp();
+  double va[S], vg[S], vv[S], vx[S], vp[S], vq[S], invd[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int i = 32 * s + lane;
+    const bool in = i < r;
+    va[s] = in ? a.mr[(size_t)c * r + i] : 0.0;
+    vg[s] = in ? a.g[(size_t)c * r + i] : 0.0;
+    vv[s] = va[s] + vg[s];
+    vx[s] = in ? xi_s[w][i] : 0.0;
+    invd[s] = in ? 1.0 / L[tri(i) + i] : 0.0;
+  }
+  warp_lower_solve<S>(L, r, invd, vv);
+  warp_upper_solve<S>(L, r, invd, vv);  // vv = (I+H)^-1 (a + g)
+  warp_upper_solve<S>(L, r, invd, vx);  // vx = L^-T xi
+  const double s_ = a.s, cs = sqrt(1.0 - s_ * s_);
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int i = 32 * s + lane;
+    const double mu = va[s] - (1.0 - s_) * vv[s];
+    const double b = mu + cs * vx[s];
+    vx[s] = i < r ? b : 0.0;
+    if (i < r) {
+      a.mu[(size_t)c * r + i] = mu;
+      a.b[(size_t)c * r + i] = b;
+      if (a.b_bf16)
+        split_bf16_store(b, a.b_bf16 + (size_t)c * a.b_ld + i, a.b_plane, a.b_slices);
+    }
+  }
+  // log rho_{0,r}(a -> b) with the geometry at a
+  warp_upper_matvec<S>(L, r, va, vp);  // p = L^T a
+  warp_lower_matvec<S>(L, r, vp, vq);  // q = (I+H) a
+  double t1 = 0.0, t2 = 0.0, nm = 0.0;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int i = 32 * s + lane;
+    if (i < r) {
+      const double wv = vq[s] - va[s] - vg[s];        // w = H a - g
+      const double mh = (vx[s] - s_ * va[s]) / cs;    // mhat
+      t1 += wv * (va[s] - vv[s]);
+      t2 += mh * wv;
+      nm += mh * mh;
+      vp[s] = mh;
+    } else {
+      vp[s] = 0.0;
+    }
+  }
+  t1 = warp_sum(t1);
+  t2 = warp_sum(t2);
+  nm = warp_sum(nm);
+  warp_upper_matvec<S>(L, r, vp, vq);  // q = L^T mhat
+  double t3 = 0.0;
+#pragma unroll
+  for (int s = 0; s < S; ++s) t3 += vq[s] * vq[s];
+  t3 = warp_sum(t3) - nm;
+  if (lane == 0)
+    a.lq_fwd[c] = -a.dt / 8.0 * t1 + sqrt(a.dt) / 2.0 * t2 + a.hld[c] - 0.5 * t3;
+}
+
 // I + J^T J / noise_var into the packed shared matrix, from an FP64 J:
 // chunks of kJChunk rows, FP64 products accumulated in shared memory.
 __device__ void form_h_f64(const double *J, int dy, int r, double inv_nv, double *Ls,
@@ -599,6 +797,14 @@ size_t geometry_smem_bytes(int r, int d_y, int jf_f32) {
 }
 
 cudaError_t launch_propose(const ReducedArgs &a, cudaStream_t st) {
+  if (a.r <= 32 * 7) {
+    const int grid = (a.C + kPropWarps - 1) / kPropWarps;
+    if (a.r <= 32 * 2)
+      k_propose_warp<2><<<grid, 32 * kPropWarps, 0, st>>>(a);
+    else
+      k_propose_warp<7><<<grid, 32 * kPropWarps, 0, st>>>(a);
+    return cudaGetLastError();
+  }
   const size_t smem = propose_smem_bytes(a.r);
   cudaError_t e = cudaFuncSetAttribute(k_propose, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);

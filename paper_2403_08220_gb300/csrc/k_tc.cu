@@ -359,7 +359,7 @@ __global__ void k_split_bf16(int rows, int cols, const double *__restrict__ src,
   }
 }
 
-__global__ void k_jac_init_bf16(int C, int d_y, int w, const double *__restrict__ WL,
+__global__ void k_jac_init_bf16(int C, int d_y, int w, const float *__restrict__ WL,
                                 const float *__restrict__ der, int ldd,
                                 __nv_bfloat16 *__restrict__ P, int ldp, size_t plane,
                                 int nslice) {
@@ -375,7 +375,7 @@ __global__ void k_jac_init_bf16(int C, int d_y, int w, const double *__restrict_
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int k = k0 + q;
-      x[q] = k < w ? (float)(WL[(size_t)i * w + k] * (double)der[(size_t)c * ldd + k]) : 0.0f;
+      x[q] = k < w ? WL[(size_t)i * w + k] * der[(size_t)c * ldd + k] : 0.0f;
     }
     __nv_bfloat16 *o = P + (size_t)row * ldp + k0;
     const bool vec = (ldp & 7) == 0 && k0 + 8 <= ldp;
@@ -500,7 +500,7 @@ cudaError_t launch_split_bf16_f64(int rows, int cols, const double *src, int lds
   return cudaGetLastError();
 }
 
-cudaError_t launch_jac_init_bf16(int C, int d_y, int w, const double *WL, const float *der,
+cudaError_t launch_jac_init_bf16(int C, int d_y, int w, const float *WL, const float *der,
                                  int ldd, __nv_bfloat16 *P, int ldp, size_t plane, int nslice,
                                  cudaStream_t st) {
   const size_t n = (size_t)C * d_y * ((w + 7) / 8);
