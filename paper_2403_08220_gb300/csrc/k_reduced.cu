@@ -198,92 +198,163 @@ __device__ __forceinline__ void tri_pos(int e, int &ii, int &jj) {
   jj = e - tri(ii);
 }
 
-// In-place right-looking Cholesky of the packed matrix in 8-column panels:
-// (a) warp 0 factors the 8 x 8 diagonal block, (b) every row below it is
-// solved against that block, (c) the trailing triangle takes the rank-8
-// update.  Per element this is the same sequence of fused multiply-adds as
-// the column-at-a-time algorithm.  inv[k] = 1 / L_kk.  A non-positive pivot
-// produces NaN, which the caller turns into a reject.
+// Factor the 8 x 8 diagonal block at kb (size nb) by one warp: pivots from
+// y = x^(-1/2), an FP32 estimate refined by two Newton-Raphson steps on
+// 1/y^2 - x = 0 (y <- y (3 - x y^2) / 2), then the block's own column scaling
+// and rank-1 updates.  inv[k] = 1 / L_kk.
+__device__ __forceinline__ void warp_factor_diag(double *Ls, double *inv, int kb, int nb,
+                                                 int lane) {
+  for (int q = 0; q < nb; ++q) {
+    const int kq = kb + q;
+    const double xkk = Ls[tri(kq) + kq];
+    double id = (double)rsqrtf((float)xkk);
+    id = id * (1.5 - 0.5 * xkk * id * id);
+    id = id * (1.5 - 0.5 * xkk * id * id);
+    const double d = xkk * id;
+    __syncwarp();
+    if (lane == 0) {
+      Ls[tri(kq) + kq] = d;
+      inv[kq] = id;
+    }
+    if (lane > q && lane < nb) Ls[tri(kb + lane) + kq] *= id;
+    __syncwarp();
+    for (int e = lane; e < nb * nb; e += 32) {
+      const int i = e / nb, j = e % nb;
+      if (j > q && j <= i)
+        Ls[tri(kb + i) + kb + j] -= Ls[tri(kb + i) + kq] * Ls[tri(kb + j) + kq];
+    }
+    __syncwarp();
+  }
+}
+
+// Rows i >= row0 of the panel at kb: L[i, kb:kb+nb] <- L[i, kb:kb+nb] L_bb^-T.
+__device__ __forceinline__ void panel_solve(double *Ls, const double *inv, int r, int kb, int nb,
+                                            int row0, int t0, int T) {
+  for (int i = row0 + t0; i < r; i += T) {
+    double *row = Ls + tri(i) + kb;
+    double x[kNB];
+#pragma unroll
+    for (int q = 0; q < kNB; ++q) {
+      if (q < nb) {
+        double acc = row[q];
+        const double *lq = Ls + tri(kb + q) + kb;
+#pragma unroll
+        for (int p = 0; p < q; ++p) acc -= x[p] * lq[p];
+        x[q] = acc * inv[kb + q];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kNB; ++q)
+      if (q < nb) row[q] = x[q];
+  }
+}
+
+// Rank-nb update from the panel at kb of the entries (i, j), j0 <= j <= i < r
+// and j < j1: the triangle below j0 when j1 >= r, or a column strip.
+// Threads t0, t0 + T, ... share the entries evenly; each thread works on two
+// entries at a time so that two independent FMA chains hide the FP64 latency.
+struct StripPos {
+  int ii, jj;
+};
+
+__device__ __forceinline__ void strip_advance(StripPos &p, int step, int w) {
+  p.jj += step;
+  while (true) {
+    const int len = p.ii + 1 < w ? p.ii + 1 : w;
+    if (p.jj < len) break;
+    p.jj -= len;
+    ++p.ii;
+  }
+}
+
+__device__ __forceinline__ void trailing_update(double *Ls, int r, int kb, int nb, int j0, int j1,
+                                                int t0, int T) {
+  const int n = r - j0;
+  const int w = min(j1, r) - j0;  // strip width (w == n: whole triangle)
+  const int full = w * (w + 1) / 2 + (n - w) * w;
+  if (t0 >= full) return;
+  StripPos p;
+  {
+    const int tw = w * (w + 1) / 2;
+    if (t0 < tw) {
+      tri_pos(t0, p.ii, p.jj);
+    } else {
+      p.ii = w + (t0 - tw) / w;
+      p.jj = (t0 - tw) % w;
+    }
+  }
+  for (int e = t0; e < full; e += 2 * T) {
+    StripPos q = p;
+    const bool two = e + T < full;
+    if (two) strip_advance(q, T, w);
+    const int i1 = j0 + p.ii, c1 = j0 + p.jj;
+    const int i2 = j0 + q.ii, c2 = j0 + q.jj;
+    const double *li1 = Ls + tri(i1) + kb, *lj1 = Ls + tri(c1) + kb;
+    const double *li2 = Ls + tri(i2) + kb, *lj2 = Ls + tri(c2) + kb;
+    double *a1 = Ls + tri(i1) + c1;
+    double *a2 = Ls + tri(i2) + c2;
+    double acc1 = *a1, acc2 = two ? *a2 : 0.0;
+    if (nb == kNB) {
+      double x1[kNB], y1[kNB], x2[kNB], y2[kNB];
+#pragma unroll
+      for (int k = 0; k < kNB; ++k) {
+        x1[k] = li1[k];
+        y1[k] = lj1[k];
+        x2[k] = two ? li2[k] : 0.0;
+        y2[k] = two ? lj2[k] : 0.0;
+      }
+#pragma unroll
+      for (int k = 0; k < kNB; ++k) {
+        acc1 -= x1[k] * y1[k];
+        acc2 -= x2[k] * y2[k];
+      }
+    } else {
+      for (int k = 0; k < nb; ++k) acc1 -= li1[k] * lj1[k];
+      if (two)
+        for (int k = 0; k < nb; ++k) acc2 -= li2[k] * lj2[k];
+    }
+    *a1 = acc1;
+    if (two) *a2 = acc2;
+    p = q;
+    strip_advance(p, two ? T : 0, w);
+  }
+}
+
+// In-place right-looking Cholesky of the packed matrix in 8-column panels
+// with a one-panel lookahead and warp specialisation.  Per panel:
+//   (A) all threads: the next panel's columns take this panel's rank-8 update;
+//   (B) warps 0-3 factor the next diagonal block (warp 0) and then solve the
+//       rows below it against that block, while warps 4.. apply this panel's
+//       update to the rest of the trailing triangle.
+// Two CTA barriers per panel; the serial diagonal work and the panel solve
+// run in the shadow of the trailing update.  Per element this is the same
+// sequence of fused multiply-adds as the column-at-a-time algorithm.  A
+// non-positive pivot produces NaN, which the caller turns into a reject.
+constexpr int kPanelThreads = 128;  // warps 0-3
+
+__device__ __forceinline__ void panel_group_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kPanelThreads) : "memory");
+}
+
 __device__ void cta_cholesky(double *Ls, double *inv, int r) {
   const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (warp == 0) warp_factor_diag(Ls, inv, 0, min(kNB, r), lane);
+  __syncthreads();
+  panel_solve(Ls, inv, r, 0, min(kNB, r), min(kNB, r), tid, T);
+  __syncthreads();
   for (int kb = 0; kb < r; kb += kNB) {
     const int nb = min(kNB, r - kb);
-    if (warp == 0) {
-      for (int q = 0; q < nb; ++q) {
-        const int kq = kb + q;
-        // pivot and its inverse from y = x^(-1/2): an FP32 estimate refined by
-        // two Newton-Raphson steps on 1/y^2 - x = 0, y <- y (3 - x y^2) / 2,
-        // so the serial diagonal work stays short on the FP64 pipe
-        const double xkk = Ls[tri(kq) + kq];
-        double id = (double)rsqrtf((float)xkk);
-        id = id * (1.5 - 0.5 * xkk * id * id);
-        id = id * (1.5 - 0.5 * xkk * id * id);
-        const double d = xkk * id;
-        __syncwarp();
-        if (lane == 0) {
-          Ls[tri(kq) + kq] = d;
-          inv[kq] = id;
-        }
-        if (lane > q && lane < nb) Ls[tri(kb + lane) + kq] *= id;
-        __syncwarp();
-        for (int e = lane; e < nb * nb; e += 32) {
-          const int i = e / nb, j = e % nb;
-          if (j > q && j <= i)
-            Ls[tri(kb + i) + kb + j] -= Ls[tri(kb + i) + kq] * Ls[tri(kb + j) + kq];
-        }
-        __syncwarp();
-      }
-    }
+    const int nk = kb + nb;  // next panel
+    if (nk >= r) break;
+    const int nb2 = min(kNB, r - nk);
+    trailing_update(Ls, r, kb, nb, nk, nk + nb2, tid, T);  // (A)
     __syncthreads();
-    for (int i = kb + nb + tid; i < r; i += T) {
-      double *row = Ls + tri(i) + kb;
-      double x[kNB];
-#pragma unroll
-      for (int q = 0; q < kNB; ++q) {
-        if (q < nb) {
-          double acc = row[q];
-          const double *lq = Ls + tri(kb + q) + kb;
-#pragma unroll
-          for (int p = 0; p < q; ++p) acc -= x[p] * lq[p];
-          x[q] = acc * inv[kb + q];
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < kNB; ++q)
-        if (q < nb) row[q] = x[q];
-    }
-    __syncthreads();
-    const int n = r - kb - nb;
-    const int ntri = n * (n + 1) / 2;
-    if (tid < ntri) {
-      int ii, jj;
-      tri_pos(tid, ii, jj);
-      const int base = kb + nb;
-      for (int e = tid; e < ntri; e += T) {
-        const int i = base + ii, j = base + jj;
-        const double *li = Ls + tri(i) + kb;
-        const double *lj = Ls + tri(j) + kb;
-        double *aij = Ls + tri(i) + j;
-        double acc = *aij;
-        if (nb == kNB) {
-          double pa[kNB], pb[kNB];
-#pragma unroll
-          for (int q = 0; q < kNB; ++q) {
-            pa[q] = li[q];
-            pb[q] = lj[q];
-          }
-#pragma unroll
-          for (int q = 0; q < kNB; ++q) acc -= pa[q] * pb[q];
-        } else {
-          for (int q = 0; q < nb; ++q) acc -= li[q] * lj[q];
-        }
-        *aij = acc;
-        jj += T;
-        while (jj > ii) {
-          jj -= ii + 1;
-          ++ii;
-        }
-      }
+    if (tid < kPanelThreads) {  // (B) panel group
+      if (warp == 0) warp_factor_diag(Ls, inv, nk, nb2, lane);
+      panel_group_sync();
+      panel_solve(Ls, inv, r, nk, nb2, nk + nb2, tid, kPanelThreads);
+    } else if (nk + nb2 < r) {  // (B) update group
+      trailing_update(Ls, r, kb, nb, nk + nb2, r, tid - kPanelThreads, T - kPanelThreads);
     }
     __syncthreads();
   }
