@@ -253,6 +253,47 @@ def run_ours(args, rank, world, device):
     return line
 
 
+def run_hetero(args, device=0):
+    """Eight posteriors of different size (r = 32 ... 400) stepped together.
+
+    One step = one transition of every chain of all eight pools (their kernels
+    are issued back to back on one stream).  Returns total proposals/s and the
+    per-posterior step time.
+    """
+    import torch
+    import paper_2403_08220_gb300 as dino
+    from workloads import heterogeneous_workloads
+    torch.cuda.set_device(device)
+    stream = torch.cuda.Stream(device=device)
+    ctx = dino.dino_init(device, 0, stream.cuda_stream, dino.DINO_FLAG_TIMING)
+    ws = heterogeneous_workloads()
+    pools = []
+    for k, w in enumerate(ws):
+        sid = load_surrogate(dino, ctx, w)
+        pools.append((w, dino.dino_chains_create(ctx, sid, w.n_chains, w.dt, SEED_CHAINS)))
+    for w, p in pools:
+        dino.dino_chains_step(ctx, p, 1, stats=False)
+    dino.dino_kernel_times(ctx, reset=True)
+    steps = max(1, min(args.steps, 3))
+    per = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        for w, p in pools:
+            dino.dino_chains_step(ctx, p, 1, stats=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    secs = e0.elapsed_time(e1) / 1e3
+    total = sum(w.n_chains for w, _ in pools) * steps
+    for w, p in pools:
+        dino.dino_chains_destroy(ctx, p)
+    ctx.close()
+    return {"workload": "8 posteriors, r in {32,...,400}, d_y in {50,...,400}, 512-8192 chains",
+            "proposals_per_s": total / secs, "ms_per_step": 1e3 * secs / steps,
+            "chains": [w.n_chains for w in ws], "r": [w.r for w in ws]}
+
+
 def cpu_baseline(args, sample_chains=None, sample_steps=None):
     """The FP64 oracle, untuned, on a bounded sample of the same workload."""
     from oracle import mlp, mmala, prior
@@ -295,6 +336,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-chains", type=int, default=512)
     ap.add_argument("--cpu-steps", type=int, default=4)
+    ap.add_argument("--hetero", action="store_true",
+                    help="also time the eight-posterior heterogeneous batch")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -328,6 +371,8 @@ def main():
         return
 
     line = run_ours(args, rank, world, local)
+    if rank == 0 and args.hetero and world == 1:
+        line["hetero"] = run_hetero(args, local)
     if rank == 0:
         if not args.skip_cpu and world == 1:
             line["cpu_baseline"] = cpu_baseline(args, args.cpu_chains, args.cpu_steps)

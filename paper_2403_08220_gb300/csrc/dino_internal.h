@@ -9,8 +9,11 @@
 namespace dino {
 
 // Largest reduced dimension whose packed FP64 Cholesky factor the per-chain
-// kernels keep in shared memory (r (r+1)/2 doubles plus work vectors).
+// kernels keep in shared memory (r (r+1)/2 doubles plus work vectors); larger
+// r works on a global (L2-resident) per-chain workspace.
 constexpr int kMaxRSmem = 208;
+constexpr int kMaxR = 1024;                 // largest reduced dimension supported
+constexpr size_t kSmemLimit = 227 * 1024;   // opt-in shared memory per CTA
 
 // Philox streams (counter word 3): reduced noise, accept uniform, complement
 // prior draw, initial prior draw.
@@ -32,6 +35,9 @@ struct ReducedArgs {
   double *mr = nullptr, *g = nullptr, *phi = nullptr, *hld = nullptr, *L = nullptr;
   // proposal (written by propose, read by geometry)
   double *b = nullptr, *mu = nullptr, *lq_fwd = nullptr;
+  // per-chain factor workspace (C x l_stride(r)) used when r is too large for
+  // shared memory; nullptr otherwise
+  double *Lw = nullptr;
   // surrogate output at b: J (C x d_y x r) and f (C x d_y), FP64 or FP32
   const void *J = nullptr;
   const void *f = nullptr;
@@ -51,6 +57,7 @@ struct ReducedArgs {
   size_t b_plane = 0;
 };
 
+bool uses_global_factor(int r, int d_y);
 size_t propose_smem_bytes(int r);
 size_t geometry_smem_bytes(int r, int d_y, int jf_f32);
 cudaError_t launch_propose(const ReducedArgs &a, cudaStream_t st);

@@ -228,46 +228,54 @@ static void build_kle(int n, double gamma, double delta, int r, std::vector<doub
   }
 }
 
-// Thin Householder QR of G (N x r, row-major) -> Q with positive diag(R).
+// Thin Householder QR of G (N x r, row-major) -> Q (N x r, row-major) with
+// positive diag(R).  Works on a column-major copy so every reflector
+// application streams contiguous columns.
 static std::vector<double> thin_q(const double *G, int N, int r) {
-  std::vector<double> A(G, G + (size_t)N * r);  // working copy, column j = A[p*r + j]
-  std::vector<double> vs((size_t)N * r, 0.0), beta(r, 0.0), rdiag(r, 0.0);
+  std::vector<double> A((size_t)N * r);  // column j at A[j*N ...]
+  for (int p = 0; p < N; ++p)
+    for (int j = 0; j < r; ++j) A[(size_t)j * N + p] = G[(size_t)p * r + j];
+  std::vector<double> beta(r, 0.0), rdiag(r, 0.0);
+  std::vector<double> vs((size_t)r * N, 0.0);  // reflector j at vs[j*N ...], zero above j
   for (int j = 0; j < r; ++j) {
+    double *a = &A[(size_t)j * N];
     double nrm = 0.0;
-    for (int p = j; p < N; ++p) nrm += A[(size_t)p * r + j] * A[(size_t)p * r + j];
+    for (int p = j; p < N; ++p) nrm += a[p] * a[p];
     nrm = std::sqrt(nrm);
-    const double x0 = A[(size_t)j * r + j];
-    const double alpha = x0 >= 0 ? -nrm : nrm;  // R_jj = alpha
-    double *v = &vs[(size_t)j * N];              // reflector j stored contiguously
-    for (int p = 0; p < N; ++p) v[p] = 0.0;
-    v[j] = x0 - alpha;
-    for (int p = j + 1; p < N; ++p) v[p] = A[(size_t)p * r + j];
+    const double alpha = a[j] >= 0 ? -nrm : nrm;  // R_jj = alpha
+    double *v = &vs[(size_t)j * N];
+    v[j] = a[j] - alpha;
+    for (int p = j + 1; p < N; ++p) v[p] = a[p];
     double vv = 0.0;
     for (int p = j; p < N; ++p) vv += v[p] * v[p];
     beta[j] = vv > 0 ? 2.0 / vv : 0.0;
     rdiag[j] = alpha;
     for (int k = j; k < r; ++k) {
+      double *ak = &A[(size_t)k * N];
       double d = 0.0;
-      for (int p = j; p < N; ++p) d += v[p] * A[(size_t)p * r + k];
+      for (int p = j; p < N; ++p) d += v[p] * ak[p];
       d *= beta[j];
-      for (int p = j; p < N; ++p) A[(size_t)p * r + k] -= d * v[p];
+      for (int p = j; p < N; ++p) ak[p] -= d * v[p];
     }
   }
-  // Q = H_0 H_1 ... H_{r-1} [I_r; 0]
-  std::vector<double> Q((size_t)N * r, 0.0);
-  for (int k = 0; k < r; ++k) Q[(size_t)k * r + k] = 1.0;
-  for (int j = r - 1; j >= 0; --j) {
-    const double *v = &vs[(size_t)j * N];
-    for (int k = 0; k < r; ++k) {
+  // Q = H_0 H_1 ... H_{r-1} [I_r; 0], built column by column
+  std::vector<double> Qc((size_t)r * N, 0.0);
+  for (int k = 0; k < r; ++k) {
+    double *q = &Qc[(size_t)k * N];
+    q[k] = 1.0;
+    for (int j = std::min(k, r - 1); j >= 0; --j) {
+      const double *v = &vs[(size_t)j * N];
       double d = 0.0;
-      for (int p = j; p < N; ++p) d += v[p] * Q[(size_t)p * r + k];
+      for (int p = j; p < N; ++p) d += v[p] * q[p];
       d *= beta[j];
-      for (int p = j; p < N; ++p) Q[(size_t)p * r + k] -= d * v[p];
+      for (int p = j; p < N; ++p) q[p] -= d * v[p];
     }
   }
-  for (int k = 0; k < r; ++k)
-    if (rdiag[k] < 0)
-      for (int p = 0; p < N; ++p) Q[(size_t)p * r + k] = -Q[(size_t)p * r + k];
+  std::vector<double> Q((size_t)N * r);
+  for (int k = 0; k < r; ++k) {
+    const double sg = rdiag[k] < 0 ? -1.0 : 1.0;
+    for (int p = 0; p < N; ++p) Q[(size_t)p * r + k] = sg * Qc[(size_t)k * N + p];
+  }
   return Q;
 }
 
@@ -447,9 +455,9 @@ static int load_surrogate(dino_ctx *ctx, const dino_surrogate_desc *d) {
     if (w < 1) fail(DINO_EINVAL, "every width must be >= 1");
   s->d_y = s->widths.back();
   if (s->r > s->N) fail(DINO_EINVAL, "r=%d exceeds N=%d", s->r, s->N);
-  if (s->r > kMaxRSmem) fail(DINO_EINVAL, "r=%d exceeds the supported maximum %d", s->r, kMaxRSmem);
-  if (geometry_smem_bytes(s->r, s->d_y, 1) > 227 * 1024 ||
-      geometry_smem_bytes(s->r, s->d_y, 0) > 227 * 1024)
+  if (s->r > kMaxR) fail(DINO_EINVAL, "r=%d exceeds the supported maximum %d", s->r, kMaxR);
+  if (geometry_smem_bytes(s->r, s->d_y, 1) > kSmemLimit ||
+      geometry_smem_bytes(s->r, s->d_y, 0) > kSmemLimit)
     fail(DINO_EINVAL, "r=%d, d_y=%d exceed the per-chain shared-memory budget", s->r, s->d_y);
   if (d->precision == DINO_PREC_BF16 && s->L < 2)
     fail(DINO_EINVAL, "the tensor-core path needs at least one hidden layer");
@@ -765,6 +773,7 @@ struct Pool {
   Arena ar;
   // state
   double *mr, *g, *phi, *hld, *L;
+  double *Lw;  // factor workspace when r is too large for shared memory
   void *m;  // C x N, double (FP64 path) or float (tensor path)
   double *b, *mu, *lq_fwd, *coef, *log_rho, *log_u;
   int *acc;
@@ -791,6 +800,7 @@ static void layout_pool(Pool &p, bool assign) {
   p.phi = (double *)take((size_t)C * 8);
   p.hld = (double *)take((size_t)C * 8);
   p.L = (double *)take((size_t)C * l_stride(r) * 8);
+  p.Lw = uses_global_factor(r, s->d_y) ? (double *)take((size_t)C * l_stride(r) * 8) : nullptr;
   p.m = take((size_t)C * N * fe);
   p.b = (double *)take((size_t)C * r * 8);
   p.mu = (double *)take((size_t)C * r * 8);
@@ -832,6 +842,7 @@ static ReducedArgs reduced_args(const Pool &p) {
   a.phi = p.phi;
   a.hld = p.hld;
   a.L = p.L;
+  a.Lw = p.Lw;
   a.b = p.b;
   a.mu = p.mu;
   a.lq_fwd = p.lq_fwd;

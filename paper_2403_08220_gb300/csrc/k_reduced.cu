@@ -402,9 +402,10 @@ __device__ __forceinline__ void split_bf16_store(double x, __nv_bfloat16 *dst, s
 //   Ls[ldL] inv[r] six work vectors[r] res[dy] red[34] mbar[1] flag[1] | J chunk
 struct Layout {
   size_t Ls, inv, v0, res, red, mbar, flag, tail;
-  __host__ __device__ Layout(int r, int dy, size_t ldL) {
+  // with `global` the factor lives in global memory and takes no shared memory
+  __host__ __device__ Layout(int r, int dy, size_t ldL, bool global = false) {
     Ls = 0;
-    inv = ldL;
+    inv = global ? 0 : ldL;
     v0 = inv + r;
     res = v0 + 6 * (size_t)r;
     red = res + dy;
@@ -414,18 +415,22 @@ struct Layout {
   }
 };
 
+// One CTA per chain.  G = false: the factor is bulk-copied into shared
+// memory; G = true (large r): the CTA works on the chain's factor in global
+// memory (L2-resident while the chain is processed).
+template <bool G>
 __global__ void __launch_bounds__(kThreads) k_propose(ReducedArgs a) {
   extern __shared__ __align__(16) double sm[];
   const int c = blockIdx.x, r = a.r;
   const size_t ldL = l_stride(r);
-  const Layout lay(r, 0, ldL);
-  double *Ls = sm + lay.Ls;
+  const Layout lay(r, 0, ldL, G);
+  double *Ls = G ? a.L + (size_t)c * ldL : sm + lay.Ls;
   double *inv = sm + lay.inv;
   double *va = sm + lay.v0, *vg = va + r, *vv = vg + r, *vx = vv + r, *vp = vx + r, *vq = vp + r;
   double *red = sm + lay.red;
-  if (!cta_bulk_load(Ls, a.L + (size_t)c * ldL, (uint32_t)(ldL * 8),
-                     reinterpret_cast<uint64_t *>(sm + lay.mbar),
-                     reinterpret_cast<int *>(sm + lay.flag), a.err))
+  if (!G && !cta_bulk_load(Ls, a.L + (size_t)c * ldL, (uint32_t)(ldL * 8),
+                           reinterpret_cast<uint64_t *>(sm + lay.mbar),
+                           reinterpret_cast<int *>(sm + lay.flag), a.err))
     return;
   for (int i = threadIdx.x; i < r; i += blockDim.x) {
     va[i] = a.mr[(size_t)c * r + i];
@@ -688,50 +693,11 @@ __device__ void form_h_f64(const double *J, int dy, int r, double inv_nv, double
 // The same from an FP32 J: each thread accumulates up to kHMaxTiles 4 x 4
 // tiles of J^T J in FP32 registers over all d_y rows (chunks of kJChunkF
 // rows staged in shared memory, padded to a multiple of 4 columns), then
-// writes I + H once in FP64.
+// writes I + H once in FP64.  Large r takes several rounds of tiles.
 __device__ void form_h_f32(const float *J, int dy, int r, double inv_nv, double *Ls,
                            float *Jc) {
   const int nt = (r + kHT - 1) / kHT, rp = nt * kHT;
   const int ntiles = nt * (nt + 1) / 2;
-  int ti[kHMaxTiles], tj[kHMaxTiles];
-  float acc[kHMaxTiles][kHT][kHT];
-#pragma unroll
-  for (int s = 0; s < kHMaxTiles; ++s) {
-    const int t = threadIdx.x + s * blockDim.x;
-    if (t < ntiles) {
-      tri_pos(t, ti[s], tj[s]);
-    } else {
-      ti[s] = -1;
-      tj[s] = 0;
-    }
-#pragma unroll
-    for (int p = 0; p < kHT; ++p)
-#pragma unroll
-      for (int q = 0; q < kHT; ++q) acc[s][p][q] = 0.0f;
-  }
-  for (int i0 = 0; i0 < dy; i0 += kJChunkF) {
-    const int nr = min(kJChunkF, dy - i0);
-    for (int e = threadIdx.x; e < nr * rp; e += blockDim.x) {
-      const int k = e / rp, j = e % rp;
-      Jc[e] = j < r ? J[(size_t)(i0 + k) * r + j] : 0.0f;
-    }
-    __syncthreads();
-    for (int k = 0; k < nr; ++k) {
-      const float *row = Jc + k * rp;
-#pragma unroll
-      for (int s = 0; s < kHMaxTiles; ++s) {
-        if (ti[s] < 0) continue;
-        const float4 x = *reinterpret_cast<const float4 *>(row + kHT * ti[s]);
-        const float4 y = *reinterpret_cast<const float4 *>(row + kHT * tj[s]);
-        const float xa[4] = {x.x, x.y, x.z, x.w}, ya[4] = {y.x, y.y, y.z, y.w};
-#pragma unroll
-        for (int p = 0; p < kHT; ++p)
-#pragma unroll
-          for (int q = 0; q < kHT; ++q) acc[s][p][q] = fmaf(xa[p], ya[q], acc[s][p][q]);
-      }
-    }
-    __syncthreads();
-  }
   if (dy == 0) {
     for (int e = threadIdx.x; e < tri(r); e += blockDim.x) Ls[e] = 0.0;
     __syncthreads();
@@ -739,28 +705,71 @@ __device__ void form_h_f32(const float *J, int dy, int r, double inv_nv, double 
     __syncthreads();
     return;
   }
+  for (int t0 = 0; t0 < ntiles; t0 += kHMaxTiles * blockDim.x) {
+    int ti[kHMaxTiles], tj[kHMaxTiles];
+    float acc[kHMaxTiles][kHT][kHT];
 #pragma unroll
-  for (int s = 0; s < kHMaxTiles; ++s) {
-    if (ti[s] < 0) continue;
-#pragma unroll
-    for (int p = 0; p < kHT; ++p)
-#pragma unroll
-      for (int q = 0; q < kHT; ++q) {
-        const int i = kHT * ti[s] + p, j = kHT * tj[s] + q;
-        if (i < r && j <= i)
-          Ls[tri(i) + j] = (i == j ? 1.0 : 0.0) + (double)acc[s][p][q] * inv_nv;
+    for (int s = 0; s < kHMaxTiles; ++s) {
+      const int t = t0 + threadIdx.x + s * blockDim.x;
+      if (t < ntiles) {
+        tri_pos(t, ti[s], tj[s]);
+      } else {
+        ti[s] = -1;
+        tj[s] = 0;
       }
+#pragma unroll
+      for (int p = 0; p < kHT; ++p)
+#pragma unroll
+        for (int q = 0; q < kHT; ++q) acc[s][p][q] = 0.0f;
+    }
+    for (int i0 = 0; i0 < dy; i0 += kJChunkF) {
+      const int nr = min(kJChunkF, dy - i0);
+      for (int e = threadIdx.x; e < nr * rp; e += blockDim.x) {
+        const int k = e / rp, j = e % rp;
+        Jc[e] = j < r ? J[(size_t)(i0 + k) * r + j] : 0.0f;
+      }
+      __syncthreads();
+      for (int k = 0; k < nr; ++k) {
+        const float *row = Jc + k * rp;
+#pragma unroll
+        for (int s = 0; s < kHMaxTiles; ++s) {
+          if (ti[s] < 0) continue;
+          const float4 x = *reinterpret_cast<const float4 *>(row + kHT * ti[s]);
+          const float4 y = *reinterpret_cast<const float4 *>(row + kHT * tj[s]);
+          const float xa[4] = {x.x, x.y, x.z, x.w}, ya[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+          for (int p = 0; p < kHT; ++p)
+#pragma unroll
+            for (int q = 0; q < kHT; ++q) acc[s][p][q] = fmaf(xa[p], ya[q], acc[s][p][q]);
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int s = 0; s < kHMaxTiles; ++s) {
+      if (ti[s] < 0) continue;
+#pragma unroll
+      for (int p = 0; p < kHT; ++p)
+#pragma unroll
+        for (int q = 0; q < kHT; ++q) {
+          const int i = kHT * ti[s] + p, j = kHT * tj[s] + q;
+          if (i < r && j <= i)
+            Ls[tri(i) + j] = (i == j ? 1.0 : 0.0) + (double)acc[s][p][q] * inv_nv;
+        }
+    }
   }
   __syncthreads();
 }
 
-template <typename TJ>
+// G = false: the factor is built in shared memory; G = true (large r): in the
+// chain's slot of the global workspace a.Lw.
+template <typename TJ, bool G>
 __global__ void __launch_bounds__(kThreads) k_geometry(ReducedArgs a, int mode) {
   extern __shared__ __align__(16) double sm[];
   const int c = blockIdx.x, r = a.r, dy = a.d_y;
   const size_t ldL = l_stride(r);
-  const Layout lay(r, dy, ldL);
-  double *Ls = sm + lay.Ls;
+  const Layout lay(r, dy, ldL, G);
+  double *Ls = G ? a.Lw + (size_t)c * ldL : sm + lay.Ls;
   double *inv = sm + lay.inv;
   double *vb = sm + lay.v0, *vg = vb + r, *va = vg + r, *vv = va + r, *vp = vv + r, *vq = vp + r;
   double *res = sm + lay.res;
@@ -855,13 +864,21 @@ __global__ void __launch_bounds__(kThreads) k_geometry(ReducedArgs a, int mode) 
 
 }  // namespace
 
+bool uses_global_factor(int r, int d_y) {
+  const Layout lay(r, d_y, l_stride(r));
+  const size_t jc = (size_t)kJChunkF * ((r + kHT - 1) / kHT * kHT) * sizeof(float);
+  return r > kMaxRSmem || lay.tail * sizeof(double) + jc > kSmemLimit;
+}
+
 size_t propose_smem_bytes(int r) {
-  const Layout lay(r, 0, l_stride(r));
+  const bool G = uses_global_factor(r, 0);
+  const Layout lay(r, 0, l_stride(r), G);
   return lay.tail * sizeof(double);
 }
 
 size_t geometry_smem_bytes(int r, int d_y, int jf_f32) {
-  const Layout lay(r, d_y, l_stride(r));
+  const bool G = uses_global_factor(r, d_y);
+  const Layout lay(r, d_y, l_stride(r), G);
   const size_t jc = jf_f32 ? (size_t)kJChunkF * ((r + kHT - 1) / kHT * kHT) * sizeof(float)
                            : (size_t)kJChunk * r * sizeof(double);
   return lay.tail * sizeof(double) + jc;
@@ -877,28 +894,39 @@ cudaError_t launch_propose(const ReducedArgs &a, cudaStream_t st) {
     return cudaGetLastError();
   }
   const size_t smem = propose_smem_bytes(a.r);
-  cudaError_t e = cudaFuncSetAttribute(k_propose, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  if (uses_global_factor(a.r, 0)) {
+    cudaError_t e = cudaFuncSetAttribute(k_propose<true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_propose<true><<<a.C, kThreads, smem, st>>>(a);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(k_propose<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_propose<false><<<a.C, kThreads, smem, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+template <typename TJ, bool G>
+static cudaError_t launch_geometry_t(const ReducedArgs &a, int mode, size_t smem,
+                                     cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_geometry<TJ, G>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_propose<<<a.C, kThreads, smem, st>>>(a);
+  k_geometry<TJ, G><<<a.C, kThreads, smem, st>>>(a, mode);
   return cudaGetLastError();
 }
 
 cudaError_t launch_geometry(const ReducedArgs &a, int mode, cudaStream_t st) {
   const size_t smem = geometry_smem_bytes(a.r, a.d_y, a.jf_f32);
-  cudaError_t e;
-  if (a.jf_f32) {
-    e = cudaFuncSetAttribute(k_geometry<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
-    k_geometry<float><<<a.C, kThreads, smem, st>>>(a, mode);
-  } else {
-    e = cudaFuncSetAttribute(k_geometry<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
-    k_geometry<double><<<a.C, kThreads, smem, st>>>(a, mode);
-  }
-  return cudaGetLastError();
+  const bool G = uses_global_factor(a.r, a.d_y);
+  if (G && !a.Lw) return cudaErrorInvalidValue;
+  if (a.jf_f32)
+    return G ? launch_geometry_t<float, true>(a, mode, smem, st)
+             : launch_geometry_t<float, false>(a, mode, smem, st);
+  return G ? launch_geometry_t<double, true>(a, mode, smem, st)
+           : launch_geometry_t<double, false>(a, mode, smem, st);
 }
 
 }  // namespace dino
