@@ -294,6 +294,112 @@ def run_hetero(args, device=0):
             "chains": [w.n_chains for w in ws], "r": [w.r for w in ws]}
 
 
+def serving_workload(n_surrogates=16, seed=2024):
+    """Resident surrogates of the serving mix: r ~ U{32..400}, d_y ~ U{50..400}, r-2r-2r-d_y GELU."""
+    from workloads import ACT_GELU, BASIS_DIS, Workload
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n_surrogates):
+        r = int(rng.integers(32, 401))
+        dy = int(rng.integers(50, 401))
+        out.append(Workload(f"serve_{k}", n_grid=65, r=r, widths=[r, 2 * r, 2 * r, dy],
+                            activation=ACT_GELU, basis_kind=BASIS_DIS, n_chains=0, n_steps=0,
+                            precision="bf16", seed_offset=1000 + 10 * k))
+    return out
+
+
+def run_serving(args, device=0):
+    """Continuous batching under Poisson arrivals: p50/p99 latency and proposals/s.
+
+    Latency is measured on the host: from the submit call to the poll that
+    returns the request's outputs.  Two runs on the same resident surrogates:
+    * stable load: steps uniform in [10, 100], chains log-uniform in
+      [256, 2048], arrivals at 0.7 of the capacity measured just before on a
+      batch of such requests; all requests drain;
+    * written load: 20 requests/s, chains log-uniform in [256, 8192], steps
+      uniform in [1000, 10000], for a fixed window.  The offered work is far
+      above one GPU's capacity, so the queue grows; completed requests, queue
+      length and the offered GPU-seconds per second are reported.
+    """
+    import torch
+    import paper_2403_08220_gb300 as dino
+    torch.cuda.set_device(device)
+    ws = serving_workload(args.serve_surrogates)
+    rng = np.random.default_rng(7)
+
+    def draw(lo_c, hi_c, lo_s, hi_s):
+        k = int(rng.integers(0, len(ws)))
+        C = int(np.exp(rng.uniform(np.log(lo_c), np.log(hi_c))))
+        return k, C, int(rng.integers(lo_s, hi_s + 1))
+
+    def run(ctx, sids, rate, window, lo_c, hi_c, lo_s, hi_s, max_requests, drain):
+        outstanding, done = {}, []
+        t_start = time.perf_counter()
+        t_next = t_start
+        n = 0
+        while True:
+            now = time.perf_counter()
+            open_ = now - t_start <= window and n < max_requests
+            if not open_ and (not drain or not outstanding):
+                break
+            if open_ and now >= t_next:
+                k, C, S = draw(lo_c, hi_c, lo_s, hi_s)
+                w = ws[k]
+                t = dino.dino_serve_submit(ctx, sids[k], C, S, w.dt, 15 + n, w.r, w.N)
+                outstanding[t] = (time.perf_counter(), C * S)
+                n += 1
+                t_next += rng.exponential(1.0 / rate)
+            for t in list(outstanding):
+                o = dino.dino_serve_poll(ctx, t)
+                if o is not None:
+                    t0, work = outstanding.pop(t)
+                    done.append((time.perf_counter() - t0, work))
+            time.sleep(0.001)
+        return done, outstanding, time.perf_counter() - t_start, n
+
+    ctx = dino.dino_init(device, 0, None, 0)
+    t0 = time.perf_counter()
+    sids = [load_surrogate(dino, ctx, w) for w in ws]
+    setup_s = time.perf_counter() - t0
+    dino.dino_serve_config(ctx, n_streams=8, steps_per_round=4, max_active=32)
+    # capacity on a batch of stable-size requests submitted at once
+    cal, _, cal_s, _ = run(ctx, sids, 1e9, 1e9, 256, 2048, 10, 100, 16, True)
+    capacity = sum(wk for _, wk in cal) / cal_s
+    mean_work = float(np.mean([wk for _, wk in cal]))
+    rate = 0.7 * capacity / mean_work
+    st, _, st_s, _ = run(ctx, sids, rate, args.serve_window, 256, 2048, 10, 100, 10 ** 6, True)
+    lat = np.array([l for l, _ in st])
+    stable = {"offered_load_of_capacity": 0.7, "rate_per_s": rate, "requests": len(st),
+              "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+              "proposals_per_s": sum(wk for _, wk in st) / st_s,
+              "capacity_proposals_per_s": capacity,
+              "request": "chains log-uniform [256, 2048], steps U[10, 100]"}
+    ctx.close()
+
+    ctx = dino.dino_init(device, 0, None, 0)
+    sids = [load_surrogate(dino, ctx, w) for w in ws]
+    dino.dino_serve_config(ctx, n_streams=8, steps_per_round=2, max_active=32)
+    wr, left, wr_s, n = run(ctx, sids, 20.0, args.serve_window, 256, 8192, 1000, 10000, 600,
+                            False)
+    status = dino.dino_serve_status(ctx)
+    lat_w = np.array([l for l, _ in wr])
+    works = [wk for _, wk in wr] + [wk for _, wk in left.values()]
+    written = {"rate_per_s": 20.0, "window_s": args.serve_window, "submitted": n,
+               "completed": len(wr), "queued_at_end": status["queued"],
+               "resident_at_end": status["active"],
+               "peak_resident": status["peak_active"],
+               "peak_hbm_gb": status["peak_hbm_used"] / 1e9,
+               "p50_s": float(np.percentile(lat_w, 50)) if len(lat_w) else None,
+               "p99_s": float(np.percentile(lat_w, 99)) if len(lat_w) else None,
+               "offered_gpu_s_per_s": float(20.0 * np.mean(works) / capacity) if works else 0.0,
+               "request": "chains log-uniform [256, 8192], steps U[1000, 10000]"}
+    t_close = time.perf_counter()
+    ctx.close()   # cancels what is still queued; lets resident rounds finish
+    written["close_s"] = time.perf_counter() - t_close
+    return {"surrogates": len(ws), "r": [w.r for w in ws], "d_y": [w.d_y for w in ws],
+            "setup_s": setup_s, "stable": stable, "written_load": written}
+
+
 def cpu_baseline(args, sample_chains=None, sample_steps=None):
     """The FP64 oracle, untuned, on a bounded sample of the same workload."""
     from oracle import mlp, mmala, prior
@@ -338,6 +444,9 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--hetero", action="store_true",
                     help="also time the eight-posterior heterogeneous batch")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving load test")
+    ap.add_argument("--serve-window", type=float, default=10.0)
+    ap.add_argument("--serve-surrogates", type=int, default=16)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -373,6 +482,8 @@ def main():
     line = run_ours(args, rank, world, local)
     if rank == 0 and args.hetero and world == 1:
         line["hetero"] = run_hetero(args, local)
+    if rank == 0 and not args.no_serve and world == 1:
+        line["serving"] = run_serving(args, local)
     if rank == 0:
         if not args.skip_cpu and world == 1:
             line["cpu_baseline"] = cpu_baseline(args, args.cpu_chains, args.cpu_steps)

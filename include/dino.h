@@ -211,6 +211,64 @@ int dino_chains_read_last(dino_ctx *ctx, int pool_id, double *b, double *mu,
 
 int dino_chains_destroy(dino_ctx *ctx, int pool_id);
 
+/* ---- serving: continuous batching of chain ensembles -------------------- */
+
+/* A request: n_chains chains of a loaded surrogate advanced n_steps
+ * transitions, exactly as dino_chains_create + dino_chains_step would (same
+ * random numbers for the same seed and chain ids), with the results copied
+ * into caller buffers when it finishes.  m0 (n_chains x N, host, may be NULL
+ * for prior draws) is copied at submit.  The output buffers (any may be NULL)
+ * must stay valid until dino_serve_poll returns DINO_OK for the ticket:
+ * m_r_out n_chains x r, phi_out n_chains, accepts_out n_chains,
+ * m_out n_chains x N. */
+typedef struct {
+  int surrogate_id;
+  int n_chains;
+  int n_steps;
+  double dt;
+  uint64_t seed;
+  uint64_t chain_id_base;
+  const double *m0;
+  double *m_r_out;
+  double *phi_out;
+  uint64_t *accepts_out;
+  double *m_out;
+} dino_request;
+
+typedef struct {
+  dino_step_stats stats;
+  double queue_s;    /* submit -> admitted (device memory reserved) */
+  double latency_s;  /* submit -> results in the caller's buffers */
+} dino_result;
+
+/* Optional, before the first submit: number of CUDA streams requests are
+ * spread over (1..32, default 4), transitions issued per scheduling round
+ * (default 8) and the most requests resident at once (default 32).
+ * ESTATE once serving has started. */
+int dino_serve_config(dino_ctx *ctx, int n_streams, int steps_per_round, int max_active);
+
+/* Queue a request; returns immediately with a ticket.  A background thread
+ * admits queued requests in arrival order as soon as their device footprint
+ * (the pool's arena) fits in the HBM budget, so requests arriving while
+ * others run are batched with them, each on its own stream.
+ * Errors: ENOTFOUND (surrogate), ESTATE (no data), EINVAL, EBUSY (queue full),
+ * ENOMEM (the request alone exceeds the whole budget). */
+int dino_serve_submit(dino_ctx *ctx, const dino_request *req, uint64_t *ticket);
+
+/* DINO_PENDING while queued or running; DINO_OK once the outputs are in the
+ * caller's buffers (res, may be NULL, gets stats and timings); the request's
+ * error code if it failed; ENOTFOUND for an unknown ticket.  Never blocks
+ * beyond the context lock. */
+int dino_serve_poll(dino_ctx *ctx, uint64_t ticket, dino_result *res);
+
+/* Poll until done or timeout_s seconds have passed (then ETIMEOUT). */
+int dino_serve_wait(dino_ctx *ctx, uint64_t ticket, double timeout_s, dino_result *res);
+
+/* Queue length, resident requests, the most resident at once, and device
+ * memory in use now and at peak since serving started. */
+int dino_serve_status(dino_ctx *ctx, int *queued, int *active, int *peak_active,
+                      size_t *hbm_used, size_t *peak_hbm_used);
+
 /* ---- instrumentation --------------------------------------------------- */
 
 /* Number of kernels this context has launched since creation. */

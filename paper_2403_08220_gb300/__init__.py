@@ -62,6 +62,18 @@ class _Stats(ct.Structure):
                 ("nan_rejects", ct.c_uint64), ("sum_alpha", ct.c_double)]
 
 
+class _Request(ct.Structure):
+    _fields_ = [("surrogate_id", ct.c_int), ("n_chains", ct.c_int), ("n_steps", ct.c_int),
+                ("dt", ct.c_double), ("seed", ct.c_uint64), ("chain_id_base", ct.c_uint64),
+                ("m0", ct.POINTER(ct.c_double)), ("m_r_out", ct.POINTER(ct.c_double)),
+                ("phi_out", ct.POINTER(ct.c_double)), ("accepts_out", ct.POINTER(ct.c_uint64)),
+                ("m_out", ct.POINTER(ct.c_double))]
+
+
+class _Result(ct.Structure):
+    _fields_ = [("stats", _Stats), ("queue_s", ct.c_double), ("latency_s", ct.c_double)]
+
+
 _lib = None
 _P = ct.c_void_p
 _D = ct.POINTER(ct.c_double)
@@ -87,6 +99,12 @@ _SIGNATURES = {
     "dino_launch_count": ([_P], ct.c_uint64),
     "dino_kernel_times": ([_P, ct.c_char_p, _D, ct.POINTER(ct.c_uint64), _I, ct.POINTER(_I), _I],
                           _I),
+    "dino_serve_config": ([_P, _I, _I, _I], _I),
+    "dino_serve_submit": ([_P, ct.POINTER(_Request), ct.POINTER(ct.c_uint64)], _I),
+    "dino_serve_poll": ([_P, ct.c_uint64, ct.POINTER(_Result)], _I),
+    "dino_serve_wait": ([_P, ct.c_uint64, ct.c_double, ct.POINTER(_Result)], _I),
+    "dino_serve_status": ([_P, ct.POINTER(_I), ct.POINTER(_I), ct.POINTER(_I),
+                           ct.POINTER(ct.c_size_t), ct.POINTER(ct.c_size_t)], _I),
     "dino_surrogate_jacobian_noalloc": ([_I, _I, ct.POINTER(_I), _I, ct.POINTER(_P),
                                          ct.POINTER(_P), _P, _P, _P, _P], _I),
 }
@@ -304,3 +322,63 @@ def dino_surrogate_jacobian_noalloc(n: int, widths, activation: int, W_ptrs, b_p
                                                   _P(stream) if stream else None)
     if code != DINO_OK:
         raise DinoError(code, "dino_surrogate_jacobian_noalloc rejected the request")
+
+
+# ---- serving -------------------------------------------------------------
+
+_SERVE_OUT = {}   # (ctx address, ticket) -> numpy outputs kept alive until completion
+
+
+def dino_serve_config(ctx: Ctx, n_streams: int = 4, steps_per_round: int = 8,
+                      max_active: int = 32):
+    _check(ctx, lib().dino_serve_config(ctx.ptr, n_streams, steps_per_round, max_active))
+
+
+def dino_serve_submit(ctx: Ctx, sid: int, n_chains: int, n_steps: int, dt: float, seed: int,
+                      r: int, N: int, chain_id_base: int = 0, m0=None,
+                      want_field: bool = False) -> int:
+    """Queue a request; returns its ticket.  Outputs are filled on completion."""
+    out = dict(m_r=np.empty((n_chains, r)), phi=np.empty(n_chains),
+               accepts=np.empty(n_chains, dtype=np.uint64),
+               m=np.empty((n_chains, N)) if want_field else None)
+    m = _f64(m0) if m0 is not None else None
+    req = _Request(sid, n_chains, n_steps, float(dt), int(seed), int(chain_id_base), _dptr(m),
+                   _dptr(out["m_r"]), _dptr(out["phi"]),
+                   out["accepts"].ctypes.data_as(ct.POINTER(ct.c_uint64)), _dptr(out["m"]))
+    t = ct.c_uint64()
+    _check(ctx, lib().dino_serve_submit(ctx.ptr, ct.byref(req), ct.byref(t)))
+    _SERVE_OUT[(ctx.ptr.value, t.value)] = out
+    return t.value
+
+
+def _result(ctx, ticket, res):
+    out = _SERVE_OUT.pop((ctx.ptr.value, ticket))
+    out.update(stats=dict(proposals=res.stats.proposals, accepts=res.stats.accepts,
+                          nan_rejects=res.stats.nan_rejects, sum_alpha=res.stats.sum_alpha),
+               queue_s=res.queue_s, latency_s=res.latency_s)
+    return out
+
+
+def dino_serve_poll(ctx: Ctx, ticket: int):
+    """None while the request is queued or running, else its outputs."""
+    res = _Result()
+    code = lib().dino_serve_poll(ctx.ptr, ticket, ct.byref(res))
+    if code == DINO_PENDING:
+        return None
+    _check(ctx, code)
+    return _result(ctx, ticket, res)
+
+
+def dino_serve_wait(ctx: Ctx, ticket: int, timeout_s: float = 600.0):
+    res = _Result()
+    _check(ctx, lib().dino_serve_wait(ctx.ptr, ticket, float(timeout_s), ct.byref(res)))
+    return _result(ctx, ticket, res)
+
+
+def dino_serve_status(ctx: Ctx) -> dict:
+    q, a, pa = _I(), _I(), _I()
+    u, pu = ct.c_size_t(), ct.c_size_t()
+    _check(ctx, lib().dino_serve_status(ctx.ptr, ct.byref(q), ct.byref(a), ct.byref(pa),
+                                        ct.byref(u), ct.byref(pu)))
+    return dict(queued=q.value, active=a.value, peak_active=pa.value, hbm_used=u.value,
+                peak_hbm_used=pu.value)

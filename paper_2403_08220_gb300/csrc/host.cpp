@@ -8,7 +8,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <thread>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -59,6 +63,7 @@ struct Arena {
 
 struct Surrogate;
 struct Pool;
+struct Server;
 
 }  // namespace dino
 
@@ -85,6 +90,7 @@ struct dino_ctx {
   };
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> event_pool;
+  std::unique_ptr<dino::Server> server;
 };
 
 namespace dino {
@@ -112,6 +118,29 @@ void dev_free(dino_ctx *ctx, void *p, size_t bytes) {
   ctx->used -= std::min(ctx->used, bytes);
 }
 
+// Stream-ordered allocation for pools that come and go while other pools run
+// (serving): no device-wide synchronisation on free.
+void *dev_alloc_async(dino_ctx *ctx, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return nullptr;
+  if (ctx->used + bytes > ctx->budget)
+    fail(DINO_ENOMEM, "HBM budget exceeded: need %zu more bytes, %zu of %zu used", bytes,
+         ctx->used, ctx->budget);
+  void *p = nullptr;
+  cudaError_t e = cudaMallocAsync(&p, bytes, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(DINO_ENOMEM, "cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));
+  }
+  ctx->used += bytes;
+  return p;
+}
+
+void dev_free_async(dino_ctx *ctx, void *p, size_t bytes, cudaStream_t st) {
+  if (!p) return;
+  cudaFreeAsync(p, st);
+  ctx->used -= std::min(ctx->used, bytes);
+}
+
 template <typename T>
 T *upload(dino_ctx *ctx, const T *host, size_t n) {
   T *d = (T *)dev_alloc(ctx, n * sizeof(T));
@@ -122,7 +151,7 @@ T *upload(dino_ctx *ctx, const T *host, size_t n) {
 // ---------------------------------------------------------------------------
 // kernel launch bookkeeping (count + optional CUDA-event timing)
 template <class F>
-void launch(dino_ctx *ctx, const char *name, F &&fn) {
+void launch(dino_ctx *ctx, cudaStream_t st, const char *name, F &&fn) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   const bool timing = (ctx->flags & DINO_FLAG_TIMING) != 0;
   if (timing) {
@@ -134,22 +163,22 @@ void launch(dino_ctx *ctx, const char *name, F &&fn) {
         CK(cudaEventCreate(e));
       }
     }
-    CK(cudaEventRecord(e0, ctx->stream));
+    CK(cudaEventRecord(e0, st));
   }
   cudaError_t err = fn();
   ctx->launches += 1;
   if (err != cudaSuccess) fail(DINO_ECUDA, "kernel %s: %s", name, cudaGetErrorString(err));
   if (timing) {
-    CK(cudaEventRecord(e1, ctx->stream));
+    CK(cudaEventRecord(e1, st));
     ctx->pending.push_back({name, e0, e1});
   }
 }
 
 void collect_times(dino_ctx *ctx) {
   if (ctx->pending.empty()) return;
-  CK(cudaStreamSynchronize(ctx->stream));
   for (auto &p : ctx->pending) {
     float ms = 0;
+    CK(cudaEventSynchronize(p.e1));
     CK(cudaEventElapsedTime(&ms, p.e0, p.e1));
     auto &kt = ctx->ktimes[p.name];
     kt.ms += ms;
@@ -622,46 +651,46 @@ static void layout_work(const Surrogate *s, int C, Arena &ar, Work &w, bool assi
 
 // Forward pass and Jacobian at the C points in `x` (FP64 C x r; the tensor
 // path reads the bf16 planes in w.xb, which the caller has filled).
-static void eval_surrogate(dino_ctx *ctx, const Surrogate *s, Work &w, const double *x) {
+static void eval_surrogate(dino_ctx *ctx, const Surrogate *s, Work &w, const double *x,
+                           cudaStream_t st) {
   const int C = w.C, L = s->L, dy = s->d_y, r = s->r;
-  cudaStream_t st = ctx->stream;
   if (s->precision == DINO_PREC_FP64) {
     const double *a = x;
     int lda = r;
     for (int l = 0; l + 1 < L; ++l) {
       const int wo = s->widths[l + 1], wi = s->widths[l];
-      launch(ctx, "mlp_f64", [&] {
+      launch(ctx, st, "mlp_f64", [&] {
         return gemm_bias_act<double>(C, wo, wi, a, lda, s->dW[l], wi, s->db[l], s->act,
                                      w.act64[l], w.der64[l], wo, st);
       });
       a = w.act64[l];
       lda = wo;
     }
-    launch(ctx, "mlp_f64", [&] {
+    launch(ctx, st, "mlp_f64", [&] {
       return gemm_bias_act<double>(C, dy, s->widths[L - 1], a, lda, s->dW[L - 1],
                                    s->widths[L - 1], s->db[L - 1], 0, w.f64, nullptr, dy, st);
     });
     if (L == 1) {
-      launch(ctx, "jac_broadcast", [&] {
+      launch(ctx, st, "jac_broadcast", [&] {
         return launch_broadcast<double>(C, (size_t)dy * r, s->dW[0], w.J64, st);
       });
       return;
     }
     // reverse mode: P = W_{L-1} .* d_{L-2}; P <- (P W_l) .* d_{l-1}; J = P W_0
     const int wl = s->widths[L - 1];
-    launch(ctx, "jac_init_f64", [&] {
+    launch(ctx, st, "jac_init_f64", [&] {
       return launch_jac_init<double>(C, dy, wl, s->dW[L - 1], w.der64[L - 2], wl, w.P64[0], st);
     });
     int cur = 0;
     for (int l = L - 2; l >= 1; --l) {
       const int wi = s->widths[l], wo = s->widths[l + 1];
-      launch(ctx, "jac_gemm_f64", [&] {
+      launch(ctx, st, "jac_gemm_f64", [&] {
         return gemm_scale_group<double>(C * dy, wi, wo, w.P64[cur], wo, s->dWT[l], wo,
                                         w.der64[l - 1], wi, dy, w.P64[1 - cur], wi, st);
       });
       cur = 1 - cur;
     }
-    launch(ctx, "jac_gemm_f64", [&] {
+    launch(ctx, st, "jac_gemm_f64", [&] {
       return gemm_store<double>(C * dy, r, s->widths[1], w.P64[cur], s->widths[1], s->dWT[0],
                                 s->widths[1], w.J64, r, st);
     });
@@ -691,7 +720,7 @@ static void eval_surrogate(dino_ctx *ctx, const Surrogate *s, Work &w, const dou
     g.out_plane = w.plact[l];
     g.out_slices = s->fwd_slices;
     g.der = w.der32[l];
-    launch(ctx, "mlp_tc", [&] { return launch_tc_gemm(g, st); });
+    launch(ctx, st, "mlp_tc", [&] { return launch_tc_gemm(g, st); });
     a = w.actb[l];
     lda = w.ldact[l];
     pla = w.plact[l];
@@ -712,10 +741,10 @@ static void eval_surrogate(dino_ctx *ctx, const Surrogate *s, Work &w, const dou
     g.bias = s->fb[L - 1];
     g.outf = w.f32;
     g.ldo = dy;
-    launch(ctx, "mlp_tc", [&] { return launch_tc_gemm(g, st); });
+    launch(ctx, st, "mlp_tc", [&] { return launch_tc_gemm(g, st); });
   }
   const int wl = s->widths[L - 1];
-  launch(ctx, "jac_init_tc", [&] {
+  launch(ctx, st, "jac_init_tc", [&] {
     return launch_jac_init_bf16(C, dy, wl, s->fW[L - 1], w.der32[L - 2], wl, w.Pb[0], w.ldp,
                                 w.plp, s->jac_slices, st);
   });
@@ -740,7 +769,7 @@ static void eval_surrogate(dino_ctx *ctx, const Surrogate *s, Work &w, const dou
     g.ldo = w.ldp;
     g.out_plane = w.plp;
     g.out_slices = s->jac_slices;
-    launch(ctx, "jac_tc", [&] { return launch_tc_gemm(g, st); });
+    launch(ctx, st, "jac_tc", [&] { return launch_tc_gemm(g, st); });
     cur = 1 - cur;
   }
   TcGemmArgs g;
@@ -757,7 +786,7 @@ static void eval_surrogate(dino_ctx *ctx, const Surrogate *s, Work &w, const dou
   g.epi = TC_EPI_STORE_F32;
   g.outf = w.J32;
   g.ldo = r;
-  launch(ctx, "jac_tc", [&] { return launch_tc_gemm(g, st); });
+  launch(ctx, st, "jac_tc", [&] { return launch_tc_gemm(g, st); });
 }
 
 // ---------------------------------------------------------------------------
@@ -766,6 +795,8 @@ static void eval_surrogate(dino_ctx *ctx, const Surrogate *s, Work &w, const dou
 struct Pool {
   int id = 0;
   Surrogate *s = nullptr;
+  cudaStream_t st = nullptr;  // stream all of this pool's work goes to
+  bool async_mem = false;     // arena from the stream-ordered allocator
   int C = 0;
   double dt = 0, sc = 0;
   uint64_t seed = 0, id_base = 0;
@@ -871,16 +902,19 @@ static ReducedArgs reduced_args(const Pool &p) {
   return a;
 }
 
-static void split_input(dino_ctx *ctx, const Surrogate *s, Work &w, const double *x) {
+static void split_input(dino_ctx *ctx, const Surrogate *s, Work &w, const double *x,
+                        cudaStream_t st) {
   if (s->precision != DINO_PREC_BF16) return;
-  launch(ctx, "split_bf16", [&] {
-    return launch_split_bf16_f64(w.C, s->r, x, s->r, w.xb, w.ldx, w.plx, s->fwd_slices,
-                                 ctx->stream);
+  launch(ctx, st, "split_bf16", [&] {
+    return launch_split_bf16_f64(w.C, s->r, x, s->r, w.xb, w.ldx, w.plx, s->fwd_slices, st);
   });
 }
 
-static int create_pool(dino_ctx *ctx, int sid, int C, double dt, uint64_t seed,
-                       uint64_t id_base, const double *m0) {
+static size_t pool_footprint(const Surrogate *s, int C);
+
+static Pool *create_pool_on(dino_ctx *ctx, int sid, int C, double dt, uint64_t seed,
+                            uint64_t id_base, const double *m0, cudaStream_t st,
+                            bool serving) {
   Surrogate *s = get_surrogate(ctx, sid);
   if (C < 1) fail(DINO_EINVAL, "n_chains must be >= 1");
   if (!(dt > 0) || !std::isfinite(dt)) fail(DINO_EINVAL, "dt must be > 0");
@@ -893,13 +927,15 @@ static int create_pool(dino_ctx *ctx, int sid, int C, double dt, uint64_t seed,
   p->sc = (4.0 - dt) / (4.0 + dt);
   p->seed = seed;
   p->id_base = id_base;
+  p->st = st;
+  p->async_mem = serving;
   layout_pool(*p, false);
   p->ar.bytes = p->ar.off;
-  p->ar.base = (char *)dev_alloc(ctx, p->ar.bytes);
+  p->ar.base = (char *)(serving ? dev_alloc_async(ctx, p->ar.bytes, st)
+                                : dev_alloc(ctx, p->ar.bytes));
   try {
     layout_pool(*p, true);
     const int r = s->r, N = s->N;
-    cudaStream_t st = ctx->stream;
     CK(cudaMemsetAsync(p->acc_count, 0, (size_t)C * 8, st));
     CK(cudaMemsetAsync(p->counters, 0, 16, st));
     CK(cudaMemsetAsync(p->sum_alpha, 0, 8, st));
@@ -909,70 +945,86 @@ static int create_pool(dino_ctx *ctx, int sid, int C, double dt, uint64_t seed,
     if (m0) {
       CK(cudaMemcpyAsync(m64, m0, (size_t)C * N * 8, cudaMemcpyHostToDevice, st));
     } else {
-      launch(ctx, "prior_draw_f64", [&] {
+      launch(ctx, st, "prior_draw_f64", [&] {
         return launch_prior_draw<double>(C, s->n_grid, s->dSqrtLam, s->dS, seed, id_base,
                                          STREAM_INIT_ID, 0, m64, N, st);
       });
     }
     // m_r = E m0 (eq:projector), then the geometry at m_r
-    launch(ctx, "encode_f64", [&] {
+    launch(ctx, st, "encode_f64", [&] {
       return gemm_store<double>(C, r, N, m64, N, s->dE, N, p->b, r, st);
     });
     if (s->precision == DINO_PREC_FP64) {
       CK(cudaMemcpyAsync(p->m, m64, (size_t)C * N * 8, cudaMemcpyDeviceToDevice, st));
     } else {
-      launch(ctx, "convert", [&] {
+      launch(ctx, st, "convert", [&] {
         return launch_f64_to_f32((size_t)C * N, m64, (float *)p->m, st);
       });
     }
-    split_input(ctx, s, p->w, p->b);
-    eval_surrogate(ctx, s, p->w, p->b);
+    split_input(ctx, s, p->w, p->b, st);
+    eval_surrogate(ctx, s, p->w, p->b, st);
     ReducedArgs ra = reduced_args(*p);
-    launch(ctx, "geometry_init", [&] { return launch_geometry(ra, 0, st); });
-    CK(cudaStreamSynchronize(st));
+    launch(ctx, st, "geometry_init", [&] { return launch_geometry(ra, 0, st); });
+    if (!serving) CK(cudaStreamSynchronize(st));
   } catch (...) {
-    dev_free(ctx, p->ar.base, p->ar.bytes);
+    if (serving)
+      dev_free_async(ctx, p->ar.base, p->ar.bytes, st);
+    else
+      dev_free(ctx, p->ar.base, p->ar.bytes);
     throw;
   }
   s->pools += 1;
-  const int id = p->id;
-  ctx->pools[id] = std::move(p);
-  return id;
+  Pool *raw = p.get();
+  ctx->pools[p->id] = std::move(p);
+  return raw;
+}
+
+static int create_pool(dino_ctx *ctx, int sid, int C, double dt, uint64_t seed,
+                       uint64_t id_base, const double *m0) {
+  return create_pool_on(ctx, sid, C, dt, seed, id_base, m0, ctx->stream, false)->id;
+}
+
+static size_t pool_footprint(const Surrogate *s, int C) {
+  Pool p;
+  p.s = const_cast<Surrogate *>(s);
+  p.C = C;
+  layout_pool(p, false);
+  return p.ar.off;
 }
 
 // One transition of every chain of the pool.
 static void step_pool(dino_ctx *ctx, Pool &p) {
   const Surrogate *s = p.s;
   const int C = p.C, r = s->r, N = s->N;
-  cudaStream_t st = ctx->stream;
+  cudaStream_t st = p.st;
   const double cs = std::sqrt(1.0 - p.sc * p.sc);
   ReducedArgs ra = reduced_args(p);
-  launch(ctx, "propose", [&] { return launch_propose(ra, st); });
-  eval_surrogate(ctx, s, p.w, p.b);
-  launch(ctx, "geometry_accept", [&] { return launch_geometry(ra, 1, st); });
+  launch(ctx, st, "propose", [&] { return launch_propose(ra, st); });
+  eval_surrogate(ctx, s, p.w, p.b, st);
+  launch(ctx, st, "geometry_accept", [&] { return launch_geometry(ra, 1, st); });
   // complement (Prop. 5.1): M prior draw, coef2 = (b - s a) - cs E M, m <- s m + cs M + D coef2
   if (s->precision == DINO_PREC_FP64) {
     double *Mf = (double *)p.Mf, *coef2 = (double *)p.coef2, *m = (double *)p.m;
-    launch(ctx, "prior_draw_f64", [&] {
+    launch(ctx, st, "prior_draw_f64", [&] {
       return launch_prior_draw<double>(C, s->n_grid, s->dSqrtLam, s->dS, p.seed, p.id_base,
                                        STREAM_Z_ID, p.step, Mf, N, st);
     });
-    launch(ctx, "field_coef_f64", [&] {
+    launch(ctx, st, "field_coef_f64", [&] {
       return gemm_coef<double>(C, r, N, Mf, N, s->dE, N, p.coef, r, cs, coef2, r, st);
     });
-    launch(ctx, "field_update_f64", [&] {
+    launch(ctx, st, "field_update_f64", [&] {
       return gemm_field<double>(C, N, r, coef2, r, s->dD, r, p.acc, p.sc, cs, m, Mf, N, st);
     });
   } else {
     float *Mf = (float *)p.Mf, *coef2 = (float *)p.coef2, *m = (float *)p.m;
-    launch(ctx, "prior_draw_f32", [&] {
+    launch(ctx, st, "prior_draw_f32", [&] {
       return launch_prior_draw<float>(C, s->n_grid, s->fSqrtLam, s->fS, p.seed, p.id_base,
                                       STREAM_Z_ID, p.step, Mf, N, st);
     });
-    launch(ctx, "field_coef_f32", [&] {
+    launch(ctx, st, "field_coef_f32", [&] {
       return gemm_coef<float>(C, r, N, Mf, N, s->fE, N, p.coef, r, cs, coef2, r, st);
     });
-    launch(ctx, "field_update_f32", [&] {
+    launch(ctx, st, "field_update_f32", [&] {
       return gemm_field<float>(C, N, r, coef2, r, s->fD, r, p.acc, p.sc, cs, m, Mf, N, st);
     });
   }
@@ -981,8 +1033,12 @@ static void step_pool(dino_ctx *ctx, Pool &p) {
 
 static void destroy_pool(dino_ctx *ctx, int id) {
   Pool *p = get_pool(ctx, id);
-  cudaStreamSynchronize(ctx->stream);
-  dev_free(ctx, p->ar.base, p->ar.bytes);
+  if (p->async_mem) {
+    dev_free_async(ctx, p->ar.base, p->ar.bytes, p->st);
+  } else {
+    cudaStreamSynchronize(p->st);
+    dev_free(ctx, p->ar.base, p->ar.bytes);
+  }
   p->s->pools -= 1;
   ctx->pools.erase(id);
 }
@@ -1016,11 +1072,11 @@ static void surrogate_eval(dino_ctx *ctx, int sid, int n, const double *x_host, 
       CK(cudaMemcpyAsync(s->dy, yzero.data(), dy * 8, cudaMemcpyHostToDevice, st));
     }
     CK(cudaMemcpyAsync(p.b, x_host, (size_t)n * r * 8, cudaMemcpyHostToDevice, st));
-    split_input(ctx, s, p.w, p.b);
-    eval_surrogate(ctx, s, p.w, p.b);
+    split_input(ctx, s, p.w, p.b, st);
+    eval_surrogate(ctx, s, p.w, p.b, st);
     ReducedArgs ra = reduced_args(p);
     ra.noise_var = s->has_data ? s->noise_var : 1.0;
-    launch(ctx, "geometry_init", [&] { return launch_geometry(ra, 0, st); });
+    launch(ctx, st, "geometry_init", [&] { return launch_geometry(ra, 0, st); });
     CK(cudaStreamSynchronize(st));
     std::vector<double> tmp;
     auto fetch = [&](const void *src, size_t cnt, bool f32, double *dst) {
@@ -1056,6 +1112,279 @@ static void surrogate_eval(dino_ctx *ctx, int sid, int n, const double *x_host, 
   }
   s->dy = ysave;
   dev_free(ctx, p.ar.base, p.ar.bytes);
+}
+
+// ---------------------------------------------------------------------------
+// serving: continuous batching of chain ensembles
+//
+// A background thread owns admission and issue.  Requests wait in a FIFO
+// until their pool's device footprint fits the context's HBM budget; each
+// admitted request gets its own pool on one of several CUDA streams, and its
+// transitions are issued in rounds of `steps_per_round` with at most two
+// rounds in flight, so requests that arrive while others run join between
+// rounds and their kernels overlap on the device.  A request's results depend
+// only on its surrogate, seed, chain ids, step count and initial fields, not
+// on what else is running.
+
+static double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+struct Request {
+  uint64_t ticket = 0;
+  dino_request req{};
+  std::vector<double> m0;
+  size_t footprint = 0;
+  double t_submit = 0, t_admit = 0, t_done = 0;
+  int state = 0;  // 0 queued, 1 active, 2 done, 3 failed
+  int status = DINO_OK;
+  std::string err;
+  Pool *pool = nullptr;
+  int issued = 0;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  int ev_issued[2] = {0, 0};  // steps issued when each event was recorded
+  int in_flight = 0, next_ev = 0;
+  dino_step_stats stats{};
+};
+
+struct Server {
+  dino_ctx *ctx;
+  std::thread th;
+  std::condition_variable_any cv;
+  bool stop = false;
+  std::deque<Request *> queue;
+  std::vector<Request *> active;
+  std::map<uint64_t, std::unique_ptr<Request>> reqs;
+  std::vector<cudaStream_t> streams;
+  std::vector<int> load;          // resident requests per stream
+  std::vector<int> stream_rounds; // rounds in flight per stream
+  int steps_per_round = 8;
+  int max_active = 32;
+  size_t max_queue = 100000;
+  uint64_t next_ticket = 1;
+  int peak_active = 0;
+  size_t peak_used = 0;
+
+  Server(dino_ctx *c, int nstreams, int spr, int max_act)
+      : ctx(c), steps_per_round(spr), max_active(max_act) {
+    for (int k = 0; k < nstreams; ++k) {
+      cudaStream_t st;
+      CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+      streams.push_back(st);
+      load.push_back(0);
+      stream_rounds.push_back(0);
+    }
+    th = std::thread([this] { loop(); });
+  }
+
+  // After the thread has stopped: free the pools still resident (on their
+  // live streams), then the events and streams.
+  void release() {
+    for (auto &kv : reqs) {
+      Request *r = kv.second.get();
+      if (r->pool) {
+        const int id = r->pool->id;
+        cudaStreamSynchronize(r->pool->st);
+        try {
+          destroy_pool(ctx, id);
+        } catch (...) {
+        }
+        r->pool = nullptr;
+      }
+      for (cudaEvent_t e : r->ev)
+        if (e) cudaEventDestroy(e);
+      r->ev[0] = r->ev[1] = nullptr;
+    }
+    for (cudaStream_t st : streams) {
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+    }
+    streams.clear();
+  }
+
+  void fail_request(Request *r, int code, const std::string &msg) {
+    r->state = 3;
+    r->status = code;
+    r->err = msg;
+    r->t_done = now_s();
+    if (r->pool) {
+      const int id = r->pool->id;
+      for (size_t k = 0; k < streams.size(); ++k)
+        if (streams[k] == r->pool->st) {
+          load[k] -= 1;
+          stream_rounds[k] -= r->in_flight;
+        }
+      r->in_flight = 0;
+      cudaStreamSynchronize(r->pool->st);
+      try {
+        destroy_pool(ctx, id);
+      } catch (...) {
+      }
+      r->pool = nullptr;
+    }
+  }
+
+  void finish(Request *r) {
+    Pool *p = r->pool;
+    const int C = p->C, rr = p->s->r, N = p->s->N;
+    CK(cudaStreamSynchronize(p->st));
+    unsigned long long c[2];
+    double a = 0;
+    int err = 0;
+    CK(cudaMemcpy(c, p->counters, 16, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&a, p->sum_alpha, 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&err, p->err, 4, cudaMemcpyDeviceToHost));
+    if (err) fail(DINO_ETIMEOUT, "a device wait gave up (code %d)", err);
+    if (r->req.m_r_out)
+      CK(cudaMemcpy(r->req.m_r_out, p->mr, (size_t)C * rr * 8, cudaMemcpyDeviceToHost));
+    if (r->req.phi_out) CK(cudaMemcpy(r->req.phi_out, p->phi, (size_t)C * 8, cudaMemcpyDeviceToHost));
+    if (r->req.accepts_out)
+      CK(cudaMemcpy(r->req.accepts_out, p->acc_count, (size_t)C * 8, cudaMemcpyDeviceToHost));
+    if (r->req.m_out) {
+      if (p->s->precision == DINO_PREC_FP64) {
+        CK(cudaMemcpy(r->req.m_out, p->m, (size_t)C * N * 8, cudaMemcpyDeviceToHost));
+      } else {
+        std::vector<float> t((size_t)C * N);
+        CK(cudaMemcpy(t.data(), p->m, t.size() * 4, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < t.size(); ++i) r->req.m_out[i] = t[i];
+      }
+    }
+    r->stats.proposals = (uint64_t)C * (uint64_t)r->req.n_steps;
+    r->stats.accepts = c[0];
+    r->stats.nan_rejects = c[1];
+    r->stats.sum_alpha = a;
+    const int id = p->id;
+    for (size_t k = 0; k < streams.size(); ++k)
+      if (streams[k] == p->st) load[k] -= 1;
+    destroy_pool(ctx, id);
+    r->pool = nullptr;
+    r->state = 2;
+    r->t_done = now_s();
+  }
+
+  // One scheduling pass under the context lock; true when it did any work.
+  bool pass() {
+    bool did = false;
+    // completed rounds and requests
+    for (size_t k = 0; k < active.size();) {
+      Request *r = active[k];
+      bool removed = false;
+      while (r->in_flight > 0) {
+        const int slot = (r->next_ev + 2 - r->in_flight) % 2;
+        const cudaError_t q = cudaEventQuery(r->ev[slot]);
+        if (q == cudaErrorNotReady) break;
+        r->in_flight -= 1;
+        for (size_t j = 0; j < streams.size(); ++j)
+          if (r->pool && streams[j] == r->pool->st) stream_rounds[j] -= 1;
+        did = true;
+        if (q != cudaSuccess) {
+          cudaGetLastError();
+          fail_request(r, DINO_ECUDA, cudaGetErrorString(q));
+          removed = true;
+          break;
+        }
+      }
+      if (!removed && r->in_flight == 0 && r->issued >= r->req.n_steps) {
+        try {
+          finish(r);
+        } catch (const Error &e) {
+          fail_request(r, e.code, e.msg);
+        }
+        removed = true;
+        did = true;
+      }
+      if (removed) {
+        active.erase(active.begin() + k);
+      } else {
+        ++k;
+      }
+    }
+    // admission in arrival order while the head fits the budget
+    while (!queue.empty() && (int)active.size() < max_active) {
+      Request *r = queue.front();
+      if (ctx->used + r->footprint > ctx->budget) break;
+      queue.pop_front();
+      int k = 0;
+      for (size_t j = 1; j < streams.size(); ++j)
+        if (load[j] < load[k]) k = (int)j;
+      try {
+        r->pool = create_pool_on(ctx, r->req.surrogate_id, r->req.n_chains, r->req.dt,
+                                 r->req.seed, r->req.chain_id_base,
+                                 r->m0.empty() ? nullptr : r->m0.data(), streams[k], true);
+        load[k] += 1;
+        for (int e = 0; e < 2; ++e)
+          if (!r->ev[e]) CK(cudaEventCreateWithFlags(&r->ev[e], cudaEventDisableTiming));
+        r->state = 1;
+        r->t_admit = now_s();
+        active.push_back(r);
+      } catch (const Error &e) {
+        fail_request(r, e.code, e.msg);
+      }
+      did = true;
+    }
+    // issue rounds: at most two in flight per request and per stream, so the
+    // launch queues stay short and this thread never blocks in a launch
+    for (Request *r : active) {
+      if (r->in_flight >= 2 || r->issued >= r->req.n_steps) continue;
+      size_t sj = 0;
+      for (size_t j = 0; j < streams.size(); ++j)
+        if (streams[j] == r->pool->st) sj = j;
+      if (stream_rounds[sj] >= 2) continue;
+      const int k = std::min(steps_per_round, r->req.n_steps - r->issued);
+      try {
+        for (int s = 0; s < k; ++s) step_pool(ctx, *r->pool);
+      } catch (const Error &e) {
+        fail_request(r, e.code, e.msg);
+        continue;
+      }
+      r->issued += k;
+      CK(cudaEventRecord(r->ev[r->next_ev], r->pool->st));
+      r->next_ev ^= 1;
+      r->in_flight += 1;
+      stream_rounds[sj] += 1;
+      did = true;
+    }
+    active.erase(std::remove_if(active.begin(), active.end(),
+                                [](Request *r) { return r->state == 3; }),
+                 active.end());
+    peak_active = std::max(peak_active, (int)active.size());
+    peak_used = std::max(peak_used, ctx->used);
+    return did;
+  }
+
+  void loop() {
+    std::unique_lock<std::recursive_mutex> lk(ctx->mu);
+    cudaSetDevice(ctx->device);
+    while (!stop) {
+      bool did = false;
+      try {
+        did = pass();
+      } catch (...) {
+        did = false;
+      }
+      if (!did) {
+        cv.wait_for(lk, std::chrono::microseconds(200));
+      } else {
+        lk.unlock();
+        std::this_thread::yield();
+        lk.lock();
+      }
+    }
+  }
+};
+
+static void stop_server(dino_ctx *ctx) {
+  if (!ctx->server) return;
+  {
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    ctx->server->stop = true;
+  }
+  ctx->server->cv.notify_all();
+  if (ctx->server->th.joinable()) ctx->server->th.join();
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  ctx->server->release();
+  ctx->server.reset();
 }
 
 }  // namespace dino
@@ -1122,6 +1451,7 @@ int dino_init(dino_ctx **out, int device, size_t hbm_budget_bytes, void *stream,
 
 int dino_destroy(dino_ctx *ctx) {
   if (!ctx) return DINO_EINVAL;
+  stop_server(ctx);
   {
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     cudaSetDevice(ctx->device);
@@ -1219,18 +1549,18 @@ int dino_chains_step(dino_ctx *ctx, int pool_id, int n_steps, dino_step_stats *s
     unsigned long long c0[2] = {0, 0};
     double a0 = 0;
     if (stats) {
-      CK(cudaMemcpyAsync(c0, p->counters, 16, cudaMemcpyDeviceToHost, ctx->stream));
-      CK(cudaMemcpyAsync(&a0, p->sum_alpha, 8, cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaMemcpyAsync(c0, p->counters, 16, cudaMemcpyDeviceToHost, p->st));
+      CK(cudaMemcpyAsync(&a0, p->sum_alpha, 8, cudaMemcpyDeviceToHost, p->st));
     }
     for (int k = 0; k < n_steps; ++k) step_pool(ctx, *p);
     if (stats) {
       unsigned long long c1[2];
       double a1 = 0;
       int err = 0;
-      CK(cudaMemcpyAsync(c1, p->counters, 16, cudaMemcpyDeviceToHost, ctx->stream));
-      CK(cudaMemcpyAsync(&a1, p->sum_alpha, 8, cudaMemcpyDeviceToHost, ctx->stream));
-      CK(cudaMemcpyAsync(&err, p->err, 4, cudaMemcpyDeviceToHost, ctx->stream));
-      CK(cudaStreamSynchronize(ctx->stream));
+      CK(cudaMemcpyAsync(c1, p->counters, 16, cudaMemcpyDeviceToHost, p->st));
+      CK(cudaMemcpyAsync(&a1, p->sum_alpha, 8, cudaMemcpyDeviceToHost, p->st));
+      CK(cudaMemcpyAsync(&err, p->err, 4, cudaMemcpyDeviceToHost, p->st));
+      CK(cudaStreamSynchronize(p->st));
       if (err) fail(DINO_ETIMEOUT, "a device wait gave up (code %d); the pool state is invalid", err);
       stats->proposals = (uint64_t)p->C * (uint64_t)n_steps;
       stats->accepts = c1[0] - c0[0];
@@ -1248,8 +1578,8 @@ int dino_chains_read(dino_ctx *ctx, int pool_id, double *m, double *m_r, double 
     Pool *p = get_pool(ctx, pool_id);
     const int C = p->C, r = p->s->r, N = p->s->N;
     int err = 0;
-    CK(cudaMemcpyAsync(&err, p->err, 4, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpyAsync(&err, p->err, 4, cudaMemcpyDeviceToHost, p->st));
+    CK(cudaStreamSynchronize(p->st));
     if (err) fail(DINO_ETIMEOUT, "a device wait gave up (code %d); the pool state is invalid", err);
     if (m) {
       if (p->s->precision == DINO_PREC_FP64) {
@@ -1272,7 +1602,7 @@ int dino_chains_read_last(dino_ctx *ctx, int pool_id, double *b, double *mu, dou
     cudaSetDevice(ctx->device);
     Pool *p = get_pool(ctx, pool_id);
     const int C = p->C, r = p->s->r;
-    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaStreamSynchronize(p->st));
     if (b) CK(cudaMemcpy(b, p->b, (size_t)C * r * 8, cudaMemcpyDeviceToHost));
     if (mu) CK(cudaMemcpy(mu, p->mu, (size_t)C * r * 8, cudaMemcpyDeviceToHost));
     if (log_rho) CK(cudaMemcpy(log_rho, p->log_rho, (size_t)C * 8, cudaMemcpyDeviceToHost));
@@ -1307,6 +1637,88 @@ int dino_kernel_times(dino_ctx *ctx, char *names, double *total_ms, uint64_t *la
     }
     if (n) *n = (int)ctx->ktimes.size();
     if (reset) ctx->ktimes.clear();
+  });
+}
+
+int dino_serve_config(dino_ctx *ctx, int n_streams, int steps_per_round, int max_active) {
+  return guarded(ctx, [&] {
+    if (ctx->server) fail(DINO_ESTATE, "serving already started");
+    if (n_streams < 1 || n_streams > 32 || steps_per_round < 1 || max_active < 1)
+      fail(DINO_EINVAL, "n_streams in 1..32, steps_per_round >= 1, max_active >= 1");
+    cudaSetDevice(ctx->device);
+    ctx->server.reset(new Server(ctx, n_streams, steps_per_round, max_active));
+  });
+}
+
+int dino_serve_submit(dino_ctx *ctx, const dino_request *req, uint64_t *ticket) {
+  return guarded(ctx, [&] {
+    if (!req || !ticket) fail(DINO_EINVAL, "request and ticket must be non-NULL");
+    Surrogate *s = get_surrogate(ctx, req->surrogate_id);
+    if (!s->has_data) fail(DINO_ESTATE, "surrogate %d has no data", req->surrogate_id);
+    if (req->n_chains < 1 || req->n_steps < 0 || !(req->dt > 0))
+      fail(DINO_EINVAL, "n_chains >= 1, n_steps >= 0 and dt > 0 required");
+    cudaSetDevice(ctx->device);
+    if (!ctx->server) ctx->server.reset(new Server(ctx, 4, 8, 32));
+    Server &sv = *ctx->server;
+    if (sv.queue.size() >= sv.max_queue) fail(DINO_EBUSY, "serving queue is full");
+    auto r = std::make_unique<Request>();
+    r->ticket = sv.next_ticket++;
+    r->req = *req;
+    r->footprint = pool_footprint(s, req->n_chains);
+    if (r->footprint > ctx->budget)
+      fail(DINO_ENOMEM, "request needs %zu bytes, more than the whole HBM budget %zu",
+           r->footprint, ctx->budget);
+    if (req->m0) r->m0.assign(req->m0, req->m0 + (size_t)req->n_chains * s->N);
+    r->t_submit = now_s();
+    *ticket = r->ticket;
+    sv.queue.push_back(r.get());
+    sv.reqs[r->ticket] = std::move(r);
+    sv.cv.notify_all();
+  });
+}
+
+int dino_serve_poll(dino_ctx *ctx, uint64_t ticket, dino_result *res) {
+  int pending = 0;
+  const int rc = guarded(ctx, [&] {
+    if (!ctx->server) fail(DINO_ENOTFOUND, "no request has been submitted");
+    auto it = ctx->server->reqs.find(ticket);
+    if (it == ctx->server->reqs.end()) fail(DINO_ENOTFOUND, "unknown ticket %llu",
+                                            (unsigned long long)ticket);
+    Request *r = it->second.get();
+    if (r->state < 2) {
+      pending = 1;
+      return;
+    }
+    if (r->state == 3) fail(r->status, "request failed: %s", r->err.c_str());
+    if (res) {
+      res->stats = r->stats;
+      res->queue_s = r->t_admit - r->t_submit;
+      res->latency_s = r->t_done - r->t_submit;
+    }
+  });
+  return rc == DINO_OK && pending ? DINO_PENDING : rc;
+}
+
+int dino_serve_wait(dino_ctx *ctx, uint64_t ticket, double timeout_s, dino_result *res) {
+  if (!ctx) return DINO_EINVAL;
+  const double deadline = now_s() + (timeout_s > 0 ? timeout_s : 0.0);
+  while (true) {
+    const int rc = dino_serve_poll(ctx, ticket, res);
+    if (rc != DINO_PENDING) return rc;
+    if (now_s() >= deadline) return DINO_ETIMEOUT;
+    std::this_thread::sleep_for(std::chrono::microseconds(200));
+  }
+}
+
+int dino_serve_status(dino_ctx *ctx, int *queued, int *active, int *peak_active,
+                      size_t *hbm_used, size_t *peak_hbm_used) {
+  return guarded(ctx, [&] {
+    Server *sv = ctx->server.get();
+    if (queued) *queued = sv ? (int)sv->queue.size() : 0;
+    if (active) *active = sv ? (int)sv->active.size() : 0;
+    if (peak_active) *peak_active = sv ? sv->peak_active : 0;
+    if (hbm_used) *hbm_used = ctx->used;
+    if (peak_hbm_used) *peak_hbm_used = sv ? sv->peak_used : ctx->used;
   });
 }
 
