@@ -55,12 +55,13 @@ def geometry_traffic_per_chain(workload: str):
 
 
 def fp64_flops_geometry(r: int, d_y: int) -> float:
-    """Algorithmic FP64 flops of one geometry/accept launch per chain.
+    """Algorithmic FP64 flops of one geometry launch per chain.
 
-    Cholesky r^3/3, two triangular solves 2 r^2, three triangular matvecs 3 r^2,
-    gradient J^T res 2 r d_y (the Gauss-Newton product J^T J runs in FP32).
+    Cholesky of I + H, r^3/3, and the gradient J^T res, 2 r d_y (the
+    Gauss-Newton product J^T J runs in FP32; the log-ratio solves run in the
+    accept kernel).
     """
-    return r ** 3 / 3.0 + 5.0 * r * r + 2.0 * r * d_y
+    return r ** 3 / 3.0 + 2.0 * r * d_y
 
 
 class ClockSampler:
@@ -211,7 +212,7 @@ def run_ours(args, rank, world, device):
     flops = fp64_flops_geometry(w.r, w.d_y) * C
     achieved = flops / (geo_ms * 1e-3) / 1e12
     tpc = geometry_traffic_per_chain(args.workload)
-    roofline = {"bound": "alu", "pipe": "fp64", "kernel": "geometry_accept",
+    roofline = {"bound": "alu", "pipe": "fp64", "kernel": "geometry",
                 "achieved": round(achieved, 4), "peak": FP64_NOMINAL_TFLOPS,
                 "peak_source": "nominal GB300 FP64 (no measured FP64 peak in MEASURED_PEAKS.json); "
                                "a DFMA probe on this pool measured 1.19 TFLOP/s",

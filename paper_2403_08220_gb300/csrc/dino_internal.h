@@ -35,9 +35,13 @@ struct ReducedArgs {
   double *mr = nullptr, *g = nullptr, *phi = nullptr, *hld = nullptr, *L = nullptr;
   // proposal (written by propose, read by geometry)
   double *b = nullptr, *mu = nullptr, *lq_fwd = nullptr;
-  // per-chain factor workspace (C x l_stride(r)) used when r is too large for
-  // shared memory; nullptr otherwise
-  double *Lw = nullptr;
+  // the factor is double-buffered: slot cur[c] holds the chain's current
+  // factor, the other slot receives the factor at the proposal; accepting
+  // flips cur[c].  L_slot = elements between the slots (C * l_stride(r)).
+  int *cur = nullptr;
+  size_t L_slot = 0;
+  // geometry at the proposal, written by the geometry kernel for the accept kernel
+  double *g_c = nullptr, *phi_c = nullptr, *hld_c = nullptr;
   // surrogate output at b: J (C x d_y x r) and f (C x d_y), FP64 or FP32
   const void *J = nullptr;
   const void *f = nullptr;
@@ -61,8 +65,11 @@ bool uses_global_factor(int r, int d_y);
 size_t propose_smem_bytes(int r);
 size_t geometry_smem_bytes(int r, int d_y, int jf_f32);
 cudaError_t launch_propose(const ReducedArgs &a, cudaStream_t st);
-// mode 0: initialise the state at b (no accept); mode 1: MH step
+// mode 0: initialise the state at b; mode 1: geometry at the proposal into
+// the candidate slot and buffers
 cudaError_t launch_geometry(const ReducedArgs &a, int mode, cudaStream_t st);
+// log-acceptance with the candidate geometry, accept test and state update
+cudaError_t launch_accept(const ReducedArgs &a, cudaStream_t st);
 
 // ---- SIMT GEMMs: out = epilogue(A B^T), A: M x K (lda), B: N x K (ldb) ----
 template <typename T>

@@ -804,7 +804,8 @@ struct Pool {
   Arena ar;
   // state
   double *mr, *g, *phi, *hld, *L;
-  double *Lw;  // factor workspace when r is too large for shared memory
+  int *cur;  // per-chain slot (0/1) of the current factor in L
+  double *g_c, *phi_c, *hld_c;  // geometry at the proposal
   void *m;  // C x N, double (FP64 path) or float (tensor path)
   double *b, *mu, *lq_fwd, *coef, *log_rho, *log_u;
   int *acc;
@@ -830,8 +831,11 @@ static void layout_pool(Pool &p, bool assign) {
   p.g = (double *)take((size_t)C * r * 8);
   p.phi = (double *)take((size_t)C * 8);
   p.hld = (double *)take((size_t)C * 8);
-  p.L = (double *)take((size_t)C * l_stride(r) * 8);
-  p.Lw = uses_global_factor(r, s->d_y) ? (double *)take((size_t)C * l_stride(r) * 8) : nullptr;
+  p.L = (double *)take(2 * (size_t)C * l_stride(r) * 8);  // two slots
+  p.cur = (int *)take((size_t)C * 4);
+  p.g_c = (double *)take((size_t)C * r * 8);
+  p.phi_c = (double *)take((size_t)C * 8);
+  p.hld_c = (double *)take((size_t)C * 8);
   p.m = take((size_t)C * N * fe);
   p.b = (double *)take((size_t)C * r * 8);
   p.mu = (double *)take((size_t)C * r * 8);
@@ -873,7 +877,11 @@ static ReducedArgs reduced_args(const Pool &p) {
   a.phi = p.phi;
   a.hld = p.hld;
   a.L = p.L;
-  a.Lw = p.Lw;
+  a.cur = p.cur;
+  a.L_slot = (size_t)p.C * l_stride(s->r);
+  a.g_c = p.g_c;
+  a.phi_c = p.phi_c;
+  a.hld_c = p.hld_c;
   a.b = p.b;
   a.mu = p.mu;
   a.lq_fwd = p.lq_fwd;
@@ -940,6 +948,7 @@ static Pool *create_pool_on(dino_ctx *ctx, int sid, int C, double dt, uint64_t s
     CK(cudaMemsetAsync(p->counters, 0, 16, st));
     CK(cudaMemsetAsync(p->sum_alpha, 0, 8, st));
     CK(cudaMemsetAsync(p->err, 0, 16, st));
+    CK(cudaMemsetAsync(p->cur, 0, (size_t)C * 4, st));
     CK(cudaMemsetAsync(p->acc, 0, (size_t)C * 4, st));
     double *m64 = (double *)p->Mf;  // FP64 initial field
     if (m0) {
@@ -1001,7 +1010,8 @@ static void step_pool(dino_ctx *ctx, Pool &p) {
   ReducedArgs ra = reduced_args(p);
   launch(ctx, st, "propose", [&] { return launch_propose(ra, st); });
   eval_surrogate(ctx, s, p.w, p.b, st);
-  launch(ctx, st, "geometry_accept", [&] { return launch_geometry(ra, 1, st); });
+  launch(ctx, st, "geometry", [&] { return launch_geometry(ra, 1, st); });
+  launch(ctx, st, "accept", [&] { return launch_accept(ra, st); });
   // complement (Prop. 5.1): M prior draw, coef2 = (b - s a) - cs E M, m <- s m + cs M + D coef2
   if (s->precision == DINO_PREC_FP64) {
     double *Mf = (double *)p.Mf, *coef2 = (double *)p.coef2, *m = (double *)p.m;
@@ -1065,6 +1075,7 @@ static void surrogate_eval(dino_ctx *ctx, int sid, int n, const double *x_host, 
     layout_pool(p, true);
     cudaStream_t st = ctx->stream;
     CK(cudaMemsetAsync(p.err, 0, 16, st));
+    CK(cudaMemsetAsync(p.cur, 0, (size_t)n * 4, st));
     if (!s->has_data) {
       // geometry needs some data vector: evaluate against zeros (phi and g then meaningless)
       yzero.assign(dy, 0.0);

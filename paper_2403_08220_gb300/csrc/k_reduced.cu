@@ -424,11 +424,12 @@ __global__ void __launch_bounds__(kThreads) k_propose(ReducedArgs a) {
   const int c = blockIdx.x, r = a.r;
   const size_t ldL = l_stride(r);
   const Layout lay(r, 0, ldL, G);
-  double *Ls = G ? a.L + (size_t)c * ldL : sm + lay.Ls;
+  double *Lcur = a.L + (size_t)a.cur[c] * a.L_slot + (size_t)c * ldL;
+  double *Ls = G ? Lcur : sm + lay.Ls;
   double *inv = sm + lay.inv;
   double *va = sm + lay.v0, *vg = va + r, *vv = vg + r, *vx = vv + r, *vp = vx + r, *vq = vp + r;
   double *red = sm + lay.red;
-  if (!G && !cta_bulk_load(Ls, a.L + (size_t)c * ldL, (uint32_t)(ldL * 8),
+  if (!G && !cta_bulk_load(Ls, Lcur, (uint32_t)(ldL * 8),
                            reinterpret_cast<uint64_t *>(sm + lay.mbar),
                            reinterpret_cast<int *>(sm + lay.flag), a.err))
     return;
@@ -595,7 +596,7 @@ __global__ void __launch_bounds__(32 * kPropWarps) k_propose_warp(ReducedArgs a)
   const int c = blockIdx.x * kPropWarps + w;
   if (c >= a.C) return;  // whole warp
   const int r = a.r;
-  const double *L = a.L + (size_t)c * l_stride(r);
+  const double *L = a.L + (size_t)a.cur[c] * a.L_slot + (size_t)c * l_stride(r);
   const uint32_t chain = (uint32_t)(a.id_base + (uint64_t)c);
   for (int blk = lane; blk < (r + 3) / 4; blk += 32) {
     double n4[4];
@@ -761,23 +762,26 @@ __device__ void form_h_f32(const float *J, int dy, int r, double inv_nv, double 
   __syncthreads();
 }
 
-// G = false: the factor is built in shared memory; G = true (large r): in the
-// chain's slot of the global workspace a.Lw.
+// G = false: the factor is built in shared memory and copied to its slot;
+// G = true (large r): built directly in its global slot.  Mode 0 writes the
+// chain state (slot cur[c]); mode 1 writes the geometry at the proposal into
+// the other slot and the candidate buffers, for the accept kernel.
 template <typename TJ, bool G>
 __global__ void __launch_bounds__(kThreads) k_geometry(ReducedArgs a, int mode) {
   extern __shared__ __align__(16) double sm[];
   const int c = blockIdx.x, r = a.r, dy = a.d_y;
   const size_t ldL = l_stride(r);
   const Layout lay(r, dy, ldL, G);
-  double *Ls = G ? a.Lw + (size_t)c * ldL : sm + lay.Ls;
+  const int slot = mode == 0 ? a.cur[c] : 1 - a.cur[c];
+  double *Lg = a.L + (size_t)slot * a.L_slot + (size_t)c * ldL;
+  double *Ls = G ? Lg : sm + lay.Ls;
   double *inv = sm + lay.inv;
-  double *vb = sm + lay.v0, *vg = vb + r, *va = vg + r, *vv = va + r, *vp = vv + r, *vq = vp + r;
+  double *vb = sm + lay.v0, *vg = vb + r;
   double *res = sm + lay.res;
   double *red = sm + lay.red;
   const TJ *J = reinterpret_cast<const TJ *>(a.J) + (size_t)c * dy * r;
   const TJ *f = reinterpret_cast<const TJ *>(a.f) + (size_t)c * dy;
   const double inv_nv = 1.0 / a.noise_var;
-  const double phi_a = mode ? a.phi[c] : 0.0;  // read before any thread may overwrite it
 
   for (int i = threadIdx.x; i < r; i += blockDim.x) vb[i] = a.b[(size_t)c * r + i];
   double ph = 0.0;
@@ -809,55 +813,149 @@ __global__ void __launch_bounds__(kThreads) k_geometry(ReducedArgs a, int mode) 
   for (int i = threadIdx.x; i < r; i += blockDim.x) ld += log(Ls[tri(i) + i]);
   const double hld_b = block_sum(ld, red);
 
-  double *Lg = a.L + (size_t)c * ldL;
-  const int lsz = tri(r);
-  if (mode == 0) {
+  if (!G) {
+    const int lsz = tri(r);
     for (int e = threadIdx.x; e < lsz; e += blockDim.x) Lg[e] = Ls[e];
-    for (int i = threadIdx.x; i < r; i += blockDim.x) {
-      a.g[(size_t)c * r + i] = vg[i];
-      a.mr[(size_t)c * r + i] = vb[i];
-    }
-    if (threadIdx.x == 0) {
-      a.phi[c] = phi_b;
-      a.hld[c] = hld_b;
-    }
-    return;
   }
-
-  // log rho_{0,r}(b -> a) with the geometry at b
+  double *gout = mode == 0 ? a.g : a.g_c;
   for (int i = threadIdx.x; i < r; i += blockDim.x) {
-    va[i] = a.mr[(size_t)c * r + i];
-    vv[i] = vb[i] + vg[i];
+    gout[(size_t)c * r + i] = vg[i];
+    if (mode == 0) a.mr[(size_t)c * r + i] = vb[i];
   }
-  __syncthreads();
-  cta_lower_solve(Ls, inv, r, vv);
-  cta_upper_solve(Ls, inv, r, vv);  // vv = (I+H_b)^-1 (b + g_b)
-  const double lq_rev = log_rho0(Ls, r, vb, vg, vv, va, hld_b, a.s, a.dt, vp, vq, red);
-  const double lr = phi_a - phi_b + lq_rev - a.lq_fwd[c];
+  if (threadIdx.x == 0) {
+    (mode == 0 ? a.phi : a.phi_c)[c] = phi_b;
+    (mode == 0 ? a.hld : a.hld_c)[c] = hld_b;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Accept: log rho_{0,r}(b -> a) with the candidate factor, log rho_r^(1)
+// (eq:da_dino_trr_1), the test log u <= min(0, log rho) (Alg. 1 line 6) and
+// the state update.  Warp per chain like the proposal; an accepted chain
+// takes the candidate factor by flipping its slot index.
+
+__device__ __forceinline__ void accept_tail(const ReducedArgs &a, int c, double lr) {
+  // lane-0 bookkeeping shared by the warp and CTA variants; returns via a.acc
   const uint32_t chain = (uint32_t)(a.id_base + (uint64_t)c);
   const double log_u = log(word_to_uniform(philox_block(a.seed, STREAM_U, a.step, chain, 0).x));
   const bool finite = isfinite(lr);
   const bool accept = finite && log_u <= fmin(0.0, lr);
-  for (int i = threadIdx.x; i < r; i += blockDim.x)
-    a.coef[(size_t)c * r + i] = vb[i] - a.s * va[i];
-  if (threadIdx.x == 0) {
-    a.log_rho[c] = lr;
-    a.log_u[c] = log_u;
-    a.acc[c] = accept ? 1 : 0;
-    if (accept) {
-      a.acc_count[c] += 1;
-      atomicAdd(&a.counters[0], 1ull);
-      a.phi[c] = phi_b;
-      a.hld[c] = hld_b;
-    }
-    if (!finite) atomicAdd(&a.counters[1], 1ull);
-    atomicAdd(a.sum_alpha, finite ? exp(fmin(0.0, lr)) : 0.0);
-  }
+  a.log_rho[c] = lr;
+  a.log_u[c] = log_u;
+  a.acc[c] = accept ? 1 : 0;
   if (accept) {
-    for (int e = threadIdx.x; e < lsz; e += blockDim.x) Lg[e] = Ls[e];
-    for (int i = threadIdx.x; i < r; i += blockDim.x) {
-      a.g[(size_t)c * r + i] = vg[i];
+    a.acc_count[c] += 1;
+    atomicAdd(&a.counters[0], 1ull);
+    a.phi[c] = a.phi_c[c];
+    a.hld[c] = a.hld_c[c];
+    a.cur[c] ^= 1;
+  }
+  if (!finite) atomicAdd(&a.counters[1], 1ull);
+  atomicAdd(a.sum_alpha, finite ? exp(fmin(0.0, lr)) : 0.0);
+}
+
+template <int S>
+__global__ void __launch_bounds__(32 * kPropWarps) k_accept_warp(ReducedArgs a) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int c = blockIdx.x * kPropWarps + w;
+  if (c >= a.C) return;  // whole warp
+  const int r = a.r;
+  const double *L = a.L + (size_t)(1 - a.cur[c]) * a.L_slot + (size_t)c * l_stride(r);
+  double va[S], vb[S], vg[S], vv[S], vp[S], vq[S], invd[S];
+  const double s_ = a.s, cs = sqrt(1.0 - s_ * s_);
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int i = 32 * s + lane;
+    const bool in = i < r;
+    va[s] = in ? a.mr[(size_t)c * r + i] : 0.0;
+    vb[s] = in ? a.b[(size_t)c * r + i] : 0.0;
+    vg[s] = in ? a.g_c[(size_t)c * r + i] : 0.0;
+    vv[s] = vb[s] + vg[s];
+    invd[s] = in ? 1.0 / L[tri(i) + i] : 0.0;
+  }
+  warp_lower_solve<S>(L, r, invd, vv);
+  warp_upper_solve<S>(L, r, invd, vv);  // vv = (I+H_b)^-1 (b + g_b)
+  warp_upper_matvec<S>(L, r, vb, vp);   // p = L^T b
+  warp_lower_matvec<S>(L, r, vp, vq);   // q = (I+H_b) b
+  double t1 = 0.0, t2 = 0.0, nm = 0.0;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int i = 32 * s + lane;
+    if (i < r) {
+      const double wv = vq[s] - vb[s] - vg[s];       // w = H_b b - g_b
+      const double mh = (va[s] - s_ * vb[s]) / cs;   // mhat for b -> a
+      t1 += wv * (vb[s] - vv[s]);
+      t2 += mh * wv;
+      nm += mh * mh;
+      vp[s] = mh;
+    } else {
+      vp[s] = 0.0;
+    }
+  }
+  t1 = warp_sum(t1);
+  t2 = warp_sum(t2);
+  nm = warp_sum(nm);
+  warp_upper_matvec<S>(L, r, vp, vq);  // q = L^T mhat
+  double t3 = 0.0;
+#pragma unroll
+  for (int s = 0; s < S; ++s) t3 += vq[s] * vq[s];
+  t3 = warp_sum(t3) - nm;
+  const double lq_rev = -a.dt / 8.0 * t1 + sqrt(a.dt) / 2.0 * t2 + a.hld_c[c] - 0.5 * t3;
+  const double lr = a.phi[c] - a.phi_c[c] + lq_rev - a.lq_fwd[c];
+  __syncwarp();
+  int accept = 0;
+  if (lane == 0) {
+    accept_tail(a, c, lr);
+    accept = a.acc[c];
+  }
+  accept = __shfl_sync(kFull, accept, 0);
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int i = 32 * s + lane;
+    if (i < r) {
+      a.coef[(size_t)c * r + i] = vb[s] - s_ * va[s];
+      if (accept) {
+        a.mr[(size_t)c * r + i] = vb[s];
+        a.g[(size_t)c * r + i] = vg[s];
+      }
+    }
+  }
+}
+
+// CTA variant for r beyond the register-resident warp kernel (factor in global memory).
+__global__ void __launch_bounds__(kThreads) k_accept_cta(ReducedArgs a) {
+  extern __shared__ __align__(16) double sm[];
+  const int c = blockIdx.x, r = a.r;
+  const Layout lay(r, 0, l_stride(r), true);
+  const double *Ls = a.L + (size_t)(1 - a.cur[c]) * a.L_slot + (size_t)c * l_stride(r);
+  double *inv = sm + lay.inv;
+  double *va = sm + lay.v0, *vb = va + r, *vg = vb + r, *vv = vg + r, *vp = vv + r, *vq = vp + r;
+  double *red = sm + lay.red;
+  for (int i = threadIdx.x; i < r; i += blockDim.x) {
+    va[i] = a.mr[(size_t)c * r + i];
+    vb[i] = a.b[(size_t)c * r + i];
+    vg[i] = a.g_c[(size_t)c * r + i];
+    vv[i] = vb[i] + vg[i];
+    inv[i] = 1.0 / Ls[tri(i) + i];
+  }
+  __syncthreads();
+  cta_lower_solve(Ls, inv, r, vv);
+  cta_upper_solve(Ls, inv, r, vv);
+  const double phi_a = a.phi[c];  // read before thread 0 may overwrite it
+  const double lq_rev = log_rho0(Ls, r, vb, vg, vv, va, a.hld_c[c], a.s, a.dt, vp, vq, red);
+  const double lr = phi_a - a.phi_c[c] + lq_rev - a.lq_fwd[c];
+  int *flag = reinterpret_cast<int *>(sm + lay.flag);
+  if (threadIdx.x == 0) {
+    accept_tail(a, c, lr);
+    *flag = a.acc[c];
+  }
+  __syncthreads();
+  const int accept = *flag;
+  for (int i = threadIdx.x; i < r; i += blockDim.x) {
+    a.coef[(size_t)c * r + i] = vb[i] - a.s * va[i];
+    if (accept) {
       a.mr[(size_t)c * r + i] = vb[i];
+      a.g[(size_t)c * r + i] = vg[i];
     }
   }
 }
@@ -918,10 +1016,27 @@ static cudaError_t launch_geometry_t(const ReducedArgs &a, int mode, size_t smem
   return cudaGetLastError();
 }
 
+cudaError_t launch_accept(const ReducedArgs &a, cudaStream_t st) {
+  if (a.r <= 32 * 7) {
+    const int grid = (a.C + kPropWarps - 1) / kPropWarps;
+    if (a.r <= 32 * 2)
+      k_accept_warp<2><<<grid, 32 * kPropWarps, 0, st>>>(a);
+    else
+      k_accept_warp<7><<<grid, 32 * kPropWarps, 0, st>>>(a);
+    return cudaGetLastError();
+  }
+  const Layout lay(a.r, 0, l_stride(a.r), true);
+  const size_t smem = lay.tail * sizeof(double);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_accept_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_accept_cta<<<a.C, kThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_geometry(const ReducedArgs &a, int mode, cudaStream_t st) {
   const size_t smem = geometry_smem_bytes(a.r, a.d_y, a.jf_f32);
   const bool G = uses_global_factor(a.r, a.d_y);
-  if (G && !a.Lw) return cudaErrorInvalidValue;
   if (a.jf_f32)
     return G ? launch_geometry_t<float, true>(a, mode, smem, st)
              : launch_geometry_t<float, false>(a, mode, smem, st);
