@@ -57,11 +57,11 @@ def geometry_traffic_per_chain(workload: str):
 def fp64_flops_geometry(r: int, d_y: int) -> float:
     """Algorithmic FP64 flops of one geometry launch per chain.
 
-    Cholesky of I + H, r^3/3, and the gradient J^T res, 2 r d_y (the
-    Gauss-Newton product J^T J runs in FP32; the log-ratio solves run in the
-    accept kernel).
+    Cholesky of I + H bordered by one row, (r+1)^3/3; the products L^T b and
+    L^T a of the reverse density, 2 r^2; the gradient J^T res, 2 r d_y.  The
+    Gauss-Newton product J^T J runs in FP32 and is not counted.
     """
-    return r ** 3 / 3.0 + 2.0 * r * d_y
+    return (r + 1) ** 3 / 3.0 + 2.0 * r * r + 2.0 * r * d_y
 
 
 class ClockSampler:
@@ -207,7 +207,7 @@ def run_ours(args, rank, world, device):
     ctx_t.close()
     total = sum(v[0] for v in kt.values()) or 1.0
     dom = max(kt.items(), key=lambda kv: kv[1][0])
-    geo = kt.get("geometry_accept", dom[1])
+    geo = kt.get("geometry", dom[1])
     geo_ms = geo[0] / max(1, geo[1])
     flops = fp64_flops_geometry(w.r, w.d_y) * C
     achieved = flops / (geo_ms * 1e-3) / 1e12

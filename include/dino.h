@@ -2,8 +2,8 @@
  * dino.h -- C ABI of the many-chain surrogate (DINO) mMALA sampler for GB300.
  *
  * One transition of C independent chains of surrogate-driven mMALA with
- * surrogate-only acceptance (Algorithm 1 lines 1-6 of Cao, O'Leary-Roseberry
- * and Ghattas, "Derivative-informed neural operator acceleration of geometric
+ * surrogate-only acceptance (the surrogate stage of Algorithm 1 of Cao,
+ * O'Leary-Roseberry and Ghattas, "Derivative-informed neural operator acceleration of geometric
  * MCMC for infinite-dimensional Bayesian inverse problems"), with the
  * prior-complement draw of Proposition 5.1 (Sec. 5.3) applied to every
  * proposal so that accepted chains move their full parameter field.
@@ -158,7 +158,7 @@ int dino_unload_surrogate(dino_ctx *ctx, int surrogate_id);
 int dino_read_basis(dino_ctx *ctx, int surrogate_id, double *E, double *D);
 
 /* Evaluate the surrogate and its geometry at n reduced points m_r (n x r,
- * host) with the surrogate's precision path (Sec. 5.1; Alg. 1 lines 3-4):
+ * host) with the surrogate's precision path (Sec. 5.1; Algorithm 1):
  *   f (n x d_y), J (n x d_y x r), phi (n), g (n x r),
  *   L (n x r x r, full lower-triangular with zeros above), hld (n).
  * Any output may be NULL.  With y unset, phi and g are not defined. */

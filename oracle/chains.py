@@ -2,11 +2,11 @@
 
 TEST INFRASTRUCTURE ONLY (see `oracle/__init__.py`).
 
-One step is one transition of every chain: Alg. 1 lines 1-6 (reduced proposal,
-surrogate evaluation, first-stage acceptance with rho_r^(1)) with the
-complement drawn as in Prop. 5.1 so that an accepted chain moves its full
-field m to m^dagger (Alg. 1 lines 7-8).  There is no second stage: the target
-is the surrogate posterior.
+One step is one transition of every chain: the surrogate stage of
+Algorithm 1 (reduced proposal, surrogate evaluation, first-stage acceptance
+with rho_r^(1)) with the complement drawn as in Prop. 5.1, so that an
+accepted chain moves its full field m to m^dagger.  There is no second stage:
+the target is the surrogate posterior.
 
 Random numbers (see `philox`): step j of chain c uses XI(j, c) for the r
 reduced normals, U(j, c) for the accept uniform and Z(j, c) for the N normals

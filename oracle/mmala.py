@@ -69,7 +69,7 @@ class Geometry:
 
 
 def geometry(sur: Surrogate, m_r) -> Geometry:
-    """Misfit, gradient, Gauss-Newton Hessian and its factor at m_r (Sec. 5.1, Alg. 1 lines 3-4)."""
+    """Misfit, gradient, Gauss-Newton Hessian and its factor at m_r (Sec. 5.1; the geometry step of Algorithm 1)."""
     m_r = np.asarray(m_r, dtype=np.float64)
     f, zs = mlp.forward(sur.Ws, sur.bs, sur.act, m_r)
     if len(sur.Ws) == 1:
@@ -145,7 +145,7 @@ def log_rho(a, geo_a: Geometry, b, geo_b: Geometry, dt: float):
 
 
 def accept(log_u, log_rho_val):
-    """Alg. 1 line 6: accept iff alpha >= u, i.e. log u <= min(0, log rho); NaN rejects."""
+    """The accept test of Algorithm 1: accept iff alpha >= u, i.e. log u <= min(0, log rho); NaN rejects."""
     lr = np.asarray(log_rho_val)
     return np.isfinite(lr) & (np.asarray(log_u) <= np.minimum(0.0, lr))
 

@@ -16,9 +16,9 @@ by u = (x + 1/2) 2^-32 (exact in float64); (u0, u1) and (u2, u3) give two
 pairs of standard normals by the Box-Muller transform, so block k carries the
 normals 4k .. 4k+3.
 
-Streams: XI (reduced proposal noise, Alg. 1 line 1), U (the accept uniform,
-Alg. 1 line 6), Z (prior draw for the complement, Prop. 5.1 / Alg. 1 line 7),
-INIT (prior draw of the initial state).
+Streams: XI (reduced proposal noise of Algorithm 1), U (the uniform of its
+accept test), Z (prior draw for the complement, Prop. 5.1), INIT (prior draw
+of the initial state).
 """
 from __future__ import annotations
 

@@ -20,10 +20,13 @@ constexpr size_t kSmemLimit = 227 * 1024;   // opt-in shared memory per CTA
 constexpr uint32_t STREAM_XI_ID = 0, STREAM_U_ID = 1, STREAM_Z_ID = 2, STREAM_INIT_ID = 3;
 
 inline __host__ __device__ size_t tri_size(int r) { return (size_t)r * (r + 1) / 2; }
-// Per-chain stride of the packed factor in global memory: rounded up to an
-// even number of doubles so that every chain's factor starts on 16 bytes
-// (the alignment bulk copies need).
-inline __host__ __device__ size_t l_stride(int r) { return (tri_size(r) + 1) & ~(size_t)1; }
+// Per-chain factor slot in global memory: the packed lower Cholesky factor
+// of I + H bordered by the row (m_r + g)^T (r + 1 rows; row r holds
+// L^-1 (m_r + g)), then p = L^T m_r (r doubles); rounded up to an even number
+// of doubles so that every slot starts on 16 bytes.
+inline __host__ __device__ size_t slot_stride(int r) {
+  return (tri_size(r + 1) + r + 1) & ~(size_t)1;
+}
 
 // ---- per-chain reduced-space kernels (FP64) -----------------------------
 struct ReducedArgs {
@@ -35,13 +38,11 @@ struct ReducedArgs {
   double *mr = nullptr, *g = nullptr, *phi = nullptr, *hld = nullptr, *L = nullptr;
   // proposal (written by propose, read by geometry)
   double *b = nullptr, *mu = nullptr, *lq_fwd = nullptr;
-  // the factor is double-buffered: slot cur[c] holds the chain's current
-  // factor, the other slot receives the factor at the proposal; accepting
-  // flips cur[c].  L_slot = elements between the slots (C * l_stride(r)).
+  // the factor slot is double-buffered: slot cur[c] holds the chain's
+  // current one; an accepted proposal's slot is written into the other and
+  // cur[c] flips.  L_slot = elements between the slots (C * slot_stride(r)).
   int *cur = nullptr;
   size_t L_slot = 0;
-  // geometry at the proposal, written by the geometry kernel for the accept kernel
-  double *g_c = nullptr, *phi_c = nullptr, *hld_c = nullptr;
   // surrogate output at b: J (C x d_y x r) and f (C x d_y), FP64 or FP32
   const void *J = nullptr;
   const void *f = nullptr;
@@ -65,11 +66,9 @@ bool uses_global_factor(int r, int d_y);
 size_t propose_smem_bytes(int r);
 size_t geometry_smem_bytes(int r, int d_y, int jf_f32);
 cudaError_t launch_propose(const ReducedArgs &a, cudaStream_t st);
-// mode 0: initialise the state at b; mode 1: geometry at the proposal into
-// the candidate slot and buffers
+// mode 0: initialise the state at b; mode 1: geometry at the proposal b,
+// log-acceptance, accept test and state update
 cudaError_t launch_geometry(const ReducedArgs &a, int mode, cudaStream_t st);
-// log-acceptance with the candidate geometry, accept test and state update
-cudaError_t launch_accept(const ReducedArgs &a, cudaStream_t st);
 
 // ---- SIMT GEMMs: out = epilogue(A B^T), A: M x K (lda), B: N x K (ldb) ----
 template <typename T>

@@ -805,7 +805,6 @@ struct Pool {
   // state
   double *mr, *g, *phi, *hld, *L;
   int *cur;  // per-chain slot (0/1) of the current factor in L
-  double *g_c, *phi_c, *hld_c;  // geometry at the proposal
   void *m;  // C x N, double (FP64 path) or float (tensor path)
   double *b, *mu, *lq_fwd, *coef, *log_rho, *log_u;
   int *acc;
@@ -831,11 +830,8 @@ static void layout_pool(Pool &p, bool assign) {
   p.g = (double *)take((size_t)C * r * 8);
   p.phi = (double *)take((size_t)C * 8);
   p.hld = (double *)take((size_t)C * 8);
-  p.L = (double *)take(2 * (size_t)C * l_stride(r) * 8);  // two slots
+  p.L = (double *)take(2 * (size_t)C * slot_stride(r) * 8);  // two slots
   p.cur = (int *)take((size_t)C * 4);
-  p.g_c = (double *)take((size_t)C * r * 8);
-  p.phi_c = (double *)take((size_t)C * 8);
-  p.hld_c = (double *)take((size_t)C * 8);
   p.m = take((size_t)C * N * fe);
   p.b = (double *)take((size_t)C * r * 8);
   p.mu = (double *)take((size_t)C * r * 8);
@@ -878,10 +874,7 @@ static ReducedArgs reduced_args(const Pool &p) {
   a.hld = p.hld;
   a.L = p.L;
   a.cur = p.cur;
-  a.L_slot = (size_t)p.C * l_stride(s->r);
-  a.g_c = p.g_c;
-  a.phi_c = p.phi_c;
-  a.hld_c = p.hld_c;
+  a.L_slot = (size_t)p.C * slot_stride(s->r);
   a.b = p.b;
   a.mu = p.mu;
   a.lq_fwd = p.lq_fwd;
@@ -1011,7 +1004,6 @@ static void step_pool(dino_ctx *ctx, Pool &p) {
   launch(ctx, st, "propose", [&] { return launch_propose(ra, st); });
   eval_surrogate(ctx, s, p.w, p.b, st);
   launch(ctx, st, "geometry", [&] { return launch_geometry(ra, 1, st); });
-  launch(ctx, st, "accept", [&] { return launch_accept(ra, st); });
   // complement (Prop. 5.1): M prior draw, coef2 = (b - s a) - cs E M, m <- s m + cs M + D coef2
   if (s->precision == DINO_PREC_FP64) {
     double *Mf = (double *)p.Mf, *coef2 = (double *)p.coef2, *m = (double *)p.m;
@@ -1107,7 +1099,7 @@ static void surrogate_eval(dino_ctx *ctx, int sid, int n, const double *x_host, 
     fetch(p.g, (size_t)n * r, false, g);
     fetch(p.hld, n, false, hld);
     if (Lfull) {
-      const size_t ts = l_stride(r);
+      const size_t ts = slot_stride(r);
       std::vector<double> packed((size_t)n * ts);
       CK(cudaMemcpy(packed.data(), p.L, packed.size() * 8, cudaMemcpyDeviceToHost));
       for (int c = 0; c < n; ++c)

@@ -1,27 +1,35 @@
 // Per-chain reduced-space kernels of the surrogate mMALA step, in FP64.
 //
-// One CTA per chain keeps the packed lower Cholesky factor L of I + H
-// (r (r+1)/2 doubles, row-major: entry (i, j), j <= i, at i (i+1)/2 + j) in
-// shared memory and runs every r x r operation of the step on it:
+// Besides m_r, g, Phi and half log det(I + H), each chain keeps one factor
+// slot: the packed lower Cholesky factor (row-major, entry (i, j), j <= i, at
+// i (i+1)/2 + j) of I + H bordered below by the row (m_r + g)^T, so that its
+// row r holds t = L^-1 (m_r + g); then p = L^T m_r.
 //
-//   k_propose   reduced proposal (eq:reduced_space_sampling in Cholesky form)
+//   k_propose_warp / k_propose
+//               reduced proposal (eq:reduced_space_sampling in Cholesky form)
 //               m_r^dag = mu + sqrt(1-s^2) L^-T xi,
-//               mu = m_r - (1-s) (I+H)^-1 (m_r + g),
-//               and log rho_{0,r}(m_r, m_r^dag) with the geometry at m_r (Sec. 5.4).
-//   k_geometry  misfit, gradient, H = J^T J / noise_var + I, its Cholesky
-//               factor and half log-determinant at m_r^dag (Alg. 1 lines 3-4),
-//               log rho_{0,r}(m_r^dag, m_r), log rho_r^(1) (eq:da_dino_trr_1),
-//               the accept test (Alg. 1 line 6) and the state update.
+//               mu = m_r - (1-s) (I+H)^-1 (m_r + g) = m_r - (1-s) L^-T t,
+//               both from one two-column back substitution, and
+//               log rho_{0,r}(m_r, m_r^dag) with the geometry at m_r (Sec. 5.4).
+//   k_geometry  misfit, gradient, H = J^T J / noise_var + I and the bordered
+//               factor at m_r^dag (Algorithm 1), log rho_{0,r}(m_r^dag, m_r),
+//               log rho_r^(1) (eq:da_dino_trr_1), the accept test and the
+//               state update.
 //
-// Identities used with L L^T = I + H (exact in real arithmetic):
-//   (I+H)^-1 w_a = a - v_a     for w_a = H a - g_a, v_a = (I+H)^-1 (a + g_a),
-//   H x = L (L^T x) - x,       x^T H x = |L^T x|^2 - |x|^2.
+// With L L^T = I + H, w = H x - g, mhat = (z - s x) / sqrt(1-s^2) for a move
+// x -> z, t = L^-1 (x + g) and p = L^T x (exact in real arithmetic):
+//   w^T (I+H)^-1 w = |p - t|^2,
+//   mhat^T w = (L^T mhat)^T p - mhat^T (x + g),
+//   mhat^T H mhat = |L^T mhat|^2 - |mhat|^2,
+// so log rho_0 needs no pass over the factor beyond L^T mhat, and that one
+// is known in closed form on both sides: on the forward side
+// L^T mhat = ((1-s)(p - t) + sqrt(1-s^2) xi) / sqrt(1-s^2); on the reverse
+// side the geometry kernel forms L^T z and L^T x from the factor it holds.
 //
-// The FP64 pipe bounds both kernels (1/64 of the FP32 rate on GB300), so the
-// Cholesky is blocked (8-column panels, 3 barriers per panel) to keep the
-// FP64 units fed from shared memory, and on the tensor-core path the product
-// J^T J is formed from the FP32 Jacobian in FP32 register tiles, off the FP64
-// pipe.  Factors move from HBM into shared memory by TMA bulk copies.
+// The FP64 pipe bounds these kernels (1/64 of the FP32 rate on GB300), so the
+// Cholesky is blocked (8-column panels with lookahead) to keep the FP64 units
+// fed from shared memory, and on the tensor-core path the product J^T J is
+// formed from the FP32 Jacobian in FP32 register tiles, off the FP64 pipe.
 #include "dino_internal.h"
 #include "philox.cuh"
 
@@ -35,14 +43,9 @@ constexpr int kJChunkF = 32;   // rows of an FP32 J staged per pass
 constexpr int kNB = 8;         // Cholesky panel width
 constexpr int kHT = 4;         // FP32 register tile edge for J^T J
 constexpr int kHMaxTiles = 3;  // tiles per thread: ceil(52*53/2 / 512) for r <= 208
-constexpr uint32_t kSpinLimit = 1u << 24;
+constexpr int kRed = 100;      // reduction scratch (doubles) of block_sum3
 
 __device__ __forceinline__ int tri(int i) { return i * (i + 1) / 2; }
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
 // Sum over the CTA; `red` holds >= 33 doubles.  Every thread gets the sum.
 __device__ double block_sum(double v, double *red) {
 #pragma unroll
@@ -61,86 +64,41 @@ __device__ double block_sum(double v, double *red) {
   return red[32];
 }
 
-__device__ __forceinline__ bool mbar_try0(uint32_t bar) {
-  uint32_t done;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(done)
-      : "r"(bar)
-      : "memory");
-  return done != 0;
-}
-
-__device__ bool mbar_wait0_bounded(uint32_t bar) {
-  for (uint32_t it = 0; it < kSpinLimit; ++it) {
-    if (mbar_try0(bar)) return true;
-    if (it > 32) __nanosleep(64);
+// Three sums over the CTA at once; `red` holds >= kRed doubles.
+__device__ void block_sum3(double &x, double &y, double &z, double *red) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    x += __shfl_xor_sync(kFull, x, o);
+    y += __shfl_xor_sync(kFull, y, o);
+    z += __shfl_xor_sync(kFull, z, o);
   }
-  return false;
-}
-
-// TMA bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned)
-// from global to shared memory.  Thread 0 issues and waits with a bounded
-// spin; the verdict is shared through `flag`.  On timeout it raises bit 4 of
-// `err`, waits once more (bounded) for the copies in flight, and every thread
-// gets false.
-__device__ bool cta_bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *mbar,
-                              int *flag, int *err) {
-  if (threadIdx.x == 0) {
-    const uint32_t bar = smem_u32(mbar);
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-    const char *s = static_cast<const char *>(src);
-    const uint32_t d = smem_u32(dst);
-    for (uint32_t off = 0; off < bytes; off += 65536u) {
-      const uint32_t n = bytes - off < 65536u ? bytes - off : 65536u;
-      asm volatile(
-          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
-          "[%3];" ::"r"(d + off),
-          "l"(s + off), "r"(n), "r"(bar)
-          : "memory");
-    }
-    const bool ok = mbar_wait0_bounded(bar);
-    if (!ok) {
-      atomicOr(err, 4);
-      mbar_wait0_bounded(bar);
-    }
-    *flag = ok ? 1 : 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    red[warp] = x;
+    red[32 + warp] = y;
+    red[64 + warp] = z;
   }
   __syncthreads();
-  return *flag != 0;
-}
-
-// x <- L^-1 x.  32-row diagonal blocks are solved by warp 0 with shuffles,
-// the rows below each block are updated by the whole CTA.
-__device__ void cta_lower_solve(const double *Ls, const double *inv, int r, double *x) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int jb = 0; jb < r; jb += 32) {
-    const int nb = min(32, r - jb);
-    if (warp == 0) {
-      double xl = lane < nb ? x[jb + lane] : 0.0;
-      for (int k = 0; k < nb; ++k) {
-        const double yk = __shfl_sync(kFull, xl, k) * inv[jb + k];
-        if (lane == k)
-          xl = yk;
-        else if (lane > k && lane < nb)
-          xl -= Ls[tri(jb + lane) + jb + k] * yk;
-      }
-      if (lane < nb) x[jb + lane] = xl;
+  if (warp == 0) {
+    const bool in = lane < (int)(blockDim.x >> 5);
+    double a = in ? red[lane] : 0.0, b = in ? red[32 + lane] : 0.0, c = in ? red[64 + lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      a += __shfl_xor_sync(kFull, a, o);
+      b += __shfl_xor_sync(kFull, b, o);
+      c += __shfl_xor_sync(kFull, c, o);
     }
-    __syncthreads();
-    for (int i = jb + nb + threadIdx.x; i < r; i += blockDim.x) {
-      const double *row = Ls + tri(i) + jb;
-      double acc = x[i];
-      for (int k = 0; k < nb; ++k) acc -= row[k] * x[jb + k];
-      x[i] = acc;
+    if (lane == 0) {
+      red[96] = a;
+      red[97] = b;
+      red[98] = c;
     }
-    __syncthreads();
   }
+  __syncthreads();
+  x = red[96];
+  y = red[97];
+  z = red[98];
 }
 
 // x <- L^-T x (back substitution on the upper factor L^T).
@@ -169,23 +127,19 @@ __device__ void cta_upper_solve(const double *Ls, const double *inv, int r, doub
   }
 }
 
-// y = L^T x  (y_j = sum_{i >= j} L_ij x_i)
-__device__ void cta_upper_matvec(const double *Ls, int r, const double *x, double *y) {
+// y1 = L^T x1 and, when `two`, y2 = L^T x2 over the leading r rows of L
+// (y_j = sum_{j <= i < r} L_ij x_i): column j by thread j, rows in order.
+__device__ void cta_upper_matvec2(const double *Ls, int r, const double *x1, const double *x2,
+                                  double *y1, double *y2, bool two) {
   for (int j = threadIdx.x; j < r; j += blockDim.x) {
-    double acc = 0.0;
-    for (int i = j; i < r; ++i) acc += Ls[tri(i) + j] * x[i];
-    y[j] = acc;
-  }
-  __syncthreads();
-}
-
-// y = L x  (y_i = sum_{j <= i} L_ij x_j)
-__device__ void cta_lower_matvec(const double *Ls, int r, const double *x, double *y) {
-  for (int i = threadIdx.x; i < r; i += blockDim.x) {
-    const double *row = Ls + tri(i);
-    double acc = 0.0;
-    for (int j = 0; j <= i; ++j) acc += row[j] * x[j];
-    y[i] = acc;
+    double a1 = 0.0, a2 = 0.0;
+    for (int i = j; i < r; ++i) {
+      const double l = Ls[tri(i) + j];
+      a1 += l * x1[i];
+      if (two) a2 += l * x2[i];
+    }
+    y1[j] = a1;
+    if (two) y2[j] = a2;
   }
   __syncthreads();
 }
@@ -360,34 +314,6 @@ __device__ void cta_cholesky(double *Ls, double *inv, int r) {
   }
 }
 
-// log rho_{0,r}(x -> z) with the geometry (L, g, hld) at x, given v = (I+H)^-1 (x + g).
-// Work vectors p, q (length r) are clobbered.
-__device__ double log_rho0(const double *Ls, int r, const double *x, const double *gx,
-                           const double *v, const double *z, double hld, double s, double dt,
-                           double *p, double *q, double *red) {
-  const double cs = sqrt(1.0 - s * s);
-  cta_upper_matvec(Ls, r, x, p);  // p = L^T x
-  cta_lower_matvec(Ls, r, p, q);  // q = (I+H) x
-  double t1 = 0.0, t2 = 0.0, nm = 0.0;
-  for (int i = threadIdx.x; i < r; i += blockDim.x) {
-    const double w = q[i] - x[i] - gx[i];      // w = H x - g
-    const double mh = (z[i] - s * x[i]) / cs;  // mhat
-    t1 += w * (x[i] - v[i]);                   // w^T (I+H)^-1 w
-    t2 += mh * w;
-    nm += mh * mh;
-    p[i] = mh;
-  }
-  __syncthreads();
-  t1 = block_sum(t1, red);
-  t2 = block_sum(t2, red);
-  nm = block_sum(nm, red);
-  cta_upper_matvec(Ls, r, p, q);  // q = L^T mhat
-  double t3 = 0.0;
-  for (int i = threadIdx.x; i < r; i += blockDim.x) t3 += q[i] * q[i];
-  t3 = block_sum(t3, red) - nm;  // mhat^T H mhat
-  return -dt / 8.0 * t1 + sqrt(dt) / 2.0 * t2 + hld - 0.5 * t3;
-}
-
 __device__ __forceinline__ void split_bf16_store(double x, __nv_bfloat16 *dst, size_t plane,
                                                  int nslice) {
   float rem = (float)x;
@@ -399,44 +325,37 @@ __device__ __forceinline__ void split_bf16_store(double x, __nv_bfloat16 *dst, s
 }
 
 // Shared-memory layout in doubles:
-//   Ls[ldL] inv[r] six work vectors[r] res[dy] red[34] mbar[1] flag[1] | J chunk
+//   Ls[slot_stride(r)] inv[r+1] five work vectors[r] res[dy] red[kRed] flag[1] | J chunk
+// With `global` the factor lives in its global slot and takes no shared memory.
 struct Layout {
-  size_t Ls, inv, v0, res, red, mbar, flag, tail;
-  // with `global` the factor lives in global memory and takes no shared memory
-  __host__ __device__ Layout(int r, int dy, size_t ldL, bool global = false) {
+  size_t Ls, inv, v0, res, red, flag, tail;
+  __host__ __device__ Layout(int r, int dy, bool global) {
     Ls = 0;
-    inv = global ? 0 : ldL;
-    v0 = inv + r;
-    res = v0 + 6 * (size_t)r;
+    inv = global ? 0 : slot_stride(r);
+    v0 = inv + r + 1;
+    res = v0 + 5 * (size_t)r;
     red = res + dy;
-    mbar = (red + 34 + 1) & ~(size_t)1;  // 8-byte mbarrier, kept 16-byte aligned
-    flag = mbar + 1;
+    flag = red + kRed;
     tail = (flag + 1 + 1) & ~(size_t)1;  // 16-byte aligned start of the J chunk
   }
 };
 
-// One CTA per chain.  G = false: the factor is bulk-copied into shared
-// memory; G = true (large r): the CTA works on the chain's factor in global
-// memory (L2-resident while the chain is processed).
-template <bool G>
+// One CTA per chain, for r beyond the register-resident warp kernel: the
+// factor is read from its global slot (L2-resident while the chain is
+// processed), the vectors live in shared memory.
 __global__ void __launch_bounds__(kThreads) k_propose(ReducedArgs a) {
   extern __shared__ __align__(16) double sm[];
   const int c = blockIdx.x, r = a.r;
-  const size_t ldL = l_stride(r);
-  const Layout lay(r, 0, ldL, G);
-  double *Lcur = a.L + (size_t)a.cur[c] * a.L_slot + (size_t)c * ldL;
-  double *Ls = G ? Lcur : sm + lay.Ls;
+  const Layout lay(r, 0, true);
+  const double *Ls = a.L + (size_t)a.cur[c] * a.L_slot + (size_t)c * slot_stride(r);
+  const double *tv = Ls + tri(r), *pv = Ls + tri(r + 1);
   double *inv = sm + lay.inv;
-  double *va = sm + lay.v0, *vg = va + r, *vv = vg + r, *vx = vv + r, *vp = vx + r, *vq = vp + r;
+  double *va = sm + lay.v0, *vg = va + r, *vx = vg + r, *z1 = vx + r, *z2 = z1 + r;
   double *red = sm + lay.red;
-  if (!G && !cta_bulk_load(Ls, Lcur, (uint32_t)(ldL * 8),
-                           reinterpret_cast<uint64_t *>(sm + lay.mbar),
-                           reinterpret_cast<int *>(sm + lay.flag), a.err))
-    return;
   for (int i = threadIdx.x; i < r; i += blockDim.x) {
     va[i] = a.mr[(size_t)c * r + i];
     vg[i] = a.g[(size_t)c * r + i];
-    vv[i] = va[i] + vg[i];
+    z1[i] = tv[i];
     inv[i] = 1.0 / Ls[tri(i) + i];
   }
   const uint32_t chain = (uint32_t)(a.id_base + (uint64_t)c);
@@ -444,142 +363,85 @@ __global__ void __launch_bounds__(kThreads) k_propose(ReducedArgs a) {
     double n4[4];
     normals4_f64(philox_block(a.seed, STREAM_XI, a.step, chain, blk), n4);
     for (int q = 0; q < 4; ++q)
-      if (4 * blk + q < r) vx[4 * blk + q] = n4[q];
+      if (4 * blk + q < r) vx[4 * blk + q] = z2[4 * blk + q] = n4[q];
   }
   __syncthreads();
-  cta_lower_solve(Ls, inv, r, vv);
-  cta_upper_solve(Ls, inv, r, vv);  // vv = (I+H)^-1 (a + g)
-  cta_upper_solve(Ls, inv, r, vx);  // vx = L^-T xi
+  cta_upper_solve(Ls, inv, r, z1);  // z1 = L^-T t = (I+H)^-1 (a + g)
+  cta_upper_solve(Ls, inv, r, z2);  // z2 = L^-T xi
   const double s = a.s, cs = sqrt(1.0 - s * s);
+  double t1 = 0.0, t2 = 0.0, t3 = 0.0;
   for (int i = threadIdx.x; i < r; i += blockDim.x) {
-    const double mu = va[i] - (1.0 - s) * vv[i];
-    const double b = mu + cs * vx[i];
-    vx[i] = b;
+    const double mu = va[i] - (1.0 - s) * z1[i];
+    const double b = mu + cs * z2[i];
     a.mu[(size_t)c * r + i] = mu;
     a.b[(size_t)c * r + i] = b;
     if (a.b_bf16)
       split_bf16_store(b, a.b_bf16 + (size_t)c * a.b_ld + i, a.b_plane, a.b_slices);
+    const double p = pv[i], d = p - tv[i];               // d = L^-1 w
+    const double mh = (b - s * va[i]) / cs;               // mhat
+    const double u = ((1.0 - s) * d + cs * vx[i]) / cs;   // L^T mhat
+    t1 += d * d;
+    t2 += u * p - mh * (va[i] + vg[i]);
+    t3 += u * u - mh * mh;
   }
-  __syncthreads();
-  const double lq = log_rho0(Ls, r, va, vg, vv, vx, a.hld[c], s, a.dt, vp, vq, red);
-  if (threadIdx.x == 0) a.lq_fwd[c] = lq;
+  block_sum3(t1, t2, t3, red);
+  if (threadIdx.x == 0)
+    a.lq_fwd[c] = -a.dt / 8.0 * t1 + sqrt(a.dt) / 2.0 * t2 + a.hld[c] - 0.5 * t3;
 }
 
 // ---------------------------------------------------------------------------
 // Warp-per-chain reduced proposal.  Each warp owns one chain; vectors live in
 // registers distributed over lanes (element i in lane i % 32, slot i / 32) and
 // L is read from global memory (L1/L2), so an SM keeps 16 chains in flight
-// and the serial parts of the triangular solves of one chain overlap with the
+// and the serial parts of the back substitution of one chain overlap with the
 // FP64 work of the others.
 
 constexpr int kPropWarps = 4;  // chains per CTA
 
+// [x, z] <- L^-T [x, z]: back substitution with two right-hand sides, so the
+// factor is read once for both.  Column k of a 32-row diagonal block is
+// broadcast by shuffles; the blocks above it take the update with lanes
+// reading contiguous parts of row k.
 template <int S>
-__device__ __forceinline__ void warp_lower_solve(const double *__restrict__ L, int r,
-                                                 const double (&invd)[S], double (&t)[S]) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int b = 0; b < S; ++b) {
-    if (32 * b >= r) break;
-    const int jb = 32 * b, nb = min(32, r - jb);
-    double tb = t[b];
-    const double ib = invd[b];
-    for (int k = 0; k < nb; ++k) {
-      const double yk = __shfl_sync(kFull, tb, k) * __shfl_sync(kFull, ib, k);
-      if (lane == k)
-        tb = yk;
-      else if (lane > k && lane < nb)
-        tb -= L[tri(jb + lane) + jb + k] * yk;
-    }
-    t[b] = tb;
-#pragma unroll
-    for (int b2 = b + 1; b2 < S; ++b2) {
-      if (32 * b2 >= r) break;
-      const int i = 32 * b2 + lane;
-      const double *row = L + tri(i) + jb;
-      double acc = t[b2];
-      for (int k = 0; k < nb; ++k) {
-        const double yk = __shfl_sync(kFull, tb, k);
-        if (i < r) acc -= row[k] * yk;
-      }
-      t[b2] = acc;
-    }
-  }
-}
-
-template <int S>
-__device__ __forceinline__ void warp_upper_solve(const double *__restrict__ L, int r,
-                                                 const double (&invd)[S], double (&t)[S]) {
+__device__ __forceinline__ void warp_upper_solve2(const double *__restrict__ L, int r,
+                                                  const double (&invd)[S], double (&x)[S],
+                                                  double (&z)[S]) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int b = S - 1; b >= 0; --b) {
     if (32 * b >= r) continue;
     const int jb = 32 * b, nb = min(32, r - jb);
-    double tb = t[b];
+    double xb = x[b], zb = z[b];
     const double ib = invd[b];
     for (int k = nb - 1; k >= 0; --k) {
-      const double xk = __shfl_sync(kFull, tb, k) * __shfl_sync(kFull, ib, k);
-      if (lane == k)
-        tb = xk;
-      else if (lane < k)
-        tb -= L[tri(jb + k) + jb + lane] * xk;
+      const double d = __shfl_sync(kFull, ib, k);
+      const double xk = __shfl_sync(kFull, xb, k) * d;
+      const double zk = __shfl_sync(kFull, zb, k) * d;
+      if (lane == k) {
+        xb = xk;
+        zb = zk;
+      } else if (lane < k) {
+        const double l = L[tri(jb + k) + jb + lane];
+        xb -= l * xk;
+        zb -= l * zk;
+      }
     }
-    t[b] = tb;
-#pragma unroll
-    for (int b2 = 0; b2 < b; ++b2) {
-      const int i = 32 * b2 + lane;
-      double acc = t[b2];
-      for (int k = 0; k < nb; ++k) acc -= L[tri(jb + k) + i] * __shfl_sync(kFull, tb, k);
-      t[b2] = acc;
-    }
-  }
-}
-
-// y = L^T x: for each row i of L (coalesced across lanes j <= i)
-template <int S>
-__device__ __forceinline__ void warp_upper_matvec(const double *__restrict__ L, int r,
-                                                  const double (&x)[S], double (&y)[S]) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int s = 0; s < S; ++s) y[s] = 0.0;
-#pragma unroll
-  for (int b = 0; b < S; ++b) {
-    if (32 * b >= r) break;
-    const int nb = min(32, r - 32 * b);
+    x[b] = xb;
+    z[b] = zb;
+    if (b == 0) continue;
     for (int k = 0; k < nb; ++k) {
-      const int i = 32 * b + k;
-      const double xi = __shfl_sync(kFull, x[b], k);
-      const double *row = L + tri(i);
+      const double xk = __shfl_sync(kFull, xb, k);
+      const double zk = __shfl_sync(kFull, zb, k);
+      const double *row = L + tri(jb + k);
 #pragma unroll
-      for (int s = 0; s <= b; ++s) {
-        const int j = 32 * s + lane;
-        if (j <= i) y[s] += row[j] * xi;
+      for (int b2 = 0; b2 < S; ++b2) {
+        if (b2 < b) {
+          const double l = row[32 * b2 + lane];
+          x[b2] -= l * xk;
+          z[b2] -= l * zk;
+        }
       }
     }
-  }
-}
-
-// y = L x: each lane its own rows, contiguous along the row
-template <int S>
-__device__ __forceinline__ void warp_lower_matvec(const double *__restrict__ L, int r,
-                                                  const double (&x)[S], double (&y)[S]) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int s = 0; s < S; ++s) {
-    y[s] = 0.0;
-    if (32 * s >= r) continue;
-    const int i = 32 * s + lane;
-    const double *row = L + tri(min(i, r - 1));
-    double acc = 0.0;
-#pragma unroll
-    for (int b = 0; b <= s; ++b) {
-      for (int k = 0; k < 32; ++k) {
-        const int j = 32 * b + k;
-        const double xj = __shfl_sync(kFull, x[b], k);
-        if (i < r && j <= i) acc += row[j] * xj;
-      }
-    }
-    y[s] = acc;
   }
 }
 
@@ -596,7 +458,8 @@ __global__ void __launch_bounds__(32 * kPropWarps) k_propose_warp(ReducedArgs a)
   const int c = blockIdx.x * kPropWarps + w;
   if (c >= a.C) return;  // whole warp
   const int r = a.r;
-  const double *L = a.L + (size_t)a.cur[c] * a.L_slot + (size_t)c * l_stride(r);
+  const double *L = a.L + (size_t)a.cur[c] * a.L_slot + (size_t)c * slot_stride(r);
+  const double *tv = L + tri(r), *pv = L + tri(r + 1);
   const uint32_t chain = (uint32_t)(a.id_base + (uint64_t)c);
   for (int blk = lane; blk < (r + 3) / 4; blk += 32) {
     double n4[4];
@@ -605,60 +468,43 @@ __global__ void __launch_bounds__(32 * kPropWarps) k_propose_warp(ReducedArgs a)
       if (4 * blk + q < r) xi_s[w][4 * blk + q] = n4[q];
   }
   __syncwarp();
-  double va[S], vg[S], vv[S], vx[S], vp[S], vq[S], invd[S];
+  double va[S], vg[S], vt[S], vx[S], z1[S], z2[S], invd[S];
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     const int i = 32 * s + lane;
     const bool in = i < r;
     va[s] = in ? a.mr[(size_t)c * r + i] : 0.0;
     vg[s] = in ? a.g[(size_t)c * r + i] : 0.0;
-    vv[s] = va[s] + vg[s];
+    vt[s] = in ? tv[i] : 0.0;
     vx[s] = in ? xi_s[w][i] : 0.0;
     invd[s] = in ? 1.0 / L[tri(i) + i] : 0.0;
+    z1[s] = vt[s];
+    z2[s] = vx[s];
   }
-  warp_lower_solve<S>(L, r, invd, vv);
-  warp_upper_solve<S>(L, r, invd, vv);  // vv = (I+H)^-1 (a + g)
-  warp_upper_solve<S>(L, r, invd, vx);  // vx = L^-T xi
+  warp_upper_solve2<S>(L, r, invd, z1, z2);  // z1 = (I+H)^-1 (a + g), z2 = L^-T xi
   const double s_ = a.s, cs = sqrt(1.0 - s_ * s_);
+  double t1 = 0.0, t2 = 0.0, t3 = 0.0;
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     const int i = 32 * s + lane;
-    const double mu = va[s] - (1.0 - s_) * vv[s];
-    const double b = mu + cs * vx[s];
-    vx[s] = i < r ? b : 0.0;
     if (i < r) {
+      const double mu = va[s] - (1.0 - s_) * z1[s];
+      const double b = mu + cs * z2[s];
       a.mu[(size_t)c * r + i] = mu;
       a.b[(size_t)c * r + i] = b;
       if (a.b_bf16)
         split_bf16_store(b, a.b_bf16 + (size_t)c * a.b_ld + i, a.b_plane, a.b_slices);
-    }
-  }
-  // log rho_{0,r}(a -> b) with the geometry at a
-  warp_upper_matvec<S>(L, r, va, vp);  // p = L^T a
-  warp_lower_matvec<S>(L, r, vp, vq);  // q = (I+H) a
-  double t1 = 0.0, t2 = 0.0, nm = 0.0;
-#pragma unroll
-  for (int s = 0; s < S; ++s) {
-    const int i = 32 * s + lane;
-    if (i < r) {
-      const double wv = vq[s] - va[s] - vg[s];        // w = H a - g
-      const double mh = (vx[s] - s_ * va[s]) / cs;    // mhat
-      t1 += wv * (va[s] - vv[s]);
-      t2 += mh * wv;
-      nm += mh * mh;
-      vp[s] = mh;
-    } else {
-      vp[s] = 0.0;
+      const double p = pv[i], d = p - vt[s];                 // d = L^-1 w
+      const double mh = (b - s_ * va[s]) / cs;                // mhat
+      const double u = ((1.0 - s_) * d + cs * vx[s]) / cs;    // L^T mhat
+      t1 += d * d;
+      t2 += u * p - mh * (va[s] + vg[s]);
+      t3 += u * u - mh * mh;
     }
   }
   t1 = warp_sum(t1);
   t2 = warp_sum(t2);
-  nm = warp_sum(nm);
-  warp_upper_matvec<S>(L, r, vp, vq);  // q = L^T mhat
-  double t3 = 0.0;
-#pragma unroll
-  for (int s = 0; s < S; ++s) t3 += vq[s] * vq[s];
-  t3 = warp_sum(t3) - nm;
+  t3 = warp_sum(t3);
   if (lane == 0)
     a.lq_fwd[c] = -a.dt / 8.0 * t1 + sqrt(a.dt) / 2.0 * t2 + a.hld[c] - 0.5 * t3;
 }
@@ -762,28 +608,64 @@ __device__ void form_h_f32(const float *J, int dy, int r, double inv_nv, double 
   __syncthreads();
 }
 
-// G = false: the factor is built in shared memory and copied to its slot;
-// G = true (large r): built directly in its global slot.  Mode 0 writes the
-// chain state (slot cur[c]); mode 1 writes the geometry at the proposal into
-// the other slot and the candidate buffers, for the accept kernel.
+// The accept test log u <= min(0, log rho) (Algorithm 1; NaN rejects), the
+// counters, and the scalar state of an accepted chain.  Thread 0 only.
+__device__ bool accept_test(const ReducedArgs &a, int c, double lr, double phi_b, double hld_b) {
+  const uint32_t chain = (uint32_t)(a.id_base + (uint64_t)c);
+  const double log_u = log(word_to_uniform(philox_block(a.seed, STREAM_U, a.step, chain, 0).x));
+  const bool finite = isfinite(lr);
+  const bool accept = finite && log_u <= fmin(0.0, lr);
+  a.log_rho[c] = lr;
+  a.log_u[c] = log_u;
+  a.acc[c] = accept ? 1 : 0;
+  if (accept) {
+    a.acc_count[c] += 1;
+    atomicAdd(&a.counters[0], 1ull);
+    a.phi[c] = phi_b;
+    a.hld[c] = hld_b;
+    a.cur[c] ^= 1;
+  }
+  if (!finite) atomicAdd(&a.counters[1], 1ull);
+  atomicAdd(a.sum_alpha, finite ? exp(fmin(0.0, lr)) : 0.0);
+  return accept;
+}
+
+// One CTA per chain at the point b.  G = false: the factor is built in shared
+// memory; G = true (large r): directly in the other global slot.
+//
+// The matrix factored is I + H bordered by the row v^T = (b + g_b)^T with
+// pivot 1 + |v|^2.  Its factor's leading block is L_b and its last row is
+// t_b^T = (L_b^-1 v)^T; the last pivot stays >= 1 since |L_b^-1 v| <= |v|
+// when I + H >= I.  With p_b = L_b^T b and q_b = L_b^T a the reverse density
+// takes L_b^T mhat = (q_b - s p_b) / sqrt(1-s^2) for mhat = (a - s b) / sqrt(1-s^2).
+//
+// Mode 0 makes b the chain state (slot cur[c]).  Mode 1 evaluates
+// log rho_r^(1) against the current state a, takes the accept test and moves
+// an accepted chain to b: its factor slot (written only then, into the other
+// slot, which becomes current) and its state vectors.  The complement
+// coefficient b - s a is written for every chain.
 template <typename TJ, bool G>
 __global__ void __launch_bounds__(kThreads) k_geometry(ReducedArgs a, int mode) {
   extern __shared__ __align__(16) double sm[];
   const int c = blockIdx.x, r = a.r, dy = a.d_y;
-  const size_t ldL = l_stride(r);
-  const Layout lay(r, dy, ldL, G);
+  const size_t ldL = slot_stride(r), lsz = tri_size(r + 1);
+  const Layout lay(r, dy, G);
   const int slot = mode == 0 ? a.cur[c] : 1 - a.cur[c];
   double *Lg = a.L + (size_t)slot * a.L_slot + (size_t)c * ldL;
   double *Ls = G ? Lg : sm + lay.Ls;
   double *inv = sm + lay.inv;
-  double *vb = sm + lay.v0, *vg = vb + r;
+  double *vb = sm + lay.v0, *vg = vb + r, *va = vg + r, *vp = va + r, *vq = vp + r;
   double *res = sm + lay.res;
   double *red = sm + lay.red;
+  int *flag = reinterpret_cast<int *>(sm + lay.flag);
   const TJ *J = reinterpret_cast<const TJ *>(a.J) + (size_t)c * dy * r;
   const TJ *f = reinterpret_cast<const TJ *>(a.f) + (size_t)c * dy;
   const double inv_nv = 1.0 / a.noise_var;
 
-  for (int i = threadIdx.x; i < r; i += blockDim.x) vb[i] = a.b[(size_t)c * r + i];
+  for (int i = threadIdx.x; i < r; i += blockDim.x) {
+    vb[i] = a.b[(size_t)c * r + i];
+    va[i] = mode == 1 ? a.mr[(size_t)c * r + i] : 0.0;
+  }
   double ph = 0.0;
   for (int i = threadIdx.x; i < dy; i += blockDim.x) {
     const double rs = (double)f[i] - a.y[i];
@@ -808,175 +690,82 @@ __global__ void __launch_bounds__(kThreads) k_geometry(ReducedArgs a, int mode) 
       __syncthreads();
     }
   }
-  cta_cholesky(Ls, inv, r);
+  double vv = 0.0;  // bordered row v = b + g_b (each thread its own j, as for g)
+  for (int j = threadIdx.x; j < r; j += blockDim.x) {
+    const double v = vb[j] + vg[j];
+    Ls[tri(r) + j] = v;
+    vv += v * v;
+  }
+  vv = block_sum(vv, red);
+  if (threadIdx.x == 0) Ls[tri(r) + r] = 1.0 + vv;
+  __syncthreads();
+  cta_cholesky(Ls, inv, r + 1);
   double ld = 0.0;
   for (int i = threadIdx.x; i < r; i += blockDim.x) ld += log(Ls[tri(i) + i]);
   const double hld_b = block_sum(ld, red);
+  cta_upper_matvec2(Ls, r, vb, va, vp, vq, mode == 1);  // p_b = L^T b, q_b = L^T a
 
-  if (!G) {
-    const int lsz = tri(r);
-    for (int e = threadIdx.x; e < lsz; e += blockDim.x) Lg[e] = Ls[e];
+  if (mode == 0) {
+    if (!G)
+      for (size_t e = threadIdx.x; e < lsz; e += blockDim.x) Lg[e] = Ls[e];
+    for (int i = threadIdx.x; i < r; i += blockDim.x) {
+      Lg[lsz + i] = vp[i];
+      a.g[(size_t)c * r + i] = vg[i];
+      a.mr[(size_t)c * r + i] = vb[i];
+    }
+    if (threadIdx.x == 0) {
+      a.phi[c] = phi_b;
+      a.hld[c] = hld_b;
+    }
+    return;
   }
-  double *gout = mode == 0 ? a.g : a.g_c;
+  const double *tb = Ls + tri(r);
+  const double s = a.s, cs = sqrt(1.0 - s * s);
+  double t1 = 0.0, t2 = 0.0, t3 = 0.0;
   for (int i = threadIdx.x; i < r; i += blockDim.x) {
-    gout[(size_t)c * r + i] = vg[i];
-    if (mode == 0) a.mr[(size_t)c * r + i] = vb[i];
+    const double d = vp[i] - tb[i];                // L_b^-1 w, w = H_b b - g_b
+    const double mh = (va[i] - s * vb[i]) / cs;    // mhat for b -> a
+    const double u = (vq[i] - s * vp[i]) / cs;     // L_b^T mhat
+    t1 += d * d;
+    t2 += u * vp[i] - mh * (vb[i] + vg[i]);
+    t3 += u * u - mh * mh;
   }
+  block_sum3(t1, t2, t3, red);
   if (threadIdx.x == 0) {
-    (mode == 0 ? a.phi : a.phi_c)[c] = phi_b;
-    (mode == 0 ? a.hld : a.hld_c)[c] = hld_b;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Accept: log rho_{0,r}(b -> a) with the candidate factor, log rho_r^(1)
-// (eq:da_dino_trr_1), the test log u <= min(0, log rho) (Alg. 1 line 6) and
-// the state update.  Warp per chain like the proposal; an accepted chain
-// takes the candidate factor by flipping its slot index.
-
-__device__ __forceinline__ void accept_tail(const ReducedArgs &a, int c, double lr) {
-  // lane-0 bookkeeping shared by the warp and CTA variants; returns via a.acc
-  const uint32_t chain = (uint32_t)(a.id_base + (uint64_t)c);
-  const double log_u = log(word_to_uniform(philox_block(a.seed, STREAM_U, a.step, chain, 0).x));
-  const bool finite = isfinite(lr);
-  const bool accept = finite && log_u <= fmin(0.0, lr);
-  a.log_rho[c] = lr;
-  a.log_u[c] = log_u;
-  a.acc[c] = accept ? 1 : 0;
-  if (accept) {
-    a.acc_count[c] += 1;
-    atomicAdd(&a.counters[0], 1ull);
-    a.phi[c] = a.phi_c[c];
-    a.hld[c] = a.hld_c[c];
-    a.cur[c] ^= 1;
-  }
-  if (!finite) atomicAdd(&a.counters[1], 1ull);
-  atomicAdd(a.sum_alpha, finite ? exp(fmin(0.0, lr)) : 0.0);
-}
-
-template <int S>
-__global__ void __launch_bounds__(32 * kPropWarps) k_accept_warp(ReducedArgs a) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int c = blockIdx.x * kPropWarps + w;
-  if (c >= a.C) return;  // whole warp
-  const int r = a.r;
-  const double *L = a.L + (size_t)(1 - a.cur[c]) * a.L_slot + (size_t)c * l_stride(r);
-  double va[S], vb[S], vg[S], vv[S], vp[S], vq[S], invd[S];
-  const double s_ = a.s, cs = sqrt(1.0 - s_ * s_);
-#pragma unroll
-  for (int s = 0; s < S; ++s) {
-    const int i = 32 * s + lane;
-    const bool in = i < r;
-    va[s] = in ? a.mr[(size_t)c * r + i] : 0.0;
-    vb[s] = in ? a.b[(size_t)c * r + i] : 0.0;
-    vg[s] = in ? a.g_c[(size_t)c * r + i] : 0.0;
-    vv[s] = vb[s] + vg[s];
-    invd[s] = in ? 1.0 / L[tri(i) + i] : 0.0;
-  }
-  warp_lower_solve<S>(L, r, invd, vv);
-  warp_upper_solve<S>(L, r, invd, vv);  // vv = (I+H_b)^-1 (b + g_b)
-  warp_upper_matvec<S>(L, r, vb, vp);   // p = L^T b
-  warp_lower_matvec<S>(L, r, vp, vq);   // q = (I+H_b) b
-  double t1 = 0.0, t2 = 0.0, nm = 0.0;
-#pragma unroll
-  for (int s = 0; s < S; ++s) {
-    const int i = 32 * s + lane;
-    if (i < r) {
-      const double wv = vq[s] - vb[s] - vg[s];       // w = H_b b - g_b
-      const double mh = (va[s] - s_ * vb[s]) / cs;   // mhat for b -> a
-      t1 += wv * (vb[s] - vv[s]);
-      t2 += mh * wv;
-      nm += mh * mh;
-      vp[s] = mh;
-    } else {
-      vp[s] = 0.0;
-    }
-  }
-  t1 = warp_sum(t1);
-  t2 = warp_sum(t2);
-  nm = warp_sum(nm);
-  warp_upper_matvec<S>(L, r, vp, vq);  // q = L^T mhat
-  double t3 = 0.0;
-#pragma unroll
-  for (int s = 0; s < S; ++s) t3 += vq[s] * vq[s];
-  t3 = warp_sum(t3) - nm;
-  const double lq_rev = -a.dt / 8.0 * t1 + sqrt(a.dt) / 2.0 * t2 + a.hld_c[c] - 0.5 * t3;
-  const double lr = a.phi[c] - a.phi_c[c] + lq_rev - a.lq_fwd[c];
-  __syncwarp();
-  int accept = 0;
-  if (lane == 0) {
-    accept_tail(a, c, lr);
-    accept = a.acc[c];
-  }
-  accept = __shfl_sync(kFull, accept, 0);
-#pragma unroll
-  for (int s = 0; s < S; ++s) {
-    const int i = 32 * s + lane;
-    if (i < r) {
-      a.coef[(size_t)c * r + i] = vb[s] - s_ * va[s];
-      if (accept) {
-        a.mr[(size_t)c * r + i] = vb[s];
-        a.g[(size_t)c * r + i] = vg[s];
-      }
-    }
-  }
-}
-
-// CTA variant for r beyond the register-resident warp kernel (factor in global memory).
-__global__ void __launch_bounds__(kThreads) k_accept_cta(ReducedArgs a) {
-  extern __shared__ __align__(16) double sm[];
-  const int c = blockIdx.x, r = a.r;
-  const Layout lay(r, 0, l_stride(r), true);
-  const double *Ls = a.L + (size_t)(1 - a.cur[c]) * a.L_slot + (size_t)c * l_stride(r);
-  double *inv = sm + lay.inv;
-  double *va = sm + lay.v0, *vb = va + r, *vg = vb + r, *vv = vg + r, *vp = vv + r, *vq = vp + r;
-  double *red = sm + lay.red;
-  for (int i = threadIdx.x; i < r; i += blockDim.x) {
-    va[i] = a.mr[(size_t)c * r + i];
-    vb[i] = a.b[(size_t)c * r + i];
-    vg[i] = a.g_c[(size_t)c * r + i];
-    vv[i] = vb[i] + vg[i];
-    inv[i] = 1.0 / Ls[tri(i) + i];
+    const double lq_rev = -a.dt / 8.0 * t1 + sqrt(a.dt) / 2.0 * t2 + hld_b - 0.5 * t3;
+    const double lr = a.phi[c] - phi_b + lq_rev - a.lq_fwd[c];
+    *flag = accept_test(a, c, lr, phi_b, hld_b) ? 1 : 0;
   }
   __syncthreads();
-  cta_lower_solve(Ls, inv, r, vv);
-  cta_upper_solve(Ls, inv, r, vv);
-  const double phi_a = a.phi[c];  // read before thread 0 may overwrite it
-  const double lq_rev = log_rho0(Ls, r, vb, vg, vv, va, a.hld_c[c], a.s, a.dt, vp, vq, red);
-  const double lr = phi_a - a.phi_c[c] + lq_rev - a.lq_fwd[c];
-  int *flag = reinterpret_cast<int *>(sm + lay.flag);
-  if (threadIdx.x == 0) {
-    accept_tail(a, c, lr);
-    *flag = a.acc[c];
-  }
-  __syncthreads();
-  const int accept = *flag;
+  const bool accept = *flag != 0;
   for (int i = threadIdx.x; i < r; i += blockDim.x) {
-    a.coef[(size_t)c * r + i] = vb[i] - a.s * va[i];
+    a.coef[(size_t)c * r + i] = vb[i] - s * va[i];
     if (accept) {
       a.mr[(size_t)c * r + i] = vb[i];
       a.g[(size_t)c * r + i] = vg[i];
+      Lg[lsz + i] = vp[i];
     }
   }
+  if (accept && !G)
+    for (size_t e = threadIdx.x; e < lsz; e += blockDim.x) Lg[e] = Ls[e];
 }
 
 }  // namespace
 
 bool uses_global_factor(int r, int d_y) {
-  const Layout lay(r, d_y, l_stride(r));
+  const Layout lay(r, d_y, false);
   const size_t jc = (size_t)kJChunkF * ((r + kHT - 1) / kHT * kHT) * sizeof(float);
   return r > kMaxRSmem || lay.tail * sizeof(double) + jc > kSmemLimit;
 }
 
 size_t propose_smem_bytes(int r) {
-  const bool G = uses_global_factor(r, 0);
-  const Layout lay(r, 0, l_stride(r), G);
+  const Layout lay(r, 0, true);
   return lay.tail * sizeof(double);
 }
 
 size_t geometry_smem_bytes(int r, int d_y, int jf_f32) {
   const bool G = uses_global_factor(r, d_y);
-  const Layout lay(r, d_y, l_stride(r), G);
+  const Layout lay(r, d_y, G);
   const size_t jc = jf_f32 ? (size_t)kJChunkF * ((r + kHT - 1) / kHT * kHT) * sizeof(float)
                            : (size_t)kJChunk * r * sizeof(double);
   return lay.tail * sizeof(double) + jc;
@@ -992,17 +781,10 @@ cudaError_t launch_propose(const ReducedArgs &a, cudaStream_t st) {
     return cudaGetLastError();
   }
   const size_t smem = propose_smem_bytes(a.r);
-  if (uses_global_factor(a.r, 0)) {
-    cudaError_t e = cudaFuncSetAttribute(k_propose<true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_propose<true><<<a.C, kThreads, smem, st>>>(a);
-  } else {
-    cudaError_t e = cudaFuncSetAttribute(k_propose<false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_propose<false><<<a.C, kThreads, smem, st>>>(a);
-  }
+  cudaError_t e =
+      cudaFuncSetAttribute(k_propose, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_propose<<<a.C, kThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -1013,24 +795,6 @@ static cudaError_t launch_geometry_t(const ReducedArgs &a, int mode, size_t smem
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_geometry<TJ, G><<<a.C, kThreads, smem, st>>>(a, mode);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_accept(const ReducedArgs &a, cudaStream_t st) {
-  if (a.r <= 32 * 7) {
-    const int grid = (a.C + kPropWarps - 1) / kPropWarps;
-    if (a.r <= 32 * 2)
-      k_accept_warp<2><<<grid, 32 * kPropWarps, 0, st>>>(a);
-    else
-      k_accept_warp<7><<<grid, 32 * kPropWarps, 0, st>>>(a);
-    return cudaGetLastError();
-  }
-  const Layout lay(a.r, 0, l_stride(a.r), true);
-  const size_t smem = lay.tail * sizeof(double);
-  cudaError_t e =
-      cudaFuncSetAttribute(k_accept_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_accept_cta<<<a.C, kThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -209,3 +209,45 @@ def test_error_codes(dino, ctx):
     dino.dino_chains_destroy(ctx, pool)
     dino.dino_unload_surrogate(ctx, sid)
     assert dino.dino_last_error(ctx) == ""
+
+
+def test_r1_and_zero_steps(dino, ctx):
+    """Degenerate reduced space (r = 1) and a zero-step call."""
+    w = variant(CONFIGS["small_fp64"], n_grid=4, r=1, widths=[1, 6, 3], noise_frac=0.3)
+    sid = gpu_setup(dino, ctx, w)
+    sur, E, D = oracle_setup(w)
+    pool = dino.dino_chains_create(ctx, sid, 9, 0.7, SEED_CHAINS)
+    before = dino.dino_chains_read(ctx, pool, 9, w.r, w.N)
+    st = dino.dino_chains_step(ctx, pool, 0)
+    after = dino.dino_chains_read(ctx, pool, 9, w.r, w.N)
+    assert st["proposals"] == 0 and np.array_equal(before["m_r"], after["m_r"])
+    och = _oracle_chains(w, sur, E, D, 9, 0.7)
+    acc, _, _ = step_and_compare(dino, ctx, pool, och, w, 9, 40, tol=TOL)
+    assert 0.0 < np.mean(acc) <= 1.0
+    dino.dino_chains_destroy(ctx, pool)
+    dino.dino_unload_surrogate(ctx, sid)
+
+
+def test_zero_jacobian_reduces_to_pcn(dino, ctx):
+    """Zero last-layer weights: H = 0, g = 0, the proposal is pCN and log rho == 0 (Sec. 2.7)."""
+    w = variant(CONFIGS["small_fp64"], widths=[16, 12, 7])
+    inp = surrogate_inputs(w)
+    Ws = [x.copy() for x in inp["Ws"]]
+    Ws[-1][:] = 0.0
+    sid = dino.dino_load_surrogate(
+        ctx, n_grid=w.n_grid, prior_gamma=w.prior_gamma, prior_delta=w.prior_delta, r=w.r,
+        widths=w.widths, activation=w.activation, W=Ws, b=inp["bs"], basis_kind=BASIS_KLE,
+        y=np.zeros(w.d_y), noise_var=0.01)
+    C, dt = 6, 0.8
+    s = (4 - dt) / (4 + dt)
+    pool = dino.dino_chains_create(ctx, sid, C, dt, SEED_CHAINS)
+    a = dino.dino_chains_read(ctx, pool, C, w.r, w.N)["m_r"]
+    dino.dino_chains_step(ctx, pool, 1, stats=False)
+    last = dino.dino_chains_read_last(ctx, pool, C, w.r)
+    from oracle import philox
+    xi = philox.normals(SEED_CHAINS, philox.STREAM_XI, 0, np.arange(C), w.r)
+    assert rel_err(last["b"], s * a + np.sqrt(1 - s * s) * xi) <= TOL
+    assert np.abs(last["log_rho"]).max() <= 1e-12
+    assert last["accepted"].all()
+    dino.dino_chains_destroy(ctx, pool)
+    dino.dino_unload_surrogate(ctx, sid)
