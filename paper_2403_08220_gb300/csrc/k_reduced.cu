@@ -30,6 +30,8 @@
 // Cholesky is blocked (8-column panels with lookahead) to keep the FP64 units
 // fed from shared memory, and on the tensor-core path the product J^T J is
 // formed from the FP32 Jacobian in FP32 register tiles, off the FP64 pipe.
+#include <type_traits>
+
 #include "dino_internal.h"
 #include "philox.cuh"
 
@@ -43,7 +45,7 @@ constexpr int kJChunkF = 32;   // rows of an FP32 J staged per pass
 constexpr int kNB = 8;         // Cholesky panel width
 constexpr int kHT = 4;         // FP32 register tile edge for J^T J
 constexpr int kHMaxTiles = 3;  // tiles per thread: ceil(52*53/2 / 512) for r <= 208
-constexpr int kRed = 100;      // reduction scratch (doubles) of block_sum3
+constexpr int kRed = 104;      // reduction scratch (doubles): block_sum3 [0, 99), Cholesky counters [100, 103)
 
 __device__ __forceinline__ int tri(int i) { return i * (i + 1) / 2; }
 // Sum over the CTA; `red` holds >= 33 doubles.  Every thread gets the sum.
@@ -127,19 +129,129 @@ __device__ void cta_upper_solve(const double *Ls, const double *inv, int r, doub
   }
 }
 
+// Element arithmetic of the Cholesky factorisation and of the products with
+// its factor.  F64: native FP64.  DF: double-float pairs (value = h + l with
+// |l| <= ulp(h) / 2, a 48-bit significand) on the FP32 pipe, which GB300 runs
+// at 64 times the FP64 rate: products are split exactly with an FMA, sums with
+// Knuth's two-sum, and a dot product is accumulated as in the compensated
+// Dot2 of Ogita, Rump and Oishi ("Accurate sum and dot product", SIAM J. Sci.
+// Comput. 26 (2005)), whose result is as accurate as if computed in twice the
+// working precision.  Intrinsics with explicit rounding keep the compiler
+// from contracting the error-free transformations.
+struct F64 {
+  using T = double;
+  using Acc = double;
+  __device__ static T from(double x) { return x; }
+  __device__ static T from_j(double x) { return x; }
+  __device__ static double to(T x) { return x; }
+  __device__ static Acc begin(T a) { return a; }
+  __device__ static void sub(Acc &a, T x, T y) { a -= x * y; }  // a <- a - x y
+  __device__ static T end(Acc a) { return a; }
+  __device__ static T mul(T a, T b) { return a * b; }
+  __device__ static T neg(T a) { return -a; }
+  // pivot d = sqrt(x) and id = 1 / d: y = x^(-1/2) from an FP32 estimate
+  // refined by two Newton-Raphson steps on 1/y^2 - x = 0 (y <- y (3 - x y^2) / 2)
+  __device__ static void pivot(T x, T &d, T &id) {
+    double y = (double)rsqrtf((float)x);
+    y = y * (1.5 - 0.5 * x * y * y);
+    y = y * (1.5 - 0.5 * x * y * y);
+    id = y;
+    d = x * y;
+  }
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// s + e = a + b exactly, given |a| >= |b| (or a == 0)
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+struct DF {
+  using T = float2;  // (h, l)
+  struct Acc {
+    float s, c;
+  };
+  __device__ static T from(double x) {
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(x - (double)h));
+  }
+  __device__ static T from_j(float x) { return make_float2(x, 0.0f); }
+  __device__ static double to(T x) { return (double)x.x + (double)x.y; }
+  __device__ static Acc begin(T a) { return {a.x, a.y}; }
+  // a <- a - x y: the high product p and its rounding error e are exact up
+  // to the dropped l*l term; -p enters the running sum by two-sum, whose
+  // error joins e in the compensation c.
+  __device__ static void sub(Acc &a, T x, T y) {
+    const float p = __fmul_rn(x.x, y.x);
+    float e = __fmaf_rn(x.x, y.x, -p);
+    e = __fmaf_rn(x.x, y.y, e);
+    e = __fmaf_rn(x.y, y.x, e);
+    float s, q;
+    two_sum(a.s, -p, s, q);
+    a.s = s;
+    a.c = __fadd_rn(a.c, __fsub_rn(q, e));
+  }
+  __device__ static T end(Acc a) {
+    float h, l;
+    two_sum(a.s, a.c, h, l);
+    return make_float2(h, l);
+  }
+  __device__ static T mul(T a, T b) {
+    const float p = __fmul_rn(a.x, b.x);
+    float e = __fmaf_rn(a.x, b.x, -p);
+    e = __fmaf_rn(a.x, b.y, e);
+    e = __fmaf_rn(a.y, b.x, e);
+    float h, l;
+    fast_two_sum(p, e, h, l);
+    return make_float2(h, l);
+  }
+  __device__ static T neg(T a) { return make_float2(-a.x, -a.y); }
+  // The same pivot on the FP32 pipe: each Newton step y <- y + y (1 - x y^2) / 2
+  // takes the residual 1 - x y^2 exactly (double-float product, two-sum
+  // against 1) and the small correction in FP32.  From the FP32 estimate
+  // (relative error ~2^-22) the first step reaches ~2^-43, the second the
+  // double-float precision.  x <= 0 gives NaN, as in FP64.
+  __device__ static void newton_rsqrt(T x, T &y) {
+    const T y2 = mul(y, y);
+    const T xy2 = mul(x, y2);
+    float s, q;
+    two_sum(1.0f, -xy2.x, s, q);
+    const float res = __fadd_rn(s, __fsub_rn(q, xy2.y));
+    const float c = __fmul_rn(__fmul_rn(0.5f, y.x), res);
+    float h, l;
+    two_sum(y.x, c, h, l);
+    fast_two_sum(h, __fadd_rn(l, y.y), y.x, y.y);
+  }
+  __device__ static void pivot(T x, T &d, T &id) {
+    T y = make_float2(rsqrtf(x.x), 0.0f);
+    newton_rsqrt(x, y);
+    newton_rsqrt(x, y);
+    id = y;
+    d = mul(x, y);
+  }
+};
+
 // y1 = L^T x1 and, when `two`, y2 = L^T x2 over the leading r rows of L
 // (y_j = sum_{j <= i < r} L_ij x_i): column j by thread j, rows in order.
-__device__ void cta_upper_matvec2(const double *Ls, int r, const double *x1, const double *x2,
-                                  double *y1, double *y2, bool two) {
+template <class A>
+__device__ void cta_upper_matvec2(const typename A::T *Ls, int r, const typename A::T *x1,
+                                  const typename A::T *x2, double *y1, double *y2, bool two) {
+  using E = typename A::T;
   for (int j = threadIdx.x; j < r; j += blockDim.x) {
-    double a1 = 0.0, a2 = 0.0;
+    typename A::Acc a1 = A::begin(E{}), a2 = A::begin(E{});
     for (int i = j; i < r; ++i) {
-      const double l = Ls[tri(i) + j];
-      a1 += l * x1[i];
-      if (two) a2 += l * x2[i];
+      const E l = Ls[tri(i) + j];
+      A::sub(a1, l, A::neg(x1[i]));
+      if (two) A::sub(a2, l, A::neg(x2[i]));
     }
-    y1[j] = a1;
-    if (two) y2[j] = a2;
+    y1[j] = A::to(A::end(a1));
+    if (two) y2[j] = A::to(A::end(a2));
   }
   __syncthreads();
 }
@@ -152,55 +264,106 @@ __device__ __forceinline__ void tri_pos(int e, int &ii, int &jj) {
   jj = e - tri(ii);
 }
 
-// Factor the 8 x 8 diagonal block at kb (size nb) by one warp: pivots from
-// y = x^(-1/2), an FP32 estimate refined by two Newton-Raphson steps on
-// 1/y^2 - x = 0 (y <- y (3 - x y^2) / 2), then the block's own column scaling
-// and rank-1 updates.  inv[k] = 1 / L_kk.
-__device__ __forceinline__ void warp_factor_diag(double *Ls, double *inv, int kb, int nb,
-                                                 int lane) {
-  for (int q = 0; q < nb; ++q) {
-    const int kq = kb + q;
-    const double xkk = Ls[tri(kq) + kq];
-    double id = (double)rsqrtf((float)xkk);
-    id = id * (1.5 - 0.5 * xkk * id * id);
-    id = id * (1.5 - 0.5 * xkk * id * id);
-    const double d = xkk * id;
-    __syncwarp();
-    if (lane == 0) {
-      Ls[tri(kq) + kq] = d;
-      inv[kq] = id;
-    }
-    if (lane > q && lane < nb) Ls[tri(kb + lane) + kq] *= id;
-    __syncwarp();
-    for (int e = lane; e < nb * nb; e += 32) {
-      const int i = e / nb, j = e % nb;
-      if (j > q && j <= i)
-        Ls[tri(kb + i) + kb + j] -= Ls[tri(kb + i) + kq] * Ls[tri(kb + j) + kq];
-    }
-    __syncwarp();
-  }
+// Lane-to-lane copy of a factor element.
+__device__ __forceinline__ double shfl_elt(double x, int src) {
+  return __shfl_sync(kFull, x, src);
+}
+__device__ __forceinline__ float2 shfl_elt(float2 x, int src) {
+  return make_float2(__shfl_sync(kFull, x.x, src), __shfl_sync(kFull, x.y, src));
 }
 
-// Rows i >= row0 of the panel at kb: L[i, kb:kb+nb] <- L[i, kb:kb+nb] L_bb^-T.
-__device__ __forceinline__ void panel_solve(double *Ls, const double *inv, int r, int kb, int nb,
-                                            int row0, int t0, int T) {
-  for (int i = row0 + t0; i < r; i += T) {
-    double *row = Ls + tri(i) + kb;
-    double x[kNB];
+// Factor the 8 x 8 diagonal block at kb (size nb) by one warp, in registers:
+// lane i < nb holds row i of the block.  When pk >= 0 the block first takes
+// the rank-8 update from the panel at pk (final by then).  At step q, c[k]
+// holds L(i, q + k): the pivot (A::pivot, computed by every lane from the
+// broadcast diagonal entry), the scaling of column q, its store, the rank-1
+// update of the columns to its right (L(q + k, q) by shuffle from lane q + k),
+// then a shift of c by one column.  Lanes compute every column and keep
+// theirs by selects, so the independent updates interleave; the q loop stays
+// rolled to keep its code small.  inv[k] = 1 / L_kk.
+template <class A>
+__device__ __noinline__ void warp_factor_diag(typename A::T *Ls, typename A::T *inv, int kb,
+                                              int nb, int pk, int lane) {
+  using E = typename A::T;
+  E c[kNB];
+  const bool in = lane < nb;
+  const int ri = kb + (in ? lane : nb - 1);  // lanes >= nb shadow the last row
 #pragma unroll
-    for (int q = 0; q < kNB; ++q) {
-      if (q < nb) {
-        double acc = row[q];
-        const double *lq = Ls + tri(kb + q) + kb;
+  for (int j = 0; j < kNB; ++j) c[j] = j < nb ? Ls[tri(ri) + kb + min(j, lane)] : E{};
+  if (pk >= 0) {
+    E xr[kNB];
 #pragma unroll
-        for (int p = 0; p < q; ++p) acc -= x[p] * lq[p];
-        x[q] = acc * inv[kb + q];
+    for (int p = 0; p < kNB; ++p) xr[p] = Ls[tri(ri) + pk + p];
+#pragma unroll
+    for (int j = 0; j < kNB; ++j) {
+      if (j < nb) {
+        const E *lj = Ls + tri(kb + j) + pk;
+        typename A::Acc acc = A::begin(c[j]);
+#pragma unroll
+        for (int p = 0; p < kNB; ++p) A::sub(acc, xr[p], lj[p]);
+        const E u = A::end(acc);
+        c[j] = j <= lane ? u : c[j];
       }
     }
-#pragma unroll
-    for (int q = 0; q < kNB; ++q)
-      if (q < nb) row[q] = x[q];
   }
+#pragma unroll
+  for (int j = 0; j < kNB; ++j) c[j] = (in && j <= lane) ? c[j] : E{};
+#pragma unroll 1
+  for (int q = 0; q < nb; ++q) {
+    E d, id;
+    A::pivot(shfl_elt(c[0], q), d, id);
+    const E sc = A::mul(c[0], id);
+    c[0] = lane == q ? d : (lane > q ? sc : c[0]);
+    if (lane == 0) inv[kb + q] = id;
+    if (in && lane >= q) Ls[tri(kb + lane) + kb + q] = c[0];
+#pragma unroll
+    for (int k = 1; k < kNB; ++k) {
+      const E l = shfl_elt(c[0], q + k);
+      typename A::Acc acc = A::begin(c[k]);
+      A::sub(acc, c[0], l);
+      const E u = A::end(acc);
+      c[k] = lane >= q + k ? u : c[k];
+    }
+#pragma unroll
+    for (int k = 0; k + 1 < kNB; ++k) c[k] = c[k + 1];
+    c[kNB - 1] = E{};
+  }
+  __syncwarp();
+}
+
+// Row i of the panel at kb (width nb): when pk >= 0 its entries first take
+// the rank-8 update from the panel at pk, then L[i, kb:kb+nb] <- L[i, kb:kb+nb] L_bb^-T
+// against the factored diagonal block.
+template <class A>
+__device__ __noinline__ void panel_row(typename A::T *Ls, const typename A::T *inv, int kb,
+                                       int nb, int pk, int i) {
+  using E = typename A::T;
+  E *row = Ls + tri(i);
+  typename A::Acc acc[kNB];
+#pragma unroll
+  for (int q = 0; q < kNB; ++q) acc[q] = A::begin(q < nb ? row[kb + q] : E{});
+  if (pk >= 0) {
+#pragma unroll
+    for (int p = 0; p < kNB; ++p) {
+      const E x = row[pk + p];
+#pragma unroll
+      for (int q = 0; q < kNB; ++q)
+        if (q < nb) A::sub(acc[q], x, Ls[tri(kb + q) + pk + p]);
+    }
+  }
+  E x[kNB];
+#pragma unroll
+  for (int q = 0; q < kNB; ++q) {
+    if (q < nb) {
+      const E *lq = Ls + tri(kb + q) + kb;
+#pragma unroll
+      for (int p = 0; p < q; ++p) A::sub(acc[q], x[p], lq[p]);
+      x[q] = A::mul(A::end(acc[q]), inv[kb + q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kNB; ++q)
+    if (q < nb) row[kb + q] = x[q];
 }
 
 // Rank-nb update from the panel at kb of the entries (i, j), j0 <= j <= i < r
@@ -211,104 +374,158 @@ struct StripPos {
   int ii, jj;
 };
 
+// Rows ii < w of the strip are the triangle's (length ii + 1), the rows below
+// have length w: the walk crosses triangle rows one by one and the
+// rectangular part by one division.
 __device__ __forceinline__ void strip_advance(StripPos &p, int step, int w) {
   p.jj += step;
-  while (true) {
-    const int len = p.ii + 1 < w ? p.ii + 1 : w;
-    if (p.jj < len) break;
-    p.jj -= len;
+  while (p.ii < w) {
+    if (p.jj <= p.ii) return;
+    p.jj -= p.ii + 1;
     ++p.ii;
+  }
+  if (p.jj >= w) {
+    p.ii += p.jj / w;
+    p.jj %= w;
   }
 }
 
-__device__ __forceinline__ void trailing_update(double *Ls, int r, int kb, int nb, int j0, int j1,
-                                                int t0, int T) {
-  const int n = r - j0;
+__device__ __forceinline__ int strip_entries(int r, int j0, int j1) {
+  const int n = r - j0, w = min(j1, r) - j0;
+  return w * (w + 1) / 2 + (n - w) * w;
+}
+
+// Entries [e0, e1) of the enumeration (clipped to the strip).
+template <class A>
+__device__ __noinline__ void trailing_update(typename A::T *Ls, int r, int kb, int nb, int j0,
+                                                int j1, int e0, int e1, int t0, int T) {
+  using E = typename A::T;
   const int w = min(j1, r) - j0;  // strip width (w == n: whole triangle)
-  const int full = w * (w + 1) / 2 + (n - w) * w;
-  if (t0 >= full) return;
+  e1 = min(e1, strip_entries(r, j0, j1));
+  if (e0 + t0 >= e1) return;
   StripPos p;
   {
-    const int tw = w * (w + 1) / 2;
-    if (t0 < tw) {
-      tri_pos(t0, p.ii, p.jj);
+    const int tw = w * (w + 1) / 2, e = e0 + t0;
+    if (e < tw) {
+      tri_pos(e, p.ii, p.jj);
     } else {
-      p.ii = w + (t0 - tw) / w;
-      p.jj = (t0 - tw) % w;
+      p.ii = w + (e - tw) / w;
+      p.jj = (e - tw) % w;
     }
   }
-  for (int e = t0; e < full; e += 2 * T) {
+  for (int e = e0 + t0; e < e1; e += 2 * T) {
     StripPos q = p;
-    const bool two = e + T < full;
+    const bool two = e + T < e1;
     if (two) strip_advance(q, T, w);
     const int i1 = j0 + p.ii, c1 = j0 + p.jj;
     const int i2 = j0 + q.ii, c2 = j0 + q.jj;
-    const double *li1 = Ls + tri(i1) + kb, *lj1 = Ls + tri(c1) + kb;
-    const double *li2 = Ls + tri(i2) + kb, *lj2 = Ls + tri(c2) + kb;
-    double *a1 = Ls + tri(i1) + c1;
-    double *a2 = Ls + tri(i2) + c2;
-    double acc1 = *a1, acc2 = two ? *a2 : 0.0;
+    const E *li1 = Ls + tri(i1) + kb, *lj1 = Ls + tri(c1) + kb;
+    const E *li2 = Ls + tri(i2) + kb, *lj2 = Ls + tri(c2) + kb;
+    E *a1 = Ls + tri(i1) + c1;
+    E *a2 = Ls + tri(i2) + c2;
+    // without a second entry q == p: the second chain recomputes the first
+    // entry from valid addresses and is not stored (no selects in the loop)
+    typename A::Acc acc1 = A::begin(*a1), acc2 = A::begin(*a2);
     if (nb == kNB) {
-      double x1[kNB], y1[kNB], x2[kNB], y2[kNB];
+      E x1[kNB], y1[kNB], x2[kNB], y2[kNB];
 #pragma unroll
       for (int k = 0; k < kNB; ++k) {
         x1[k] = li1[k];
         y1[k] = lj1[k];
-        x2[k] = two ? li2[k] : 0.0;
-        y2[k] = two ? lj2[k] : 0.0;
+        x2[k] = li2[k];
+        y2[k] = lj2[k];
       }
 #pragma unroll
       for (int k = 0; k < kNB; ++k) {
-        acc1 -= x1[k] * y1[k];
-        acc2 -= x2[k] * y2[k];
+        A::sub(acc1, x1[k], y1[k]);
+        A::sub(acc2, x2[k], y2[k]);
       }
     } else {
-      for (int k = 0; k < nb; ++k) acc1 -= li1[k] * lj1[k];
+      for (int k = 0; k < nb; ++k) A::sub(acc1, li1[k], lj1[k]);
       if (two)
-        for (int k = 0; k < nb; ++k) acc2 -= li2[k] * lj2[k];
+        for (int k = 0; k < nb; ++k) A::sub(acc2, li2[k], lj2[k]);
     }
-    *a1 = acc1;
-    if (two) *a2 = acc2;
+    *a1 = A::end(acc1);
+    if (two) *a2 = A::end(acc2);
     p = q;
     strip_advance(p, two ? T : 0, w);
   }
 }
 
-// In-place right-looking Cholesky of the packed matrix in 8-column panels
-// with a one-panel lookahead and warp specialisation.  Per panel:
-//   (A) all threads: the next panel's columns take this panel's rank-8 update;
-//   (B) warps 0-3 factor the next diagonal block (warp 0) and then solve the
-//       rows below it against that block, while warps 4.. apply this panel's
-//       update to the rest of the trailing triangle.
-// Two CTA barriers per panel; the serial diagonal work and the panel solve
-// run in the shadow of the trailing update.  Per element this is the same
-// sequence of fused multiply-adds as the column-at-a-time algorithm.  A
-// non-positive pivot produces NaN, which the caller turns into a reject.
-constexpr int kPanelThreads = 128;  // warps 0-3
+// In-place right-looking Cholesky of the packed matrix in 8-column panels.
+// After the first panel, step kb (the panel at kb final) factors the next
+// panel nk = kb + 8 in two phases separated by CTA barriers:
+//   (A) all threads: panel nk's columns take panel kb's rank-8 update;
+//   (B) warp 0 factors the diagonal block of nk and raises a flag; all warps
+//       take work from shared counters: once the flag is up, rows of panel
+//       nk (one per lane, solved against the block), otherwise chunks of
+//       kChunk entries of the trailing triangle right of nk (panel kb's
+//       update); a warp with nothing left but rows waits for the flag
+//       (bounded: on timeout bit 8 of `err` is raised).
+// The counters and the flag alternate between two sets by step parity, so
+// that the set of the next step is cleared while this one is in use.  Per
+// element this is the same sequence of fused multiply-adds as the
+// column-at-a-time algorithm.  A non-positive pivot produces NaN, which the
+// caller turns into a reject.
+constexpr int kChunk = 128;                // trailing-update entries per warp grab
+constexpr uint32_t kFlagSpins = 1u << 22;  // polls of the diagonal-block flag
 
-__device__ __forceinline__ void panel_group_sync() {
-  asm volatile("bar.sync 1, %0;" ::"n"(kPanelThreads) : "memory");
-}
-
-__device__ void cta_cholesky(double *Ls, double *inv, int r) {
+// `ctr` is six ints of shared memory.
+template <class A>
+__device__ void cta_cholesky(typename A::T *Ls, typename A::T *inv, int r, int *ctr, int *err) {
   const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (warp == 0) warp_factor_diag(Ls, inv, 0, min(kNB, r), lane);
+  if (tid < 6) ctr[tid] = 0;
+  if (warp == 0) warp_factor_diag<A>(Ls, inv, 0, min(kNB, r), -1, lane);
   __syncthreads();
-  panel_solve(Ls, inv, r, 0, min(kNB, r), min(kNB, r), tid, T);
+  for (int i = min(kNB, r) + tid; i < r; i += T) panel_row<A>(Ls, inv, 0, min(kNB, r), -1, i);
   __syncthreads();
-  for (int kb = 0; kb < r; kb += kNB) {
-    const int nb = min(kNB, r - kb);
-    const int nk = kb + nb;  // next panel
-    if (nk >= r) break;
-    const int nb2 = min(kNB, r - nk);
-    trailing_update(Ls, r, kb, nb, nk, nk + nb2, tid, T);  // (A)
+  int step = 0;
+  for (int kb = 0; kb + kNB < r; kb += kNB, ++step) {
+    const int nk = kb + kNB, nb2 = min(kNB, r - nk), j0 = nk + nb2;
+    const int rows = r - j0, full = rows > 0 ? strip_entries(r, j0, r) : 0;
+    int *c3 = ctr + 3 * (step & 1);
+    trailing_update<A>(Ls, r, kb, kNB, nk, j0, 0, 1 << 30, tid, T);  // (A)
+    if (tid == 0) {
+      int *o = ctr + 3 * ((step + 1) & 1);
+      o[0] = o[1] = o[2] = 0;
+    }
     __syncthreads();
-    if (tid < kPanelThreads) {  // (B) panel group
-      if (warp == 0) warp_factor_diag(Ls, inv, nk, nb2, lane);
-      panel_group_sync();
-      panel_solve(Ls, inv, r, nk, nb2, nk + nb2, tid, kPanelThreads);
-    } else if (nk + nb2 < r) {  // (B) update group
-      trailing_update(Ls, r, kb, nb, nk + nb2, r, tid - kPanelThreads, T - kPanelThreads);
+    if (warp == 0) {  // (B)
+      warp_factor_diag<A>(Ls, inv, nk, nb2, -1, lane);
+      __threadfence_block();
+      if (lane == 0) atomicExch(&c3[2], 1);
+    }
+    uint32_t spins = 0;
+    for (;;) {
+      int job = 0, base = 0;  // 0 done, 1 rows, 2 trailing chunk, 3 wait
+      if (lane == 0) {
+        const bool ready = atomicAdd(&c3[2], 0) != 0;
+        if (ready && rows > 0) {
+          base = atomicAdd(&c3[1], 32);
+          if (base < rows) job = 1;
+        }
+        if (job == 0) {
+          base = atomicAdd(&c3[0], 1) * kChunk;
+          if (base < full) job = 2;
+        }
+        if (job == 0 && !ready && rows > 0) job = 3;
+      }
+      job = __shfl_sync(kFull, job, 0);
+      base = __shfl_sync(kFull, base, 0);
+      if (job == 0) break;
+      if (job == 1) {
+        __syncwarp();
+        __threadfence_block();
+        if (base + lane < rows) panel_row<A>(Ls, inv, nk, nb2, -1, j0 + base + lane);
+      } else if (job == 2) {
+        trailing_update<A>(Ls, r, kb, kNB, j0, r, base, base + kChunk, lane, 32);
+      } else {
+        if (++spins > kFlagSpins) {
+          if (lane == 0) atomicOr(err, 8);
+          break;
+        }
+        __nanosleep(32);
+      }
     }
     __syncthreads();
   }
@@ -325,15 +542,17 @@ __device__ __forceinline__ void split_bf16_store(double x, __nv_bfloat16 *dst, s
 }
 
 // Shared-memory layout in doubles:
-//   Ls[slot_stride(r)] inv[r+1] five work vectors[r] res[dy] red[kRed] flag[1] | J chunk
-// With `global` the factor lives in its global slot and takes no shared memory.
+//   Ls[slot_stride(r)] inv[r+1] seven work vectors[r] res[dy] red[kRed] flag[1] | J chunk
+// (red[100..102] hold the Cholesky's six work counters)
+// (one double, or one double-float pair, per element).  With `global` the
+// factor lives in its global slot and takes no shared memory.
 struct Layout {
   size_t Ls, inv, v0, res, red, flag, tail;
   __host__ __device__ Layout(int r, int dy, bool global) {
     Ls = 0;
     inv = global ? 0 : slot_stride(r);
     v0 = inv + r + 1;
-    res = v0 + 5 * (size_t)r;
+    res = v0 + 7 * (size_t)r;
     red = res + dy;
     flag = red + kRed;
     tail = (flag + 1 + 1) & ~(size_t)1;  // 16-byte aligned start of the J chunk
@@ -537,21 +756,24 @@ __device__ void form_h_f64(const double *J, int dy, int r, double inv_nv, double
   }
 }
 
-// The same from an FP32 J: each thread accumulates up to kHMaxTiles 4 x 4
-// tiles of J^T J in FP32 registers over all d_y rows (chunks of kJChunkF
-// rows staged in shared memory, padded to a multiple of 4 columns), then
-// writes I + H once in FP64.  Large r takes several rounds of tiles.
-__device__ void form_h_f32(const float *J, int dy, int r, double inv_nv, double *Ls,
+// The same from an FP32 J into double-float entries: each thread
+// accumulates up to kHMaxTiles 4 x 4 tiles of J^T J in FP32 registers over
+// all d_y rows (chunks of kJChunkF rows staged in shared memory, padded to a
+// multiple of 4 columns), then writes I + H once, the product with
+// 1 / noise_var taken exactly as a double-float.  Large r takes several
+// rounds of tiles.
+__device__ void form_h_f32(const float *J, int dy, int r, double inv_nv, float2 *Ls,
                            float *Jc) {
   const int nt = (r + kHT - 1) / kHT, rp = nt * kHT;
   const int ntiles = nt * (nt + 1) / 2;
   if (dy == 0) {
-    for (int e = threadIdx.x; e < tri(r); e += blockDim.x) Ls[e] = 0.0;
+    for (int e = threadIdx.x; e < tri(r); e += blockDim.x) Ls[e] = make_float2(0.0f, 0.0f);
     __syncthreads();
-    for (int i = threadIdx.x; i < r; i += blockDim.x) Ls[tri(i) + i] = 1.0;
+    for (int i = threadIdx.x; i < r; i += blockDim.x) Ls[tri(i) + i] = make_float2(1.0f, 0.0f);
     __syncthreads();
     return;
   }
+  const float nh = __double2float_rn(inv_nv), nl = __double2float_rn(inv_nv - (double)nh);
   for (int t0 = 0; t0 < ntiles; t0 += kHMaxTiles * blockDim.x) {
     int ti[kHMaxTiles], tj[kHMaxTiles];
     float acc[kHMaxTiles][kHT][kHT];
@@ -600,8 +822,19 @@ __device__ void form_h_f32(const float *J, int dy, int r, double inv_nv, double 
 #pragma unroll
         for (int q = 0; q < kHT; ++q) {
           const int i = kHT * ti[s] + p, j = kHT * tj[s] + q;
-          if (i < r && j <= i)
-            Ls[tri(i) + j] = (i == j ? 1.0 : 0.0) + (double)acc[s][p][q] * inv_nv;
+          if (i < r && j <= i) {
+            const float x = acc[s][p][q], ph = __fmul_rn(x, nh);
+            float e = __fmaf_rn(x, nh, -ph);
+            e = __fmaf_rn(x, nl, e);
+            float h, l;
+            fast_two_sum(ph, e, h, l);
+            if (i == j) {
+              float s1, q1;
+              two_sum(1.0f, h, s1, q1);
+              fast_two_sum(s1, __fadd_rn(q1, l), h, l);
+            }
+            Ls[tri(i) + j] = make_float2(h, l);
+          }
         }
     }
   }
@@ -646,16 +879,21 @@ __device__ bool accept_test(const ReducedArgs &a, int c, double lr, double phi_b
 // coefficient b - s a is written for every chain.
 template <typename TJ, bool G>
 __global__ void __launch_bounds__(kThreads) k_geometry(ReducedArgs a, int mode) {
+  // FP32 Jacobian (tensor-core path): double-float Cholesky; FP64 Jacobian: FP64
+  using A = std::conditional_t<sizeof(TJ) == 4, DF, F64>;
+  using E = typename A::T;
+  static_assert(sizeof(E) == sizeof(double), "one factor element per double of the slot");
   extern __shared__ __align__(16) double sm[];
   const int c = blockIdx.x, r = a.r, dy = a.d_y;
   const size_t ldL = slot_stride(r), lsz = tri_size(r + 1);
   const Layout lay(r, dy, G);
   const int slot = mode == 0 ? a.cur[c] : 1 - a.cur[c];
   double *Lg = a.L + (size_t)slot * a.L_slot + (size_t)c * ldL;
-  double *Ls = G ? Lg : sm + lay.Ls;
-  double *inv = sm + lay.inv;
+  E *Ls = reinterpret_cast<E *>(G ? Lg : sm + lay.Ls);
+  E *inv = reinterpret_cast<E *>(sm + lay.inv);
   double *vb = sm + lay.v0, *vg = vb + r, *va = vg + r, *vp = va + r, *vq = vp + r;
-  double *res = sm + lay.res;
+  E *be = reinterpret_cast<E *>(vq + r), *ae = be + r;  // b and a as factor elements
+  E *res = reinterpret_cast<E *>(sm + lay.res);  // f - y as factor elements
   double *red = sm + lay.red;
   int *flag = reinterpret_cast<int *>(sm + lay.flag);
   const TJ *J = reinterpret_cast<const TJ *>(a.J) + (size_t)c * dy * r;
@@ -665,49 +903,59 @@ __global__ void __launch_bounds__(kThreads) k_geometry(ReducedArgs a, int mode) 
   for (int i = threadIdx.x; i < r; i += blockDim.x) {
     vb[i] = a.b[(size_t)c * r + i];
     va[i] = mode == 1 ? a.mr[(size_t)c * r + i] : 0.0;
+    be[i] = A::from(vb[i]);
+    ae[i] = A::from(va[i]);
   }
   double ph = 0.0;
   for (int i = threadIdx.x; i < dy; i += blockDim.x) {
     const double rs = (double)f[i] - a.y[i];
-    res[i] = rs;
+    res[i] = A::neg(A::from(rs));
     ph += rs * rs;
   }
   const double phi_b = 0.5 * block_sum(ph, red) * inv_nv;  // includes a barrier
   for (int j = threadIdx.x; j < r; j += blockDim.x) {
-    double acc = 0.0;
-    for (int i = 0; i < dy; ++i) acc += (double)J[(size_t)i * r + j] * res[i];
-    vg[j] = acc * inv_nv;  // g = J^T (f - y) / noise_var
+    typename A::Acc acc = A::begin(E{});
+    for (int i = 0; i < dy; ++i) A::sub(acc, A::from_j(J[(size_t)i * r + j]), res[i]);
+    vg[j] = A::to(A::end(acc)) * inv_nv;  // g = J^T (f - y) / noise_var
   }
   if constexpr (sizeof(TJ) == 4) {
-    form_h_f32(reinterpret_cast<const float *>(J), dy, r, inv_nv, Ls,
+    form_h_f32(reinterpret_cast<const float *>(J), dy, r, inv_nv, reinterpret_cast<float2 *>(Ls),
                reinterpret_cast<float *>(sm + lay.tail));
   } else {
-    form_h_f64(reinterpret_cast<const double *>(J), dy, r, inv_nv, Ls, sm + lay.tail);
+    double *Ld = reinterpret_cast<double *>(Ls);
+    form_h_f64(reinterpret_cast<const double *>(J), dy, r, inv_nv, Ld, sm + lay.tail);
     if (dy == 0) {
-      for (int e = threadIdx.x; e < tri(r); e += blockDim.x) Ls[e] = 0.0;
+      for (int e = threadIdx.x; e < tri(r); e += blockDim.x) Ld[e] = 0.0;
       __syncthreads();
-      for (int i = threadIdx.x; i < r; i += blockDim.x) Ls[tri(i) + i] = 1.0;
+      for (int i = threadIdx.x; i < r; i += blockDim.x) Ld[tri(i) + i] = 1.0;
       __syncthreads();
     }
   }
   double vv = 0.0;  // bordered row v = b + g_b (each thread its own j, as for g)
   for (int j = threadIdx.x; j < r; j += blockDim.x) {
     const double v = vb[j] + vg[j];
-    Ls[tri(r) + j] = v;
+    Ls[tri(r) + j] = A::from(v);
     vv += v * v;
   }
   vv = block_sum(vv, red);
-  if (threadIdx.x == 0) Ls[tri(r) + r] = 1.0 + vv;
+  if (threadIdx.x == 0) Ls[tri(r) + r] = A::from(1.0 + vv);
   __syncthreads();
-  cta_cholesky(Ls, inv, r + 1);
+  cta_cholesky<A>(Ls, inv, r + 1, reinterpret_cast<int *>(red + 100), a.err);
   double ld = 0.0;
-  for (int i = threadIdx.x; i < r; i += blockDim.x) ld += log(Ls[tri(i) + i]);
+  for (int i = threadIdx.x; i < r; i += blockDim.x) ld += log(A::to(Ls[tri(i) + i]));
   const double hld_b = block_sum(ld, red);
-  cta_upper_matvec2(Ls, r, vb, va, vp, vq, mode == 1);  // p_b = L^T b, q_b = L^T a
+  cta_upper_matvec2<A>(Ls, r, be, ae, vp, vq, mode == 1);  // p_b = L^T b, q_b = L^T a
 
+  // the slot holds FP64: copied from shared memory, or converted in place
+  // (each thread its own elements) when the factor was built in the slot
+  auto store_factor = [&]() {
+    for (size_t e = threadIdx.x; e < lsz; e += blockDim.x) {
+      const double x = A::to(Ls[e]);
+      Lg[e] = x;
+    }
+  };
   if (mode == 0) {
-    if (!G)
-      for (size_t e = threadIdx.x; e < lsz; e += blockDim.x) Lg[e] = Ls[e];
+    store_factor();
     for (int i = threadIdx.x; i < r; i += blockDim.x) {
       Lg[lsz + i] = vp[i];
       a.g[(size_t)c * r + i] = vg[i];
@@ -719,11 +967,11 @@ __global__ void __launch_bounds__(kThreads) k_geometry(ReducedArgs a, int mode) 
     }
     return;
   }
-  const double *tb = Ls + tri(r);
+  const E *tb = Ls + tri(r);
   const double s = a.s, cs = sqrt(1.0 - s * s);
   double t1 = 0.0, t2 = 0.0, t3 = 0.0;
   for (int i = threadIdx.x; i < r; i += blockDim.x) {
-    const double d = vp[i] - tb[i];                // L_b^-1 w, w = H_b b - g_b
+    const double d = vp[i] - A::to(tb[i]);         // L_b^-1 w, w = H_b b - g_b
     const double mh = (va[i] - s * vb[i]) / cs;    // mhat for b -> a
     const double u = (vq[i] - s * vp[i]) / cs;     // L_b^T mhat
     t1 += d * d;
@@ -746,8 +994,7 @@ __global__ void __launch_bounds__(kThreads) k_geometry(ReducedArgs a, int mode) 
       Lg[lsz + i] = vp[i];
     }
   }
-  if (accept && !G)
-    for (size_t e = threadIdx.x; e < lsz; e += blockDim.x) Lg[e] = Ls[e];
+  if (accept) store_factor();
 }
 
 }  // namespace

@@ -13,8 +13,11 @@ Bars (stated for the BF16 path):
   accept         under shared uniforms a decision may differ from the FP64 one
                  only when log u lies between the two log rho values (or within
                  1e-3 of the FP64 threshold); the flipped fraction is bounded.
-The Cholesky factor, its log-determinant and log rho are computed in FP64
-from the BF16/FP32 Jacobian, so their error is the Jacobian's, propagated.
+The Cholesky factor and its log-determinant are computed in double-float
+arithmetic (a 48-bit significand on the FP32 pipe) and log rho in FP64 from
+the BF16/FP32 Jacobian, so their error is the Jacobian's, propagated; the
+factorisation itself is pinned to FP64 on an exactly representable Hessian
+(`test_double_float_cholesky_on_exact_hessian`).
 """
 import numpy as np
 import pytest
@@ -22,7 +25,7 @@ import pytest
 from helpers import gpu_setup, oracle_setup, rel_err, variant
 from oracle import mmala
 from oracle.chains import OracleChains
-from workloads import BASIS_DIS, CONFIGS, SEED_CHAINS
+from workloads import ACT_IDENTITY, BASIS_DIS, BASIS_KLE, CONFIGS, SEED_CHAINS
 
 pytestmark = pytest.mark.gpu
 
@@ -149,3 +152,31 @@ def test_bf16_full_size_sampled(dino, ctx):
     sample = [0, 1, 127, 128, 5000, 9999, 16000, C - 1]
     out = _precision_run(dino, ctx, w, C, w.dt, 2, sample=sample)
     _check_bars(out)
+
+
+@pytest.mark.parametrize("r,h,dy", [(45, 24, 12), (200, 64, 50), (256, 48, 40)])
+def test_double_float_cholesky_on_exact_hessian(dino, ctx, r, h, dy):
+    """Weights in {-1, 0, 1} and the identity activation make the tensor-core
+    Jacobian J = W2 W1 exact (small integers), so I + J^T J (noise variance 1)
+    is exact in FP32 and the double-float factor must agree with an FP64
+    Cholesky to 1e-10 of max |L| (an FP32 factorisation of the same matrix
+    misses by about 4e-8).  r = 256 runs with the factor in its global slot."""
+    rng = np.random.default_rng(21)
+    W1 = rng.integers(-1, 2, size=(h, r)).astype(float)
+    W2 = rng.integers(-1, 2, size=(dy, h)).astype(float)
+    n = int(np.ceil(np.sqrt(r))) + 1
+    sid = dino.dino_load_surrogate(
+        ctx, n_grid=n, prior_gamma=0.1, prior_delta=1.0, r=r, widths=[r, h, dy],
+        activation=ACT_IDENTITY, W=[W1, W2], b=[np.zeros(h), np.zeros(dy)],
+        basis_kind=BASIS_KLE, y=np.zeros(dy), noise_var=1.0, precision=dino.DINO_PREC_BF16)
+    x = rng.standard_normal((3, r))
+    g = dino.dino_surrogate_eval(ctx, sid, x, dy)
+    J = W2 @ W1
+    L = np.linalg.cholesky(np.eye(r) + J.T @ J)
+    hld = np.log(np.diag(L)).sum()
+    for c in range(3):
+        assert np.array_equal(g["J"][c], J)
+        assert np.abs(g["L"][c] - L).max() <= 1e-10 * np.abs(L).max()
+        assert abs(g["hld"][c] - hld) <= 1e-10 * abs(hld)
+        assert rel_err(g["g"][c], J.T @ g["f"][c]) <= 1e-12
+    dino.dino_unload_surrogate(ctx, sid)
