@@ -39,7 +39,8 @@ FP64_NOMINAL_TFLOPS = 1.25
 # 12 of them per double-float multiply-add (the compensated dot-product step
 # of the factorisation), 2 flops per multiply-add.
 FP32_LANES, SMS, SM_GHZ, DF_INSTR_PER_FMA = 128, 152, 2.07, 12
-DF_PEAK_TFLOPS = SMS * FP32_LANES * SM_GHZ * 1e9 / DF_INSTR_PER_FMA * 2 / 1e12
+FP32_PEAK_TFLOPS = SMS * FP32_LANES * SM_GHZ * 1e9 * 2 / 1e12
+DF_PEAK_TFLOPS = FP32_PEAK_TFLOPS / DF_INSTR_PER_FMA
 
 
 def geometry_traffic_per_chain(workload: str):
@@ -49,7 +50,9 @@ def geometry_traffic_per_chain(workload: str):
     the per-chain traffic does not depend on the chain count.  None when no
     capture of this workload's kernel exists.
     """
-    path = os.path.join(ROOT, "profiles", f"k_geometry_{workload}.txt")
+    w = CONFIGS[workload]
+    kernel = "k_wb_geometry" if w.d_y < w.r else "k_geometry"
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.txt")
     try:
         with open(path) as fh:
             for line in fh:
@@ -58,6 +61,26 @@ def geometry_traffic_per_chain(workload: str):
     except OSError:
         pass
     return None
+
+
+def geometry_work(r: int, d_y: int) -> dict:
+    """Algorithmic work of one geometry launch per chain, by pipe.
+
+    d_y < r (Woodbury path): the FP32 Gram product J J^T, d_y (d_y + 1) r
+    flops, and in double-float arithmetic the bordered Cholesky of the
+    (d_y + 1)-matrix, (d_y + 1)^3 / 3, plus the products K b and K a, 4 r d_y.
+    Otherwise: the FP32 product J^T J, r (r + 1) d_y, and in double-float the
+    bordered r-Cholesky with the reverse-density products and the gradient
+    (`fp64_flops_geometry`).  A double-float multiply-add takes 12 FP32
+    instructions, so the FP32-pipe charge is fp32 + 12 x df flops.
+    """
+    if d_y < r:
+        fp32 = d_y * (d_y + 1) * r
+        df = (d_y + 1) ** 3 / 3.0 + 4.0 * r * d_y
+    else:
+        fp32 = r * (r + 1) * d_y
+        df = fp64_flops_geometry(r, d_y)
+    return {"fp32": fp32, "df": df, "fp32_charge": fp32 + DF_INSTR_PER_FMA * df}
 
 
 def fp64_flops_geometry(r: int, d_y: int) -> float:
@@ -215,20 +238,18 @@ def run_ours(args, rank, world, device):
     dom = max(kt.items(), key=lambda kv: kv[1][0])
     geo = kt.get("geometry", dom[1])
     geo_ms = geo[0] / max(1, geo[1])
-    flops = fp64_flops_geometry(w.r, w.d_y) * C
-    achieved = flops / (geo_ms * 1e-3) / 1e12
+    work = geometry_work(w.r, w.d_y)
+    achieved = work["fp32_charge"] * C / (geo_ms * 1e-3) / 1e12
     tpc = geometry_traffic_per_chain(args.workload)
-    roofline = {"bound": "alu", "pipe": "fp32 (double-float arithmetic)", "kernel": "geometry",
-                "achieved": round(achieved, 4), "peak": round(DF_PEAK_TFLOPS, 3),
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz / 12 FP32 "
-                               "instructions per double-float multiply-add x 2 flops "
-                               "(FP64-equivalent flops)",
-                "unit": "TFLOP/s", "frac": round(achieved / DF_PEAK_TFLOPS, 4),
-                "frac_of_native_fp64": round(achieved / FP64_NOMINAL_TFLOPS, 4),
+    roofline = {"bound": "alu", "pipe": "fp32", "kernel": "geometry",
+                "achieved": round(achieved, 4), "peak": round(FP32_PEAK_TFLOPS, 2),
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz x 2 flops; "
+                               "double-float multiply-adds charged at 12 FP32 instructions",
+                "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
+                "work_per_chain": {"fp32_flops": work["fp32"], "df_flops": work["df"]},
                 "traffic": tpc * C if tpc else None,
                 "traffic_note": "dram bytes per launch scaled from a 1216-chain ncu capture",
-                "share_of_step": round(geo[0] / total, 4),
-                "flops_per_chain": fp64_flops_geometry(w.r, w.d_y)}
+                "share_of_step": round(geo[0] / total, 4)}
 
     # FP64 plain step beside it (fewer steps: it runs its GEMMs in FP64)
     fp64_line = None

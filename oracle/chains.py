@@ -10,7 +10,9 @@ the target is the surrogate posterior.
 
 Random numbers (see `philox`): step j of chain c uses XI(j, c) for the r
 reduced normals, U(j, c) for the accept uniform and Z(j, c) for the N normals
-of the complement prior draw; the initial prior draw uses INIT(0, c).
+of the complement prior draw; the initial prior draw uses INIT(0, c).  With
+the perturbation noise map (`mmala.noise_map`: d_y < r) the d_y further
+normals come from XI2(j, c).
 """
 from __future__ import annotations
 
@@ -21,10 +23,12 @@ from . import mmala, philox, prior
 
 class OracleChains:
     def __init__(self, sur: mmala.Surrogate, E, D, n_grid: int, gamma: float, delta: float,
-                 n_chains: int, dt: float, seed: int, m0=None, chain_ids=None):
+                 n_chains: int, dt: float, seed: int, m0=None, chain_ids=None,
+                 noise: str = "auto"):
         self.sur, self.E, self.D = sur, np.asarray(E), np.asarray(D)
         self.n_grid, self.gamma, self.delta = n_grid, gamma, delta
         self.dt, self.seed = float(dt), int(seed)
+        self.noise = mmala.noise_map(sur.r, sur.d_y) if noise == "auto" else noise
         self.ids = (np.arange(n_chains, dtype=np.uint64) if chain_ids is None
                     else np.asarray(chain_ids, dtype=np.uint64))
         C = len(self.ids)
@@ -50,7 +54,11 @@ class OracleChains:
         xi = philox.normals(self.seed, philox.STREAM_XI, j, self.ids, r)
         u = philox.uniform(self.seed, philox.STREAM_U, j, self.ids)
         a, geo_a = self.m_r, self.geo
-        mu, b = mmala.reduced_proposal(a, geo_a, xi, dt)
+        if self.noise == "perturbation":
+            xi2 = philox.normals(self.seed, philox.STREAM_XI2, j, self.ids, sur.d_y)
+            mu, b = mmala.reduced_proposal_perturbation(a, geo_a, xi, xi2, sur.noise_var, dt)
+        else:
+            mu, b = mmala.reduced_proposal(a, geo_a, xi, dt)
         geo_b = mmala.geometry(sur, b)
         lr = mmala.log_rho(a, geo_a, b, geo_b, dt)
         # magnitude of the terms log rho sums (the scale its rounding error lives on)

@@ -21,6 +21,10 @@ Readings of the paper taken here (each also listed in the design notes):
   factor).  It has the law of the eigen form of eq:reduced_space_sampling
   (covariance (1 - s^2)(I + H)^-1); `reduced_proposal_eigen` keeps the
   paper's map for distribution checks.
+* When d_y < r the noise is drawn instead as zeta = (I + H)^-1 (xi1 + K^T xi2)
+  with K = J / sqrt(noise_var) and d_y further normals xi2: the same law
+  (`reduced_proposal_perturbation`), which needs only the d_y x d_y matrix
+  I + K K^T to be factored (`noise_map`).
 * Accept iff log u <= min(0, log rho) (Alg. 1 rejects iff alpha < u);
   a non-finite log rho is a reject.
 """
@@ -107,6 +111,30 @@ def reduced_proposal(a, geo: Geometry, xi, dt: float):
     LT = np.swapaxes(geo.L, -1, -2)
     eta = _solve(LT, np.asarray(xi, dtype=np.float64))
     return mu, mu + np.sqrt(1.0 - s * s) * eta
+
+
+def noise_map(r: int, d_y: int) -> str:
+    """The proposal noise map used for a surrogate with reduced dimension r and
+    d_y observables: "perturbation" when d_y < r, else "cholesky"."""
+    return "perturbation" if d_y < r else "cholesky"
+
+
+def reduced_proposal_perturbation(a, geo: Geometry, xi1, xi2, noise_var: float, dt: float):
+    """m_r^dagger = mu + sqrt(1 - s^2) zeta, zeta = (I + H)^-1 (xi1 + K^T xi2), K = J / sqrt(noise_var).
+
+    With xi1 ~ N(0, I_r) and xi2 ~ N(0, I_{d_y}) independent, zeta is Gaussian
+    with covariance (I + H)^-1 (I + K^T K) (I + H)^-1 = (I + H)^-1, because
+    H = K^T K (eq:surrogate_rppgnh, Gamma = noise_var I): the law of the noise
+    of eq:reduced_space_sampling.  The mean is `proposal_mean`.  Returns (mu, b).
+    """
+    s = s_of_dt(dt)
+    mu = proposal_mean(a, geo, dt)
+    r = a.shape[-1]
+    K = geo.J / np.sqrt(noise_var)
+    rhs = (np.asarray(xi1, dtype=np.float64)
+           + np.einsum("...ij,...i->...j", K, np.asarray(xi2, dtype=np.float64)))
+    zeta = _solve(np.eye(r) + geo.H, rhs)
+    return mu, mu + np.sqrt(1.0 - s * s) * zeta
 
 
 def reduced_proposal_eigen(a, H, g, xi, dt: float):

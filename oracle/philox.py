@@ -18,7 +18,8 @@ normals 4k .. 4k+3.
 
 Streams: XI (reduced proposal noise of Algorithm 1), U (the uniform of its
 accept test), Z (prior draw for the complement, Prop. 5.1), INIT (prior draw
-of the initial state).
+of the initial state), XI2 (the d_y observation-space normals of the
+perturbation noise map, see `mmala.reduced_proposal_perturbation`).
 """
 from __future__ import annotations
 
@@ -28,6 +29,7 @@ STREAM_XI = 0
 STREAM_U = 1
 STREAM_Z = 2
 STREAM_INIT = 3
+STREAM_XI2 = 4
 
 _M0 = np.uint64(0xD2511F53)
 _M1 = np.uint64(0xCD9E8D57)

@@ -16,8 +16,10 @@ constexpr int kMaxR = 1024;                 // largest reduced dimension support
 constexpr size_t kSmemLimit = 227 * 1024;   // opt-in shared memory per CTA
 
 // Philox streams (counter word 3): reduced noise, accept uniform, complement
-// prior draw, initial prior draw.
-constexpr uint32_t STREAM_XI_ID = 0, STREAM_U_ID = 1, STREAM_Z_ID = 2, STREAM_INIT_ID = 3;
+// prior draw, initial prior draw, observation-space noise of the
+// perturbation map (d_y < r).
+constexpr uint32_t STREAM_XI_ID = 0, STREAM_U_ID = 1, STREAM_Z_ID = 2, STREAM_INIT_ID = 3,
+                   STREAM_XI2_ID = 4;
 
 inline __host__ __device__ size_t tri_size(int r) { return (size_t)r * (r + 1) / 2; }
 // Per-chain factor slot in global memory: the packed lower Cholesky factor
@@ -26,6 +28,12 @@ inline __host__ __device__ size_t tri_size(int r) { return (size_t)r * (r + 1) /
 // of doubles so that every slot starts on 16 bytes.
 inline __host__ __device__ size_t slot_stride(int r) {
   return (tri_size(r + 1) + r + 1) & ~(size_t)1;
+}
+// Per-chain factor slot of the Woodbury path (d_y < r): the packed factor of
+// I + K K^T bordered by u^T (d_y + 1 rows), the d_y + 1 inverse pivots, u, v
+// and the scalar t1, rounded up to an even number of doubles.
+inline __host__ __device__ size_t wb_slot_stride(int d_y) {
+  return (tri_size(d_y + 1) + (d_y + 1) + 2 * (size_t)d_y + 1 + 1) & ~(size_t)1;
 }
 
 // ---- per-chain reduced-space kernels (FP64) -----------------------------
@@ -43,6 +51,8 @@ struct ReducedArgs {
   // cur[c] flips.  L_slot = elements between the slots (C * slot_stride(r)).
   int *cur = nullptr;
   size_t L_slot = 0;
+  // Woodbury path: J at each chain's current point (C x d_y x r, FP64 or FP32)
+  void *Js = nullptr;
   // surrogate output at b: J (C x d_y x r) and f (C x d_y), FP64 or FP32
   const void *J = nullptr;
   const void *f = nullptr;
@@ -69,6 +79,11 @@ cudaError_t launch_propose(const ReducedArgs &a, cudaStream_t st);
 // mode 0: initialise the state at b; mode 1: geometry at the proposal b,
 // log-acceptance, accept test and state update
 cudaError_t launch_geometry(const ReducedArgs &a, int mode, cudaStream_t st);
+// The Woodbury path (d_y < r): the same two steps with the d_y x d_y factor
+// of I + K K^T (K = J / sigma) and the perturbation noise map.
+size_t wb_smem_bytes(int r, int d_y, int jf_f32);
+cudaError_t launch_wb_propose(const ReducedArgs &a, cudaStream_t st);
+cudaError_t launch_wb_geometry(const ReducedArgs &a, int mode, cudaStream_t st);
 
 // ---- SIMT GEMMs: out = epilogue(A B^T), A: M x K (lda), B: N x K (ldb) ----
 template <typename T>

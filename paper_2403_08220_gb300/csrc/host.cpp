@@ -391,6 +391,8 @@ struct Surrogate {
   std::vector<double> E, D, y;
   double noise_var = 0;
   bool has_data = false;
+  // d_y < r: chains use the Woodbury path (d_y x d_y factor, perturbation noise map)
+  bool wb = false;
   int pools = 0;
   // device
   std::vector<std::pair<void *, size_t>> allocs;
@@ -488,6 +490,11 @@ static int load_surrogate(dino_ctx *ctx, const dino_surrogate_desc *d) {
   if (geometry_smem_bytes(s->r, s->d_y, 1) > kSmemLimit ||
       geometry_smem_bytes(s->r, s->d_y, 0) > kSmemLimit)
     fail(DINO_EINVAL, "r=%d, d_y=%d exceed the per-chain shared-memory budget", s->r, s->d_y);
+  s->wb = s->d_y < s->r;
+  if (s->wb && (wb_smem_bytes(s->r, s->d_y, 1) > kSmemLimit ||
+                wb_smem_bytes(s->r, s->d_y, 0) > kSmemLimit))
+    fail(DINO_EINVAL, "d_y=%d < r=%d: the d_y x d_y factor exceeds the shared-memory budget",
+         s->d_y, s->r);
   if (d->precision == DINO_PREC_BF16 && s->L < 2)
     fail(DINO_EINVAL, "the tensor-core path needs at least one hidden layer");
   if (d->precision == DINO_PREC_BF16) {
@@ -802,9 +809,12 @@ struct Pool {
   uint64_t seed = 0, id_base = 0;
   uint32_t step = 0;
   Arena ar;
+  bool wb = false;  // Woodbury path (the surrogate's d_y < r); scratch pools of
+                    // surrogate_eval always take the r-sized path
   // state
   double *mr, *g, *phi, *hld, *L;
   int *cur;  // per-chain slot (0/1) of the current factor in L
+  void *Js;  // Woodbury path: J at each chain's current point
   void *m;  // C x N, double (FP64 path) or float (tensor path)
   double *b, *mu, *lq_fwd, *coef, *log_rho, *log_u;
   int *acc;
@@ -830,8 +840,10 @@ static void layout_pool(Pool &p, bool assign) {
   p.g = (double *)take((size_t)C * r * 8);
   p.phi = (double *)take((size_t)C * 8);
   p.hld = (double *)take((size_t)C * 8);
-  p.L = (double *)take(2 * (size_t)C * slot_stride(r) * 8);  // two slots
+  const size_t ss = p.wb ? wb_slot_stride(s->d_y) : slot_stride(r);
+  p.L = (double *)take(2 * (size_t)C * ss * 8);  // two slots
   p.cur = (int *)take((size_t)C * 4);
+  p.Js = p.wb ? take((size_t)C * s->d_y * r * fe) : nullptr;
   p.m = take((size_t)C * N * fe);
   p.b = (double *)take((size_t)C * r * 8);
   p.mu = (double *)take((size_t)C * r * 8);
@@ -874,7 +886,8 @@ static ReducedArgs reduced_args(const Pool &p) {
   a.hld = p.hld;
   a.L = p.L;
   a.cur = p.cur;
-  a.L_slot = (size_t)p.C * slot_stride(s->r);
+  a.L_slot = (size_t)p.C * (p.wb ? wb_slot_stride(s->d_y) : slot_stride(s->r));
+  a.Js = p.Js;
   a.b = p.b;
   a.mu = p.mu;
   a.lq_fwd = p.lq_fwd;
@@ -930,6 +943,7 @@ static Pool *create_pool_on(dino_ctx *ctx, int sid, int C, double dt, uint64_t s
   p->id_base = id_base;
   p->st = st;
   p->async_mem = serving;
+  p->wb = s->wb;
   layout_pool(*p, false);
   p->ar.bytes = p->ar.off;
   p->ar.base = (char *)(serving ? dev_alloc_async(ctx, p->ar.bytes, st)
@@ -966,7 +980,9 @@ static Pool *create_pool_on(dino_ctx *ctx, int sid, int C, double dt, uint64_t s
     split_input(ctx, s, p->w, p->b, st);
     eval_surrogate(ctx, s, p->w, p->b, st);
     ReducedArgs ra = reduced_args(*p);
-    launch(ctx, st, "geometry_init", [&] { return launch_geometry(ra, 0, st); });
+    launch(ctx, st, "geometry_init", [&] {
+      return p->wb ? launch_wb_geometry(ra, 0, st) : launch_geometry(ra, 0, st);
+    });
     if (!serving) CK(cudaStreamSynchronize(st));
   } catch (...) {
     if (serving)
@@ -990,6 +1006,7 @@ static size_t pool_footprint(const Surrogate *s, int C) {
   Pool p;
   p.s = const_cast<Surrogate *>(s);
   p.C = C;
+  p.wb = s->wb;
   layout_pool(p, false);
   return p.ar.off;
 }
@@ -1001,9 +1018,13 @@ static void step_pool(dino_ctx *ctx, Pool &p) {
   cudaStream_t st = p.st;
   const double cs = std::sqrt(1.0 - p.sc * p.sc);
   ReducedArgs ra = reduced_args(p);
-  launch(ctx, st, "propose", [&] { return launch_propose(ra, st); });
+  launch(ctx, st, "propose", [&] {
+    return p.wb ? launch_wb_propose(ra, st) : launch_propose(ra, st);
+  });
   eval_surrogate(ctx, s, p.w, p.b, st);
-  launch(ctx, st, "geometry", [&] { return launch_geometry(ra, 1, st); });
+  launch(ctx, st, "geometry", [&] {
+    return p.wb ? launch_wb_geometry(ra, 1, st) : launch_geometry(ra, 1, st);
+  });
   // complement (Prop. 5.1): M prior draw, coef2 = (b - s a) - cs E M, m <- s m + cs M + D coef2
   if (s->precision == DINO_PREC_FP64) {
     double *Mf = (double *)p.Mf, *coef2 = (double *)p.coef2, *m = (double *)p.m;

@@ -1,0 +1,354 @@
+// Per-chain kernels of the surrogate mMALA step when d_y < r (Woodbury form).
+//
+// With K = J / sigma (d_y x r, sigma^2 = noise_var), eps = (f - y) / sigma,
+// H = K^T K, g = K^T eps and M = I_{d_y} + K K^T = R R^T (lower Cholesky
+// factor), the push-through and Woodbury identities give (exact in real
+// arithmetic):
+//   log det(I_r + H) = log det M,           (I + H)^-1 K^T = K^T M^-1,
+//   (I + H)^-1 (x + g) = x - K^T M^-1 u,     u = K x - eps,
+//   w = H x - g = K^T u,   w^T (I + H)^-1 w = |u|^2 - |R^-1 u|^2,
+//   mhat^T w = (K mhat)^T u,   mhat^T H mhat = |K mhat|^2,
+// and the perturbation noise (I + H)^-1 (xi1 + K^T xi2) = xi1 + K^T M^-1 (xi2 - K xi1).
+// The proposal from x (eq:reduced_space_sampling with that noise) is then
+//   mu      = s x + (1 - s) K^T v,                  v = M^-1 u,
+//   m_r^dag = s x + sqrt(1-s^2) xi1 + K^T M^-1 y,   y = (1-s) u + sqrt(1-s^2) (xi2 - K xi1),
+// with K mhat = K xi1 + (y - M^-1 y) / sqrt(1-s^2) for the forward move, and
+// log rho_{0,r} (Sec. 5.4) needs only d_y-vectors: the d_y x d_y matrix M is
+// the only one factored.
+//
+// State per chain: J at the current point (Js) and a factor slot holding the
+// packed factor of M bordered by u^T (its row d_y is R^-1 u), 1 / R_ii, u, v
+// and t1 = |u|^2 - |R^-1 u|^2, double-buffered like the r-sized path's slots.
+//
+//   k_wb_propose   the proposal and log rho_{0,r}(m_r, m_r^dag) from the state;
+//   k_wb_geometry  at m_r^dag: misfit, K m_r^dag and K m_r, M and its bordered
+//                  factor, log rho_{0,r}(m_r^dag, m_r), log rho_r^(1)
+//                  (eq:da_dino_trr_1), the accept test and the state update
+//                  (mode 1); mode 0 makes m_r^dag the state.
+// The tensor-core path (FP32 J) computes in double-float arithmetic on the
+// FP32 pipe, the FP64 path in FP64.
+#include "chol.cuh"
+
+namespace dino {
+namespace {
+
+constexpr int kWbThreads = 256;
+
+// Slot offsets (8-byte elements).
+struct WbSlot {
+  size_t R, inv, u, v, t1;
+  __host__ __device__ explicit WbSlot(int dy) {
+    R = 0;
+    inv = tri_size(dy + 1);
+    u = inv + dy + 1;
+    v = u + dy;
+    t1 = v + dy;
+  }
+};
+
+// Shared-memory layout in 8-byte elements:
+//   Ms[tri(dy+1)] inv[dy+1] | r-vectors: vb va be ae | dy-vectors: Kb Ka u sv eE zE vE
+//   | red[kRed] flag | staging of J (geometry only)
+struct WbLayout {
+  size_t Ms, inv, vb, va, be, ae, Kb, Ka, u, sv, eE, zE, vE, red, flag, tail;
+  __host__ __device__ WbLayout(int r, int dy) {
+    Ms = 0;
+    inv = (tri_size(dy + 1) + 1) & ~(size_t)1;
+    vb = inv + dy + 1;
+    va = vb + r;
+    be = va + r;
+    ae = be + r;
+    Kb = ae + r;
+    Ka = Kb + dy;
+    u = Ka + dy;
+    sv = u + dy;
+    eE = sv + dy;
+    zE = eE + dy;
+    vE = zE + dy;
+    red = vE + dy;
+    flag = red + kRed;
+    tail = (flag + 1 + 1) & ~(size_t)1;
+  }
+};
+
+template <typename TJ>
+__host__ __device__ size_t wb_stage_bytes(int r, int dy) {
+  return sizeof(TJ) == 4 ? (size_t)kJChunkF * ((dy + kHT - 1) / kHT * kHT) * sizeof(float)
+                         : (size_t)kJChunk * dy * sizeof(double);
+}
+
+// y1 = (K x1) and, when `two`, y2 = (K x2) as doubles: warp per row of J,
+// lanes along the row (coalesced), the row sums combined by shuffles.
+template <class A, typename TJ>
+__device__ void rows_times(const TJ *J, int dy, int r, double inv_sigma, const typename A::T *x1,
+                           const typename A::T *x2, bool two, double *y1, double *y2) {
+  using E = typename A::T;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = warp; i < dy; i += nw) {
+    const TJ *Ji = J + (size_t)i * r;
+    typename A::Acc a1 = A::begin(E{}), a2 = A::begin(E{});
+    for (int k = lane; k < r; k += 32) {
+      const E jk = A::from_j(Ji[k]);
+      A::sub(a1, jk, A::neg(x1[k]));
+      if (two) A::sub(a2, jk, A::neg(x2[k]));
+    }
+    const E s1 = warp_sum_elt<A>(A::end(a1));
+    const E s2 = warp_sum_elt<A>(A::end(a2));
+    if (lane == 0) {
+      y1[i] = A::to(s1) * inv_sigma;
+      if (two) y2[i] = A::to(s2) * inv_sigma;
+    }
+  }
+  __syncthreads();
+}
+
+template <typename TJ, class A>
+__device__ void wb_store_factor(double *Lg, const typename A::T *Ms, const typename A::T *inv,
+                                const double *u, const double *v, double t1, int dy) {
+  using E = typename A::T;
+  const WbSlot sl(dy);
+  E *G = reinterpret_cast<E *>(Lg);
+  for (size_t e = threadIdx.x; e < tri_size(dy + 1); e += blockDim.x) G[sl.R + e] = Ms[e];
+  for (int i = threadIdx.x; i <= dy; i += blockDim.x) G[sl.inv + i] = inv[i];
+  for (int i = threadIdx.x; i < dy; i += blockDim.x) {
+    Lg[sl.u + i] = u[i];
+    Lg[sl.v + i] = v[i];
+  }
+  if (threadIdx.x == 0) Lg[sl.t1] = t1;
+}
+
+// One CTA per chain at the point b (see the file comment).
+template <typename TJ>
+__global__ void __launch_bounds__(kWbThreads, 2) k_wb_geometry(ReducedArgs a, int mode) {
+  using A = std::conditional_t<sizeof(TJ) == 4, DF, F64>;
+  using E = typename A::T;
+  static_assert(sizeof(E) == sizeof(double), "one factor element per double of the slot");
+  extern __shared__ __align__(16) double sm[];
+  const int c = blockIdx.x, r = a.r, dy = a.d_y;
+  const WbLayout lay(r, dy);
+  const WbSlot sl(dy);
+  const size_t ldW = wb_slot_stride(dy);
+  const int slot = mode == 0 ? a.cur[c] : 1 - a.cur[c];
+  double *Lg = a.L + (size_t)slot * a.L_slot + (size_t)c * ldW;
+  E *Ms = reinterpret_cast<E *>(sm + lay.Ms);
+  E *inv = reinterpret_cast<E *>(sm + lay.inv);
+  double *vb = sm + lay.vb, *va = sm + lay.va;
+  E *be = reinterpret_cast<E *>(sm + lay.be), *ae = reinterpret_cast<E *>(sm + lay.ae);
+  double *Kb = sm + lay.Kb, *Ka = sm + lay.Ka, *u = sm + lay.u, *sv = sm + lay.sv;
+  E *vE = reinterpret_cast<E *>(sm + lay.vE);
+  double *red = sm + lay.red;
+  int *flag = reinterpret_cast<int *>(sm + lay.flag);
+  const TJ *J = reinterpret_cast<const TJ *>(a.J) + (size_t)c * dy * r;
+  const TJ *f = reinterpret_cast<const TJ *>(a.f) + (size_t)c * dy;
+  const double inv_nv = 1.0 / a.noise_var, inv_sigma = sqrt(inv_nv);
+
+  for (int k = threadIdx.x; k < r; k += blockDim.x) {
+    vb[k] = a.b[(size_t)c * r + k];
+    va[k] = mode == 1 ? a.mr[(size_t)c * r + k] : 0.0;
+    be[k] = A::from(vb[k]);
+    ae[k] = A::from(va[k]);
+  }
+  double ph = 0.0;
+  for (int i = threadIdx.x; i < dy; i += blockDim.x) {
+    const double rs = (double)f[i] - a.y[i];
+    sv[i] = rs;  // f - y, until the factor's row replaces it
+    ph += rs * rs;
+  }
+  const double phi_b = 0.5 * block_sum(ph, red) * inv_nv;  // includes a barrier
+  rows_times<A, TJ>(J, dy, r, inv_sigma, be, ae, mode == 1, Kb, Ka);  // K b, K a
+  double uu = 0.0;
+  for (int i = threadIdx.x; i < dy; i += blockDim.x) {
+    u[i] = Kb[i] - sv[i] * inv_sigma;  // u = K b - eps
+    uu += u[i] * u[i];
+  }
+  if constexpr (sizeof(TJ) == 4) {
+    form_gram_f32<true>(reinterpret_cast<const float *>(J), r, dy, r, inv_nv,
+                        reinterpret_cast<float2 *>(Ms), reinterpret_cast<float *>(sm + lay.tail));
+  } else {
+    form_gram_f64<true>(reinterpret_cast<const double *>(J), r, dy, r, inv_nv,
+                        reinterpret_cast<double *>(Ms), sm + lay.tail);
+  }
+  // bordered row u^T with pivot 1 + |u|^2 (the last pivot stays >= 1: |R^-1 u| <= |u|)
+  uu = block_sum(uu, red);
+  for (int i = threadIdx.x; i < dy; i += blockDim.x) Ms[tri(dy) + i] = A::from(u[i]);
+  if (threadIdx.x == 0) Ms[tri(dy) + dy] = A::from(1.0 + uu);
+  __syncthreads();
+  cta_cholesky<A>(Ms, inv, dy + 1, reinterpret_cast<int *>(red + 100), a.err);
+  double ld = 0.0, ss = 0.0;
+  for (int i = threadIdx.x; i < dy; i += blockDim.x) {
+    ld += log(A::to(Ms[tri(i) + i]));
+    sv[i] = A::to(Ms[tri(dy) + i]);  // R^-1 u
+    ss += sv[i] * sv[i];
+  }
+  const double hld_b = block_sum(ld, red);
+  const double t1 = uu - block_sum(ss, red);  // w^T (I+H)^-1 w at b
+
+  // v = M^-1 u = R^-T (R^-1 u), needed by the next proposal from b
+  auto solve_v = [&]() {
+    for (int i = threadIdx.x; i < dy; i += blockDim.x) vE[i] = A::from(sv[i]);
+    __syncthreads();
+    cta_upper_solve_t<A>(Ms, inv, dy, vE);
+    double *vv = Ka;  // K a is no longer needed
+    for (int i = threadIdx.x; i < dy; i += blockDim.x) vv[i] = A::to(vE[i]);
+    __syncthreads();
+    return vv;
+  };
+  auto take_state = [&]() {
+    TJ *Js = reinterpret_cast<TJ *>(a.Js) + (size_t)c * dy * r;
+    for (size_t e = threadIdx.x; e < (size_t)dy * r; e += blockDim.x) Js[e] = J[e];
+    for (int k = threadIdx.x; k < r; k += blockDim.x) a.mr[(size_t)c * r + k] = vb[k];
+  };
+
+  if (mode == 0) {
+    const double *vv = solve_v();
+    wb_store_factor<TJ, A>(Lg, Ms, inv, u, vv, t1, dy);
+    take_state();
+    if (threadIdx.x == 0) {
+      a.phi[c] = phi_b;
+      a.hld[c] = hld_b;
+    }
+    return;
+  }
+  const double s = a.s, cs = sqrt(1.0 - s * s);
+  double t2 = 0.0, t3 = 0.0, unused = 0.0;
+  for (int i = threadIdx.x; i < dy; i += blockDim.x) {
+    const double km = (Ka[i] - s * Kb[i]) / cs;  // K mhat for b -> a
+    t2 += km * u[i];
+    t3 += km * km;
+  }
+  block_sum3(t2, t3, unused, red);
+  if (threadIdx.x == 0) {
+    const double lq_rev = -a.dt / 8.0 * t1 + sqrt(a.dt) / 2.0 * t2 + hld_b - 0.5 * t3;
+    const double lr = a.phi[c] - phi_b + lq_rev - a.lq_fwd[c];
+    *flag = accept_test(a, c, lr, phi_b, hld_b) ? 1 : 0;
+  }
+  __syncthreads();
+  const bool accept = *flag != 0;
+  for (int k = threadIdx.x; k < r; k += blockDim.x) a.coef[(size_t)c * r + k] = vb[k] - s * va[k];
+  if (accept) {
+    const double *vv = solve_v();
+    wb_store_factor<TJ, A>(Lg, Ms, inv, u, vv, t1, dy);
+    take_state();
+  }
+}
+
+// One CTA per chain at the state x = m_r (see the file comment).
+template <typename TJ>
+__global__ void __launch_bounds__(kWbThreads, 2) k_wb_propose(ReducedArgs a) {
+  using A = std::conditional_t<sizeof(TJ) == 4, DF, F64>;
+  using E = typename A::T;
+  extern __shared__ __align__(16) double sm[];
+  const int c = blockIdx.x, r = a.r, dy = a.d_y;
+  const WbLayout lay(r, dy);
+  const WbSlot sl(dy);
+  const double *Lg = a.L + (size_t)a.cur[c] * a.L_slot + (size_t)c * wb_slot_stride(dy);
+  const E *G = reinterpret_cast<const E *>(Lg);
+  E *Ms = reinterpret_cast<E *>(sm + lay.Ms);
+  E *inv = reinterpret_cast<E *>(sm + lay.inv);
+  double *xa = sm + lay.vb, *xi1 = sm + lay.va;
+  E *x1E = reinterpret_cast<E *>(sm + lay.be);
+  double *Kxi = sm + lay.Kb, *xi2 = sm + lay.Ka, *u = sm + lay.u, *yv = sm + lay.sv;
+  E *zE = reinterpret_cast<E *>(sm + lay.zE), *vE = reinterpret_cast<E *>(sm + lay.vE);
+  double *red = sm + lay.red;
+  const TJ *J = reinterpret_cast<const TJ *>(a.Js) + (size_t)c * dy * r;
+  const double inv_sigma = sqrt(1.0 / a.noise_var);
+  const double s = a.s, cs = sqrt(1.0 - s * s);
+
+  for (size_t e = threadIdx.x; e < tri_size(dy); e += blockDim.x) Ms[e] = G[sl.R + e];
+  for (int i = threadIdx.x; i < dy; i += blockDim.x) {
+    inv[i] = G[sl.inv + i];
+    u[i] = Lg[sl.u + i];
+    vE[i] = A::from((1.0 - s) * Lg[sl.v + i]);
+  }
+  const uint32_t chain = (uint32_t)(a.id_base + (uint64_t)c);
+  for (int k = threadIdx.x; k < r; k += blockDim.x) xa[k] = a.mr[(size_t)c * r + k];
+  for (int blk = threadIdx.x; blk < (r + 3) / 4; blk += blockDim.x) {
+    double n4[4];
+    normals4_f64(philox_block(a.seed, STREAM_XI, a.step, chain, blk), n4);
+    for (int q = 0; q < 4; ++q)
+      if (4 * blk + q < r) {
+        xi1[4 * blk + q] = n4[q];
+        x1E[4 * blk + q] = A::from(n4[q]);
+      }
+  }
+  for (int blk = threadIdx.x; blk < (dy + 3) / 4; blk += blockDim.x) {
+    double n4[4];
+    normals4_f64(philox_block(a.seed, STREAM_XI2, a.step, chain, blk), n4);
+    for (int q = 0; q < 4; ++q)
+      if (4 * blk + q < dy) xi2[4 * blk + q] = n4[q];
+  }
+  __syncthreads();
+  rows_times<A, TJ>(J, dy, r, inv_sigma, x1E, x1E, false, Kxi, Kxi);  // K xi1
+  for (int i = threadIdx.x; i < dy; i += blockDim.x) {
+    yv[i] = (1.0 - s) * u[i] + cs * (xi2[i] - Kxi[i]);
+    zE[i] = A::from(yv[i]);
+  }
+  __syncthreads();
+  cta_lower_solve_t<A>(Ms, inv, dy, zE);
+  cta_upper_solve_t<A>(Ms, inv, dy, zE);  // z = M^-1 y
+  // K^T z and K^T ((1-s) v): thread per column of J (coalesced across threads)
+  for (int k = threadIdx.x; k < r; k += blockDim.x) {
+    typename A::Acc az = A::begin(E{}), av = A::begin(E{});
+    for (int i = 0; i < dy; ++i) {
+      const E jk = A::from_j(J[(size_t)i * r + k]);
+      A::sub(az, jk, A::neg(zE[i]));
+      A::sub(av, jk, A::neg(vE[i]));
+    }
+    const double bk = s * xa[k] + cs * xi1[k] + A::to(A::end(az)) * inv_sigma;
+    const double mk = s * xa[k] + A::to(A::end(av)) * inv_sigma;
+    a.mu[(size_t)c * r + k] = mk;
+    a.b[(size_t)c * r + k] = bk;
+    if (a.b_bf16) split_bf16_store(bk, a.b_bf16 + (size_t)c * a.b_ld + k, a.b_plane, a.b_slices);
+  }
+  double t2 = 0.0, t3 = 0.0, unused = 0.0;
+  for (int i = threadIdx.x; i < dy; i += blockDim.x) {
+    const double km = Kxi[i] + (yv[i] - A::to(zE[i])) / cs;  // K mhat
+    t2 += km * u[i];
+    t3 += km * km;
+  }
+  block_sum3(t2, t3, unused, red);
+  if (threadIdx.x == 0)
+    a.lq_fwd[c] = -a.dt / 8.0 * Lg[sl.t1] + sqrt(a.dt) / 2.0 * t2 + a.hld[c] - 0.5 * t3;
+}
+
+template <typename TJ>
+size_t wb_geometry_smem(int r, int dy) {
+  return WbLayout(r, dy).tail * sizeof(double) + wb_stage_bytes<TJ>(r, dy);
+}
+
+template <typename TJ>
+cudaError_t launch_wb_geometry_t(const ReducedArgs &a, int mode, cudaStream_t st) {
+  const size_t smem = wb_geometry_smem<TJ>(a.r, a.d_y);
+  cudaError_t e = cudaFuncSetAttribute(k_wb_geometry<TJ>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_wb_geometry<TJ><<<a.C, kWbThreads, smem, st>>>(a, mode);
+  return cudaGetLastError();
+}
+
+template <typename TJ>
+cudaError_t launch_wb_propose_t(const ReducedArgs &a, cudaStream_t st) {
+  const size_t smem = WbLayout(a.r, a.d_y).tail * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(k_wb_propose<TJ>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_wb_propose<TJ><<<a.C, kWbThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t wb_smem_bytes(int r, int d_y, int jf_f32) {
+  return jf_f32 ? wb_geometry_smem<float>(r, d_y) : wb_geometry_smem<double>(r, d_y);
+}
+
+cudaError_t launch_wb_geometry(const ReducedArgs &a, int mode, cudaStream_t st) {
+  return a.jf_f32 ? launch_wb_geometry_t<float>(a, mode, st)
+                  : launch_wb_geometry_t<double>(a, mode, st);
+}
+
+cudaError_t launch_wb_propose(const ReducedArgs &a, cudaStream_t st) {
+  return a.jf_f32 ? launch_wb_propose_t<float>(a, st) : launch_wb_propose_t<double>(a, st);
+}
+
+}  // namespace dino

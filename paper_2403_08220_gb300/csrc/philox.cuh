@@ -10,7 +10,7 @@
 
 namespace dino {
 
-enum : uint32_t { STREAM_XI = 0, STREAM_U = 1, STREAM_Z = 2, STREAM_INIT = 3 };
+enum : uint32_t { STREAM_XI = 0, STREAM_U = 1, STREAM_Z = 2, STREAM_INIT = 3, STREAM_XI2 = 4 };
 
 __host__ __device__ __forceinline__ uint32_t mulhi32(uint32_t a, uint32_t b) {
 #ifdef __CUDA_ARCH__

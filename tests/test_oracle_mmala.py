@@ -10,7 +10,10 @@ p4  gradient = finite differences of the misfit; Gauss-Newton = exact Hessian
 p5  full-field proposal of Prop. 5.1 has mean s m + (1-s) A~(m) and covariance
     (1-s^2) C~_post(m) of eq:surrogate_cpost;
 p6  the Cholesky and eigen noise maps have the same law;
-p8  r = 1: long-run chain moments equal 1-D quadrature of the target.
+p8  r = 1: long-run chain moments equal 1-D quadrature of the target;
+p9  the perturbation noise map (d_y < r) has the proposal covariance
+    (1-s^2)(I+H)^-1, and with it a linear surrogate's chain is still the
+    exact AR(1) of p2.
 """
 import numpy as np
 import pytest
@@ -216,3 +219,44 @@ def test_p8_r1_chain_moments_match_quadrature():
     assert abs(S[-1].mean() - mean_q) < 5 * sd / np.sqrt(C)
     assert abs(S.mean() - mean_q) < 5 * sd / np.sqrt(C)
     assert abs(S.var() / var_q - 1) < 0.06
+
+
+def test_p9_perturbation_map_has_the_proposal_covariance():
+    r, dy, dt, nv = 7, 3, 0.5, 0.1
+    s = mmala.s_of_dt(dt)
+    sur = _surrogate([r, 8, dy], mlp.ACT_TANH, noise_var=nv)
+    a = np.random.default_rng(8).standard_normal(r)
+    geo = mmala.geometry(sur, a)
+    mu, b0 = mmala.reduced_proposal_perturbation(a, geo, np.zeros(r), np.zeros(dy), nv, dt)
+    assert np.allclose(b0, mu, atol=1e-13) and np.allclose(mu, mmala.proposal_mean(a, geo, dt))
+    cols = [mmala.reduced_proposal_perturbation(a, geo, e[:r], e[r:], nv, dt)[1] - b0
+            for e in np.eye(r + dy)]
+    T = np.array(cols).T                                   # b - mu = T [xi1; xi2]
+    cov_ref = (1 - s * s) * np.linalg.inv(np.eye(r) + geo.J.T @ geo.J / nv)
+    assert np.allclose(T @ T.T, cov_ref, atol=1e-12 * np.abs(cov_ref).max())
+    # dropping the observation-space normals (or mis-scaling K) breaks the law
+    T1 = T[:, :r]
+    assert np.abs(T1 @ T1.T - cov_ref).max() > 1e-3 * np.abs(cov_ref).max()
+    assert mmala.noise_map(r, dy) == "perturbation" and mmala.noise_map(dy, r) == "cholesky"
+
+
+def test_p9_perturbation_chain_is_exact_ar1_for_linear_surrogate():
+    n, r, dy = 3, 5, 2
+    sur = _surrogate([r, 4, dy], mlp.ACT_IDENTITY, noise_var=0.3)
+    E, D = prior.kle_basis(n, GAMMA, DELTA, r)
+    C, dt = 4000, 0.5
+    s = mmala.s_of_dt(dt)
+    ch = OracleChains(sur, E, D, n, GAMMA, DELTA, C, dt, seed=32, m0=np.zeros(n * n))
+    assert ch.noise == "perturbation"
+    W = sur.Ws[1] @ sur.Ws[0]
+    c = sur.Ws[1] @ sur.bs[0] + sur.bs[1]
+    Cpost = np.linalg.inv(np.eye(r) + W.T @ W / sur.noise_var)
+    mpost = Cpost @ W.T @ (sur.y - c) / sur.noise_var
+    for j in range(1, 4):
+        ch.step()
+        assert ch.last["accepted"].all()
+        mean = mpost + s ** j * (np.zeros(r) - mpost)
+        cov = (1 - s ** (2 * j)) * Cpost
+        w = np.linalg.solve(np.linalg.cholesky(cov), (ch.m_r - mean).T).T
+        assert np.all(np.abs(w.mean(0)) < 5 / np.sqrt(C))
+        assert np.abs(np.cov(w.T) - np.eye(r)).max() < 7 / np.sqrt(C)
