@@ -582,12 +582,15 @@ __device__ void form_gram_f64(const double *X, int m, int n, int ldx, double inv
   const int lsz = tri(n);
   for (int i0 = 0; i0 < m; i0 += kJChunk) {
     const int nr = min(kJChunk, m - i0);
+    // unrolled so that each thread has several independent loads in flight
     if (kRedContig) {
+#pragma unroll 8
       for (int e = threadIdx.x; e < nr * n; e += blockDim.x) {
         const int i = e / nr, k = e % nr;
         Jc[k * n + i] = X[(size_t)i * ldx + i0 + k];
       }
     } else {
+#pragma unroll 8
       for (int e = threadIdx.x; e < nr * n; e += blockDim.x) {
         const int k = e / n, i = e % n;
         Jc[e] = X[(size_t)(i0 + k) * ldx + i];
@@ -651,12 +654,15 @@ __device__ void form_gram_f32(const float *X, int m, int n, int ldx, double inv_
     }
     for (int i0 = 0; i0 < dy; i0 += kJChunkF) {
       const int nr = min(kJChunkF, dy - i0);
+      // unrolled so that each thread has several independent loads in flight
       if (kRedContig) {
+#pragma unroll 8
         for (int e = threadIdx.x; e < nr * rp; e += blockDim.x) {
           const int j = e / nr, k = e % nr;
           Jc[k * rp + j] = j < r ? X[(size_t)j * ldx + i0 + k] : 0.0f;
         }
       } else {
+#pragma unroll 8
         for (int e = threadIdx.x; e < nr * rp; e += blockDim.x) {
           const int k = e / rp, j = e % rp;
           Jc[e] = j < r ? X[(size_t)(i0 + k) * ldx + j] : 0.0f;

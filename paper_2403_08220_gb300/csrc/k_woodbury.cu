@@ -32,7 +32,8 @@
 namespace dino {
 namespace {
 
-constexpr int kWbThreads = 256;
+constexpr int kWbThreads = 128;
+constexpr int kWbMinBlocks = 3;  // CTAs per SM the register budget is sized for
 
 // Slot offsets (8-byte elements).
 struct WbSlot {
@@ -72,10 +73,7 @@ struct WbLayout {
 };
 
 template <typename TJ>
-__host__ __device__ size_t wb_stage_bytes(int r, int dy) {
-  return sizeof(TJ) == 4 ? (size_t)kJChunkF * ((dy + kHT - 1) / kHT * kHT) * sizeof(float)
-                         : (size_t)kJChunk * dy * sizeof(double);
-}
+__host__ __device__ size_t wb_stage_bytes(int r, int dy);
 
 // y1 = (K x1) and, when `two`, y2 = (K x2) as doubles: warp per row of J,
 // lanes along the row (coalesced), the row sums combined by shuffles.
@@ -87,6 +85,7 @@ __device__ void rows_times(const TJ *J, int dy, int r, double inv_sigma, const t
   for (int i = warp; i < dy; i += nw) {
     const TJ *Ji = J + (size_t)i * r;
     typename A::Acc a1 = A::begin(E{}), a2 = A::begin(E{});
+#pragma unroll 4
     for (int k = lane; k < r; k += 32) {
       const E jk = A::from_j(Ji[k]);
       A::sub(a1, jk, A::neg(x1[k]));
@@ -98,6 +97,190 @@ __device__ void rows_times(const TJ *J, int dy, int r, double inv_sigma, const t
       y1[i] = A::to(s1) * inv_sigma;
       if (two) y2[i] = A::to(s2) * inv_sigma;
     }
+  }
+  __syncthreads();
+}
+
+constexpr int kWbKc = 16;          // J columns per staged chunk (tensor-core path)
+constexpr int kWbLd = kWbKc + 4;   // padded row length (floats) of a staged chunk
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// 16-byte asynchronous copy global -> shared; bytes beyond `src_bytes` (0..16)
+// are zero-filled.  Both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src),
+               "r"(src_bytes)
+               : "memory");
+}
+// 4-byte variant (src_bytes 0 or 4).
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_addr(dst)), "l"(src),
+               "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Shared bytes of the two staging buffers of wb_gram_rows.
+__host__ __device__ inline size_t wb_stage2_bytes(int dy) {
+  return 2 * (size_t)((dy + kHT - 1) / kHT * kHT) * kWbLd * sizeof(float);
+}
+
+template <typename TJ>
+__host__ __device__ size_t wb_stage_bytes(int r, int dy) {
+  return sizeof(TJ) == 4 ? wb_stage2_bytes(dy) : (size_t)kJChunk * dy * sizeof(double);
+}
+
+// M = I + J J^T / noise_var (double-float entries, FP32 register tiles) and,
+// from the same pass over J, Kb = (J b) / sigma and Ka = (J a) / sigma
+// (double-float dot products, thread per row).  J (dy x r, row-major FP32)
+// streams through two shared buffers in chunks of kWbKc columns by
+// asynchronous copies, the next chunk in flight while the current one is
+// used; rows are kept in natural order (padded to kWbLd floats) and read as
+// float4 along the reduction index.
+template <class A>
+__device__ void wb_gram_rows(const float *J, int dy, int r, double inv_nv, double inv_sigma,
+                             float2 *Ms, float *stage, const float2 *be, const float2 *ae,
+                             bool two, double *Kb, double *Ka) {
+  const int tid = threadIdx.x, T = blockDim.x;
+  const int nt = (dy + kHT - 1) / kHT, dyp = nt * kHT;
+  const int ntiles = nt * (nt + 1) / 2;
+  const int nch = (r + kWbKc - 1) / kWbKc;
+  const bool vec = (r % 4) == 0;  // 16-byte aligned rows
+  const size_t bstride = (size_t)dyp * kWbLd;  // floats between the two buffers
+  for (int e = tid; e < (dyp - dy) * kWbLd; e += T) {  // padding rows stay zero
+    stage[(size_t)dy * kWbLd + e] = 0.0f;
+    stage[bstride + (size_t)dy * kWbLd + e] = 0.0f;
+  }
+  auto issue = [&](int ch) {
+    float *dst = stage + (ch & 1) * bstride;
+    const int k0 = ch * kWbKc;
+    if (vec) {
+      for (int e = tid; e < dy * (kWbKc / 4); e += T) {
+        const int j = e / (kWbKc / 4), k = 4 * (e % (kWbKc / 4));
+        const int left = r - (k0 + k);
+        const int bytes = left >= 4 ? 16 : (left > 0 ? 4 * left : 0);
+        const float *src = J + (size_t)j * r + (left > 0 ? k0 + k : 0);
+        cp_async16(dst + (size_t)j * kWbLd + k, src, bytes);
+      }
+    } else {
+      for (int e = tid; e < dy * kWbKc; e += T) {
+        const int j = e / kWbKc, k = e % kWbKc;
+        const bool in = k0 + k < r;
+        cp_async4(dst + (size_t)j * kWbLd + k, J + (size_t)j * r + (in ? k0 + k : 0), in ? 4 : 0);
+      }
+    }
+    cp_async_commit();
+  };
+
+  int ti[kHMaxTiles], tj[kHMaxTiles];
+  float acc[kHMaxTiles][kHT][kHT];
+#pragma unroll
+  for (int s = 0; s < kHMaxTiles; ++s) {
+    const int tt = tid + s * T;
+    if (tt < ntiles) {
+      tri_pos(tt, ti[s], tj[s]);
+    } else {
+      ti[s] = -1;
+      tj[s] = 0;
+    }
+#pragma unroll
+    for (int p = 0; p < kHT; ++p)
+#pragma unroll
+      for (int q = 0; q < kHT; ++q) acc[s][p][q] = 0.0f;
+  }
+  typename A::Acc kb[2] = {A::begin(float2{}), A::begin(float2{})};
+  typename A::Acc ka[2] = {A::begin(float2{}), A::begin(float2{})};
+
+  issue(0);
+  for (int ch = 0; ch < nch; ++ch) {
+    if (ch + 1 < nch) {
+      issue(ch + 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const float *x = stage + (ch & 1) * bstride;
+    const int k0 = ch * kWbKc;
+#pragma unroll
+    for (int kk = 0; kk < kWbKc; kk += 4) {
+#pragma unroll
+      for (int s = 0; s < kHMaxTiles; ++s) {
+        if (ti[s] < 0) continue;
+        float4 xa[kHT], ya[kHT];
+#pragma unroll
+        for (int p = 0; p < kHT; ++p) {
+          xa[p] = *reinterpret_cast<const float4 *>(x + (size_t)(kHT * ti[s] + p) * kWbLd + kk);
+          ya[p] = *reinterpret_cast<const float4 *>(x + (size_t)(kHT * tj[s] + p) * kWbLd + kk);
+        }
+#pragma unroll
+        for (int p = 0; p < kHT; ++p)
+#pragma unroll
+          for (int q = 0; q < kHT; ++q) {
+            float v = acc[s][p][q];
+            v = fmaf(xa[p].x, ya[q].x, v);
+            v = fmaf(xa[p].y, ya[q].y, v);
+            v = fmaf(xa[p].z, ya[q].z, v);
+            v = fmaf(xa[p].w, ya[q].w, v);
+            acc[s][p][q] = v;
+          }
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = tid + h * T;
+      if (j < dy) {
+        const float *row = x + (size_t)j * kWbLd;
+        const int kn = min(kWbKc, r - k0);
+        for (int k = 0; k < kn; ++k) {
+          const float2 jk = A::from_j(row[k]);
+          A::sub(kb[h], jk, A::neg(be[k0 + k]));
+          if (two) A::sub(ka[h], jk, A::neg(ae[k0 + k]));
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int j = tid + h * T;
+    if (j < dy) {
+      Kb[j] = A::to(A::end(kb[h])) * inv_sigma;
+      Ka[j] = two ? A::to(A::end(ka[h])) * inv_sigma : 0.0;
+    }
+  }
+  const float nh = __double2float_rn(inv_nv), nl = __double2float_rn(inv_nv - (double)nh);
+#pragma unroll
+  for (int s = 0; s < kHMaxTiles; ++s) {
+    if (ti[s] < 0) continue;
+#pragma unroll
+    for (int p = 0; p < kHT; ++p)
+#pragma unroll
+      for (int q = 0; q < kHT; ++q) {
+        const int i = kHT * ti[s] + p, j = kHT * tj[s] + q;
+        if (i < dy && j <= i) {
+          const float xv = acc[s][p][q], ph = __fmul_rn(xv, nh);
+          float e = __fmaf_rn(xv, nh, -ph);
+          e = __fmaf_rn(xv, nl, e);
+          float h, l;
+          fast_two_sum(ph, e, h, l);
+          if (i == j) {
+            float s1, q1;
+            two_sum(1.0f, h, s1, q1);
+            fast_two_sum(s1, __fadd_rn(q1, l), h, l);
+          }
+          Ms[tri(i) + j] = make_float2(h, l);
+        }
+      }
   }
   __syncthreads();
 }
@@ -119,7 +302,7 @@ __device__ void wb_store_factor(double *Lg, const typename A::T *Ms, const typen
 
 // One CTA per chain at the point b (see the file comment).
 template <typename TJ>
-__global__ void __launch_bounds__(kWbThreads, 2) k_wb_geometry(ReducedArgs a, int mode) {
+__global__ void __launch_bounds__(kWbThreads, kWbMinBlocks) k_wb_geometry(ReducedArgs a, int mode) {
   using A = std::conditional_t<sizeof(TJ) == 4, DF, F64>;
   using E = typename A::T;
   static_assert(sizeof(E) == sizeof(double), "one factor element per double of the slot");
@@ -155,18 +338,20 @@ __global__ void __launch_bounds__(kWbThreads, 2) k_wb_geometry(ReducedArgs a, in
     ph += rs * rs;
   }
   const double phi_b = 0.5 * block_sum(ph, red) * inv_nv;  // includes a barrier
-  rows_times<A, TJ>(J, dy, r, inv_sigma, be, ae, mode == 1, Kb, Ka);  // K b, K a
+  if constexpr (sizeof(TJ) == 4) {  // M, K b and K a from one pass over J
+    wb_gram_rows<A>(reinterpret_cast<const float *>(J), dy, r, inv_nv, inv_sigma,
+                    reinterpret_cast<float2 *>(Ms), reinterpret_cast<float *>(sm + lay.tail),
+                    reinterpret_cast<const float2 *>(be), reinterpret_cast<const float2 *>(ae),
+                    mode == 1, Kb, Ka);
+  } else {
+    rows_times<A, TJ>(J, dy, r, inv_sigma, be, ae, mode == 1, Kb, Ka);  // K b, K a
+    form_gram_f64<true>(reinterpret_cast<const double *>(J), r, dy, r, inv_nv,
+                        reinterpret_cast<double *>(Ms), sm + lay.tail);
+  }
   double uu = 0.0;
   for (int i = threadIdx.x; i < dy; i += blockDim.x) {
     u[i] = Kb[i] - sv[i] * inv_sigma;  // u = K b - eps
     uu += u[i] * u[i];
-  }
-  if constexpr (sizeof(TJ) == 4) {
-    form_gram_f32<true>(reinterpret_cast<const float *>(J), r, dy, r, inv_nv,
-                        reinterpret_cast<float2 *>(Ms), reinterpret_cast<float *>(sm + lay.tail));
-  } else {
-    form_gram_f64<true>(reinterpret_cast<const double *>(J), r, dy, r, inv_nv,
-                        reinterpret_cast<double *>(Ms), sm + lay.tail);
   }
   // bordered row u^T with pivot 1 + |u|^2 (the last pivot stays >= 1: |R^-1 u| <= |u|)
   uu = block_sum(uu, red);
@@ -234,7 +419,7 @@ __global__ void __launch_bounds__(kWbThreads, 2) k_wb_geometry(ReducedArgs a, in
 
 // One CTA per chain at the state x = m_r (see the file comment).
 template <typename TJ>
-__global__ void __launch_bounds__(kWbThreads, 2) k_wb_propose(ReducedArgs a) {
+__global__ void __launch_bounds__(kWbThreads, kWbMinBlocks) k_wb_propose(ReducedArgs a) {
   using A = std::conditional_t<sizeof(TJ) == 4, DF, F64>;
   using E = typename A::T;
   extern __shared__ __align__(16) double sm[];
@@ -289,6 +474,7 @@ __global__ void __launch_bounds__(kWbThreads, 2) k_wb_propose(ReducedArgs a) {
   // K^T z and K^T ((1-s) v): thread per column of J (coalesced across threads)
   for (int k = threadIdx.x; k < r; k += blockDim.x) {
     typename A::Acc az = A::begin(E{}), av = A::begin(E{});
+#pragma unroll 8
     for (int i = 0; i < dy; ++i) {
       const E jk = A::from_j(J[(size_t)i * r + k]);
       A::sub(az, jk, A::neg(zE[i]));
