@@ -169,11 +169,10 @@ struct DF {
     return make_float2(h, l);
   }
   __device__ static T neg(T a) { return make_float2(-a.x, -a.y); }
-  // The same pivot on the FP32 pipe: each Newton step y <- y + y (1 - x y^2) / 2
+  // The same pivot on the FP32 pipe: the Newton step y <- y + y (1 - x y^2) / 2
   // takes the residual 1 - x y^2 exactly (double-float product, two-sum
-  // against 1) and the small correction in FP32.  From the FP32 estimate
-  // (relative error ~2^-22) the first step reaches ~2^-43, the second the
-  // double-float precision.  x <= 0 gives NaN, as in FP64.
+  // against 1) and the small correction in FP32, so from an estimate with
+  // relative error e it reaches about 1.5 e^2.  x <= 0 gives NaN, as in FP64.
   __device__ static void newton_rsqrt(T x, T &y) {
     const T y2 = mul(y, y);
     const T xy2 = mul(x, y2);
@@ -186,8 +185,11 @@ struct DF {
     fast_two_sum(h, __fadd_rn(l, y.y), y.x, y.y);
   }
   __device__ static void pivot(T x, T &d, T &id) {
-    T y = make_float2(rsqrtf(x.x), 0.0f);
-    newton_rsqrt(x, y);
+    // FP32 estimate, one FP32 Newton step (relative error ~2^-23), then one
+    // double-float step (~2^-45)
+    float y0 = rsqrtf(x.x);
+    y0 = y0 * (1.5f - 0.5f * x.x * y0 * y0);
+    T y = make_float2(y0, 0.0f);
     newton_rsqrt(x, y);
     id = y;
     d = mul(x, y);
@@ -292,60 +294,45 @@ __device__ __forceinline__ void tri_pos(int e, int &ii, int &jj) {
 
 
 // Factor the 8 x 8 diagonal block at kb (size nb) by one warp, in registers:
-// lane i < nb holds row i of the block.  When pk >= 0 the block first takes
-// the rank-8 update from the panel at pk (final by then).  At step q, c[k]
-// holds L(i, q + k): the pivot (A::pivot, computed by every lane from the
-// broadcast diagonal entry), the scaling of column q, its store, the rank-1
-// update of the columns to its right (L(q + k, q) by shuffle from lane q + k),
-// then a shift of c by one column.  Lanes compute every column and keep
-// theirs by selects, so the independent updates interleave; the q loop stays
-// rolled to keep its code small.  inv[k] = 1 / L_kk.
+// lane i < nb holds row i of the block (c[j] = L(i, j)).  Per column q: the
+// pivot (A::pivot, computed by every lane from the broadcast diagonal
+// entry), the scaling of column q, its store, and the rank-1 update of the
+// columns to its right, L(k, q) coming by shuffle from lane k.  Lanes
+// compute every column and keep theirs by selects (no divergent branches),
+// and the q loop is unrolled, so the updates of one column overlap the next
+// pivot's dependent chain.  inv[k] = 1 / L_kk.
 template <class A>
 __device__ __noinline__ void warp_factor_diag(typename A::T *Ls, typename A::T *inv, int kb,
-                                              int nb, int pk, int lane) {
+                                              int nb, int lane) {
   using E = typename A::T;
   E c[kNB];
   const bool in = lane < nb;
   const int ri = kb + (in ? lane : nb - 1);  // lanes >= nb shadow the last row
 #pragma unroll
-  for (int j = 0; j < kNB; ++j) c[j] = j < nb ? Ls[tri(ri) + kb + min(j, lane)] : E{};
-  if (pk >= 0) {
-    E xr[kNB];
-#pragma unroll
-    for (int p = 0; p < kNB; ++p) xr[p] = Ls[tri(ri) + pk + p];
-#pragma unroll
-    for (int j = 0; j < kNB; ++j) {
-      if (j < nb) {
-        const E *lj = Ls + tri(kb + j) + pk;
-        typename A::Acc acc = A::begin(c[j]);
-#pragma unroll
-        for (int p = 0; p < kNB; ++p) A::sub(acc, xr[p], lj[p]);
-        const E u = A::end(acc);
-        c[j] = j <= lane ? u : c[j];
-      }
-    }
+  for (int j = 0; j < kNB; ++j) {
+    const E x = j < nb ? Ls[tri(ri) + kb + min(j, lane)] : E{};
+    c[j] = (in && j <= lane) ? x : E{};
   }
 #pragma unroll
-  for (int j = 0; j < kNB; ++j) c[j] = (in && j <= lane) ? c[j] : E{};
-#pragma unroll 1
-  for (int q = 0; q < nb; ++q) {
-    E d, id;
-    A::pivot(shfl_elt(c[0], q), d, id);
-    const E sc = A::mul(c[0], id);
-    c[0] = lane == q ? d : (lane > q ? sc : c[0]);
-    if (lane == 0) inv[kb + q] = id;
-    if (in && lane >= q) Ls[tri(kb + lane) + kb + q] = c[0];
+  for (int q = 0; q < kNB; ++q) {
+    if (q < nb) {
+      E d, id;
+      A::pivot(shfl_elt(c[q], q), d, id);
+      const E sc = A::mul(c[q], id);
+      c[q] = lane == q ? d : (lane > q ? sc : c[q]);
+      if (lane == 0) inv[kb + q] = id;
+      if (in && lane >= q) Ls[tri(kb + lane) + kb + q] = c[q];
 #pragma unroll
-    for (int k = 1; k < kNB; ++k) {
-      const E l = shfl_elt(c[0], q + k);
-      typename A::Acc acc = A::begin(c[k]);
-      A::sub(acc, c[0], l);
-      const E u = A::end(acc);
-      c[k] = lane >= q + k ? u : c[k];
+      for (int k = q + 1; k < kNB; ++k) {
+        if (k < nb) {
+          const E l = shfl_elt(c[q], k);
+          typename A::Acc acc = A::begin(c[k]);
+          A::sub(acc, c[q], l);
+          const E u = A::end(acc);
+          c[k] = lane >= k ? u : c[k];
+        }
+      }
     }
-#pragma unroll
-    for (int k = 0; k + 1 < kNB; ++k) c[k] = c[k + 1];
-    c[kNB - 1] = E{};
   }
   __syncwarp();
 }
@@ -494,7 +481,7 @@ template <class A>
 __device__ void cta_cholesky(typename A::T *Ls, typename A::T *inv, int r, int *ctr, int *err) {
   const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid < 6) ctr[tid] = 0;
-  if (warp == 0) warp_factor_diag<A>(Ls, inv, 0, min(kNB, r), -1, lane);
+  if (warp == 0) warp_factor_diag<A>(Ls, inv, 0, min(kNB, r), lane);
   __syncthreads();
   for (int i = min(kNB, r) + tid; i < r; i += T) panel_row<A>(Ls, inv, 0, min(kNB, r), -1, i);
   __syncthreads();
@@ -510,7 +497,7 @@ __device__ void cta_cholesky(typename A::T *Ls, typename A::T *inv, int r, int *
     }
     __syncthreads();
     if (warp == 0) {  // (B)
-      warp_factor_diag<A>(Ls, inv, nk, nb2, -1, lane);
+      warp_factor_diag<A>(Ls, inv, nk, nb2, lane);
       __threadfence_block();
       if (lane == 0) atomicExch(&c3[2], 1);
     }

@@ -33,7 +33,7 @@ namespace dino {
 namespace {
 
 constexpr int kWbThreads = 128;
-constexpr int kWbMinBlocks = 3;  // CTAs per SM the register budget is sized for
+constexpr int kWbMinBlocks = 4;  // CTAs per SM the register budget is sized for
 
 // Slot offsets (8-byte elements).
 struct WbSlot {
@@ -49,7 +49,9 @@ struct WbSlot {
 
 // Shared-memory layout in 8-byte elements:
 //   Ms[tri(dy+1)] inv[dy+1] | r-vectors: vb va be ae | dy-vectors: Kb Ka u sv eE zE vE
-//   | red[kRed] flag | staging of J (geometry only)
+//   | red[kRed] flag | staging of J (FP64 geometry only)
+// On the tensor-core path J is staged inside Ms, which holds nothing until
+// the Gram tiles are written (wb_stage_fits).
 struct WbLayout {
   size_t Ms, inv, vb, va, be, ae, Kb, Ka, u, sv, eE, zE, vE, red, flag, tail;
   __host__ __device__ WbLayout(int r, int dy) {
@@ -134,9 +136,16 @@ __host__ __device__ inline size_t wb_stage2_bytes(int dy) {
   return 2 * (size_t)((dy + kHT - 1) / kHT * kHT) * kWbLd * sizeof(float);
 }
 
+// The two FP32 staging buffers fit in the factor's region when
+// 2 ceil4(d_y) kWbLd floats <= tri(d_y + 1) doubles (from d_y of about 36 up).
+__host__ __device__ inline bool wb_stage_fits(int dy) {
+  return wb_stage2_bytes(dy) <= ((tri_size(dy + 1) + 1) & ~(size_t)1) * sizeof(double);
+}
+
 template <typename TJ>
 __host__ __device__ size_t wb_stage_bytes(int r, int dy) {
-  return sizeof(TJ) == 4 ? wb_stage2_bytes(dy) : (size_t)kJChunk * dy * sizeof(double);
+  if (sizeof(TJ) == 4) return wb_stage_fits(dy) ? 0 : wb_stage2_bytes(dy);
+  return (size_t)kJChunk * dy * sizeof(double);
 }
 
 // M = I + J J^T / noise_var (double-float entries, FP32 register tiles) and,
@@ -339,8 +348,10 @@ __global__ void __launch_bounds__(kWbThreads, kWbMinBlocks) k_wb_geometry(Reduce
   }
   const double phi_b = 0.5 * block_sum(ph, red) * inv_nv;  // includes a barrier
   if constexpr (sizeof(TJ) == 4) {  // M, K b and K a from one pass over J
+    float *stage = wb_stage_fits(dy) ? reinterpret_cast<float *>(sm + lay.Ms)
+                                     : reinterpret_cast<float *>(sm + lay.tail);
     wb_gram_rows<A>(reinterpret_cast<const float *>(J), dy, r, inv_nv, inv_sigma,
-                    reinterpret_cast<float2 *>(Ms), reinterpret_cast<float *>(sm + lay.tail),
+                    reinterpret_cast<float2 *>(Ms), stage,
                     reinterpret_cast<const float2 *>(be), reinterpret_cast<const float2 *>(ae),
                     mode == 1, Kb, Ka);
   } else {
