@@ -109,6 +109,8 @@ cudaError_t gemm_field(int M, int N, int K, const T *A, int lda, const T *B, int
                        cudaStream_t st);
 
 // ---- elementwise / per-chain helpers -------------------------------------
+// Shared memory of the prior draw of one chain on an n x n grid (elements of `elem` bytes).
+size_t prior_draw_smem_bytes(int n, int elem);
 // Prior draw from the full KLE: out[c] = S^T (sqrt(Lambda) .* Z_c) S,
 // Z_c from Philox stream `stream` at `step` for chain id_base + c.
 template <typename T>

@@ -474,6 +474,9 @@ static int load_surrogate(dino_ctx *ctx, const dino_surrogate_desc *d) {
   s->id = ctx->next_id++;
   s->n_grid = d->n_grid;
   s->N = d->n_grid * d->n_grid;
+  if (prior_draw_smem_bytes(s->n_grid, 8) > kSmemLimit)
+    fail(DINO_EINVAL, "n_grid=%d exceeds the per-chain prior draw's shared-memory budget",
+         s->n_grid);
   s->gamma = d->prior_gamma;
   s->delta = d->prior_delta;
   s->r = d->r;

@@ -146,48 +146,88 @@ cudaError_t run_gemm(int M, int N, int K, const T *A, int lda, const T *B, int l
 }
 
 // Prior draw: one CTA per chain; X = sqrt(Lambda) .* Z (spectral), Y = X S,
-// M = S^T Y, all n x n in shared memory.
+// M = S^T Y, all n x n in shared memory with rows padded to a multiple of 4
+// (zero-filled).  Each product is computed in 4 x 4 register tiles: per step
+// of the reduction a tile reads one float4 (or double4-as-two-loads) row
+// segment of the right operand and four broadcast values of the left one.
+constexpr int kPriorThreads = 256;
+
+__host__ __device__ inline int prior_ld(int n) { return (n + 3) / 4 * 4; }
+
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kPriorThreads)
     k_prior_draw(int n, const T *__restrict__ sqrtlam, const T *__restrict__ S, uint64_t seed,
                  uint64_t id_base, uint32_t stream, uint32_t step, T *out, int ldo) {
-  extern __shared__ unsigned char smraw[];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int ld = prior_ld(n), nt = ld / 4, NN = ld * ld;
   T *X = reinterpret_cast<T *>(smraw);
-  T *Ss = X + n * n;
-  T *Y = Ss + n * n;
+  T *Ss = X + NN;
+  T *Y = Ss + NN;
   const int c = blockIdx.x, N = n * n;
   const uint32_t chain = (uint32_t)(id_base + (uint64_t)c);
+  for (int e = threadIdx.x; e < NN; e += blockDim.x) {
+    const int row = e / ld, col = e % ld;
+    const bool in = row < n && col < n;
+    X[e] = T(0);
+    Ss[e] = in ? S[row * n + col] : T(0);
+  }
+  __syncthreads();
   for (int blk = threadIdx.x; blk < (N + 3) / 4; blk += blockDim.x) {
     const uint4 w = philox_block(seed, stream, step, chain, blk);
+    T z[4];
     if constexpr (sizeof(T) == 8) {
-      double z[4];
       normals4_f64(w, z);
-      for (int q = 0; q < 4; ++q)
-        if (4 * blk + q < N) X[4 * blk + q] = sqrtlam[4 * blk + q] * z[q];
     } else {
-      float z[4];
       normals4_f32(w, z);
-      for (int q = 0; q < 4; ++q)
-        if (4 * blk + q < N) X[4 * blk + q] = sqrtlam[4 * blk + q] * z[q];
+    }
+    for (int q = 0; q < 4; ++q) {
+      const int m = 4 * blk + q;
+      if (m < N) X[(m / n) * ld + m % n] = sqrtlam[m] * z[q];
     }
   }
-  for (int e = threadIdx.x; e < N; e += blockDim.x) Ss[e] = S[e];
   __syncthreads();
-  // X is indexed [ky-1][kx-1]; Y[ky][i] = sum_kx X[ky][kx] S[kx][i]
-  for (int e = threadIdx.x; e < N; e += blockDim.x) {
-    const int ky = e / n, i = e % n;
-    T acc = 0;
-    for (int kx = 0; kx < n; ++kx) acc += X[ky * n + kx] * Ss[kx * n + i];
-    Y[e] = acc;
+  // Y[ky][i] = sum_kx X[ky][kx] S[kx][i]
+  for (int tt = threadIdx.x; tt < nt * nt; tt += blockDim.x) {
+    const int r0 = 4 * (tt / nt), c0 = 4 * (tt % nt);
+    T acc[4][4] = {};
+    for (int k = 0; k < n; ++k) {
+      T a[4], b[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) a[p] = X[(r0 + p) * ld + k];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) b[q] = Ss[k * ld + c0 + q];
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] += a[p] * b[q];
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) Y[(r0 + p) * ld + c0 + q] = acc[p][q];
   }
   __syncthreads();
   // M[j][i] = sum_ky S[ky][j] Y[ky][i]; node p = i + n j
   T *o = out + (size_t)c * ldo;
-  for (int e = threadIdx.x; e < N; e += blockDim.x) {
-    const int j = e / n, i = e % n;
-    T acc = 0;
-    for (int ky = 0; ky < n; ++ky) acc += Ss[ky * n + j] * Y[ky * n + i];
-    o[e] = acc;
+  for (int tt = threadIdx.x; tt < nt * nt; tt += blockDim.x) {
+    const int r0 = 4 * (tt / nt), c0 = 4 * (tt % nt);
+    T acc[4][4] = {};
+    for (int k = 0; k < n; ++k) {
+      T a[4], b[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) a[p] = Ss[k * ld + r0 + p];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) b[q] = Y[k * ld + c0 + q];
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] += a[p] * b[q];
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (r0 + p < n && c0 + q < n) o[(r0 + p) * n + c0 + q] = acc[p][q];
   }
 }
 
@@ -259,16 +299,21 @@ cudaError_t gemm_field(int M, int N, int K, const T *A, int lda, const T *B, int
   return run_gemm(M, N, K, A, lda, B, ldb, EpiField<T>{acc_flag, s, c, m, Mf, ldm}, st);
 }
 
+size_t prior_draw_smem_bytes(int n, int elem) {
+  return 3 * (size_t)prior_ld(n) * prior_ld(n) * elem;
+}
+
 template <typename T>
 cudaError_t launch_prior_draw(int C, int n, const T *sqrtlam, const T *S, uint64_t seed,
                               uint64_t id_base, uint32_t stream, uint32_t step, T *out, int ldo,
                               cudaStream_t st) {
   if (C <= 0) return cudaSuccess;
-  const size_t smem = 3 * (size_t)n * n * sizeof(T);
+  const size_t smem = prior_draw_smem_bytes(n, (int)sizeof(T));
   cudaError_t e = cudaFuncSetAttribute(k_prior_draw<T>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_prior_draw<T><<<C, 256, smem, st>>>(n, sqrtlam, S, seed, id_base, stream, step, out, ldo);
+  k_prior_draw<T><<<C, kPriorThreads, smem, st>>>(n, sqrtlam, S, seed, id_base, stream, step, out,
+                                                   ldo);
   return cudaGetLastError();
 }
 
