@@ -98,10 +98,12 @@ template <typename T>
 cudaError_t gemm_scale_group(int M, int N, int K, const T *A, int lda, const T *B, int ldb,
                              const T *scale, int lds, int group, T *out, int ldo,
                              cudaStream_t st);
-// complement coefficient: out[row, col] = coef[row * ldc + col] - c * acc
+// complement coefficient: out[row, col] = coef[row * ldc + col] - c * acc.
+// FP32: split over K into partial sums in ws (ws_floats floats; nullptr: no split).
 template <typename T>
 cudaError_t gemm_coef(int M, int N, int K, const T *A, int lda, const T *B, int ldb,
-                      const double *coef, int ldc, double c, T *out, int ldo, cudaStream_t st);
+                      const double *coef, int ldc, double c, T *out, int ldo, cudaStream_t st,
+                      float *ws = nullptr, size_t ws_floats = 0);
 // field update: if acc_flag[row]: m[row, col] = s m + c Mf[row, col] + acc
 template <typename T>
 cudaError_t gemm_field(int M, int N, int K, const T *A, int lda, const T *B, int ldb,

@@ -1048,7 +1048,10 @@ static void step_pool(dino_ctx *ctx, Pool &p) {
                                       STREAM_Z_ID, p.step, Mf, N, st);
     });
     launch(ctx, st, "field_coef_f32", [&] {
-      return gemm_coef<float>(C, r, N, Mf, N, s->fE, N, p.coef, r, cs, coef2, r, st);
+      // split-K partials in the Jacobian's P buffer, free once the Jacobian is formed
+      const size_t ws = p.w.Pb[0] ? p.w.plp * s->jac_slices / 2 : 0;  // bf16 -> float
+      return gemm_coef<float>(C, r, N, Mf, N, s->fE, N, p.coef, r, cs, coef2, r, st,
+                              reinterpret_cast<float *>(p.w.Pb[0]), ws);
     });
     launch(ctx, st, "field_update_f32", [&] {
       return gemm_field<float>(C, N, r, coef2, r, s->fD, r, p.acc, p.sc, cs, m, Mf, N, st);
