@@ -13,6 +13,10 @@ namespace dino {
 // r works on a global (L2-resident) per-chain workspace.
 constexpr int kMaxRSmem = 208;
 constexpr int kMaxR = 1024;                 // largest reduced dimension supported
+// Largest d_y of the Woodbury path (d_y < r): its (d_y+1)-square factor and
+// vectors then fit one CTA's shared memory for every r <= kMaxR, in both
+// precisions.  Larger d_y takes the r-sized path.
+constexpr int kMaxWbDy = 192;
 constexpr size_t kSmemLimit = 227 * 1024;   // opt-in shared memory per CTA
 
 // Philox streams (counter word 3): reduced noise, accept uniform, complement

@@ -493,11 +493,11 @@ static int load_surrogate(dino_ctx *ctx, const dino_surrogate_desc *d) {
   if (geometry_smem_bytes(s->r, s->d_y, 1) > kSmemLimit ||
       geometry_smem_bytes(s->r, s->d_y, 0) > kSmemLimit)
     fail(DINO_EINVAL, "r=%d, d_y=%d exceed the per-chain shared-memory budget", s->r, s->d_y);
-  s->wb = s->d_y < s->r;
+  s->wb = s->d_y < s->r && s->d_y <= kMaxWbDy;
   if (s->wb && (wb_smem_bytes(s->r, s->d_y, 1) > kSmemLimit ||
                 wb_smem_bytes(s->r, s->d_y, 0) > kSmemLimit))
     fail(DINO_EINVAL, "d_y=%d < r=%d: the d_y x d_y factor exceeds the shared-memory budget",
-         s->d_y, s->r);
+         s->d_y, s->r);  // not reached for r <= kMaxR
   if (d->precision == DINO_PREC_BF16 && s->L < 2)
     fail(DINO_EINVAL, "the tensor-core path needs at least one hidden layer");
   if (d->precision == DINO_PREC_BF16) {

@@ -251,3 +251,20 @@ def test_zero_jacobian_reduces_to_pcn(dino, ctx):
     assert last["accepted"].all()
     dino.dino_chains_destroy(ctx, pool)
     dino.dino_unload_surrogate(ctx, sid)
+
+
+@pytest.mark.parametrize("dy", [192, 193])
+def test_noise_map_boundary_matches_oracle(dino, ctx, dy):
+    """r = 200: d_y = 192 runs the Woodbury path (perturbation noise), d_y = 193
+    the r-sized path (Cholesky noise); both follow the oracle's rule at 1e-10."""
+    from oracle import mmala as om
+    w = variant(CONFIGS["small_fp64"], n_grid=15, r=200, widths=[200, 64, dy],
+                activation=ACT_TANH, noise_frac=0.2)
+    assert om.noise_map(w.r, dy) == ("perturbation" if dy == 192 else "cholesky")
+    sid = gpu_setup(dino, ctx, w)
+    sur, E, D = oracle_setup(w)
+    pool = dino.dino_chains_create(ctx, sid, 3, 2e-4, SEED_CHAINS)
+    och = _oracle_chains(w, sur, E, D, 3, 2e-4)
+    step_and_compare(dino, ctx, pool, och, w, 3, 3, tol=TOL)
+    dino.dino_chains_destroy(ctx, pool)
+    dino.dino_unload_surrogate(ctx, sid)

@@ -238,6 +238,7 @@ def test_p9_perturbation_map_has_the_proposal_covariance():
     T1 = T[:, :r]
     assert np.abs(T1 @ T1.T - cov_ref).max() > 1e-3 * np.abs(cov_ref).max()
     assert mmala.noise_map(r, dy) == "perturbation" and mmala.noise_map(dy, r) == "cholesky"
+    assert mmala.noise_map(400, 192) == "perturbation" and mmala.noise_map(400, 193) == "cholesky"
 
 
 def test_p9_perturbation_chain_is_exact_ar1_for_linear_surrogate():
