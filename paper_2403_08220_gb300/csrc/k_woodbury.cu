@@ -155,7 +155,8 @@ __host__ __device__ size_t wb_stage_bytes(int r, int dy) {
 // asynchronous copies, the next chunk in flight while the current one is
 // used; rows are kept in natural order (padded to kWbLd floats) and read as
 // float4 along the reduction index.
-template <class A>
+// kGram = false: only the row products (no Gram tiles, Ms untouched).
+template <class A, bool kGram = true>
 __device__ void wb_gram_rows(const float *J, int dy, int r, double inv_nv, double inv_sigma,
                              float2 *Ms, float *stage, const float2 *be, const float2 *ae,
                              bool two, double *Kb, double *Ka) {
@@ -224,7 +225,7 @@ __device__ void wb_gram_rows(const float *J, int dy, int r, double inv_nv, doubl
     for (int kk = 0; kk < kWbKc; kk += 4) {
 #pragma unroll
       for (int s = 0; s < kHMaxTiles; ++s) {
-        if (ti[s] < 0) continue;
+        if (!kGram || ti[s] < 0) continue;
         float4 xa[kHT], ya[kHT];
 #pragma unroll
         for (int p = 0; p < kHT; ++p) {
@@ -264,13 +265,13 @@ __device__ void wb_gram_rows(const float *J, int dy, int r, double inv_nv, doubl
     const int j = tid + h * T;
     if (j < dy) {
       Kb[j] = A::to(A::end(kb[h])) * inv_sigma;
-      Ka[j] = two ? A::to(A::end(ka[h])) * inv_sigma : 0.0;
+      if (two) Ka[j] = A::to(A::end(ka[h])) * inv_sigma;
     }
   }
   const float nh = __double2float_rn(inv_nv), nl = __double2float_rn(inv_nv - (double)nh);
 #pragma unroll
   for (int s = 0; s < kHMaxTiles; ++s) {
-    if (ti[s] < 0) continue;
+    if (!kGram || ti[s] < 0) continue;
 #pragma unroll
     for (int p = 0; p < kHT; ++p)
 #pragma unroll
@@ -450,7 +451,6 @@ __global__ void __launch_bounds__(kWbThreads, kWbMinBlocks) k_wb_propose(Reduced
   const double inv_sigma = sqrt(1.0 / a.noise_var);
   const double s = a.s, cs = sqrt(1.0 - s * s);
 
-  for (size_t e = threadIdx.x; e < tri_size(dy); e += blockDim.x) Ms[e] = G[sl.R + e];
   for (int i = threadIdx.x; i < dy; i += blockDim.x) {
     inv[i] = G[sl.inv + i];
     u[i] = Lg[sl.u + i];
@@ -474,7 +474,18 @@ __global__ void __launch_bounds__(kWbThreads, kWbMinBlocks) k_wb_propose(Reduced
       if (4 * blk + q < dy) xi2[4 * blk + q] = n4[q];
   }
   __syncthreads();
-  rows_times<A, TJ>(J, dy, r, inv_sigma, x1E, x1E, false, Kxi, Kxi);  // K xi1
+  if constexpr (sizeof(TJ) == 4) {  // K xi1 from J staged through the (still empty) factor region
+    if (wb_stage_fits(dy)) {
+      wb_gram_rows<A, false>(reinterpret_cast<const float *>(J), dy, r, 0.0, inv_sigma, nullptr,
+                             reinterpret_cast<float *>(sm + lay.Ms),
+                             reinterpret_cast<const float2 *>(x1E), nullptr, false, Kxi, Kxi);
+    } else {
+      rows_times<A, TJ>(J, dy, r, inv_sigma, x1E, x1E, false, Kxi, Kxi);
+    }
+  } else {
+    rows_times<A, TJ>(J, dy, r, inv_sigma, x1E, x1E, false, Kxi, Kxi);  // K xi1
+  }
+  for (size_t e = threadIdx.x; e < tri_size(dy); e += blockDim.x) Ms[e] = G[sl.R + e];
   for (int i = threadIdx.x; i < dy; i += blockDim.x) {
     yv[i] = (1.0 - s) * u[i] + cs * (xi2[i] - Kxi[i]);
     zE[i] = A::from(yv[i]);
