@@ -6,13 +6,16 @@
 // (X_0 = bf16(X), X_1 = bf16(X - X_0), ...).  nslice = 1 is the plain BF16
 // product, 2 the three-product "bf16x3" scheme, 3 six products (FP32-level).
 //
-// One CTA computes a 128 x BN output tile (cta_group::1, M = 128):
+// A persistent CTA (one per SM) computes 128 x BN output tiles in turn (cta_group::1, M = 128):
 //   warp 0     TMA producer: 3D tiled loads (k, row, slice) of 128 x 64 A and
 //              BN x 64 B boxes, 128-byte swizzle, into a ring of stages;
-//   warp 1     allocates TMEM and issues tcgen05.mma (K = 16 per instruction,
-//              four per 64-wide stage); tcgen05.commit frees each stage;
+//   warp 1     allocates TMEM (two accumulator buffers) and issues tcgen05.mma
+//              (K = 16 per instruction, four per 64-wide stage) into the buffer of
+//              the current tile; tcgen05.commit frees each stage and, per tile,
+//              hands the buffer to the epilogue;
 //   warps 2-5  epilogue: tcgen05.ld of their 32 TMEM lanes, fused bias /
-//              activation / derivative / per-chain scaling, bf16 re-slicing.
+//              activation / derivative / per-chain scaling, bf16 re-slicing,
+//              overlapping the next tile's MMAs; then release the buffer.
 // Every mbarrier wait is bounded; on timeout the CTA raises a device error
 // flag, lets its copies and MMAs drain (bounded), frees TMEM and returns.
 #include <cuda.h>
@@ -163,6 +166,11 @@ __device__ __forceinline__ void store_slices(float x, __nv_bfloat16 *dst, size_t
   }
 }
 
+// Persistent: each CTA walks the output tiles t = blockIdx.x, + gridDim.x, ...
+// (N tiles of one M block adjacent, so that concurrent CTAs share A in L2).
+// The TMA producer and the MMA issuer run one stage ring across tiles; the
+// MMA issuer accumulates tile j into TMEM buffer j & 1 while the epilogue
+// warps drain the other buffer (acc_full / acc_empty mbarriers).
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const TcParams p) {
@@ -174,20 +182,26 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t a_bytes = kBlockM * kBlockK * 2, b_bytes = (uint32_t)p.BN * kBlockK * 2;
   const uint32_t stage_bytes = a_bytes + b_bytes;
   uint64_t *bars = reinterpret_cast<uint64_t *>(gbase + p.stages * stage_bytes);
-  // bars[0..S) full, [S..2S) empty, [2S] accumulator ready
-  volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 2 * p.stages + 1);
+  // bars[0..S) full, [S..2S) empty, [2S, 2S+2) acc_full, [2S+2, 2S+4) acc_empty, [2S+4] drain
+  const int S = p.stages;
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 2 * S + 5);
   volatile int *consumed = abort_flag + 1;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * p.stages + 2);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 6);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * kBlockM, n0 = blockIdx.y * p.BN;
+  const int ntn = (p.N + p.BN - 1) / p.BN;
+  const int ntiles = ((p.M + kBlockM - 1) / kBlockM) * ntn;
   const int n_iter = p.npairs * p.nkb;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < p.stages; ++s) {
+    for (int s = 0; s < S; ++s) {
       mbar_init(smem_u32(&bars[s]), 1);
-      mbar_init(smem_u32(&bars[p.stages + s]), 1);
+      mbar_init(smem_u32(&bars[S + s]), 1);
     }
-    mbar_init(smem_u32(&bars[2 * p.stages]), 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&bars[2 * S + b]), 1);
+      mbar_init(smem_u32(&bars[2 * S + 2 + b]), 4);  // one arrive per epilogue warp
+    }
+    mbar_init(smem_u32(&bars[2 * S + 4]), 1);
     *abort_flag = 0;
     *consumed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -206,68 +220,99 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      int issued = 0;
-      for (int it = 0; it < n_iter; ++it) {
-        const int s = it % p.stages;
-        const uint32_t ph = (uint32_t)(it / p.stages) & 1u;
-        if (!mbar_wait(smem_u32(&bars[p.stages + s]), ph ^ 1u, abort_flag)) {
-          *abort_flag = 1;
-          atomicOr(p.err, 1);
-          break;
+      int g = 0;  // stage iterations issued, across tiles
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int m0 = (t / ntn) * kBlockM, n0 = (t % ntn) * p.BN;
+        for (int it = 0; it < n_iter; ++it, ++g) {
+          const int s = g % S;
+          const uint32_t ph = (uint32_t)(g / S) & 1u;
+          if (!mbar_wait(smem_u32(&bars[S + s]), ph ^ 1u, abort_flag)) {
+            *abort_flag = 1;
+            atomicOr(p.err, 1);
+            ok = false;
+            break;
+          }
+          const int pr = it / p.nkb, kb = it % p.nkb;
+          const uint32_t full = smem_u32(&bars[s]);
+          mbar_expect_tx(full, stage_bytes);
+          const uint32_t sa = base + s * stage_bytes;
+          tma_load_3d(sa, &tmA, kb * kBlockK, m0, p.pair_a[pr], full);
+          tma_load_3d(sa + a_bytes, &tmB, kb * kBlockK, n0, p.pair_b[pr], full);
         }
-        const int pr = it / p.nkb, kb = it % p.nkb;
-        const uint32_t full = smem_u32(&bars[s]);
-        mbar_expect_tx(full, stage_bytes);
-        const uint32_t sa = base + s * stage_bytes;
-        tma_load_3d(sa, &tmA, kb * kBlockK, m0, p.pair_a[pr], full);
-        tma_load_3d(sa + a_bytes, &tmB, kb * kBlockK, n0, p.pair_b[pr], full);
-        issued = it + 1;
       }
       if (*abort_flag) {
         // let the copies already issued land before the CTA's memory goes away
-        for (int it = *consumed; it < issued; ++it)
-          mbar_wait(smem_u32(&bars[it % p.stages]), (uint32_t)(it / p.stages) & 1u, nullptr);
+        for (int i = *consumed; i < g; ++i)
+          mbar_wait(smem_u32(&bars[i % S]), (uint32_t)(i / S) & 1u, nullptr);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16(kBlockM, p.BN);
       bool ok = true;
-      for (int it = 0; it < n_iter; ++it) {
-        const int s = it % p.stages;
-        const uint32_t ph = (uint32_t)(it / p.stages) & 1u;
-        if (!mbar_wait(smem_u32(&bars[s]), ph, abort_flag)) {
+      int g = 0, j = 0;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++j) {
+        const int b = j & 1;
+        if (!mbar_wait(smem_u32(&bars[2 * S + 2 + b]), (((uint32_t)j >> 1) & 1u) ^ 1u,
+                       abort_flag)) {
           *abort_flag = 1;
           atomicOr(p.err, 2);
           ok = false;
           break;
         }
-        *consumed = it + 1;
         fence_after();
-        const uint32_t sa = base + s * stage_bytes;
-        const uint64_t ad = smem_desc_sw128(sa), bd = smem_desc_sw128(sa + a_bytes);
+        const uint32_t tacc = tmem + (uint32_t)(b * p.BN);
+        for (int it = 0; it < n_iter; ++it, ++g) {
+          const int s = g % S;
+          const uint32_t ph = (uint32_t)(g / S) & 1u;
+          if (!mbar_wait(smem_u32(&bars[s]), ph, abort_flag)) {
+            *abort_flag = 1;
+            atomicOr(p.err, 2);
+            ok = false;
+            break;
+          }
+          *consumed = g + 1;
+          fence_after();
+          const uint32_t sa = base + s * stage_bytes;
+          const uint64_t ad = smem_desc_sw128(sa), bd = smem_desc_sw128(sa + a_bytes);
 #pragma unroll
-        for (int k = 0; k < kBlockK / 16; ++k)
-          mma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc, (it > 0 || k > 0) ? 1u : 0u);
-        mma_commit(smem_u32(&bars[p.stages + s]));
+          for (int k = 0; k < kBlockK / 16; ++k)
+            mma_bf16(tacc, ad + 2 * k, bd + 2 * k, idesc, (it > 0 || k > 0) ? 1u : 0u);
+          mma_commit(smem_u32(&bars[S + s]));
+        }
+        if (ok) mma_commit(smem_u32(&bars[2 * S + b]));
       }
-      mma_commit(smem_u32(&bars[2 * p.stages]));
-      if (!ok) mbar_wait(smem_u32(&bars[2 * p.stages]), 0, nullptr);  // drain issued MMAs
+      if (!ok) {  // drain the MMAs already issued
+        mma_commit(smem_u32(&bars[2 * S + 4]));
+        mbar_wait(smem_u32(&bars[2 * S + 4]), 0, nullptr);
+      }
     }
   } else {
     // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31
     const int quarter = warp & 3;
-    const int row = m0 + quarter * 32 + lane;
-    // one lane waits, the warp follows its verdict (tcgen05.ld is warp-collective)
-    int okl = 0;
-    if (lane == 0) okl = mbar_wait(smem_u32(&bars[2 * p.stages]), 0, abort_flag) ? 1 : 0;
-    const bool ok = __shfl_sync(0xffffffffu, okl, 0) != 0;
-    fence_after();
-    if (ok && n_iter > 0) {
+    int j = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+      const int b = j & 1;
+      const int m0 = (t / ntn) * kBlockM, n0 = (t % ntn) * p.BN;
+      const int row = m0 + quarter * 32 + lane;
+      // one lane waits, the warp follows its verdict (tcgen05.ld is warp-collective)
+      int okl = 0;
+      if (lane == 0)
+        okl = mbar_wait(smem_u32(&bars[2 * S + b]), ((uint32_t)j >> 1) & 1u, abort_flag) ? 1 : 0;
+      if (__shfl_sync(0xffffffffu, okl, 0) == 0) {
+        if (lane == 0) {
+          *abort_flag = 1;
+          atomicOr(p.err, 4);
+        }
+        break;
+      }
+      fence_after();
+      const uint32_t tacc = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * p.BN);
       const int nvalid = min(p.BN, p.N - n0);
       for (int c0 = 0; c0 < nvalid; c0 += 16) {
         float v[16];
-        tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
+        tmem_ld16(tacc + (uint32_t)c0, v);
         if (row >= p.M) continue;
         const int ncols = min(16, nvalid - c0);
         const int col0 = n0 + c0;
@@ -336,6 +381,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       }
+      // buffer b drained: hand it back to the MMA issuer
+      fence_before();
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bars[2 * S + 2 + b]))
+                     : "memory");
     }
   }
   fence_before();
@@ -363,33 +414,46 @@ __global__ void k_jac_init_bf16(int C, int d_y, int w, const float *__restrict__
                                 const float *__restrict__ der, int ldd,
                                 __nv_bfloat16 *__restrict__ P, int ldp, size_t plane,
                                 int nslice) {
-  // each thread fills 8 consecutive columns of one row: P = W_L .* der (per chain)
-  const int wv = (w + 7) / 8;
-  const long long total = (long long)C * d_y * wv;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long row = e / wv;
-    const int k0 = (int)(e - row * wv) * 8;
-    const int c = (int)(row / d_y), i = (int)(row - (long long)c * d_y);
-    float x[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int k = k0 + q;
-      x[q] = k < w ? WL[(size_t)i * w + k] * der[(size_t)c * ldd + k] : 0.0f;
-    }
-    __nv_bfloat16 *o = P + (size_t)row * ldp + k0;
-    const bool vec = (ldp & 7) == 0 && k0 + 8 <= ldp;
-    for (int sl = 0; sl < nslice; ++sl) {
-      __nv_bfloat16 h[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        h[q] = __float2bfloat16_rn(x[q]);
-        x[q] -= __bfloat162float(h[q]);
-      }
-      if (vec) {
-        *reinterpret_cast<uint4 *>(o + sl * plane) = *reinterpret_cast<const uint4 *>(h);
+  // P = W_L .* der (per chain): a warp per row (c, i), each lane 8 consecutive
+  // columns at a time; 32-bit index arithmetic once per row, float4 loads
+  // when the rows are 16-byte aligned.
+  const int lane = threadIdx.x & 31;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  const int rows = C * d_y, groups = (w + 7) / 8;
+  const bool vload = (w & 3) == 0 && (ldd & 3) == 0;
+  const bool vstore = (ldp & 7) == 0;
+  for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += nwarps) {
+    const int c = row / d_y, i = row - c * d_y;
+    const float *wr = WL + (size_t)i * w;
+    const float *dr = der + (size_t)c * ldd;
+    __nv_bfloat16 *o = P + (size_t)row * ldp;
+    for (int g = lane; g < groups; g += 32) {
+      const int k0 = 8 * g;
+      float x[8];
+      if (vload && k0 + 8 <= w) {
+        const float4 w0 = *reinterpret_cast<const float4 *>(wr + k0);
+        const float4 w1 = *reinterpret_cast<const float4 *>(wr + k0 + 4);
+        const float4 d0 = *reinterpret_cast<const float4 *>(dr + k0);
+        const float4 d1 = *reinterpret_cast<const float4 *>(dr + k0 + 4);
+        x[0] = w0.x * d0.x; x[1] = w0.y * d0.y; x[2] = w0.z * d0.z; x[3] = w0.w * d0.w;
+        x[4] = w1.x * d1.x; x[5] = w1.y * d1.y; x[6] = w1.z * d1.z; x[7] = w1.w * d1.w;
       } else {
-        for (int q = 0; q < 8 && k0 + q < w; ++q) o[sl * plane + q] = h[q];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) x[q] = k0 + q < w ? wr[k0 + q] * dr[k0 + q] : 0.0f;
+      }
+      const bool vec = vstore && k0 + 8 <= ldp;
+      for (int sl = 0; sl < nslice; ++sl) {
+        __nv_bfloat16 h[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          h[q] = __float2bfloat16_rn(x[q]);
+          x[q] -= __bfloat162float(h[q]);
+        }
+        if (vec) {
+          *reinterpret_cast<uint4 *>(o + sl * plane + k0) = *reinterpret_cast<const uint4 *>(h);
+        } else {
+          for (int q = 0; q < 8 && k0 + q < w; ++q) o[sl * plane + k0 + q] = h[q];
+        }
       }
     }
   }
@@ -458,7 +522,7 @@ cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st) {
     p.pair_b[i] = pb[i];
   }
   const int stage_bytes = kBlockM * kBlockK * 2 + p.BN * kBlockK * 2;
-  p.stages = (110 * 1024) / stage_bytes;
+  p.stages = (200 * 1024) / stage_bytes;
   if (p.stages > kMaxStages) p.stages = kMaxStages;
   if (p.stages < 2) p.stages = 2;
   p.epi = a.epi;
@@ -473,8 +537,8 @@ cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st) {
   p.out_bf = a.out_bf;
   p.der = a.der;
   p.scale = a.scale;
-  uint32_t cols = 32;
-  while (cols < (uint32_t)p.BN) cols <<= 1;
+  uint32_t cols = 32;  // two accumulator buffers of BN columns
+  while (cols < 2u * (uint32_t)p.BN) cols <<= 1;
   p.tmem_cols = cols;
   p.err = error_word();
   if (!p.err) return cudaErrorMemoryAllocation;
@@ -482,12 +546,16 @@ cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st) {
   if (!make_map(&tmA, a.A, a.K, a.M, a.lda, a.a_plane, a.nslice, kBlockM) ||
       !make_map(&tmB, a.B, a.K, a.N, a.ldb, a.b_plane, a.nslice, p.BN))
     return cudaErrorInvalidValue;
-  const size_t smem = 1024 + (size_t)p.stages * stage_bytes + (2 * p.stages + 4) * 8;
+  const size_t smem = 1024 + (size_t)p.stages * stage_bytes + (2 * p.stages + 8) * 8;
   cudaError_t e =
       cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((a.M + kBlockM - 1) / kBlockM, ntiles);
-  k_tc_gemm<<<grid, kThreads, smem, st>>>(tmA, tmB, p);
+  int dev = 0, sms = 0;  // persistent grid: one CTA per SM (its shared memory allows one)
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+    return cudaErrorInvalidValue;
+  const int total = ((a.M + kBlockM - 1) / kBlockM) * ntiles;
+  k_tc_gemm<<<std::min(total, sms), kThreads, smem, st>>>(tmA, tmB, p);
   return cudaGetLastError();
 }
 
@@ -503,8 +571,8 @@ cudaError_t launch_split_bf16_f64(int rows, int cols, const double *src, int lds
 cudaError_t launch_jac_init_bf16(int C, int d_y, int w, const float *WL, const float *der,
                                  int ldd, __nv_bfloat16 *P, int ldp, size_t plane, int nslice,
                                  cudaStream_t st) {
-  const size_t n = (size_t)C * d_y * ((w + 7) / 8);
-  const int grid = (int)std::min<size_t>((n + 255) / 256, 152 * 32);
+  const size_t rows = (size_t)C * d_y;  // one warp per row, 8 warps per block
+  const int grid = (int)std::min<size_t>((rows + 7) / 8, 152 * 16);
   k_jac_init_bf16<<<grid > 0 ? grid : 1, 256, 0, st>>>(C, d_y, w, WL, der, ldd, P, ldp, plane,
                                                        nslice);
   return cudaGetLastError();
