@@ -458,9 +458,20 @@ __global__ void __launch_bounds__(kWbThreads, kWbMinBlocks) k_wb_propose(Reduced
   }
   const uint32_t chain = (uint32_t)(a.id_base + (uint64_t)c);
   for (int k = threadIdx.x; k < r; k += blockDim.x) xa[k] = a.mr[(size_t)c * r + k];
+  // Box-Muller in FP32 on the tensor-core path (its precision bars are far
+  // above FP32's), in FP64 on the FP64 path (FP64 parity with the oracle)
+  auto normals4 = [&](uint4 w, double n4[4]) {
+    if constexpr (sizeof(TJ) == 4) {
+      float f4[4];
+      normals4_f32(w, f4);
+      for (int q = 0; q < 4; ++q) n4[q] = f4[q];
+    } else {
+      normals4_f64(w, n4);
+    }
+  };
   for (int blk = threadIdx.x; blk < (r + 3) / 4; blk += blockDim.x) {
     double n4[4];
-    normals4_f64(philox_block(a.seed, STREAM_XI, a.step, chain, blk), n4);
+    normals4(philox_block(a.seed, STREAM_XI, a.step, chain, blk), n4);
     for (int q = 0; q < 4; ++q)
       if (4 * blk + q < r) {
         xi1[4 * blk + q] = n4[q];
@@ -469,7 +480,7 @@ __global__ void __launch_bounds__(kWbThreads, kWbMinBlocks) k_wb_propose(Reduced
   }
   for (int blk = threadIdx.x; blk < (dy + 3) / 4; blk += blockDim.x) {
     double n4[4];
-    normals4_f64(philox_block(a.seed, STREAM_XI2, a.step, chain, blk), n4);
+    normals4(philox_block(a.seed, STREAM_XI2, a.step, chain, blk), n4);
     for (int q = 0; q < 4; ++q)
       if (4 * blk + q < dy) xi2[4 * blk + q] = n4[q];
   }
