@@ -293,47 +293,49 @@ __device__ __forceinline__ void tri_pos(int e, int &ii, int &jj) {
 }
 
 
-// Factor the 8 x 8 diagonal block at kb (size nb) by one warp, in registers:
-// lane i < nb holds row i of the block (c[j] = L(i, j)).  Per column q: the
-// pivot (A::pivot, computed by every lane from the broadcast diagonal
-// entry), the scaling of column q, its store, and the rank-1 update of the
-// columns to its right, L(k, q) coming by shuffle from lane k.  Lanes
-// compute every column and keep theirs by selects (no divergent branches),
-// and the q loop is unrolled, so the updates of one column overlap the next
-// pivot's dependent chain.  inv[k] = 1 / L_kk.
+// Factor the 8 x 8 diagonal block at kb (size nb) by one warp, in registers.
+// Every lane holds the whole lower block and factors it (column q: the pivot
+// A::pivot, the scaling of column q, the rank-1 update of the columns to its
+// right), so no value crosses lanes and the dependent chain per column is
+// only pivot -> scale -> next diagonal update; the off-diagonal updates of
+// the unrolled loop overlap it.  Rows and columns >= nb are padded with the
+// identity, which leaves the rows < nb unchanged and is never stored.  The
+// arithmetic per entry is the column-at-a-time sequence.  After a warp
+// barrier (the block is read by all lanes and overwritten in place) lanes
+// share the stores: entry e of the block by lane e mod 32, inv[k] = 1 / L_kk.
 template <class A>
 __device__ __noinline__ void warp_factor_diag(typename A::T *Ls, typename A::T *inv, int kb,
                                               int nb, int lane) {
   using E = typename A::T;
-  E c[kNB];
-  const bool in = lane < nb;
-  const int ri = kb + (in ? lane : nb - 1);  // lanes >= nb shadow the last row
+  E c[kNB][kNB];
 #pragma unroll
-  for (int j = 0; j < kNB; ++j) {
-    const E x = j < nb ? Ls[tri(ri) + kb + min(j, lane)] : E{};
-    c[j] = (in && j <= lane) ? x : E{};
-  }
+  for (int i = 0; i < kNB; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j)
+      c[i][j] = i < nb ? Ls[tri(kb + i) + kb + j] : (i == j ? A::from_j(1.0f) : E{});
 #pragma unroll
   for (int q = 0; q < kNB; ++q) {
-    if (q < nb) {
-      E d, id;
-      A::pivot(shfl_elt(c[q], q), d, id);
-      const E sc = A::mul(c[q], id);
-      c[q] = lane == q ? d : (lane > q ? sc : c[q]);
-      if (lane == 0) inv[kb + q] = id;
-      if (in && lane >= q) Ls[tri(kb + lane) + kb + q] = c[q];
+    E d, id;
+    A::pivot(c[q][q], d, id);
+    c[q][q] = d;
+    if (lane == 0 && q < nb) inv[kb + q] = id;
 #pragma unroll
-      for (int k = q + 1; k < kNB; ++k) {
-        if (k < nb) {
-          const E l = shfl_elt(c[q], k);
-          typename A::Acc acc = A::begin(c[k]);
-          A::sub(acc, c[q], l);
-          const E u = A::end(acc);
-          c[k] = lane >= k ? u : c[k];
-        }
+    for (int i = q + 1; i < kNB; ++i) c[i][q] = A::mul(c[i][q], id);
+#pragma unroll
+    for (int k = q + 1; k < kNB; ++k)
+#pragma unroll
+      for (int i = k; i < kNB; ++i) {
+        typename A::Acc acc = A::begin(c[i][k]);
+        A::sub(acc, c[i][q], c[k][q]);
+        c[i][k] = A::end(acc);
       }
-    }
   }
+  __syncwarp();  // every lane's loads of the block precede any lane's stores
+#pragma unroll
+  for (int i = 0; i < kNB; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j)
+      if (lane == (tri(i) + j) % 32 && i < nb) Ls[tri(kb + i) + kb + j] = c[i][j];
   __syncwarp();
 }
 

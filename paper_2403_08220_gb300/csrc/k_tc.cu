@@ -33,6 +33,7 @@ constexpr int kBlockK = 64;  // 128 bytes of bf16: one swizzle row
 constexpr int kThreads = 192;
 constexpr uint32_t kSpinLimit = 1u << 24;
 constexpr int kMaxStages = 4;
+constexpr int kStageTiles = 4 * 32 * 128;  // epilogue staging: 32 rows x 128 B per warp
 
 struct TcParams {
   int M, N, K, BN, nkb, npairs, stages;
@@ -140,6 +141,79 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Wider TMEM reads for the coalesced epilogue: lane i gets 32 (64) consecutive
+// columns of TMEM lane (taddr lane + i); the wait is inside the same asm
+// statement, so no use of the values can be scheduled before it.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "{\n tcgen05.ld.sync.aligned.32x32b.x32.b32 {"
+      "%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31"
+      "}, [%32];\n tcgen05.wait::ld.sync.aligned;\n}\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float v[64]) {
+  uint32_t r[64];
+  asm volatile(
+      "{\n tcgen05.ld.sync.aligned.32x32b.x64.b32 {"
+      "%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
+      "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+      "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63"
+      "}, [%64];\n tcgen05.wait::ld.sync.aligned;\n}\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+        "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+        "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
+        "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+        "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Coalesced row stores through a per-warp staging tile.  Lane i holds 128
+// bytes (w[0..31]) of output row i of a 32-row block whose first byte is at
+// dst + i * ld_bytes (16-byte aligned); rows >= nrows are not stored.  The
+// lanes write their rows into `stg` (32 x 128 bytes, 16-byte chunks XOR-
+// swizzled by row, so both phases take the minimum four wavefronts per
+// instruction), then read it back so that each store instruction writes four
+// whole 128-byte row segments instead of 32 scattered 16-byte pieces.
+__device__ __forceinline__ void store_rows_coalesced(uint4 *stg, const uint32_t w[32], char *dst,
+                                                     size_t ld_bytes, int nrows, int lane) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c)
+    stg[lane * 8 + (c ^ (lane & 7))] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int r = q * 4 + (lane >> 3), c = lane & 7;
+    const uint4 x = stg[r * 8 + (c ^ (r & 7))];
+    if (r < nrows) *reinterpret_cast<uint4 *>(dst + (size_t)r * ld_bytes + c * 16) = x;
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float &a, float &b) {
+  // bf16 of a and b (low half a), leaving the remainders a - bf16(a), b - bf16(b)
+  const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
+  a -= __bfloat162float(ha);
+  b -= __bfloat162float(hb);
+  return (uint32_t)__bfloat16_as_ushort(ha) | ((uint32_t)__bfloat16_as_ushort(hb) << 16);
+}
+
 __device__ __forceinline__ float act_fn(int kind, float z) {
   if (kind == 1) return tanhf(z);
   if (kind == 2) return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
@@ -181,7 +255,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   unsigned char *gbase = smraw + (base - raw);
   const uint32_t a_bytes = kBlockM * kBlockK * 2, b_bytes = (uint32_t)p.BN * kBlockK * 2;
   const uint32_t stage_bytes = a_bytes + b_bytes;
-  uint64_t *bars = reinterpret_cast<uint64_t *>(gbase + p.stages * stage_bytes);
+  // after the ring: four 4 KB epilogue staging tiles, then the barriers
+  uint4 *stg_all = reinterpret_cast<uint4 *>(gbase + p.stages * stage_bytes);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(gbase + p.stages * stage_bytes + kStageTiles);
   // bars[0..S) full, [S..2S) empty, [2S, 2S+2) acc_full, [2S+2, 2S+4) acc_empty, [2S+4] drain
   const int S = p.stages;
   volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 2 * S + 5);
@@ -310,7 +386,71 @@ __global__ void __launch_bounds__(kThreads, 1)
       fence_after();
       const uint32_t tacc = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * p.BN);
       const int nvalid = min(p.BN, p.N - n0);
-      for (int c0 = 0; c0 < nvalid; c0 += 16) {
+      const int row0 = m0 + quarter * 32, nrows = min(32, p.M - row0);
+      uint4 *stg = stg_all + quarter * 256;
+      int c0 = 0;  // columns [0, c0) done by the coalesced groups below
+      if ((p.epi == TC_EPI_STORE_F32 || p.epi == TC_EPI_BIAS_F32) && (p.ldo & 3) == 0) {
+        // 32 FP32 columns = 128 bytes per row
+        for (; c0 + 32 <= nvalid; c0 += 32) {
+          float v[32];
+          tmem_ld32(tacc + (uint32_t)c0, v);
+          uint32_t w[32];
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            w[j] = __float_as_uint(p.epi == TC_EPI_BIAS_F32 ? v[j] + p.bias[n0 + c0 + j] : v[j]);
+          store_rows_coalesced(stg, w, reinterpret_cast<char *>(p.outf + (size_t)row0 * p.ldo + n0 + c0),
+                               (size_t)p.ldo * 4, nrows, lane);
+        }
+      } else if ((p.epi == TC_EPI_SCALE_GROUP && (p.lds & 3) == 0) ||
+                 (p.epi == TC_EPI_BIAS_ACT && (p.N & 3) == 0)) {
+        // 64 columns = 128 bytes per row and bf16 slice (the derivative: two
+        // 128-byte FP32 halves)
+        if ((p.ldo & 7) == 0) {
+          for (; c0 + 64 <= nvalid; c0 += 64) {
+            float v[64];
+            tmem_ld64(tacc + (uint32_t)c0, v);
+            if (p.epi == TC_EPI_SCALE_GROUP) {
+              if (row < p.M) {
+                const float4 *sc = reinterpret_cast<const float4 *>(
+                    p.scale + (size_t)(row / p.group) * p.lds + n0 + c0);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                  const float4 t = sc[q];
+                  v[4 * q] *= t.x;
+                  v[4 * q + 1] *= t.y;
+                  v[4 * q + 2] *= t.z;
+                  v[4 * q + 3] *= t.w;
+                }
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < 64; ++j) v[j] += p.bias[n0 + c0 + j];
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                uint32_t w[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) w[j] = __float_as_uint(act_deriv(p.act, v[32 * h + j]));
+                store_rows_coalesced(
+                    stg, w, reinterpret_cast<char *>(p.der + (size_t)row0 * p.N + n0 + c0 + 32 * h),
+                    (size_t)p.N * 4, nrows, lane);
+              }
+#pragma unroll
+              for (int j = 0; j < 64; ++j) v[j] = act_fn(p.act, v[j]);
+            }
+            for (int sl = 0; sl < p.out_slices; ++sl) {
+              uint32_t w[32];
+#pragma unroll
+              for (int j = 0; j < 32; ++j) w[j] = pack_bf16x2(v[2 * j], v[2 * j + 1]);
+              store_rows_coalesced(
+                  stg, w,
+                  reinterpret_cast<char *>(p.out_bf + (size_t)row0 * p.ldo + n0 + c0 +
+                                           (size_t)sl * p.out_plane),
+                  (size_t)p.ldo * 2, nrows, lane);
+            }
+          }
+        }
+      }
+      for (; c0 < nvalid; c0 += 16) {
         float v[16];
         tmem_ld16(tacc + (uint32_t)c0, v);
         if (row >= p.M) continue;
@@ -546,7 +686,7 @@ cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st) {
   if (!make_map(&tmA, a.A, a.K, a.M, a.lda, a.a_plane, a.nslice, kBlockM) ||
       !make_map(&tmB, a.B, a.K, a.N, a.ldb, a.b_plane, a.nslice, p.BN))
     return cudaErrorInvalidValue;
-  const size_t smem = 1024 + (size_t)p.stages * stage_bytes + (2 * p.stages + 8) * 8;
+  const size_t smem = 1024 + (size_t)p.stages * stage_bytes + kStageTiles + (2 * p.stages + 8) * 8;
   cudaError_t e =
       cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
