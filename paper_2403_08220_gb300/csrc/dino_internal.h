@@ -118,11 +118,15 @@ cudaError_t gemm_field(int M, int N, int K, const T *A, int lda, const T *B, int
 // Shared memory of the prior draw of one chain on an n x n grid (elements of `elem` bytes).
 size_t prior_draw_smem_bytes(int n, int elem);
 // Prior draw from the full KLE: out[c] = S^T (sqrt(Lambda) .* Z_c) S,
-// Z_c from Philox stream `stream` at `step` for chain id_base + c.
+// Z_c from Philox stream `stream` at `step` for chain id_base + c.  With `ms`
+// (FP32 only) the draw is also written as ms_slices bf16 slice planes
+// (row pitch ldms, plane stride ms_plane) for the tensor-core projections.
 template <typename T>
 cudaError_t launch_prior_draw(int C, int n, const T *sqrtlam, const T *S, uint64_t seed,
                               uint64_t id_base, uint32_t stream, uint32_t step, T *out,
-                              int ldo, cudaStream_t st);
+                              int ldo, cudaStream_t st,
+                              __nv_bfloat16 *ms = nullptr, int ldms = 0, size_t ms_plane = 0,
+                              int ms_slices = 0);
 // P[(c d_y + i) w + k] = WL[i w + k] * der[c ldd + k]
 template <typename T>
 cudaError_t launch_jac_init(int C, int d_y, int w, const T *WL, const T *der, int ldd, T *P,
@@ -141,7 +145,10 @@ enum TcEpi : int {
   TC_EPI_STORE_F32 = 0,   // outf[row, col] = acc
   TC_EPI_BIAS_F32 = 1,    // outf = acc + bias[col]
   TC_EPI_BIAS_ACT = 2,    // z = acc + bias; out slices = act(z); der = act'(z) (fp32)
-  TC_EPI_SCALE_GROUP = 3  // out slices = acc * scale[(row/group)*lds + col]
+  TC_EPI_SCALE_GROUP = 3,  // out slices = acc * scale[(row/group)*lds + col]
+  TC_EPI_COEF = 4,         // out slices = coef[row*ldc + col] - cs * acc (coef FP64)
+  TC_EPI_FIELD_T = 5       // rows are field nodes, columns chains: where acc[col],
+                           // m[col*ldm + row] = (s m + cs Mf)[same] + acc
 };
 struct TcGemmArgs {
   int M = 0, N = 0, K = 0;
@@ -163,6 +170,13 @@ struct TcGemmArgs {
   float *der = nullptr;
   const float *scale = nullptr;
   int lds = 0, group = 1;
+  const double *coef = nullptr;  // TC_EPI_COEF
+  int ldc = 0;
+  double cs = 0.0, sc = 0.0;     // TC_EPI_COEF (cs), TC_EPI_FIELD_T (sc, cs)
+  const int *acc = nullptr;      // TC_EPI_FIELD_T
+  float *m = nullptr;
+  const float *Mf = nullptr;
+  int ldm = 0;
 };
 cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st);
 // Split FP32/FP64 values into bf16 slice planes (x ~= sum_s slice_s).

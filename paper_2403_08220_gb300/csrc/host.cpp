@@ -48,6 +48,8 @@ struct Error {
   } while (0)
 
 static inline int pad8(int x) { return (x + 7) & ~7; }
+// bf16 slices of the operands of the tensor-core complement projections
+constexpr int kFieldSlices = 3;
 
 // One device allocation carved into aligned sub-buffers.
 struct Arena {
@@ -398,6 +400,11 @@ struct Surrogate {
   std::vector<std::pair<void *, size_t>> allocs;
   double *dE = nullptr, *dD = nullptr, *dS = nullptr, *dSqrtLam = nullptr, *dy = nullptr;
   float *fE = nullptr, *fD = nullptr, *fS = nullptr, *fSqrtLam = nullptr;
+  // tensor path: bf16 slice planes of E (r x N, pitch ldE) and D (N x r, pitch ldD)
+  // for the complement projections
+  __nv_bfloat16 *bE = nullptr, *bD = nullptr;
+  int ldE = 0, ldD = 0;
+  size_t plE = 0, plD = 0;
   std::vector<double *> dW, dWT, db;
   std::vector<float *> fb, fW;
   std::vector<__nv_bfloat16 *> bW, bWT;
@@ -575,6 +582,12 @@ static int load_surrogate(dino_ctx *ctx, const dino_surrogate_desc *d) {
     s->fD = sur_upload(ctx, s.get(), fD.data(), fD.size());
     s->fS = sur_upload(ctx, s.get(), fS.data(), fS.size());
     s->fSqrtLam = sur_upload(ctx, s.get(), fL.data(), fL.size());
+    s->ldE = pad8(s->N);
+    s->ldD = pad8(s->r);
+    const auto be = split_planes(s->E, s->r, s->N, s->ldE, kFieldSlices, s->plE);
+    const auto bd = split_planes(s->D, s->N, s->r, s->ldD, kFieldSlices, s->plD);
+    s->bE = sur_upload(ctx, s.get(), be.data(), be.size());
+    s->bD = sur_upload(ctx, s.get(), bd.data(), bd.size());
   }
   if (d->y) {
     if (!(d->noise_var > 0)) fail(DINO_EINVAL, "noise_var must be > 0");
@@ -826,6 +839,8 @@ struct Pool {
   int *err;  // raised by a kernel whose bounded wait gave up
   // field scratch
   void *Mf, *coef2;
+  // tensor path: bf16 slice planes of the prior draw (C x ldE) and of coef2 (C x ldD)
+  __nv_bfloat16 *Ms = nullptr, *coef2s = nullptr;
   Work w;
 };
 
@@ -862,6 +877,10 @@ static void layout_pool(Pool &p, bool assign) {
   // FP64 at init even on the FP32 path; also holds a zero data vector in surrogate_eval
   p.Mf = take(std::max((size_t)C * N, (size_t)s->d_y) * std::max(fe, (size_t)8));
   p.coef2 = take((size_t)C * r * fe);
+  if (s->precision != DINO_PREC_FP64) {
+    p.Ms = (__nv_bfloat16 *)take((size_t)C * s->ldE * kFieldSlices * 2);
+    p.coef2s = (__nv_bfloat16 *)take((size_t)C * s->ldD * kFieldSlices * 2);
+  }
   layout_work(s, C, ar, p.w, assign);
 }
 
@@ -1042,19 +1061,58 @@ static void step_pool(dino_ctx *ctx, Pool &p) {
       return gemm_field<double>(C, N, r, coef2, r, s->dD, r, p.acc, p.sc, cs, m, Mf, N, st);
     });
   } else {
-    float *Mf = (float *)p.Mf, *coef2 = (float *)p.coef2, *m = (float *)p.m;
+    // FP32 draw plus its bf16 slices; both projections on the tensor cores
+    // with three slices (six products, FP32-level operands)
+    float *Mf = (float *)p.Mf, *m = (float *)p.m;
     launch(ctx, st, "prior_draw_f32", [&] {
       return launch_prior_draw<float>(C, s->n_grid, s->fSqrtLam, s->fS, p.seed, p.id_base,
-                                      STREAM_Z_ID, p.step, Mf, N, st);
+                                      STREAM_Z_ID, p.step, Mf, N, st, p.Ms, s->ldE,
+                                      (size_t)C * s->ldE, kFieldSlices);
     });
-    launch(ctx, st, "field_coef_f32", [&] {
-      // split-K partials in the Jacobian's P buffer, free once the Jacobian is formed
-      const size_t ws = p.w.Pb[0] ? p.w.plp * s->jac_slices / 2 : 0;  // bf16 -> float
-      return gemm_coef<float>(C, r, N, Mf, N, s->fE, N, p.coef, r, cs, coef2, r, st,
-                              reinterpret_cast<float *>(p.w.Pb[0]), ws);
+    launch(ctx, st, "field_coef_tc", [&] {
+      // coef2 (C x r) = coef - cs M E^T, written as bf16 slices
+      TcGemmArgs g;
+      g.M = C;
+      g.N = r;
+      g.K = N;
+      g.A = p.Ms;
+      g.lda = s->ldE;
+      g.a_plane = (size_t)C * s->ldE;
+      g.B = s->bE;
+      g.ldb = s->ldE;
+      g.b_plane = s->plE;
+      g.nslice = kFieldSlices;
+      g.epi = TC_EPI_COEF;
+      g.coef = p.coef;
+      g.ldc = r;
+      g.cs = cs;
+      g.out_bf = p.coef2s;
+      g.ldo = s->ldD;
+      g.out_plane = (size_t)C * s->ldD;
+      g.out_slices = kFieldSlices;
+      return launch_tc_gemm(g, st);
     });
-    launch(ctx, st, "field_update_f32", [&] {
-      return gemm_field<float>(C, N, r, coef2, r, s->fD, r, p.acc, p.sc, cs, m, Mf, N, st);
+    launch(ctx, st, "field_update_tc", [&] {
+      // (D coef2^T) (N x C), added where accepted: m <- s m + cs M + D coef2
+      TcGemmArgs g;
+      g.M = N;
+      g.N = C;
+      g.K = r;
+      g.A = s->bD;
+      g.lda = s->ldD;
+      g.a_plane = s->plD;
+      g.B = p.coef2s;
+      g.ldb = s->ldD;
+      g.b_plane = (size_t)C * s->ldD;
+      g.nslice = kFieldSlices;
+      g.epi = TC_EPI_FIELD_T;
+      g.acc = p.acc;
+      g.sc = p.sc;
+      g.cs = cs;
+      g.m = m;
+      g.Mf = Mf;
+      g.ldm = N;
+      return launch_tc_gemm(g, st);
     });
   }
   p.step += 1;

@@ -241,7 +241,8 @@ __host__ __device__ inline int prior_ld(int n) { return (n + 3) / 4 * 4; }
 template <typename T>
 __global__ void __launch_bounds__(kPriorThreads)
     k_prior_draw(int n, const T *__restrict__ sqrtlam, const T *__restrict__ S, uint64_t seed,
-                 uint64_t id_base, uint32_t stream, uint32_t step, T *out, int ldo) {
+                 uint64_t id_base, uint32_t stream, uint32_t step, T *out, int ldo,
+                 __nv_bfloat16 *ms, int ldms, size_t ms_plane, int ms_slices) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int ld = prior_ld(n), nt = ld / 4, NN = ld * ld;
   T *X = reinterpret_cast<T *>(smraw);
@@ -311,7 +312,20 @@ __global__ void __launch_bounds__(kPriorThreads)
     for (int p = 0; p < 4; ++p)
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        if (r0 + p < n && c0 + q < n) o[(r0 + p) * n + c0 + q] = acc[p][q];
+        if (r0 + p < n && c0 + q < n) {
+          o[(r0 + p) * n + c0 + q] = acc[p][q];
+          if constexpr (sizeof(T) == 4) {
+            if (ms) {
+              __nv_bfloat16 *d = ms + (size_t)c * ldms + (r0 + p) * n + c0 + q;
+              float rem = acc[p][q];
+              for (int sl = 0; sl < ms_slices; ++sl) {
+                const __nv_bfloat16 hb = __float2bfloat16_rn(rem);
+                d[sl * ms_plane] = hb;
+                rem -= __bfloat162float(hb);
+              }
+            }
+          }
+        }
   }
 }
 
@@ -435,14 +449,16 @@ size_t prior_draw_smem_bytes(int n, int elem) {
 template <typename T>
 cudaError_t launch_prior_draw(int C, int n, const T *sqrtlam, const T *S, uint64_t seed,
                               uint64_t id_base, uint32_t stream, uint32_t step, T *out, int ldo,
-                              cudaStream_t st) {
+                              cudaStream_t st, __nv_bfloat16 *ms, int ldms, size_t ms_plane,
+                              int ms_slices) {
   if (C <= 0) return cudaSuccess;
+  if (ms && (sizeof(T) != 4 || ms_slices < 1 || ldms < n * n)) return cudaErrorInvalidValue;
   const size_t smem = prior_draw_smem_bytes(n, (int)sizeof(T));
   cudaError_t e = cudaFuncSetAttribute(k_prior_draw<T>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_prior_draw<T><<<C, kPriorThreads, smem, st>>>(n, sqrtlam, S, seed, id_base, stream, step, out,
-                                                   ldo);
+                                                   ldo, ms, ldms, ms_plane, ms_slices);
   return cudaGetLastError();
 }
 
@@ -484,7 +500,7 @@ cudaError_t launch_f32_to_f64(size_t n, const float *src, double *dst, cudaStrea
                                      cudaStream_t);                                           \
   template cudaError_t launch_prior_draw<T>(int, int, const T *, const T *, uint64_t,         \
                                             uint64_t, uint32_t, uint32_t, T *, int,           \
-                                            cudaStream_t);                                    \
+                                            cudaStream_t, __nv_bfloat16 *, int, size_t, int); \
   template cudaError_t launch_jac_init<T>(int, int, int, const T *, const T *, int, T *,      \
                                           cudaStream_t);                                      \
   template cudaError_t launch_broadcast<T>(int, size_t, const T *, T *, cudaStream_t);

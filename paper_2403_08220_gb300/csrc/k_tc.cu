@@ -45,6 +45,13 @@ struct TcParams {
   __nv_bfloat16 *out_bf;
   float *der;
   const float *scale;
+  const double *coef;
+  int ldc;
+  double cs, sc;
+  const int *acc;
+  float *m;
+  const float *Mf;
+  int ldm;
   uint32_t tmem_cols;
   int *err;
 };
@@ -389,7 +396,24 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int row0 = m0 + quarter * 32, nrows = min(32, p.M - row0);
       uint4 *stg = stg_all + quarter * 256;
       int c0 = 0;  // columns [0, c0) done by the coalesced groups below
-      if ((p.epi == TC_EPI_STORE_F32 || p.epi == TC_EPI_BIAS_F32) && (p.ldo & 3) == 0) {
+      if (p.epi == TC_EPI_FIELD_T) {
+        // lanes are consecutive field nodes of one chain per column: each
+        // column's loads and stores are 128 contiguous bytes per warp
+        for (; c0 < nvalid; c0 += 16) {
+          float v[16];
+          tmem_ld16(tacc + (uint32_t)c0, v);
+          if (row < p.M) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int ch = n0 + c0 + j;
+              if (c0 + j < nvalid && p.acc[ch]) {
+                const size_t o = (size_t)ch * p.ldm + row;
+                p.m[o] = (float)(p.sc * (double)p.m[o] + p.cs * (double)p.Mf[o]) + v[j];
+              }
+            }
+          }
+        }
+      } else if ((p.epi == TC_EPI_STORE_F32 || p.epi == TC_EPI_BIAS_F32) && (p.ldo & 3) == 0) {
         // 32 FP32 columns = 128 bytes per row
         for (; c0 + 32 <= nvalid; c0 += 32) {
           float v[32];
@@ -402,14 +426,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                                (size_t)p.ldo * 4, nrows, lane);
         }
       } else if ((p.epi == TC_EPI_SCALE_GROUP && (p.lds & 3) == 0) ||
-                 (p.epi == TC_EPI_BIAS_ACT && (p.N & 3) == 0)) {
+                 (p.epi == TC_EPI_BIAS_ACT && (p.N & 3) == 0) || p.epi == TC_EPI_COEF) {
         // 64 columns = 128 bytes per row and bf16 slice (the derivative: two
         // 128-byte FP32 halves)
         if ((p.ldo & 7) == 0) {
           for (; c0 + 64 <= nvalid; c0 += 64) {
             float v[64];
             tmem_ld64(tacc + (uint32_t)c0, v);
-            if (p.epi == TC_EPI_SCALE_GROUP) {
+            if (p.epi == TC_EPI_COEF) {
+              if (row < p.M) {
+                const double *cf = p.coef + (size_t)row * p.ldc + n0 + c0;
+#pragma unroll
+                for (int j = 0; j < 64; ++j) v[j] = (float)(cf[j] - p.cs * (double)v[j]);
+              }
+            } else if (p.epi == TC_EPI_SCALE_GROUP) {
               if (row < p.M) {
                 const float4 *sc = reinterpret_cast<const float4 *>(
                     p.scale + (size_t)(row / p.group) * p.lds + n0 + c0);
@@ -486,6 +516,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             } else {
               for (int j = 0; j < ncols; ++j) d[j] = v[j];
             }
+          } else if (p.epi == TC_EPI_COEF) {
+            const double *cf = p.coef + (size_t)row * p.ldc + col0;
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              x[j] = j < ncols ? (float)(cf[j] - p.cs * (double)v[j]) : 0.0f;
           } else {
             const float *sc = p.scale + (size_t)(row / p.group) * p.lds + col0;
             if (ncols == 16 && (p.lds & 3) == 0) {
@@ -677,6 +712,14 @@ cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st) {
   p.out_bf = a.out_bf;
   p.der = a.der;
   p.scale = a.scale;
+  p.coef = a.coef;
+  p.ldc = a.ldc;
+  p.cs = a.cs;
+  p.sc = a.sc;
+  p.acc = a.acc;
+  p.m = a.m;
+  p.Mf = a.Mf;
+  p.ldm = a.ldm;
   uint32_t cols = 32;  // two accumulator buffers of BN columns
   while (cols < 2u * (uint32_t)p.BN) cols <<= 1;
   p.tmem_cols = cols;
