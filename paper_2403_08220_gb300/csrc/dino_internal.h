@@ -60,6 +60,10 @@ struct ReducedArgs {
   // surrogate output at b: J (C x d_y x r) and f (C x d_y), FP64 or FP32
   const void *J = nullptr;
   const void *f = nullptr;
+  // Woodbury path, FP32 J: the Gram matrices J J^T formed beforehand (C x
+  // d_y x ldg), or nullptr to form them in the geometry kernel
+  const float *G = nullptr;
+  int ldg = 0;
   int jf_f32 = 0;
   const double *y = nullptr;
   // accept outputs
@@ -142,7 +146,7 @@ cudaError_t launch_f32_to_f64(size_t n, const float *src, double *dst, cudaStrea
 // D = sum over slice pairs (i, j), i + j < nslice, of A_i B_j^T, FP32 accum.
 // A: M x K (row pitch lda elements), B: N x K (row pitch ldb).
 enum TcEpi : int {
-  TC_EPI_STORE_F32 = 0,   // outf[row, col] = acc
+  TC_EPI_STORE_F32 = 0,   // outf[row, col] = acc (and, with out_bf, its slices)
   TC_EPI_BIAS_F32 = 1,    // outf = acc + bias[col]
   TC_EPI_BIAS_ACT = 2,    // z = acc + bias; out slices = act(z); der = act'(z) (fp32)
   TC_EPI_SCALE_GROUP = 3,  // out slices = acc * scale[(row/group)*lds + col]
@@ -165,6 +169,7 @@ struct TcGemmArgs {
   const float *bias = nullptr;
   int act = 0;
   __nv_bfloat16 *out_bf = nullptr;  // slice planes of the output
+  int ldob = 0;                      // their row pitch with TC_EPI_STORE_F32 (else ldo)
   size_t out_plane = 0;
   int out_slices = 1;
   float *der = nullptr;
@@ -179,6 +184,12 @@ struct TcGemmArgs {
   int ldm = 0;
 };
 cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st);
+// Per-group Gram matrices on the tensor cores: for c < C, with J_c the g x K
+// block of rows c g .. c g + g - 1 of the stacked bf16 slice planes J (row
+// pitch ldj, plane stride plane, nslice planes; pairs i + j < nslice),
+// out[(c g + i) ldo + j] = (J_c J_c^T)[i, j] in FP32 for i, j < g (g <= 128).
+cudaError_t launch_tc_gram(int C, int g, int K, const __nv_bfloat16 *J, int ldj, size_t plane,
+                           int nslice, float *out, int ldo, cudaStream_t st);
 // Split FP32/FP64 values into bf16 slice planes (x ~= sum_s slice_s).
 cudaError_t launch_split_bf16_f64(int rows, int cols, const double *src, int lds,
                                   __nv_bfloat16 *dst, int ldd, size_t plane, int nslice,

@@ -48,8 +48,10 @@ struct Error {
   } while (0)
 
 static inline int pad8(int x) { return (x + 7) & ~7; }
-// bf16 slices of the operands of the tensor-core complement projections
+// bf16 slices of the operands of the tensor-core complement projections and
+// of the Jacobian rows that feed the tensor-core Gram matrices
 constexpr int kFieldSlices = 3;
+constexpr int kGramSlices = 3;
 
 // One device allocation carved into aligned sub-buffers.
 struct Arena {
@@ -395,6 +397,9 @@ struct Surrogate {
   bool has_data = false;
   // d_y < r: chains use the Woodbury path (d_y x d_y factor, perturbation noise map)
   bool wb = false;
+  // Woodbury path on the tensor path with d_y <= 128 and a hidden layer: the
+  // d_y x d_y Gram matrices J J^T come from the tensor cores
+  bool tc_gram = false;
   int pools = 0;
   // device
   std::vector<std::pair<void *, size_t>> allocs;
@@ -501,6 +506,7 @@ static int load_surrogate(dino_ctx *ctx, const dino_surrogate_desc *d) {
       geometry_smem_bytes(s->r, s->d_y, 0) > kSmemLimit)
     fail(DINO_EINVAL, "r=%d, d_y=%d exceed the per-chain shared-memory budget", s->r, s->d_y);
   s->wb = s->d_y < s->r && s->d_y <= kMaxWbDy;
+  s->tc_gram = s->wb && s->precision == DINO_PREC_BF16 && s->L >= 2 && s->d_y <= 128;
   if (s->wb && (wb_smem_bytes(s->r, s->d_y, 1) > kSmemLimit ||
                 wb_smem_bytes(s->r, s->d_y, 0) > kSmemLimit))
     fail(DINO_EINVAL, "d_y=%d < r=%d: the d_y x d_y factor exceeds the shared-memory budget",
@@ -622,10 +628,16 @@ struct Work {
   __nv_bfloat16 *Pb[2] = {nullptr, nullptr};
   int ldp = 0;
   size_t plp = 0;
+  // Gram matrices on the tensor cores: J as bf16 slices (rows x ldjb) and
+  // G (C x d_y x ldg, FP32)
+  __nv_bfloat16 *Jb = nullptr;
+  int ldjb = 0, ldg = 0;
+  size_t pljb = 0;
+  float *G = nullptr;
 };
 
 // Lays out (or, with base != nullptr, assigns) the workspace in an arena.
-static void layout_work(const Surrogate *s, int C, Arena &ar, Work &w, bool assign) {
+static void layout_work(const Surrogate *s, int C, Arena &ar, Work &w, bool assign, bool gram) {
   auto take = [&](size_t bytes) -> char * {
     const size_t at = ar.reserve(bytes);
     return assign ? ar.base + at : nullptr;
@@ -669,6 +681,13 @@ static void layout_work(const Surrogate *s, int C, Arena &ar, Work &w, bool assi
       w.Pb[1] = (__nv_bfloat16 *)take(w.plp * s->jac_slices * 2);
     }
     w.J32 = (float *)take(rows * s->r * 4);
+    if (gram) {
+      w.ldjb = pad8(s->r);
+      w.pljb = rows * w.ldjb;
+      w.Jb = (__nv_bfloat16 *)take(w.pljb * kGramSlices * 2);
+      w.ldg = (dy + 3) & ~3;
+      w.G = (float *)take(rows * w.ldg * 4);
+    }
   }
 }
 
@@ -809,7 +828,17 @@ static void eval_surrogate(dino_ctx *ctx, const Surrogate *s, Work &w, const dou
   g.epi = TC_EPI_STORE_F32;
   g.outf = w.J32;
   g.ldo = r;
+  if (w.Jb) {  // also the slices the Gram matrices are formed from
+    g.out_bf = w.Jb;
+    g.ldob = w.ldjb;
+    g.out_plane = w.pljb;
+    g.out_slices = kGramSlices;
+  }
   launch(ctx, st, "jac_tc", [&] { return launch_tc_gemm(g, st); });
+  if (w.G)
+    launch(ctx, st, "gram_tc", [&] {
+      return launch_tc_gram(C, dy, r, w.Jb, w.ldjb, w.pljb, kGramSlices, w.G, w.ldg, st);
+    });
 }
 
 // ---------------------------------------------------------------------------
@@ -881,7 +910,7 @@ static void layout_pool(Pool &p, bool assign) {
     p.Ms = (__nv_bfloat16 *)take((size_t)C * s->ldE * kFieldSlices * 2);
     p.coef2s = (__nv_bfloat16 *)take((size_t)C * s->ldD * kFieldSlices * 2);
   }
-  layout_work(s, C, ar, p.w, assign);
+  layout_work(s, C, ar, p.w, assign, p.wb && s->tc_gram);
 }
 
 static Pool *get_pool(dino_ctx *ctx, int id) {
@@ -910,6 +939,8 @@ static ReducedArgs reduced_args(const Pool &p) {
   a.cur = p.cur;
   a.L_slot = (size_t)p.C * (p.wb ? wb_slot_stride(s->d_y) : slot_stride(s->r));
   a.Js = p.Js;
+  a.G = p.w.G;
+  a.ldg = p.w.ldg;
   a.b = p.b;
   a.mu = p.mu;
   a.lq_fwd = p.lq_fwd;

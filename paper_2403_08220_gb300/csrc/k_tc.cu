@@ -39,6 +39,7 @@ struct TcParams {
   int M, N, K, BN, nkb, npairs, stages;
   int pair_a[6], pair_b[6];
   int epi, ldo, act, out_slices, lds, group;
+  int ldob;  // TC_EPI_STORE_F32 with out_bf: row pitch of the bf16 slice planes
   size_t out_plane;
   float *outf;
   const float *bias;
@@ -413,6 +414,34 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         }
+      } else if (p.epi == TC_EPI_STORE_F32 && p.out_bf) {
+        // FP32 values and their bf16 slices: 64 columns = two 128-byte FP32
+        // halves and one 128-byte segment per slice
+        if ((p.ldo & 3) == 0 && (p.ldob & 7) == 0) {
+          for (; c0 + 64 <= nvalid; c0 += 64) {
+            float v[64];
+            tmem_ld64(tacc + (uint32_t)c0, v);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              uint32_t w[32];
+#pragma unroll
+              for (int j = 0; j < 32; ++j) w[j] = __float_as_uint(v[32 * h + j]);
+              store_rows_coalesced(
+                  stg, w, reinterpret_cast<char *>(p.outf + (size_t)row0 * p.ldo + n0 + c0 + 32 * h),
+                  (size_t)p.ldo * 4, nrows, lane);
+            }
+            for (int sl = 0; sl < p.out_slices; ++sl) {
+              uint32_t w[32];
+#pragma unroll
+              for (int j = 0; j < 32; ++j) w[j] = pack_bf16x2(v[2 * j], v[2 * j + 1]);
+              store_rows_coalesced(
+                  stg, w,
+                  reinterpret_cast<char *>(p.out_bf + (size_t)row0 * p.ldob + n0 + c0 +
+                                           (size_t)sl * p.out_plane),
+                  (size_t)p.ldob * 2, nrows, lane);
+            }
+          }
+        }
       } else if ((p.epi == TC_EPI_STORE_F32 || p.epi == TC_EPI_BIAS_F32) && (p.ldo & 3) == 0) {
         // 32 FP32 columns = 128 bytes per row
         for (; c0 + 32 <= nvalid; c0 += 32) {
@@ -498,6 +527,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           } else {
             for (int j = 0; j < ncols; ++j) o[j] = v[j];
           }
+          if (p.epi == TC_EPI_STORE_F32 && p.out_bf)
+            for (int j = 0; j < ncols; ++j)
+              store_slices(v[j], p.out_bf + (size_t)row * p.ldob + col0 + j, p.out_plane,
+                           p.out_slices);
         } else {
           float x[16];
           if (p.epi == TC_EPI_BIAS_ACT) {
@@ -557,6 +590,189 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       // buffer b drained: hand it back to the MMA issuer
+      fence_before();
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bars[2 * S + 2 + b]))
+                     : "memory");
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(p.tmem_cols)
+                 : "memory");
+  }
+}
+
+// Per-group Gram matrices G_c = J_c J_c^T (persistent, one CTA per SM, groups
+// c = blockIdx.x, + gridDim.x, ...).  A stage holds one 64-wide k-block of
+// all slices of the 128 rows starting at row c g (the rows past the group
+// belong to the next group or are zero-filled past the end, and are never
+// stored); both MMA operands are views of the same staged tile, B its first
+// BN = ceil16(g) rows.  Roles and bounded waits as in k_tc_gemm; the
+// epilogue writes rows i < g, columns j < g.
+struct GramParams {
+  int C, g, K, BN, nkb, nslice, npairs, stages;
+  int pair_a[6], pair_b[6];
+  float *out;
+  int ldo;
+  uint32_t tmem_cols;
+  int *err;
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tc_gram(const __grid_constant__ CUtensorMap tmJ, const GramParams p) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  const uint32_t raw = smem_u32(smraw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char *gbase = smraw + (base - raw);
+  const uint32_t tile_bytes = kBlockM * kBlockK * 2;  // one slice of the stage
+  const uint32_t stage_bytes = tile_bytes * (uint32_t)p.nslice;
+  uint4 *stg_all = reinterpret_cast<uint4 *>(gbase + p.stages * stage_bytes);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(gbase + p.stages * stage_bytes + kStageTiles);
+  const int S = p.stages;
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 2 * S + 5);
+  volatile int *consumed = abort_flag + 1;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 6);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(smem_u32(&bars[s]), 1);
+      mbar_init(smem_u32(&bars[S + s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&bars[2 * S + b]), 1);
+      mbar_init(smem_u32(&bars[2 * S + 2 + b]), 4);
+    }
+    mbar_init(smem_u32(&bars[2 * S + 4]), 1);
+    *abort_flag = 0;
+    *consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(p.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int g = 0;
+      bool ok = true;
+      for (int c = blockIdx.x; c < p.C && ok; c += gridDim.x) {
+        for (int kb = 0; kb < p.nkb; ++kb, ++g) {
+          const int s = g % S;
+          const uint32_t ph = (uint32_t)(g / S) & 1u;
+          if (!mbar_wait(smem_u32(&bars[S + s]), ph ^ 1u, abort_flag)) {
+            *abort_flag = 1;
+            atomicOr(p.err, 1);
+            ok = false;
+            break;
+          }
+          const uint32_t full = smem_u32(&bars[s]);
+          mbar_expect_tx(full, stage_bytes);
+          const uint32_t sa = base + s * stage_bytes;
+          for (int sl = 0; sl < p.nslice; ++sl)
+            tma_load_3d(sa + sl * tile_bytes, &tmJ, kb * kBlockK, c * p.g, sl, full);
+        }
+      }
+      if (*abort_flag) {
+        for (int i = *consumed; i < g; ++i)
+          mbar_wait(smem_u32(&bars[i % S]), (uint32_t)(i / S) & 1u, nullptr);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(kBlockM, p.BN);
+      bool ok = true;
+      int g = 0, j = 0;
+      for (int c = blockIdx.x; c < p.C && ok; c += gridDim.x, ++j) {
+        const int b = j & 1;
+        if (!mbar_wait(smem_u32(&bars[2 * S + 2 + b]), (((uint32_t)j >> 1) & 1u) ^ 1u,
+                       abort_flag)) {
+          *abort_flag = 1;
+          atomicOr(p.err, 2);
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t tacc = tmem + (uint32_t)(b * p.BN);
+        for (int kb = 0; kb < p.nkb; ++kb, ++g) {
+          const int s = g % S;
+          const uint32_t ph = (uint32_t)(g / S) & 1u;
+          if (!mbar_wait(smem_u32(&bars[s]), ph, abort_flag)) {
+            *abort_flag = 1;
+            atomicOr(p.err, 2);
+            ok = false;
+            break;
+          }
+          *consumed = g + 1;
+          fence_after();
+          const uint32_t sa = base + s * stage_bytes;
+          for (int pr = 0; pr < p.npairs; ++pr) {
+            const uint64_t ad = smem_desc_sw128(sa + p.pair_a[pr] * tile_bytes);
+            const uint64_t bd = smem_desc_sw128(sa + p.pair_b[pr] * tile_bytes);
+#pragma unroll
+            for (int k = 0; k < kBlockK / 16; ++k)
+              mma_bf16(tacc, ad + 2 * k, bd + 2 * k, idesc, (kb > 0 || pr > 0 || k > 0) ? 1u : 0u);
+          }
+          mma_commit(smem_u32(&bars[S + s]));
+        }
+        if (ok) mma_commit(smem_u32(&bars[2 * S + b]));
+      }
+      if (!ok) {
+        mma_commit(smem_u32(&bars[2 * S + 4]));
+        mbar_wait(smem_u32(&bars[2 * S + 4]), 0, nullptr);
+      }
+    }
+  } else {
+    const int quarter = warp & 3;
+    const int i0 = quarter * 32, nrows = min(32, p.g - i0);  // rows of this warp in the group
+    uint4 *stg = stg_all + quarter * 256;
+    int j = 0;
+    for (int c = blockIdx.x; c < p.C; c += gridDim.x, ++j) {
+      const int b = j & 1;
+      int okl = 0;
+      if (lane == 0)
+        okl = mbar_wait(smem_u32(&bars[2 * S + b]), ((uint32_t)j >> 1) & 1u, abort_flag) ? 1 : 0;
+      if (__shfl_sync(0xffffffffu, okl, 0) == 0) {
+        if (lane == 0) {
+          *abort_flag = 1;
+          atomicOr(p.err, 4);
+        }
+        break;
+      }
+      fence_after();
+      const uint32_t tacc = tmem + ((uint32_t)(i0) << 16) + (uint32_t)(b * p.BN);
+      float *orow = p.out + ((size_t)c * p.g + i0) * p.ldo;
+      int c0 = 0;
+      if ((p.ldo & 3) == 0) {
+        for (; c0 + 32 <= p.g; c0 += 32) {
+          float v[32];
+          tmem_ld32(tacc + (uint32_t)c0, v);
+          uint32_t w[32];
+#pragma unroll
+          for (int q = 0; q < 32; ++q) w[q] = __float_as_uint(v[q]);
+          store_rows_coalesced(stg, w, reinterpret_cast<char *>(orow + c0), (size_t)p.ldo * 4,
+                               nrows, lane);
+        }
+      }
+      for (; c0 < p.g; c0 += 16) {
+        float v[16];
+        tmem_ld16(tacc + (uint32_t)c0, v);
+        if (lane < nrows)
+          for (int q = 0; q < 16 && c0 + q < p.g; ++q) orow[(size_t)lane * p.ldo + c0 + q] = v[q];
+      }
       fence_before();
       __syncwarp();
       if (lane == 0)
@@ -707,6 +923,7 @@ cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st) {
   p.lds = a.lds;
   p.group = a.group > 0 ? a.group : 1;
   p.out_plane = a.out_plane;
+  p.ldob = a.ldob;
   p.outf = a.outf;
   p.bias = a.bias;
   p.out_bf = a.out_bf;
@@ -739,6 +956,50 @@ cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st) {
     return cudaErrorInvalidValue;
   const int total = ((a.M + kBlockM - 1) / kBlockM) * ntiles;
   k_tc_gemm<<<std::min(total, sms), kThreads, smem, st>>>(tmA, tmB, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_gram(int C, int g, int K, const __nv_bfloat16 *J, int ldj, size_t plane,
+                           int nslice, float *out, int ldo, cudaStream_t st) {
+  if (C <= 0) return cudaSuccess;
+  if (g < 1 || g > kBlockM || K <= 0 || nslice < 1 || nslice > 3 || (ldj & 7) || (plane & 7) ||
+      ((uintptr_t)J & 15) || ldo < g || ((uintptr_t)out & 15))
+    return cudaErrorInvalidValue;
+  GramParams p{};
+  p.C = C;
+  p.g = g;
+  p.K = K;
+  p.BN = (g + 15) / 16 * 16;
+  p.nkb = (K + kBlockK - 1) / kBlockK;
+  p.nslice = nslice;
+  static const int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 2, 1, 0};
+  p.npairs = nslice == 1 ? 1 : (nslice == 2 ? 3 : 6);
+  for (int i = 0; i < 6; ++i) {
+    p.pair_a[i] = pa[i];
+    p.pair_b[i] = pb[i];
+  }
+  const int stage_bytes = kBlockM * kBlockK * 2 * nslice;
+  p.stages = std::max(2, std::min(kMaxStages, (200 * 1024) / stage_bytes));
+  p.out = out;
+  p.ldo = ldo;
+  uint32_t cols = 32;
+  while (cols < 2u * (uint32_t)p.BN) cols <<= 1;
+  p.tmem_cols = cols;
+  p.err = error_word();
+  if (!p.err) return cudaErrorMemoryAllocation;
+  CUtensorMap tm;
+  if ((long long)C * g > 0x7fffffffLL ||
+      !make_map(&tm, J, K, C * g, ldj, plane, nslice, kBlockM))
+    return cudaErrorInvalidValue;
+  const size_t smem = 1024 + (size_t)p.stages * stage_bytes + kStageTiles + (2 * p.stages + 8) * 8;
+  cudaError_t e =
+      cudaFuncSetAttribute(k_tc_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+    return cudaErrorInvalidValue;
+  k_tc_gram<<<std::min(C, sms), kThreads, smem, st>>>(tm, p);
   return cudaGetLastError();
 }
 

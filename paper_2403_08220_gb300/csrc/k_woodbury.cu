@@ -131,6 +131,23 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// Entry of M = I + G / noise_var in double-float from the FP32 Gram value x:
+// x (nh + nl) with (nh, nl) = 1 / noise_var as a double-float pair, and 1
+// added on the diagonal.
+__device__ __forceinline__ float2 gram_entry(float x, float nh, float nl, bool diag) {
+  const float ph = __fmul_rn(x, nh);
+  float e = __fmaf_rn(x, nh, -ph);
+  e = __fmaf_rn(x, nl, e);
+  float h, l;
+  fast_two_sum(ph, e, h, l);
+  if (diag) {
+    float s1, q1;
+    two_sum(1.0f, h, s1, q1);
+    fast_two_sum(s1, __fadd_rn(q1, l), h, l);
+  }
+  return make_float2(h, l);
+}
+
 // Shared bytes of the two staging buffers of wb_gram_rows.
 __host__ __device__ inline size_t wb_stage2_bytes(int dy) {
   return 2 * (size_t)((dy + kHT - 1) / kHT * kHT) * kWbLd * sizeof(float);
@@ -277,19 +294,7 @@ __device__ void wb_gram_rows(const float *J, int dy, int r, double inv_nv, doubl
 #pragma unroll
       for (int q = 0; q < kHT; ++q) {
         const int i = kHT * ti[s] + p, j = kHT * tj[s] + q;
-        if (i < dy && j <= i) {
-          const float xv = acc[s][p][q], ph = __fmul_rn(xv, nh);
-          float e = __fmaf_rn(xv, nh, -ph);
-          e = __fmaf_rn(xv, nl, e);
-          float h, l;
-          fast_two_sum(ph, e, h, l);
-          if (i == j) {
-            float s1, q1;
-            two_sum(1.0f, h, s1, q1);
-            fast_two_sum(s1, __fadd_rn(q1, l), h, l);
-          }
-          Ms[tri(i) + j] = make_float2(h, l);
-        }
+        if (i < dy && j <= i) Ms[tri(i) + j] = gram_entry(acc[s][p][q], nh, nl, i == j);
       }
   }
   __syncthreads();
@@ -351,10 +356,24 @@ __global__ void __launch_bounds__(kWbThreads, kWbMinBlocks) k_wb_geometry(Reduce
   if constexpr (sizeof(TJ) == 4) {  // M, K b and K a from one pass over J
     float *stage = wb_stage_fits(dy) ? reinterpret_cast<float *>(sm + lay.Ms)
                                      : reinterpret_cast<float *>(sm + lay.tail);
-    wb_gram_rows<A>(reinterpret_cast<const float *>(J), dy, r, inv_nv, inv_sigma,
-                    reinterpret_cast<float2 *>(Ms), stage,
-                    reinterpret_cast<const float2 *>(be), reinterpret_cast<const float2 *>(ae),
-                    mode == 1, Kb, Ka);
+    if (a.G) {  // Gram matrix formed on the tensor cores: K b, K a only, then M from G
+      wb_gram_rows<A, false>(reinterpret_cast<const float *>(J), dy, r, inv_nv, inv_sigma,
+                             reinterpret_cast<float2 *>(Ms), stage,
+                             reinterpret_cast<const float2 *>(be),
+                             reinterpret_cast<const float2 *>(ae), mode == 1, Kb, Ka);
+      const float *Gc = a.G + (size_t)c * dy * a.ldg;
+      const float nh = __double2float_rn(inv_nv), nl = __double2float_rn(inv_nv - (double)nh);
+      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+      for (int i = warp; i < dy; i += nw)
+        for (int j = lane; j <= i; j += 32)
+          reinterpret_cast<float2 *>(Ms)[tri(i) + j] = gram_entry(Gc[(size_t)i * a.ldg + j], nh, nl, i == j);
+      __syncthreads();
+    } else {
+      wb_gram_rows<A>(reinterpret_cast<const float *>(J), dy, r, inv_nv, inv_sigma,
+                      reinterpret_cast<float2 *>(Ms), stage,
+                      reinterpret_cast<const float2 *>(be), reinterpret_cast<const float2 *>(ae),
+                      mode == 1, Kb, Ka);
+    }
   } else {
     rows_times<A, TJ>(J, dy, r, inv_sigma, be, ae, mode == 1, Kb, Ka);  // K b, K a
     form_gram_f64<true>(reinterpret_cast<const double *>(J), r, dy, r, inv_nv,
