@@ -159,6 +159,12 @@ __host__ __device__ inline bool wb_stage_fits(int dy) {
   return wb_stage2_bytes(dy) <= ((tri_size(dy + 1) + 1) & ~(size_t)1) * sizeof(double);
 }
 
+// A ring of four staging buffers (three chunks of J in flight) for the
+// row-products-only passes, when it fits in the factor's region.
+__host__ __device__ inline bool wb_ring4_fits(int dy) {
+  return 2 * wb_stage2_bytes(dy) <= ((tri_size(dy + 1) + 1) & ~(size_t)1) * sizeof(double);
+}
+
 template <typename TJ>
 __host__ __device__ size_t wb_stage_bytes(int r, int dy) {
   if (sizeof(TJ) == 4) return wb_stage_fits(dy) ? 0 : wb_stage2_bytes(dy);
@@ -168,12 +174,12 @@ __host__ __device__ size_t wb_stage_bytes(int r, int dy) {
 // M = I + J J^T / noise_var (double-float entries, FP32 register tiles) and,
 // from the same pass over J, Kb = (J b) / sigma and Ka = (J a) / sigma
 // (double-float dot products, thread per row).  J (dy x r, row-major FP32)
-// streams through two shared buffers in chunks of kWbKc columns by
-// asynchronous copies, the next chunk in flight while the current one is
-// used; rows are kept in natural order (padded to kWbLd floats) and read as
-// float4 along the reduction index.
+// streams through a ring of kDepth shared buffers in chunks of kWbKc columns
+// by asynchronous copies, kDepth - 1 chunks in flight while one is used;
+// rows are kept in natural order (padded to kWbLd floats) and read as float4
+// along the reduction index.
 // kGram = false: only the row products (no Gram tiles, Ms untouched).
-template <class A, bool kGram = true>
+template <class A, bool kGram = true, int kDepth = 2>
 __device__ void wb_gram_rows(const float *J, int dy, int r, double inv_nv, double inv_sigma,
                              float2 *Ms, float *stage, const float2 *be, const float2 *ae,
                              bool two, double *Kb, double *Ka) {
@@ -182,13 +188,12 @@ __device__ void wb_gram_rows(const float *J, int dy, int r, double inv_nv, doubl
   const int ntiles = nt * (nt + 1) / 2;
   const int nch = (r + kWbKc - 1) / kWbKc;
   const bool vec = (r % 4) == 0;  // 16-byte aligned rows
-  const size_t bstride = (size_t)dyp * kWbLd;  // floats between the two buffers
-  for (int e = tid; e < (dyp - dy) * kWbLd; e += T) {  // padding rows stay zero
-    stage[(size_t)dy * kWbLd + e] = 0.0f;
-    stage[bstride + (size_t)dy * kWbLd + e] = 0.0f;
-  }
+  const size_t bstride = (size_t)dyp * kWbLd;  // floats between consecutive buffers
+  for (int e = tid; e < (dyp - dy) * kWbLd; e += T)  // padding rows stay zero
+#pragma unroll
+    for (int q = 0; q < kDepth; ++q) stage[q * bstride + (size_t)dy * kWbLd + e] = 0.0f;
   auto issue = [&](int ch) {
-    float *dst = stage + (ch & 1) * bstride;
+    float *dst = stage + (ch % kDepth) * bstride;
     const int k0 = ch * kWbKc;
     if (vec) {
       for (int e = tid; e < dy * (kWbKc / 4); e += T) {
@@ -227,16 +232,19 @@ __device__ void wb_gram_rows(const float *J, int dy, int r, double inv_nv, doubl
   typename A::Acc kb[2] = {A::begin(float2{}), A::begin(float2{})};
   typename A::Acc ka[2] = {A::begin(float2{}), A::begin(float2{})};
 
-  issue(0);
+  // one commit group per chunk (empty past the end), so that waiting until
+  // kDepth - 1 groups are pending completes chunk ch
+  for (int ch = 0; ch < kDepth - 1; ++ch) {
+    if (ch < nch) issue(ch);
+    else cp_async_commit();
+  }
   for (int ch = 0; ch < nch; ++ch) {
-    if (ch + 1 < nch) {
-      issue(ch + 1);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
+    // refills the buffer of chunk ch - 1, released by the barrier ending its use
+    if (ch + kDepth - 1 < nch) issue(ch + kDepth - 1);
+    else cp_async_commit();
+    cp_async_wait<kDepth - 1>();
     __syncthreads();
-    const float *x = stage + (ch & 1) * bstride;
+    const float *x = stage + (ch % kDepth) * bstride;
     const int k0 = ch * kWbKc;
 #pragma unroll
     for (int kk = 0; kk < kWbKc; kk += 4) {
@@ -357,10 +365,16 @@ __global__ void __launch_bounds__(kWbThreads, kWbMinBlocks) k_wb_geometry(Reduce
     float *stage = wb_stage_fits(dy) ? reinterpret_cast<float *>(sm + lay.Ms)
                                      : reinterpret_cast<float *>(sm + lay.tail);
     if (a.G) {  // Gram matrix formed on the tensor cores: K b, K a only, then M from G
-      wb_gram_rows<A, false>(reinterpret_cast<const float *>(J), dy, r, inv_nv, inv_sigma,
-                             reinterpret_cast<float2 *>(Ms), stage,
-                             reinterpret_cast<const float2 *>(be),
-                             reinterpret_cast<const float2 *>(ae), mode == 1, Kb, Ka);
+      if (wb_ring4_fits(dy))
+        wb_gram_rows<A, false, 4>(reinterpret_cast<const float *>(J), dy, r, inv_nv, inv_sigma,
+                                  reinterpret_cast<float2 *>(Ms), stage,
+                                  reinterpret_cast<const float2 *>(be),
+                                  reinterpret_cast<const float2 *>(ae), mode == 1, Kb, Ka);
+      else
+        wb_gram_rows<A, false>(reinterpret_cast<const float *>(J), dy, r, inv_nv, inv_sigma,
+                               reinterpret_cast<float2 *>(Ms), stage,
+                               reinterpret_cast<const float2 *>(be),
+                               reinterpret_cast<const float2 *>(ae), mode == 1, Kb, Ka);
       const float *Gc = a.G + (size_t)c * dy * a.ldg;
       const float nh = __double2float_rn(inv_nv), nl = __double2float_rn(inv_nv - (double)nh);
       const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -505,7 +519,11 @@ __global__ void __launch_bounds__(kWbThreads, kWbMinBlocks) k_wb_propose(Reduced
   }
   __syncthreads();
   if constexpr (sizeof(TJ) == 4) {  // K xi1 from J staged through the (still empty) factor region
-    if (wb_stage_fits(dy)) {
+    if (wb_ring4_fits(dy)) {
+      wb_gram_rows<A, false, 4>(reinterpret_cast<const float *>(J), dy, r, 0.0, inv_sigma,
+                                nullptr, reinterpret_cast<float *>(sm + lay.Ms),
+                                reinterpret_cast<const float2 *>(x1E), nullptr, false, Kxi, Kxi);
+    } else if (wb_stage_fits(dy)) {
       wb_gram_rows<A, false>(reinterpret_cast<const float *>(J), dy, r, 0.0, inv_sigma, nullptr,
                              reinterpret_cast<float *>(sm + lay.Ms),
                              reinterpret_cast<const float2 *>(x1E), nullptr, false, Kxi, Kxi);
