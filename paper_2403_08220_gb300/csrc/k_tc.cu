@@ -805,45 +805,50 @@ __global__ void k_jac_init_bf16(int C, int d_y, int w, const float *__restrict__
                                 const float *__restrict__ der, int ldd,
                                 __nv_bfloat16 *__restrict__ P, int ldp, size_t plane,
                                 int nslice) {
-  // P = W_L .* der (per chain): a warp per row (c, i), each lane 8 consecutive
-  // columns at a time; 32-bit index arithmetic once per row, float4 loads
-  // when the rows are 16-byte aligned.
-  const int lane = threadIdx.x & 31;
-  const int nwarps = gridDim.x * (blockDim.x >> 5);
-  const int rows = C * d_y, groups = (w + 7) / 8;
+  // P = W_L .* der (per chain).  Work items are groups of 8 consecutive
+  // columns of one row (c, i), enumerated row-major over all rows, so that
+  // consecutive threads write consecutive 16-byte pieces and every thread
+  // has the same share; float4 loads when the rows are 16-byte aligned.
+  const int groups = (w + 7) / 8;
+  const size_t items = (size_t)C * d_y * groups;
   const bool vload = (w & 3) == 0 && (ldd & 3) == 0;
   const bool vstore = (ldp & 7) == 0;
-  for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += nwarps) {
-    const int c = row / d_y, i = row - c * d_y;
+  // 32-bit index arithmetic (the launcher caps items below 2^32)
+  const uint32_t nitems = (uint32_t)items, ug = (uint32_t)groups, udy = (uint32_t)d_y;
+  for (uint32_t it = blockIdx.x * blockDim.x + threadIdx.x; it < nitems;
+       it += gridDim.x * blockDim.x) {
+    const uint32_t urow = it / ug;
+    const int g = (int)(it - urow * ug);
+    const size_t row = urow;
+    const int c = (int)(urow / udy), i = (int)(urow - (uint32_t)c * udy);
     const float *wr = WL + (size_t)i * w;
     const float *dr = der + (size_t)c * ldd;
-    __nv_bfloat16 *o = P + (size_t)row * ldp;
-    for (int g = lane; g < groups; g += 32) {
-      const int k0 = 8 * g;
-      float x[8];
-      if (vload && k0 + 8 <= w) {
-        const float4 w0 = *reinterpret_cast<const float4 *>(wr + k0);
-        const float4 w1 = *reinterpret_cast<const float4 *>(wr + k0 + 4);
-        const float4 d0 = *reinterpret_cast<const float4 *>(dr + k0);
-        const float4 d1 = *reinterpret_cast<const float4 *>(dr + k0 + 4);
-        x[0] = w0.x * d0.x; x[1] = w0.y * d0.y; x[2] = w0.z * d0.z; x[3] = w0.w * d0.w;
-        x[4] = w1.x * d1.x; x[5] = w1.y * d1.y; x[6] = w1.z * d1.z; x[7] = w1.w * d1.w;
+    __nv_bfloat16 *o = P + row * ldp;
+    const int k0 = 8 * g;
+    float x[8];
+    if (vload && k0 + 8 <= w) {
+      const float4 w0 = *reinterpret_cast<const float4 *>(wr + k0);
+      const float4 w1 = *reinterpret_cast<const float4 *>(wr + k0 + 4);
+      const float4 d0 = *reinterpret_cast<const float4 *>(dr + k0);
+      const float4 d1 = *reinterpret_cast<const float4 *>(dr + k0 + 4);
+      x[0] = w0.x * d0.x; x[1] = w0.y * d0.y; x[2] = w0.z * d0.z; x[3] = w0.w * d0.w;
+      x[4] = w1.x * d1.x; x[5] = w1.y * d1.y; x[6] = w1.z * d1.z; x[7] = w1.w * d1.w;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) x[q] = k0 + q < w ? wr[k0 + q] * dr[k0 + q] : 0.0f;
+    }
+    const bool vec = vstore && k0 + 8 <= ldp;
+    for (int sl = 0; sl < nslice; ++sl) {
+      uint32_t h[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) h[q] = pack_bf16x2(x[2 * q], x[2 * q + 1]);
+      __nv_bfloat16 *os = o + sl * plane + k0;
+      if (vec) {
+        *reinterpret_cast<uint4 *>(os) = make_uint4(h[0], h[1], h[2], h[3]);
       } else {
-#pragma unroll
-        for (int q = 0; q < 8; ++q) x[q] = k0 + q < w ? wr[k0 + q] * dr[k0 + q] : 0.0f;
-      }
-      const bool vec = vstore && k0 + 8 <= ldp;
-      for (int sl = 0; sl < nslice; ++sl) {
-        __nv_bfloat16 h[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          h[q] = __float2bfloat16_rn(x[q]);
-          x[q] -= __bfloat162float(h[q]);
-        }
-        if (vec) {
-          *reinterpret_cast<uint4 *>(o + sl * plane + k0) = *reinterpret_cast<const uint4 *>(h);
-        } else {
-          for (int q = 0; q < 8 && k0 + q < w; ++q) o[sl * plane + k0 + q] = h[q];
+        for (int q = 0; q < 8 && k0 + q < w; ++q) {
+          const uint32_t hw = h[q >> 1] >> (16 * (q & 1));
+          os[q] = __ushort_as_bfloat16((unsigned short)(hw & 0xffffu));
         }
       }
     }
@@ -1015,8 +1020,9 @@ cudaError_t launch_split_bf16_f64(int rows, int cols, const double *src, int lds
 cudaError_t launch_jac_init_bf16(int C, int d_y, int w, const float *WL, const float *der,
                                  int ldd, __nv_bfloat16 *P, int ldp, size_t plane, int nslice,
                                  cudaStream_t st) {
-  const size_t rows = (size_t)C * d_y;  // one warp per row, 8 warps per block
-  const int grid = (int)std::min<size_t>((rows + 7) / 8, 152 * 16);
+  const size_t items = (size_t)C * d_y * ((w + 7) / 8);  // 8 columns per thread
+  if (items >= 0xffffffffull - 152ull * 16 * 256) return cudaErrorInvalidValue;
+  const int grid = (int)std::min<size_t>((items + 255) / 256, 152 * 16);
   k_jac_init_bf16<<<grid > 0 ? grid : 1, 256, 0, st>>>(C, d_y, w, WL, der, ldd, P, ldp, plane,
                                                        nslice);
   return cudaGetLastError();
