@@ -66,11 +66,15 @@ extern "C" {
 #define DINO_BASIS_EXPLICIT 2 /* caller supplies E (r x N) and D (N x r) */
 
 #define DINO_PREC_FP64 0      /* every step in float64 */
-#define DINO_PREC_BF16 1      /* MLP/Jacobian GEMMs on tcgen05 in BF16 (FP32 accum),
-                                 Cholesky, solves and log-acceptance in FP64,
-                                 field update in FP32 */
+#define DINO_PREC_BF16 1      /* MLP/Jacobian GEMMs on tcgen05 in BF16 (FP32 accum);
+                                 Gram matrices and complement projections on
+                                 tcgen05 with FP32-level operands (three bf16
+                                 slices); Cholesky, solves and log-acceptance
+                                 FP64-accurate (double-float); field in FP32 */
 
 #define DINO_FLAG_TIMING 1u   /* record per-kernel CUDA-event times */
+#define DINO_FLAG_NO_DIRECT_HOST 2u /* copy host fields with cudaMemcpy even where
+                                       the device reads pageable host memory */
 
 typedef struct dino_ctx dino_ctx;
 
@@ -175,7 +179,11 @@ int dino_surrogate_eval(dino_ctx *ctx, int surrogate_id, int n, const double *m_
  * prior draw, 3 = initial prior draw (step 0).  Results therefore do not
  * depend on how chains are grouped into pools.
  * m0: n_chains x N host field values, or NULL for prior draws.
- * The initial state is m_r = E m0 and the surrogate geometry at m_r.
+ * The initial state is m_r = E m0 (FP64) and the surrogate geometry at m_r.
+ * Where the device reads pageable host memory coherently (cudaDevAttr-
+ * PageableMemoryAccess, e.g. Grace over NVLink-C2C) a kernel reads m0 in
+ * place instead of a cudaMemcpy, unless the context has
+ * DINO_FLAG_NO_DIRECT_HOST; m0 is not used after the call returns either way.
  * Errors: EINVAL, ENOTFOUND, ESTATE (data unset), ENOMEM. */
 int dino_chains_create(dino_ctx *ctx, int surrogate_id, int n_chains, double dt,
                        uint64_t seed, uint64_t chain_id_base, const double *m0,

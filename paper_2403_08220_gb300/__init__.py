@@ -35,6 +35,7 @@ DINO_ACT_IDENTITY, DINO_ACT_TANH, DINO_ACT_GELU = 0, 1, 2
 DINO_BASIS_KLE, DINO_BASIS_DIS, DINO_BASIS_EXPLICIT = 0, 1, 2
 DINO_PREC_FP64, DINO_PREC_BF16 = 0, 1
 DINO_FLAG_TIMING = 1
+DINO_FLAG_NO_DIRECT_HOST = 2
 
 _ERRNAMES = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EBUSY", -5: "ETIMEOUT",
              -6: "ENOTFOUND", -7: "ENUMERIC", -8: "ESTATE"}

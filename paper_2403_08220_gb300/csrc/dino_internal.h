@@ -139,6 +139,9 @@ cudaError_t launch_jac_init(int C, int d_y, int w, const T *WL, const T *der, in
 template <typename T>
 cudaError_t launch_broadcast(int C, size_t n, const T *src, T *out, cudaStream_t st);
 cudaError_t launch_f64_to_f32(size_t n, const double *src, float *dst, cudaStream_t st);
+// dst[i] = src[i]; src may be pageable host memory on a device that reads it
+// coherently (cudaDevAttrPageableMemoryAccess)
+cudaError_t launch_copy_f64(size_t n, const double *src, double *dst, cudaStream_t st);
 cudaError_t launch_f32_to_f64(size_t n, const float *src, double *dst, cudaStream_t st);
 
 // ---- tcgen05 BF16 GEMM (sm_103a) -----------------------------------------

@@ -95,6 +95,8 @@ struct dino_ctx {
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> event_pool;
   std::unique_ptr<dino::Server> server;
+  // the device reads pageable host memory coherently (Grace: over NVLink-C2C)
+  bool pageable_access = false;
 };
 
 namespace dino {
@@ -1011,7 +1013,12 @@ static Pool *create_pool_on(dino_ctx *ctx, int sid, int C, double dt, uint64_t s
     CK(cudaMemsetAsync(p->cur, 0, (size_t)C * 4, st));
     CK(cudaMemsetAsync(p->acc, 0, (size_t)C * 4, st));
     double *m64 = (double *)p->Mf;  // FP64 initial field
-    if (m0) {
+    if (m0 && !serving && ctx->pageable_access) {
+      // synchronous create on a device that reads pageable host memory
+      // coherently (Grace: NVLink-C2C): a kernel reads m0 in place; the call
+      // returns only after the stream has drained
+      launch(ctx, st, "field_in", [&] { return launch_copy_f64((size_t)C * N, m0, m64, st); });
+    } else if (m0) {
       CK(cudaMemcpyAsync(m64, m0, (size_t)C * N * 8, cudaMemcpyHostToDevice, st));
     } else {
       launch(ctx, st, "prior_draw_f64", [&] {
@@ -1555,6 +1562,10 @@ int dino_init(dino_ctx **out, int device, size_t hbm_budget_bytes, void *stream,
     return DINO_ECUDA;
   }
   ctx->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)fr);
+  int pma = 0;
+  if (!(flags & DINO_FLAG_NO_DIRECT_HOST) &&
+      cudaDeviceGetAttribute(&pma, cudaDevAttrPageableMemoryAccess, device) == cudaSuccess)
+    ctx->pageable_access = pma != 0;
   if (stream) {
     ctx->stream = (cudaStream_t)stream;
   } else {

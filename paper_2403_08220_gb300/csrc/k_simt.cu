@@ -475,6 +475,11 @@ cudaError_t launch_broadcast(int C, size_t n, const T *src, T *out, cudaStream_t
   return cudaGetLastError();
 }
 
+cudaError_t launch_copy_f64(size_t n, const double *src, double *dst, cudaStream_t st) {
+  k_convert<double, double><<<grid_for(n), 256, 0, st>>>(n, src, dst);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_f64_to_f32(size_t n, const double *src, float *dst, cudaStream_t st) {
   k_convert<double, float><<<grid_for(n), 256, 0, st>>>(n, src, dst);
   return cudaGetLastError();

@@ -180,3 +180,31 @@ def test_double_float_cholesky_on_exact_hessian(dino, ctx, r, h, dy):
         assert abs(g["hld"][c] - hld) <= 1e-10 * abs(hld)
         assert rel_err(g["g"][c], J.T @ g["f"][c]) <= 1e-12
     dino.dino_unload_surrogate(ctx, sid)
+
+
+@pytest.mark.gpu
+def test_host_field_read_in_place_matches_copy(dino):
+    """A pool created from a host m0 gives the same chains whether the field-init
+    kernel reads m0 in place (devices that read pageable host memory) or from a
+    device copy (DINO_FLAG_NO_DIRECT_HOST), and its initial m_r is E m0 (FP64)."""
+    w = variant(CONFIGS["r200_dis_bf16"], n_chains=96)
+    rng = np.random.default_rng(31)
+    m0 = 0.05 * rng.standard_normal((w.n_chains, w.N))
+    out = []
+    for flags in (0, dino.DINO_FLAG_NO_DIRECT_HOST):
+        c = dino.dino_init(0, 0, None, flags)
+        try:
+            sid = gpu_setup(dino, c, w)
+            E, _ = dino.dino_read_basis(c, sid, w.r, w.N)
+            pool = dino.dino_chains_create(c, sid, w.n_chains, 2e-5, SEED_CHAINS, 0, m0)
+            first = dino.dino_chains_read(c, pool, w.n_chains, w.r, w.N, field=False)
+            dino.dino_chains_step(c, pool, 2)
+            last = dino.dino_chains_read(c, pool, w.n_chains, w.r, w.N, field=True)
+            out.append((first, last))
+        finally:
+            c.close()
+    ref = m0 @ E.T
+    assert rel_err(out[0][0]["m_r"], ref) <= 1e-10
+    assert np.array_equal(out[0][0]["m_r"], out[1][0]["m_r"])
+    for k in ("m_r", "phi", "accepts", "m"):
+        assert np.array_equal(out[0][1][k], out[1][1][k]), k
