@@ -63,24 +63,48 @@ def geometry_traffic_per_chain(workload: str):
     return None
 
 
-def geometry_work(r: int, d_y: int) -> dict:
+def geometry_work(r: int, d_y: int, tc_gram: bool = False) -> dict:
     """Algorithmic work of one geometry launch per chain, by pipe.
 
     d_y < r (Woodbury path): the FP32 Gram product J J^T, d_y (d_y + 1) r
-    flops, and in double-float arithmetic the bordered Cholesky of the
-    (d_y + 1)-matrix, (d_y + 1)^3 / 3, plus the products K b and K a, 4 r d_y.
-    Otherwise: the FP32 product J^T J, r (r + 1) d_y, and in double-float the
-    bordered r-Cholesky with the reverse-density products and the gradient
-    (`fp64_flops_geometry`).  A double-float multiply-add takes 12 FP32
-    instructions, so the FP32-pipe charge is fp32 + 12 x df flops.
+    flops, unless it was formed beforehand on the tensor cores (tc_gram: the
+    BF16 path with d_y <= 128), and in double-float arithmetic the bordered
+    Cholesky of the (d_y + 1)-matrix, (d_y + 1)^3 / 3, plus the products K b
+    and K a, 4 r d_y.  Otherwise: the FP32 product J^T J, r (r + 1) d_y, and in
+    double-float the bordered r-Cholesky with the reverse-density products and
+    the gradient (`fp64_flops_geometry`).  A double-float multiply-add takes 12
+    FP32 instructions, so the FP32-pipe charge is fp32 + 12 x df flops.
     """
     if d_y < r:
-        fp32 = d_y * (d_y + 1) * r
+        fp32 = 0 if tc_gram else d_y * (d_y + 1) * r
         df = (d_y + 1) ** 3 / 3.0 + 4.0 * r * d_y
     else:
         fp32 = r * (r + 1) * d_y
         df = fp64_flops_geometry(r, d_y)
     return {"fp32": fp32, "df": df, "fp32_charge": fp32 + DF_INSTR_PER_FMA * df}
+
+
+def load_peaks() -> dict:
+    """The measured HBM and bf16 peaks of this GPU pool (empty when absent)."""
+    try:
+        with open(PEAKS_PATH) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def jacobian_flops(w) -> float:
+    """Tensor-core flops per chain of the reverse-mode Jacobian GEMMs.
+
+    For layers l = L-2 .. 1 the product of the running d_y x w_{l+1} block
+    with W_l^T (2 d_y w_l w_{l+1}), then the last with W_0^T (2 d_y r w_1),
+    each once per slice pair (three pairs for two slices).
+    """
+    ws = list(w.widths)
+    L = len(ws) - 1
+    per_term = sum(2.0 * w.d_y * ws[l] * ws[l + 1] for l in range(1, L - 1))
+    per_term += 2.0 * w.d_y * w.r * ws[1]
+    return 3.0 * per_term
 
 
 def fp64_flops_geometry(r: int, d_y: int) -> float:
@@ -230,7 +254,8 @@ def run_ours(args, rank, world, device):
     pool_t = dino.dino_chains_create(ctx_t, sid_t, C, w.dt, SEED_CHAINS, base)
     dino.dino_chains_step(ctx_t, pool_t, 1, stats=False)
     dino.dino_kernel_times(ctx_t, reset=True)
-    dino.dino_chains_step(ctx_t, pool_t, max(2, min(args.steps, 5)), stats=False)
+    n_pass = max(2, min(args.steps, 5))
+    dino.dino_chains_step(ctx_t, pool_t, n_pass, stats=False)
     kt = dino.dino_kernel_times(ctx_t)
     dino.dino_chains_destroy(ctx_t, pool_t)
     ctx_t.close()
@@ -238,7 +263,8 @@ def run_ours(args, rank, world, device):
     dom = max(kt.items(), key=lambda kv: kv[1][0])
     geo = kt.get("geometry", dom[1])
     geo_ms = geo[0] / max(1, geo[1])
-    work = geometry_work(w.r, w.d_y)
+    tc_gram = w.precision == "bf16" and w.d_y < w.r and w.d_y <= 128 and len(w.widths) >= 3
+    work = geometry_work(w.r, w.d_y, tc_gram)
     achieved = work["fp32_charge"] * C / (geo_ms * 1e-3) / 1e12
     tpc = geometry_traffic_per_chain(args.workload)
     roofline = {"bound": "alu", "pipe": "fp32", "kernel": "geometry",
@@ -250,6 +276,20 @@ def run_ours(args, rank, world, device):
                 "traffic": tpc * C if tpc else None,
                 "traffic_note": "dram bytes per launch scaled from a 1216-chain ncu capture",
                 "share_of_step": round(geo[0] / total, 4)}
+    # the largest tensor-core kernel beside it: the Jacobian GEMMs (two
+    # launches per step), against the measured sustained bf16 peak
+    roofline_tensor = None
+    jt = kt.get("jac_tc")
+    if jt and w.precision == "bf16":
+        peak = load_peaks().get("bf16_tflops_sustained")
+        flops = jacobian_flops(w) * C * n_pass
+        ach = flops / (jt[0] * 1e-3) / 1e12
+        roofline_tensor = {"bound": "tensor", "kernel": "jac_tc (k_tc_gemm, Jacobian)",
+                           "achieved": round(ach, 2), "peak": peak, "unit": "TFLOP/s",
+                           "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained",
+                           "frac": round(ach / peak, 4) if peak else None,
+                           "flops_per_chain": jacobian_flops(w),
+                           "share_of_step": round(jt[0] / total, 4)}
 
     # FP64 plain step beside it (fewer steps: it runs its GEMMs in FP64)
     fp64_line = None
@@ -300,7 +340,8 @@ def run_ours(args, rank, world, device):
                        "l2": "inputs larger than L2 (Cholesky factors %.1f GB)"
                              % (C * w.r * (w.r + 1) / 2 * 8 / 1e9),
                        "parallelism": f"chains sharded over {world} GPU(s)"},
-            "roofline": roofline, "gpu_launches": int(launches),
+            "roofline": roofline, "roofline_tensor": roofline_tensor,
+            "gpu_launches": int(launches),
             "acceptance_rate": stats["accepts"] / max(1, stats["proposals"]),
             "kernel_share": {k: round(v[0] / total, 4) for k, v in kt.items()},
             "fp64_plain": fp64_line, "e2e": e2e,

@@ -178,6 +178,9 @@ struct TcGemmArgs {
   float *der = nullptr;
   const float *scale = nullptr;
   int lds = 0, group = 1;
+  // TC_EPI_COEF with few tiles: split K, FP32 partials in ws (ws_floats)
+  float *ws = nullptr;
+  size_t ws_floats = 0;
   const double *coef = nullptr;  // TC_EPI_COEF
   int ldc = 0;
   double cs = 0.0, sc = 0.0;     // TC_EPI_COEF (cs), TC_EPI_FIELD_T (sc, cs)

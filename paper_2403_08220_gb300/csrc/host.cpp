@@ -1121,6 +1121,10 @@ static void step_pool(dino_ctx *ctx, Pool &p) {
       g.b_plane = s->plE;
       g.nslice = kFieldSlices;
       g.epi = TC_EPI_COEF;
+      // split-K partials (small pools) in the Jacobian's P buffer, free once
+      // the Jacobian is formed
+      g.ws = reinterpret_cast<float *>(p.w.Pb[0]);
+      g.ws_floats = p.w.Pb[0] ? p.w.plp * s->jac_slices / 2 : 0;
       g.coef = p.coef;
       g.ldc = r;
       g.cs = cs;

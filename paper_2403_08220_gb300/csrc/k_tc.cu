@@ -40,6 +40,10 @@ struct TcParams {
   int pair_a[6], pair_b[6];
   int epi, ldo, act, out_slices, lds, group;
   int ldob;  // TC_EPI_STORE_F32 with out_bf: row pitch of the bf16 slice planes
+  // split K: work item = (tile, K chunk of kb_per k-blocks); with ksplit > 1
+  // every item stores its FP32 partial sums to ws + chunk * M * N (pitch N)
+  int ksplit, kb_per;
+  float *ws;
   size_t out_plane;
   float *outf;
   const float *bias;
@@ -274,7 +278,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntn = (p.N + p.BN - 1) / p.BN;
   const int ntiles = ((p.M + kBlockM - 1) / kBlockM) * ntn;
-  const int n_iter = p.npairs * p.nkb;
+  const int nitems = ntiles * p.ksplit;
+  // item t: tile t / ksplit, k-blocks [kb0, kb0 + nk) of chunk t % ksplit
+  auto item_k = [&](int t, int &kb0, int &nk) {
+    kb0 = (t % p.ksplit) * p.kb_per;
+    nk = min(p.kb_per, p.nkb - kb0);
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -306,8 +315,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       int g = 0;  // stage iterations issued, across tiles
       bool ok = true;
-      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const int m0 = (t / ntn) * kBlockM, n0 = (t % ntn) * p.BN;
+      for (int t = blockIdx.x; t < nitems && ok; t += gridDim.x) {
+        const int tile = t / p.ksplit;
+        const int m0 = (tile / ntn) * kBlockM, n0 = (tile % ntn) * p.BN;
+        int kb0, nk;
+        item_k(t, kb0, nk);
+        const int n_iter = p.npairs * nk;
         for (int it = 0; it < n_iter; ++it, ++g) {
           const int s = g % S;
           const uint32_t ph = (uint32_t)(g / S) & 1u;
@@ -317,7 +330,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             ok = false;
             break;
           }
-          const int pr = it / p.nkb, kb = it % p.nkb;
+          const int pr = it / nk, kb = kb0 + it % nk;
           const uint32_t full = smem_u32(&bars[s]);
           mbar_expect_tx(full, stage_bytes);
           const uint32_t sa = base + s * stage_bytes;
@@ -336,7 +349,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t idesc = idesc_bf16(kBlockM, p.BN);
       bool ok = true;
       int g = 0, j = 0;
-      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++j) {
+      for (int t = blockIdx.x; t < nitems && ok; t += gridDim.x, ++j) {
         const int b = j & 1;
         if (!mbar_wait(smem_u32(&bars[2 * S + 2 + b]), (((uint32_t)j >> 1) & 1u) ^ 1u,
                        abort_flag)) {
@@ -347,6 +360,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         fence_after();
         const uint32_t tacc = tmem + (uint32_t)(b * p.BN);
+        int kb0, nk;
+        item_k(t, kb0, nk);
+        const int n_iter = p.npairs * nk;
         for (int it = 0; it < n_iter; ++it, ++g) {
           const int s = g % S;
           const uint32_t ph = (uint32_t)(g / S) & 1u;
@@ -376,9 +392,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31
     const int quarter = warp & 3;
     int j = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+    for (int t = blockIdx.x; t < nitems; t += gridDim.x, ++j) {
       const int b = j & 1;
-      const int m0 = (t / ntn) * kBlockM, n0 = (t % ntn) * p.BN;
+      const int tile = t / p.ksplit;
+      const int m0 = (tile / ntn) * kBlockM, n0 = (tile % ntn) * p.BN;
+      // a K chunk of a split product stores FP32 partial sums (pitch N)
+      const bool split = p.ksplit > 1;
+      const int epi = split ? (int)TC_EPI_STORE_F32 : p.epi;
+      float *outf = split ? p.ws + (size_t)(t % p.ksplit) * p.M * p.N : p.outf;
+      const int ldo = split ? p.N : p.ldo;
+      __nv_bfloat16 *const out_bf = split ? nullptr : p.out_bf;
       const int row = m0 + quarter * 32 + lane;
       // one lane waits, the warp follows its verdict (tcgen05.ld is warp-collective)
       int okl = 0;
@@ -397,7 +420,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int row0 = m0 + quarter * 32, nrows = min(32, p.M - row0);
       uint4 *stg = stg_all + quarter * 256;
       int c0 = 0;  // columns [0, c0) done by the coalesced groups below
-      if (p.epi == TC_EPI_FIELD_T) {
+      if (epi == TC_EPI_FIELD_T) {
         // lanes are consecutive field nodes of one chain per column: each
         // column's loads and stores are 128 contiguous bytes per warp
         for (; c0 < nvalid; c0 += 16) {
@@ -414,10 +437,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         }
-      } else if (p.epi == TC_EPI_STORE_F32 && p.out_bf) {
+      } else if (epi == TC_EPI_STORE_F32 && out_bf) {
         // FP32 values and their bf16 slices: 64 columns = two 128-byte FP32
         // halves and one 128-byte segment per slice
-        if ((p.ldo & 3) == 0 && (p.ldob & 7) == 0) {
+        if ((ldo & 3) == 0 && (p.ldob & 7) == 0) {
           for (; c0 + 64 <= nvalid; c0 += 64) {
             float v[64];
             tmem_ld64(tacc + (uint32_t)c0, v);
@@ -427,8 +450,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
               for (int j = 0; j < 32; ++j) w[j] = __float_as_uint(v[32 * h + j]);
               store_rows_coalesced(
-                  stg, w, reinterpret_cast<char *>(p.outf + (size_t)row0 * p.ldo + n0 + c0 + 32 * h),
-                  (size_t)p.ldo * 4, nrows, lane);
+                  stg, w, reinterpret_cast<char *>(outf + (size_t)row0 * ldo + n0 + c0 + 32 * h),
+                  (size_t)ldo * 4, nrows, lane);
             }
             for (int sl = 0; sl < p.out_slices; ++sl) {
               uint32_t w[32];
@@ -436,13 +459,14 @@ __global__ void __launch_bounds__(kThreads, 1)
               for (int j = 0; j < 32; ++j) w[j] = pack_bf16x2(v[2 * j], v[2 * j + 1]);
               store_rows_coalesced(
                   stg, w,
-                  reinterpret_cast<char *>(p.out_bf + (size_t)row0 * p.ldob + n0 + c0 +
+                  reinterpret_cast<char *>(out_bf + (size_t)row0 * p.ldob + n0 + c0 +
                                            (size_t)sl * p.out_plane),
                   (size_t)p.ldob * 2, nrows, lane);
             }
           }
         }
-      } else if ((p.epi == TC_EPI_STORE_F32 || p.epi == TC_EPI_BIAS_F32) && (p.ldo & 3) == 0) {
+      } else if ((epi == TC_EPI_STORE_F32 || epi == TC_EPI_BIAS_F32) && (ldo & 3) == 0 &&
+                 (reinterpret_cast<uintptr_t>(outf) & 15) == 0) {
         // 32 FP32 columns = 128 bytes per row
         for (; c0 + 32 <= nvalid; c0 += 32) {
           float v[32];
@@ -450,25 +474,25 @@ __global__ void __launch_bounds__(kThreads, 1)
           uint32_t w[32];
 #pragma unroll
           for (int j = 0; j < 32; ++j)
-            w[j] = __float_as_uint(p.epi == TC_EPI_BIAS_F32 ? v[j] + p.bias[n0 + c0 + j] : v[j]);
-          store_rows_coalesced(stg, w, reinterpret_cast<char *>(p.outf + (size_t)row0 * p.ldo + n0 + c0),
-                               (size_t)p.ldo * 4, nrows, lane);
+            w[j] = __float_as_uint(epi == TC_EPI_BIAS_F32 ? v[j] + p.bias[n0 + c0 + j] : v[j]);
+          store_rows_coalesced(stg, w, reinterpret_cast<char *>(outf + (size_t)row0 * ldo + n0 + c0),
+                               (size_t)ldo * 4, nrows, lane);
         }
-      } else if ((p.epi == TC_EPI_SCALE_GROUP && (p.lds & 3) == 0) ||
-                 (p.epi == TC_EPI_BIAS_ACT && (p.N & 3) == 0) || p.epi == TC_EPI_COEF) {
+      } else if ((epi == TC_EPI_SCALE_GROUP && (p.lds & 3) == 0) ||
+                 (epi == TC_EPI_BIAS_ACT && (p.N & 3) == 0) || epi == TC_EPI_COEF) {
         // 64 columns = 128 bytes per row and bf16 slice (the derivative: two
         // 128-byte FP32 halves)
-        if ((p.ldo & 7) == 0) {
+        if ((ldo & 7) == 0) {
           for (; c0 + 64 <= nvalid; c0 += 64) {
             float v[64];
             tmem_ld64(tacc + (uint32_t)c0, v);
-            if (p.epi == TC_EPI_COEF) {
+            if (epi == TC_EPI_COEF) {
               if (row < p.M) {
                 const double *cf = p.coef + (size_t)row * p.ldc + n0 + c0;
 #pragma unroll
                 for (int j = 0; j < 64; ++j) v[j] = (float)(cf[j] - p.cs * (double)v[j]);
               }
-            } else if (p.epi == TC_EPI_SCALE_GROUP) {
+            } else if (epi == TC_EPI_SCALE_GROUP) {
               if (row < p.M) {
                 const float4 *sc = reinterpret_cast<const float4 *>(
                     p.scale + (size_t)(row / p.group) * p.lds + n0 + c0);
@@ -502,9 +526,9 @@ __global__ void __launch_bounds__(kThreads, 1)
               for (int j = 0; j < 32; ++j) w[j] = pack_bf16x2(v[2 * j], v[2 * j + 1]);
               store_rows_coalesced(
                   stg, w,
-                  reinterpret_cast<char *>(p.out_bf + (size_t)row0 * p.ldo + n0 + c0 +
+                  reinterpret_cast<char *>(out_bf + (size_t)row0 * ldo + n0 + c0 +
                                            (size_t)sl * p.out_plane),
-                  (size_t)p.ldo * 2, nrows, lane);
+                  (size_t)ldo * 2, nrows, lane);
             }
           }
         }
@@ -515,11 +539,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (row >= p.M) continue;
         const int ncols = min(16, nvalid - c0);
         const int col0 = n0 + c0;
-        if (p.epi == TC_EPI_STORE_F32 || p.epi == TC_EPI_BIAS_F32) {
-          if (p.epi == TC_EPI_BIAS_F32)
+        if (epi == TC_EPI_STORE_F32 || epi == TC_EPI_BIAS_F32) {
+          if (epi == TC_EPI_BIAS_F32)
             for (int j = 0; j < ncols; ++j) v[j] += p.bias[col0 + j];
-          float *o = p.outf + (size_t)row * p.ldo + col0;
-          if (ncols == 16 && (p.ldo & 3) == 0) {
+          float *o = outf + (size_t)row * ldo + col0;
+          if (ncols == 16 && (ldo & 3) == 0) {
 #pragma unroll
             for (int q = 0; q < 4; ++q)
               reinterpret_cast<float4 *>(o)[q] =
@@ -527,13 +551,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           } else {
             for (int j = 0; j < ncols; ++j) o[j] = v[j];
           }
-          if (p.epi == TC_EPI_STORE_F32 && p.out_bf)
+          if (epi == TC_EPI_STORE_F32 && out_bf)
             for (int j = 0; j < ncols; ++j)
-              store_slices(v[j], p.out_bf + (size_t)row * p.ldob + col0 + j, p.out_plane,
+              store_slices(v[j], out_bf + (size_t)row * p.ldob + col0 + j, p.out_plane,
                            p.out_slices);
         } else {
           float x[16];
-          if (p.epi == TC_EPI_BIAS_ACT) {
+          if (epi == TC_EPI_BIAS_ACT) {
             float *d = p.der + (size_t)row * p.N + col0;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
@@ -549,7 +573,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             } else {
               for (int j = 0; j < ncols; ++j) d[j] = v[j];
             }
-          } else if (p.epi == TC_EPI_COEF) {
+          } else if (epi == TC_EPI_COEF) {
             const double *cf = p.coef + (size_t)row * p.ldc + col0;
 #pragma unroll
             for (int j = 0; j < 16; ++j)
@@ -570,8 +594,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
           // x ~= sum of bf16 slices; 16-byte stores of 8 values per slice
-          __nv_bfloat16 *o = p.out_bf + (size_t)row * p.ldo + col0;
-          const bool vec = ncols == 16 && (p.ldo & 7) == 0;
+          __nv_bfloat16 *o = out_bf + (size_t)row * ldo + col0;
+          const bool vec = ncols == 16 && (ldo & 7) == 0;
           for (int sl = 0; sl < p.out_slices; ++sl) {
             __nv_bfloat16 h[16];
 #pragma unroll
@@ -790,6 +814,22 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// Split-K finish of TC_EPI_COEF: out slices = coef - cs * (sum of the K
+// chunks' FP32 partials), in chunk order.
+__global__ void k_coef_finish(uint32_t total, int N, int ksplit, const float *__restrict__ ws,
+                              const double *__restrict__ coef, int ldc, double cs,
+                              __nv_bfloat16 *__restrict__ out, int ldo, size_t plane,
+                              int nslice) {
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += gridDim.x * blockDim.x) {
+    const uint32_t row = e / (uint32_t)N, col = e - row * (uint32_t)N;
+    float acc = 0.0f;
+    for (int k = 0; k < ksplit; ++k) acc += ws[(size_t)k * total + e];
+    const float x = (float)(coef[(size_t)row * ldc + col] - cs * (double)acc);
+    store_slices(x, out + (size_t)row * ldo + col, plane, nslice);
+  }
+}
+
 __global__ void k_split_bf16(int rows, int cols, const double *__restrict__ src, int lds,
                              __nv_bfloat16 *__restrict__ dst, int ldd, size_t plane, int nslice) {
   const size_t total = (size_t)rows * cols;
@@ -960,7 +1000,28 @@ cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st) {
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
     return cudaErrorInvalidValue;
   const int total = ((a.M + kBlockM - 1) / kBlockM) * ntiles;
-  k_tc_gemm<<<std::min(total, sms), kThreads, smem, st>>>(tmA, tmB, p);
+  // split K when the tiles fill fewer than two CTAs per SM (the projections
+  // of small pools: M = chains, K = field nodes)
+  p.ksplit = 1;
+  p.kb_per = p.nkb;
+  p.ws = nullptr;
+  if (a.epi == TC_EPI_COEF && a.ws && total < 2 * sms &&
+      (size_t)a.M * a.N < 0xffffffffull - 152ull * 32 * 256) {
+    int ks = std::min({(2 * sms + total - 1) / total, 16, p.nkb});
+    while (ks > 1 && (size_t)ks * a.M * a.N > a.ws_floats) --ks;
+    if (ks > 1) {
+      p.kb_per = (p.nkb + ks - 1) / ks;
+      p.ksplit = (p.nkb + p.kb_per - 1) / p.kb_per;
+      p.ws = a.ws;
+    }
+  }
+  k_tc_gemm<<<std::min(total * p.ksplit, sms), kThreads, smem, st>>>(tmA, tmB, p);
+  cudaError_t e2 = cudaGetLastError();
+  if (e2 != cudaSuccess || p.ksplit == 1) return e2;
+  const size_t n = (size_t)a.M * a.N;
+  const int grid = (int)std::min<size_t>((n + 255) / 256, 152 * 32);
+  k_coef_finish<<<grid, 256, 0, st>>>((uint32_t)n, a.N, p.ksplit, p.ws, a.coef, a.ldc, a.cs,
+                                      a.out_bf, a.ldo, a.out_plane, a.out_slices);
   return cudaGetLastError();
 }
 
