@@ -492,28 +492,36 @@ __global__ void __launch_bounds__(kWbThreads, kWbMinBlocks) k_wb_propose(Reduced
   const uint32_t chain = (uint32_t)(a.id_base + (uint64_t)c);
   for (int k = threadIdx.x; k < r; k += blockDim.x) xa[k] = a.mr[(size_t)c * r + k];
   // Box-Muller in FP32 on the tensor-core path (its precision bars are far
-  // above FP32's), in FP64 on the FP64 path (FP64 parity with the oracle)
-  auto normals4 = [&](uint4 w, double n4[4]) {
+  // above FP32's; an FP32 normal is an exact double-float pair (x, 0), so no
+  // FP64 conversion is needed), in FP64 on the FP64 path (FP64 parity with
+  // the oracle)
+  auto normals4 = [&](uint4 w, double n4[4], E e4[4]) {
     if constexpr (sizeof(TJ) == 4) {
       float f4[4];
       normals4_f32(w, f4);
-      for (int q = 0; q < 4; ++q) n4[q] = f4[q];
+      for (int q = 0; q < 4; ++q) {
+        n4[q] = f4[q];
+        e4[q] = A::from_j(f4[q]);
+      }
     } else {
       normals4_f64(w, n4);
+      for (int q = 0; q < 4; ++q) e4[q] = A::from(n4[q]);
     }
   };
   for (int blk = threadIdx.x; blk < (r + 3) / 4; blk += blockDim.x) {
     double n4[4];
-    normals4(philox_block(a.seed, STREAM_XI, a.step, chain, blk), n4);
+    E e4[4];
+    normals4(philox_block(a.seed, STREAM_XI, a.step, chain, blk), n4, e4);
     for (int q = 0; q < 4; ++q)
       if (4 * blk + q < r) {
         xi1[4 * blk + q] = n4[q];
-        x1E[4 * blk + q] = A::from(n4[q]);
+        x1E[4 * blk + q] = e4[q];
       }
   }
   for (int blk = threadIdx.x; blk < (dy + 3) / 4; blk += blockDim.x) {
     double n4[4];
-    normals4(philox_block(a.seed, STREAM_XI2, a.step, chain, blk), n4);
+    E e4[4];
+    normals4(philox_block(a.seed, STREAM_XI2, a.step, chain, blk), n4, e4);
     for (int q = 0; q < 4; ++q)
       if (4 * blk + q < dy) xi2[4 * blk + q] = n4[q];
   }
@@ -557,8 +565,9 @@ __global__ void __launch_bounds__(kWbThreads, kWbMinBlocks) k_wb_propose(Reduced
     if (a.b_bf16) split_bf16_store(bk, a.b_bf16 + (size_t)c * a.b_ld + k, a.b_plane, a.b_slices);
   }
   double t2 = 0.0, t3 = 0.0, unused = 0.0;
+  const double inv_cs = 1.0 / cs;
   for (int i = threadIdx.x; i < dy; i += blockDim.x) {
-    const double km = Kxi[i] + (yv[i] - A::to(zE[i])) / cs;  // K mhat
+    const double km = Kxi[i] + (yv[i] - A::to(zE[i])) * inv_cs;  // K mhat
     t2 += km * u[i];
     t3 += km * km;
   }
