@@ -64,6 +64,12 @@ struct ReducedArgs {
   // d_y x ldg), or nullptr to form them in the geometry kernel
   const float *G = nullptr;
   int ldg = 0;
+  // Woodbury path with the tensor-core Gram: the proposal b and the state m_r
+  // as double-float pairs (C x r), from which a warp-per-row kernel forms K b
+  // and K a (C x d_y, already / sigma) into Kb_pre, Ka_pre right after the
+  // Jacobian; nullptr to form them in the geometry kernel
+  float2 *b_df = nullptr, *a_df = nullptr;
+  const double *Kb_pre = nullptr, *Ka_pre = nullptr;
   int jf_f32 = 0;
   const double *y = nullptr;
   // accept outputs
@@ -80,6 +86,15 @@ struct ReducedArgs {
   size_t b_plane = 0;
 };
 
+// Woodbury path on the tensor path: Kb[row] = (sum_k J[row, k] b[c, k]) *
+// kscale and Ka likewise with a (a may be nullptr), c = row / d_y, over the
+// C d_y rows of the FP32 J (row pitch r); b, a as double-float pairs (C x r).
+cudaError_t launch_rowprod(int rows, int r, int d_y, const float *J, const float2 *b,
+                           const float2 *a, double kscale, double *Kb, double *Ka,
+                           cudaStream_t st);
+// dst1[i] = dst2[i] = src[i] as a double-float pair (either dst may be nullptr)
+cudaError_t launch_to_df(size_t n, const double *src, float2 *dst1, float2 *dst2,
+                         cudaStream_t st);
 bool uses_global_factor(int r, int d_y);
 size_t propose_smem_bytes(int r);
 size_t geometry_smem_bytes(int r, int d_y, int jf_f32);

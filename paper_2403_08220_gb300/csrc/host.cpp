@@ -636,6 +636,10 @@ struct Work {
   int ldjb = 0, ldg = 0;
   size_t pljb = 0;
   float *G = nullptr;
+  // ... and K b, K a formed right after the Jacobian (warp per row): b and
+  // the state m_r as double-float pairs (C x r) in, Kb, Ka (C x d_y) out
+  float2 *b_df = nullptr, *a_df = nullptr;
+  double *Kb = nullptr, *Ka = nullptr;
 };
 
 // Lays out (or, with base != nullptr, assigns) the workspace in an arena.
@@ -689,14 +693,20 @@ static void layout_work(const Surrogate *s, int C, Arena &ar, Work &w, bool assi
       w.Jb = (__nv_bfloat16 *)take(w.pljb * kGramSlices * 2);
       w.ldg = (dy + 3) & ~3;
       w.G = (float *)take(rows * w.ldg * 4);
+      w.b_df = (float2 *)take((size_t)C * s->r * 8);
+      w.a_df = (float2 *)take((size_t)C * s->r * 8);
+      w.Kb = (double *)take(rows * 8);
+      w.Ka = (double *)take(rows * 8);
     }
   }
 }
 
 // Forward pass and Jacobian at the C points in `x` (FP64 C x r; the tensor
 // path reads the bf16 planes in w.xb, which the caller has filled).
+// with_a: the pool's state pairs w.a_df are valid (a step, not the initial
+// geometry), so K a is formed beside K b.
 static void eval_surrogate(dino_ctx *ctx, const Surrogate *s, Work &w, const double *x,
-                           cudaStream_t st) {
+                           cudaStream_t st, bool with_a = false) {
   const int C = w.C, L = s->L, dy = s->d_y, r = s->r;
   if (s->precision == DINO_PREC_FP64) {
     const double *a = x;
@@ -837,6 +847,11 @@ static void eval_surrogate(dino_ctx *ctx, const Surrogate *s, Work &w, const dou
     g.out_slices = kGramSlices;
   }
   launch(ctx, st, "jac_tc", [&] { return launch_tc_gemm(g, st); });
+  if (w.Kb)  // K b = J b / sigma (K a likewise) in double-float
+    launch(ctx, st, "rowprod", [&] {
+      return launch_rowprod(C * dy, r, dy, w.J32, w.b_df, with_a ? w.a_df : nullptr,
+                            std::sqrt(1.0 / s->noise_var), w.Kb, with_a ? w.Ka : nullptr, st);
+    });
   if (w.G)
     launch(ctx, st, "gram_tc", [&] {
       return launch_tc_gram(C, dy, r, w.Jb, w.ldjb, w.pljb, kGramSlices, w.G, w.ldg, st);
@@ -943,6 +958,10 @@ static ReducedArgs reduced_args(const Pool &p) {
   a.Js = p.Js;
   a.G = p.w.G;
   a.ldg = p.w.ldg;
+  a.b_df = p.w.b_df;
+  a.a_df = p.w.a_df;
+  a.Kb_pre = p.w.Kb;
+  a.Ka_pre = p.w.Ka;
   a.b = p.b;
   a.mu = p.mu;
   a.lq_fwd = p.lq_fwd;
@@ -1038,6 +1057,10 @@ static Pool *create_pool_on(dino_ctx *ctx, int sid, int C, double dt, uint64_t s
       });
     }
     split_input(ctx, s, p->w, p->b, st);
+    if (p->w.b_df)  // b = m_r as double-float pairs, for K b in the Jacobian GEMM
+      launch(ctx, st, "to_df", [&] {
+        return launch_to_df((size_t)C * r, p->b, p->w.b_df, p->w.a_df, st);
+      });
     eval_surrogate(ctx, s, p->w, p->b, st);
     ReducedArgs ra = reduced_args(*p);
     launch(ctx, st, "geometry_init", [&] {
@@ -1081,7 +1104,7 @@ static void step_pool(dino_ctx *ctx, Pool &p) {
   launch(ctx, st, "propose", [&] {
     return p.wb ? launch_wb_propose(ra, st) : launch_propose(ra, st);
   });
-  eval_surrogate(ctx, s, p.w, p.b, st);
+  eval_surrogate(ctx, s, p.w, p.b, st, true);
   launch(ctx, st, "geometry", [&] {
     return p.wb ? launch_wb_geometry(ra, 1, st) : launch_geometry(ra, 1, st);
   });

@@ -365,7 +365,12 @@ __global__ void __launch_bounds__(kWbThreads, kWbMinBlocks) k_wb_geometry(Reduce
     float *stage = wb_stage_fits(dy) ? reinterpret_cast<float *>(sm + lay.Ms)
                                      : reinterpret_cast<float *>(sm + lay.tail);
     if (a.G) {  // Gram matrix formed on the tensor cores: K b, K a only, then M from G
-      if (wb_ring4_fits(dy))
+      if (a.Kb_pre) {  // ... and K b, K a too (the Jacobian GEMM's epilogue)
+        for (int i = threadIdx.x; i < dy; i += blockDim.x) {
+          Kb[i] = a.Kb_pre[(size_t)c * dy + i];
+          if (mode == 1) Ka[i] = a.Ka_pre[(size_t)c * dy + i];
+        }
+      } else if (wb_ring4_fits(dy))
         wb_gram_rows<A, false, 4>(reinterpret_cast<const float *>(J), dy, r, inv_nv, inv_sigma,
                                   reinterpret_cast<float2 *>(Ms), stage,
                                   reinterpret_cast<const float2 *>(be),
@@ -426,7 +431,11 @@ __global__ void __launch_bounds__(kWbThreads, kWbMinBlocks) k_wb_geometry(Reduce
   auto take_state = [&]() {
     TJ *Js = reinterpret_cast<TJ *>(a.Js) + (size_t)c * dy * r;
     for (size_t e = threadIdx.x; e < (size_t)dy * r; e += blockDim.x) Js[e] = J[e];
-    for (int k = threadIdx.x; k < r; k += blockDim.x) a.mr[(size_t)c * r + k] = vb[k];
+    for (int k = threadIdx.x; k < r; k += blockDim.x) {
+      a.mr[(size_t)c * r + k] = vb[k];
+      if constexpr (sizeof(TJ) == 4)
+        if (a.a_df) a.a_df[(size_t)c * r + k] = a.b_df[(size_t)c * r + k];
+    }
   };
 
   if (mode == 0) {
@@ -562,6 +571,8 @@ __global__ void __launch_bounds__(kWbThreads, kWbMinBlocks) k_wb_propose(Reduced
     const double mk = s * xa[k] + A::to(A::end(av)) * inv_sigma;
     a.mu[(size_t)c * r + k] = mk;
     a.b[(size_t)c * r + k] = bk;
+    if constexpr (sizeof(TJ) == 4)
+      if (a.b_df) a.b_df[(size_t)c * r + k] = A::from(bk);
     if (a.b_bf16) split_bf16_store(bk, a.b_bf16 + (size_t)c * a.b_ld + k, a.b_plane, a.b_slices);
   }
   double t2 = 0.0, t3 = 0.0, unused = 0.0;
@@ -574,6 +585,55 @@ __global__ void __launch_bounds__(kWbThreads, kWbMinBlocks) k_wb_propose(Reduced
   block_sum3(t2, t3, unused, red);
   if (threadIdx.x == 0)
     a.lq_fwd[c] = -a.dt / 8.0 * Lg[sl.t1] + sqrt(a.dt) / 2.0 * t2 + a.hld[c] - 0.5 * t3;
+}
+
+// K b and K a from the FP32 Jacobian: eight lanes per row (c, i), four rows
+// per warp; lane q of a row takes columns q, q + 8, ... (each load
+// instruction covers four rows' whole 32-byte sectors), and the eight
+// double-float partial sums are combined by a three-level butterfly of
+// double-float additions.
+constexpr int kRowLanes = 8;
+
+__global__ void k_rowprod(int rows, int r, int dy, const float *__restrict__ J,
+                          const float2 *__restrict__ b, const float2 *__restrict__ a,
+                          double kscale, double *__restrict__ Kb, double *__restrict__ Ka) {
+  const int q = threadIdx.x & (kRowLanes - 1);
+  const int groups = (gridDim.x * blockDim.x) / kRowLanes;
+  // every lane runs the same number of iterations (rows past the end compute
+  // row rows - 1 and store nothing), so the butterfly's shuffles see full warps
+  const int iters = (rows + groups - 1) / groups;
+  int row = (blockIdx.x * blockDim.x + threadIdx.x) / kRowLanes;
+  for (int it = 0; it < iters; ++it, row += groups) {
+    const int rr = min(row, rows - 1), c = rr / dy;
+    const float *Jr = J + (size_t)rr * r;
+    const float2 *br = b + (size_t)c * r;
+    const float2 *ar = a ? a + (size_t)c * r : nullptr;
+    DF::Acc kb = DF::begin(float2{}), ka = DF::begin(float2{});
+    for (int k = q; k < r; k += kRowLanes) {
+      const float2 jk = DF::from_j(Jr[k]);
+      DF::sub(kb, jk, DF::neg(br[k]));
+      if (ar) DF::sub(ka, jk, DF::neg(ar[k]));
+    }
+    float2 vb = DF::end(kb), va = DF::end(ka);
+#pragma unroll
+    for (int o = kRowLanes / 2; o; o >>= 1) {
+      vb = DF::add(vb, shfl_xor_elt(vb, o));
+      if (ar) va = DF::add(va, shfl_xor_elt(va, o));
+    }
+    if (q == 0 && row < rows) {
+      Kb[row] = DF::to(vb) * kscale;
+      if (ar) Ka[row] = DF::to(va) * kscale;
+    }
+  }
+}
+
+__global__ void k_to_df(size_t n, const double *__restrict__ src, float2 *dst1, float2 *dst2) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const float2 x = DF::from(src[e]);
+    if (dst1) dst1[e] = x;
+    if (dst2) dst2[e] = x;
+  }
 }
 
 template <typename TJ>
@@ -614,6 +674,24 @@ cudaError_t launch_wb_geometry(const ReducedArgs &a, int mode, cudaStream_t st) 
 
 cudaError_t launch_wb_propose(const ReducedArgs &a, cudaStream_t st) {
   return a.jf_f32 ? launch_wb_propose_t<float>(a, st) : launch_wb_propose_t<double>(a, st);
+}
+
+cudaError_t launch_rowprod(int rows, int r, int d_y, const float *J, const float2 *b,
+                           const float2 *a, double kscale, double *Kb, double *Ka,
+                           cudaStream_t st) {
+  if (rows <= 0) return cudaSuccess;
+  if (d_y < 1 || r < 1) return cudaErrorInvalidValue;
+  const int grid = std::min((rows + 31) / 32, 152 * 16);  // 32 rows per 256-thread block
+  k_rowprod<<<grid, 256, 0, st>>>(rows, r, d_y, J, b, a, kscale, Kb, Ka);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_df(size_t n, const double *src, float2 *dst1, float2 *dst2,
+                         cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const int grid = (int)std::min<size_t>((n + 255) / 256, 152 * 8);
+  k_to_df<<<grid, 256, 0, st>>>(n, src, dst1, dst2);
+  return cudaGetLastError();
 }
 
 }  // namespace dino
