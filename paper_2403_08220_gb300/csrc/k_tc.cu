@@ -44,6 +44,8 @@ struct TcParams {
   // every item stores its FP32 partial sums to ws + chunk * M * N (pitch N)
   int ksplit, kb_per;
   float *ws;
+  int grouped;  // one stage per k-block carrying every slice (see the kernel)
+  int nslice;
   size_t out_plane;
   float *outf;
   const float *bias;
@@ -266,7 +268,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t base = (raw + 1023u) & ~1023u;
   unsigned char *gbase = smraw + (base - raw);
   const uint32_t a_bytes = kBlockM * kBlockK * 2, b_bytes = (uint32_t)p.BN * kBlockK * 2;
-  const uint32_t stage_bytes = a_bytes + b_bytes;
+  // grouped: a stage holds every slice of A and B of one k-block (A_0 .. A_{s-1},
+  // B_0 .. B_{s-1}) and feeds all slice pairs; otherwise one pair per stage
+  const uint32_t stage_bytes = p.grouped ? (a_bytes + b_bytes) * (uint32_t)p.nslice
+                                         : a_bytes + b_bytes;
   // after the ring: four 4 KB epilogue staging tiles, then the barriers
   uint4 *stg_all = reinterpret_cast<uint4 *>(gbase + p.stages * stage_bytes);
   uint64_t *bars = reinterpret_cast<uint64_t *>(gbase + p.stages * stage_bytes + kStageTiles);
@@ -320,7 +325,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int m0 = (tile / ntn) * kBlockM, n0 = (tile % ntn) * p.BN;
         int kb0, nk;
         item_k(t, kb0, nk);
-        const int n_iter = p.npairs * nk;
+        const int n_iter = p.grouped ? nk : p.npairs * nk;
         for (int it = 0; it < n_iter; ++it, ++g) {
           const int s = g % S;
           const uint32_t ph = (uint32_t)(g / S) & 1u;
@@ -330,12 +335,21 @@ __global__ void __launch_bounds__(kThreads, 1)
             ok = false;
             break;
           }
-          const int pr = it / nk, kb = kb0 + it % nk;
           const uint32_t full = smem_u32(&bars[s]);
           mbar_expect_tx(full, stage_bytes);
           const uint32_t sa = base + s * stage_bytes;
-          tma_load_3d(sa, &tmA, kb * kBlockK, m0, p.pair_a[pr], full);
-          tma_load_3d(sa + a_bytes, &tmB, kb * kBlockK, n0, p.pair_b[pr], full);
+          if (p.grouped) {
+            const int kb = kb0 + it;
+            for (int sl = 0; sl < p.nslice; ++sl)
+              tma_load_3d(sa + sl * a_bytes, &tmA, kb * kBlockK, m0, sl, full);
+            for (int sl = 0; sl < p.nslice; ++sl)
+              tma_load_3d(sa + p.nslice * a_bytes + sl * b_bytes, &tmB, kb * kBlockK, n0, sl,
+                          full);
+          } else {
+            const int pr = it / nk, kb = kb0 + it % nk;
+            tma_load_3d(sa, &tmA, kb * kBlockK, m0, p.pair_a[pr], full);
+            tma_load_3d(sa + a_bytes, &tmB, kb * kBlockK, n0, p.pair_b[pr], full);
+          }
         }
       }
       if (*abort_flag) {
@@ -362,7 +376,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t tacc = tmem + (uint32_t)(b * p.BN);
         int kb0, nk;
         item_k(t, kb0, nk);
-        const int n_iter = p.npairs * nk;
+        const int n_iter = p.grouped ? nk : p.npairs * nk;
         for (int it = 0; it < n_iter; ++it, ++g) {
           const int s = g % S;
           const uint32_t ph = (uint32_t)(g / S) & 1u;
@@ -375,10 +389,22 @@ __global__ void __launch_bounds__(kThreads, 1)
           *consumed = g + 1;
           fence_after();
           const uint32_t sa = base + s * stage_bytes;
-          const uint64_t ad = smem_desc_sw128(sa), bd = smem_desc_sw128(sa + a_bytes);
+          if (p.grouped) {
+            for (int pr = 0; pr < p.npairs; ++pr) {
+              const uint64_t ad = smem_desc_sw128(sa + p.pair_a[pr] * a_bytes);
+              const uint64_t bd =
+                  smem_desc_sw128(sa + p.nslice * a_bytes + p.pair_b[pr] * b_bytes);
 #pragma unroll
-          for (int k = 0; k < kBlockK / 16; ++k)
-            mma_bf16(tacc, ad + 2 * k, bd + 2 * k, idesc, (it > 0 || k > 0) ? 1u : 0u);
+              for (int k = 0; k < kBlockK / 16; ++k)
+                mma_bf16(tacc, ad + 2 * k, bd + 2 * k, idesc,
+                         (it > 0 || pr > 0 || k > 0) ? 1u : 0u);
+            }
+          } else {
+            const uint64_t ad = smem_desc_sw128(sa), bd = smem_desc_sw128(sa + a_bytes);
+#pragma unroll
+            for (int k = 0; k < kBlockK / 16; ++k)
+              mma_bf16(tacc, ad + 2 * k, bd + 2 * k, idesc, (it > 0 || k > 0) ? 1u : 0u);
+          }
           mma_commit(smem_u32(&bars[S + s]));
         }
         if (ok) mma_commit(smem_u32(&bars[2 * S + b]));
@@ -957,7 +983,13 @@ cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st) {
     p.pair_a[i] = pa[i];
     p.pair_b[i] = pb[i];
   }
-  const int stage_bytes = kBlockM * kBlockK * 2 + p.BN * kBlockK * 2;
+  // group the slices of a k-block into one stage when two such stages fit
+  // (the two-slice Jacobian products: each A and B tile loaded once per
+  // k-block instead of once per slice pair)
+  const int pair_bytes = kBlockM * kBlockK * 2 + p.BN * kBlockK * 2;
+  p.nslice = a.nslice;
+  p.grouped = a.nslice > 1 && 2 * pair_bytes * a.nslice <= 200 * 1024;
+  const int stage_bytes = p.grouped ? pair_bytes * a.nslice : pair_bytes;
   p.stages = (200 * 1024) / stage_bytes;
   if (p.stages > kMaxStages) p.stages = kMaxStages;
   if (p.stages < 2) p.stages = 2;
