@@ -351,8 +351,10 @@ __global__ void __launch_bounds__(kWbThreads, kWbMinBlocks) k_wb_geometry(Reduce
   for (int k = threadIdx.x; k < r; k += blockDim.x) {
     vb[k] = a.b[(size_t)c * r + k];
     va[k] = mode == 1 ? a.mr[(size_t)c * r + k] : 0.0;
-    be[k] = A::from(vb[k]);
-    ae[k] = A::from(va[k]);
+    if (!a.Kb_pre) {  // operands of this kernel's own K b, K a pass
+      be[k] = A::from(vb[k]);
+      ae[k] = A::from(va[k]);
+    }
   }
   double ph = 0.0;
   for (int i = threadIdx.x; i < dy; i += blockDim.x) {
@@ -609,6 +611,7 @@ __global__ void k_rowprod(int rows, int r, int dy, const float *__restrict__ J,
     const float2 *br = b + (size_t)c * r;
     const float2 *ar = a ? a + (size_t)c * r : nullptr;
     DF::Acc kb = DF::begin(float2{}), ka = DF::begin(float2{});
+#pragma unroll 5
     for (int k = q; k < r; k += kRowLanes) {
       const float2 jk = DF::from_j(Jr[k]);
       DF::sub(kb, jk, DF::neg(br[k]));
