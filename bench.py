@@ -66,18 +66,18 @@ def geometry_traffic_per_chain(workload: str):
 def geometry_work(r: int, d_y: int, tc_gram: bool = False) -> dict:
     """Algorithmic work of one geometry launch per chain, by pipe.
 
-    d_y < r (Woodbury path): the FP32 Gram product J J^T, d_y (d_y + 1) r
-    flops, unless it was formed beforehand on the tensor cores (tc_gram: the
-    BF16 path with d_y <= 128), and in double-float arithmetic the bordered
-    Cholesky of the (d_y + 1)-matrix, (d_y + 1)^3 / 3, plus the products K b
-    and K a, 4 r d_y.  Otherwise: the FP32 product J^T J, r (r + 1) d_y, and in
+    d_y < r (Woodbury path): in double-float arithmetic the bordered Cholesky
+    of the (d_y + 1)-matrix, (d_y + 1)^3 / 3, and unless they were formed
+    beforehand (tc_gram: the BF16 path with d_y <= 128, where the tensor cores
+    form J J^T and a row-product kernel K b and K a) the FP32 Gram product
+    J J^T, d_y (d_y + 1) r flops, and the products K b and K a, 4 r d_y.  Otherwise: the FP32 product J^T J, r (r + 1) d_y, and in
     double-float the bordered r-Cholesky with the reverse-density products and
     the gradient (`fp64_flops_geometry`).  A double-float multiply-add takes 12
     FP32 instructions, so the FP32-pipe charge is fp32 + 12 x df flops.
     """
     if d_y < r:
         fp32 = 0 if tc_gram else d_y * (d_y + 1) * r
-        df = (d_y + 1) ** 3 / 3.0 + 4.0 * r * d_y
+        df = (d_y + 1) ** 3 / 3.0 + (0.0 if tc_gram else 4.0 * r * d_y)
     else:
         fp32 = r * (r + 1) * d_y
         df = fp64_flops_geometry(r, d_y)
