@@ -1,4 +1,5 @@
-// Tensor-core GEMMs of the reduced MLP and its Jacobian on sm_103a (tcgen05).
+// Tensor-core GEMMs on sm_103a (tcgen05): the reduced MLP and its Jacobian,
+// the complement projections, and the per-chain Gram matrices (k_tc_gram).
 //
 //   D[M x N] = sum_{(i,j): i + j < nslice} A_i B_j^T,   FP32 accumulation in TMEM,
 //
@@ -8,14 +9,20 @@
 //
 // A persistent CTA (one per SM) computes 128 x BN output tiles in turn (cta_group::1, M = 128):
 //   warp 0     TMA producer: 3D tiled loads (k, row, slice) of 128 x 64 A and
-//              BN x 64 B boxes, 128-byte swizzle, into a ring of stages;
+//              BN x 64 B boxes, 128-byte swizzle, into a ring of stages (one
+//              stage per slice pair, or per k-block with every slice of A
+//              and B when two such stages fit);
 //   warp 1     allocates TMEM (two accumulator buffers) and issues tcgen05.mma
 //              (K = 16 per instruction, four per 64-wide stage) into the buffer of
 //              the current tile; tcgen05.commit frees each stage and, per tile,
 //              hands the buffer to the epilogue;
 //   warps 2-5  epilogue: tcgen05.ld of their 32 TMEM lanes, fused bias /
 //              activation / derivative / per-chain scaling, bf16 re-slicing,
+//              the complement's coefficient and field updates, stores of
+//              whole 128-byte row segments through swizzled staging tiles,
 //              overlapping the next tile's MMAs; then release the buffer.
+// Work items are output tiles, or (tile, K chunk) pairs when a projection of
+// a small pool splits K (FP32 partials, reduced by k_coef_finish).
 // Every mbarrier wait is bounded; on timeout the CTA raises a device error
 // flag, lets its copies and MMAs drain (bounded), frees TMEM and returns.
 #include <cuda.h>

@@ -24,7 +24,11 @@
 //   k_wb_geometry  at m_r^dag: misfit, K m_r^dag and K m_r, M and its bordered
 //                  factor, log rho_{0,r}(m_r^dag, m_r), log rho_r^(1)
 //                  (eq:da_dino_trr_1), the accept test and the state update
-//                  (mode 1); mode 0 makes m_r^dag the state.
+//                  (mode 1); mode 0 makes m_r^dag the state;
+//   k_rowprod      K m_r^dag and K m_r for k_wb_geometry, when the Gram
+//                  matrices K K^T come from the tensor cores (k_tc_gram):
+//                  the geometry kernel then reads both instead of its own
+//                  pass over J.
 // The tensor-core path (FP32 J) computes in double-float arithmetic on the
 // FP32 pipe, the FP64 path in FP64.
 #include "chol.cuh"
