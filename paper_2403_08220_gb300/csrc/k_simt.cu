@@ -321,7 +321,8 @@ __global__ void __launch_bounds__(kPriorThreads)
               for (int sl = 0; sl < ms_slices; ++sl) {
                 const __nv_bfloat16 hb = __float2bfloat16_rn(rem);
                 d[sl * ms_plane] = hb;
-                rem -= __bfloat162float(hb);
+                // exact widening: the bf16 bits in the upper half of an FP32 word
+                rem -= __uint_as_float((uint32_t)__bfloat16_as_ushort(hb) << 16);
               }
             }
           }

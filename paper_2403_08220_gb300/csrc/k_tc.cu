@@ -228,11 +228,15 @@ __device__ __forceinline__ void store_rows_coalesced(uint4 *stg, const uint32_t 
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float &a, float &b) {
-  // bf16 of a and b (low half a), leaving the remainders a - bf16(a), b - bf16(b)
-  const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
-  a -= __bfloat162float(ha);
-  b -= __bfloat162float(hb);
-  return (uint32_t)__bfloat16_as_ushort(ha) | ((uint32_t)__bfloat16_as_ushort(hb) << 16);
+  // bf16 of a and b (low half a), leaving the remainders a - bf16(a), b - bf16(b):
+  // one paired round-to-nearest conversion; a bf16 widens to FP32 exactly by
+  // moving its bits to the upper half of the word
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  const uint32_t u =
+      (uint32_t)__bfloat16_as_ushort(h.x) | ((uint32_t)__bfloat16_as_ushort(h.y) << 16);
+  a -= __uint_as_float(u << 16);
+  b -= __uint_as_float(u & 0xffff0000u);
+  return u;
 }
 
 __device__ __forceinline__ float act_fn(int kind, float z) {
@@ -630,18 +634,16 @@ __global__ void __launch_bounds__(kThreads, 1)
           __nv_bfloat16 *o = out_bf + (size_t)row * ldo + col0;
           const bool vec = ncols == 16 && (ldo & 7) == 0;
           for (int sl = 0; sl < p.out_slices; ++sl) {
-            __nv_bfloat16 h[16];
+            uint32_t h[8];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              h[j] = __float2bfloat16_rn(x[j]);
-              x[j] -= __bfloat162float(h[j]);
-            }
+            for (int j = 0; j < 8; ++j) h[j] = pack_bf16x2(x[2 * j], x[2 * j + 1]);
             __nv_bfloat16 *os = o + sl * p.out_plane;
             if (vec) {
-              reinterpret_cast<uint4 *>(os)[0] = *reinterpret_cast<const uint4 *>(h);
-              reinterpret_cast<uint4 *>(os)[1] = *reinterpret_cast<const uint4 *>(h + 8);
+              reinterpret_cast<uint4 *>(os)[0] = make_uint4(h[0], h[1], h[2], h[3]);
+              reinterpret_cast<uint4 *>(os)[1] = make_uint4(h[4], h[5], h[6], h[7]);
             } else {
-              for (int j = 0; j < ncols; ++j) os[j] = h[j];
+              for (int j = 0; j < ncols; ++j)
+                os[j] = __ushort_as_bfloat16((unsigned short)(h[j >> 1] >> (16 * (j & 1))));
             }
           }
         }
