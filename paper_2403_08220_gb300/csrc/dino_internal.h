@@ -122,11 +122,9 @@ cudaError_t gemm_scale_group(int M, int N, int K, const T *A, int lda, const T *
                              const T *scale, int lds, int group, T *out, int ldo,
                              cudaStream_t st);
 // complement coefficient: out[row, col] = coef[row * ldc + col] - c * acc.
-// FP32: split over K into partial sums in ws (ws_floats floats; nullptr: no split).
 template <typename T>
 cudaError_t gemm_coef(int M, int N, int K, const T *A, int lda, const T *B, int ldb,
-                      const double *coef, int ldc, double c, T *out, int ldo, cudaStream_t st,
-                      float *ws = nullptr, size_t ws_floats = 0);
+                      const double *coef, int ldc, double c, T *out, int ldo, cudaStream_t st);
 // field update: if acc_flag[row]: m[row, col] = s m + c Mf[row, col] + acc
 template <typename T>
 cudaError_t gemm_field(int M, int N, int K, const T *A, int lda, const T *B, int ldb,
@@ -157,7 +155,6 @@ cudaError_t launch_f64_to_f32(size_t n, const double *src, float *dst, cudaStrea
 // dst[i] = src[i]; src may be pageable host memory on a device that reads it
 // coherently (cudaDevAttrPageableMemoryAccess)
 cudaError_t launch_copy_f64(size_t n, const double *src, double *dst, cudaStream_t st);
-cudaError_t launch_f32_to_f64(size_t n, const float *src, double *dst, cudaStream_t st);
 
 // ---- tcgen05 BF16 GEMM (sm_103a) -----------------------------------------
 // Operands are bf16 "slice planes": X ~= sum_s X_s, plane s at X + s * plane.

@@ -406,7 +406,7 @@ struct Surrogate {
   // device
   std::vector<std::pair<void *, size_t>> allocs;
   double *dE = nullptr, *dD = nullptr, *dS = nullptr, *dSqrtLam = nullptr, *dy = nullptr;
-  float *fE = nullptr, *fD = nullptr, *fS = nullptr, *fSqrtLam = nullptr;
+  float *fS = nullptr, *fSqrtLam = nullptr;  // prior draw on the tensor path
   // tensor path: bf16 slice planes of E (r x N, pitch ldE) and D (N x r, pitch ldD)
   // for the complement projections
   __nv_bfloat16 *bE = nullptr, *bD = nullptr;
@@ -585,9 +585,7 @@ static int load_surrogate(dino_ctx *ctx, const dino_surrogate_desc *d) {
     }
   }
   if (s->precision == DINO_PREC_BF16) {
-    const auto fE = to_f32(s->E), fD = to_f32(s->D), fS = to_f32(S), fL = to_f32(sqrtlam);
-    s->fE = sur_upload(ctx, s.get(), fE.data(), fE.size());
-    s->fD = sur_upload(ctx, s.get(), fD.data(), fD.size());
+    const auto fS = to_f32(S), fL = to_f32(sqrtlam);
     s->fS = sur_upload(ctx, s.get(), fS.data(), fS.size());
     s->fSqrtLam = sur_upload(ctx, s.get(), fL.data(), fL.size());
     s->ldE = pad8(s->N);
@@ -922,7 +920,8 @@ static void layout_pool(Pool &p, bool assign) {
   p.err = (int *)take(16);
   // FP64 at init even on the FP32 path; also holds a zero data vector in surrogate_eval
   p.Mf = take(std::max((size_t)C * N, (size_t)s->d_y) * std::max(fe, (size_t)8));
-  p.coef2 = take((size_t)C * r * fe);
+  // FP64 path only: the tensor path keeps coef2 as bf16 slices (coef2s)
+  p.coef2 = s->precision == DINO_PREC_FP64 ? take((size_t)C * r * 8) : nullptr;
   if (s->precision != DINO_PREC_FP64) {
     p.Ms = (__nv_bfloat16 *)take((size_t)C * s->ldE * kFieldSlices * 2);
     p.coef2s = (__nv_bfloat16 *)take((size_t)C * s->ldD * kFieldSlices * 2);

@@ -138,94 +138,12 @@ struct EpiField {
   }
 };
 
-// FP32 GEMM in 128 x 128 tiles, 8 x 8 outputs per thread (rows 8 ty.., columns
-// 8 tx..): per step of the reduction a thread reads two float4 of A and two of
-// B from shared memory for 64 FMAs, which balances the shared-memory and FMA
-// rates.  Operands are staged K-major ([k][m], [k][n]) in slices of BK2; the
-// next slice is loaded into registers while the current one is used.
-constexpr int BM2 = 128, BN2 = 128, BK2 = 8;
-
-// With gridDim.z > 1 the CTA at z covers K range [z kchunk, (z + 1) kchunk).
-template <class Epi>
-__global__ void __launch_bounds__(kGemmThreads)
-    k_gemm_f32_big(int M, int N, int K, const float *__restrict__ A, int lda,
-                   const float *__restrict__ B, int ldb, Epi epi, int kchunk) {
-  __shared__ __align__(16) float As[2][BK2][BM2];
-  __shared__ __align__(16) float Bs[2][BK2][BN2];
-  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  const int row0 = blockIdx.y * BM2, col0 = blockIdx.x * BN2;
-  // each thread stages 4 elements of A and 4 of B per slice: (m, k) = (tid / 2, 4 (tid % 2) + q)
-  const int lm = tid / 2, lk = 4 * (tid % 2);
-  float ra[4], rb[4];
-  auto store = [&](int buf) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      As[buf][lk + q][lm] = ra[q];
-      Bs[buf][lk + q][lm] = rb[q];
-    }
-  };
-  float acc[8][8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i)
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
-  const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
-  // loads past kend read zeros (gk < kend); A and B are read only below K
-  auto loadk = [&](int k0) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int gk = k0 + lk + q;
-      const int gr = row0 + lm, gc = col0 + lm;
-      ra[q] = (gr < M && gk < kend) ? A[(size_t)gr * lda + gk] : 0.0f;
-      rb[q] = (gc < N && gk < kend) ? B[(size_t)gc * ldb + gk] : 0.0f;
-    }
-  };
-  loadk(kbeg);
-  store(0);
-  __syncthreads();
-  int buf = 0;
-  for (int k0 = kbeg; k0 < kend; k0 += BK2) {
-    const bool more = k0 + BK2 < kend;
-    if (more) loadk(k0 + BK2);
-#pragma unroll
-    for (int k = 0; k < BK2; ++k) {
-      const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][k][8 * ty]);
-      const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][k][8 * ty + 4]);
-      const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][k][8 * tx]);
-      const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][k][8 * tx + 4]);
-      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-    }
-    if (more) {
-      store(buf ^ 1);
-      __syncthreads();
-      buf ^= 1;
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < 8; ++i)
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int r = row0 + 8 * ty + i, c = col0 + 8 * tx + j;
-      if (r < M && c < N) epi(r, c, acc[i][j]);
-    }
-}
-
 template <typename T, class Epi>
 cudaError_t run_gemm(int M, int N, int K, const T *A, int lda, const T *B, int ldb, Epi epi,
                      cudaStream_t st) {
   if (M <= 0 || N <= 0) return cudaSuccess;
-  if constexpr (sizeof(T) == 4) {
-    dim3 grid((N + BN2 - 1) / BN2, (M + BM2 - 1) / BM2);
-    k_gemm_f32_big<Epi><<<grid, kGemmThreads, 0, st>>>(M, N, K, A, lda, B, ldb, epi, K);
-  } else {
-    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
-    k_gemm<T, Epi><<<grid, kGemmThreads, 0, st>>>(M, N, K, A, lda, B, ldb, epi);
-  }
+  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+  k_gemm<T, Epi><<<grid, kGemmThreads, 0, st>>>(M, N, K, A, lda, B, ldb, epi);
   return cudaGetLastError();
 }
 
@@ -366,47 +284,6 @@ inline int grid_for(size_t n) {
 
 }  // namespace
 
-// Split-K FP32 GEMM for small M x N with long K: partial sums of `splits`
-// K ranges go to ws (splits x M x N), then one pass sums them and applies the
-// epilogue.
-struct EpiPartial {
-  float *ws;
-  int M, N;
-  __device__ void operator()(int r, int c, float v) const {
-    ws[((size_t)blockIdx.z * M + r) * N + c] = v;
-  }
-};
-
-template <class Epi>
-__global__ void k_splitk_finish(int M, int N, int splits, const float *__restrict__ ws, Epi epi) {
-  const size_t total = (size_t)M * N;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-       e += (size_t)gridDim.x * blockDim.x) {
-    float s = 0.0f;
-    for (int z = 0; z < splits; ++z) s += ws[(size_t)z * total + e];
-    epi((int)(e / N), (int)(e % N), s);
-  }
-}
-
-template <class Epi>
-cudaError_t run_gemm_splitk_f32(int M, int N, int K, const float *A, int lda, const float *B,
-                                int ldb, Epi epi, float *ws, size_t ws_floats, cudaStream_t st) {
-  if (M <= 0 || N <= 0) return cudaSuccess;
-  const int tiles = ((N + BN2 - 1) / BN2) * ((M + BM2 - 1) / BM2);
-  int splits = (6 * 152 + tiles - 1) / tiles;
-  splits = std::max(1, std::min({splits, 8, (K + 255) / 256}));
-  while (splits > 1 && (size_t)splits * M * N > ws_floats) --splits;
-  if (splits == 1 || !ws) return run_gemm<float, Epi>(M, N, K, A, lda, B, ldb, epi, st);
-  const int kchunk = ((K + splits - 1) / splits + BK2 - 1) / BK2 * BK2;
-  dim3 grid((N + BN2 - 1) / BN2, (M + BM2 - 1) / BM2, splits);
-  k_gemm_f32_big<EpiPartial>
-      <<<grid, kGemmThreads, 0, st>>>(M, N, K, A, lda, B, ldb, EpiPartial{ws, M, N}, kchunk);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_splitk_finish<Epi><<<grid_for((size_t)M * N), 256, 0, st>>>(M, N, splits, ws, epi);
-  return cudaGetLastError();
-}
-
 template <typename T>
 cudaError_t gemm_store(int M, int N, int K, const T *A, int lda, const T *B, int ldb, T *out,
                        int ldo, cudaStream_t st) {
@@ -428,11 +305,7 @@ cudaError_t gemm_scale_group(int M, int N, int K, const T *A, int lda, const T *
 
 template <typename T>
 cudaError_t gemm_coef(int M, int N, int K, const T *A, int lda, const T *B, int ldb,
-                      const double *coef, int ldc, double c, T *out, int ldo, cudaStream_t st,
-                      float *ws, size_t ws_floats) {
-  if constexpr (sizeof(T) == 4)
-    return run_gemm_splitk_f32(M, N, K, A, lda, B, ldb, EpiCoef<T>{coef, ldc, c, out, ldo}, ws,
-                               ws_floats, st);
+                      const double *coef, int ldc, double c, T *out, int ldo, cudaStream_t st) {
   return run_gemm(M, N, K, A, lda, B, ldb, EpiCoef<T>{coef, ldc, c, out, ldo}, st);
 }
 
@@ -486,32 +359,29 @@ cudaError_t launch_f64_to_f32(size_t n, const double *src, float *dst, cudaStrea
   return cudaGetLastError();
 }
 
-cudaError_t launch_f32_to_f64(size_t n, const float *src, double *dst, cudaStream_t st) {
-  k_convert<float, double><<<grid_for(n), 256, 0, st>>>(n, src, dst);
-  return cudaGetLastError();
-}
-
-#define DINO_INST(T)                                                                          \
-  template cudaError_t gemm_store<T>(int, int, int, const T *, int, const T *, int, T *, int, \
-                                     cudaStream_t);                                           \
-  template cudaError_t gemm_bias_act<T>(int, int, int, const T *, int, const T *, int,        \
-                                        const T *, int, T *, T *, int, cudaStream_t);         \
-  template cudaError_t gemm_scale_group<T>(int, int, int, const T *, int, const T *, int,     \
-                                           const T *, int, int, T *, int, cudaStream_t);      \
-  template cudaError_t gemm_coef<T>(int, int, int, const T *, int, const T *, int,            \
-                                    const double *, int, double, T *, int, cudaStream_t,      \
-                                    float *, size_t);                                         \
-  template cudaError_t gemm_field<T>(int, int, int, const T *, int, const T *, int,           \
-                                     const int *, double, double, T *, const T *, int,        \
-                                     cudaStream_t);                                           \
+// The SIMT GEMMs serve the FP64 path; the prior draw both paths.
+template cudaError_t gemm_store<double>(int, int, int, const double *, int, const double *, int,
+                                        double *, int, cudaStream_t);
+template cudaError_t gemm_bias_act<double>(int, int, int, const double *, int, const double *,
+                                           int, const double *, int, double *, double *, int,
+                                           cudaStream_t);
+template cudaError_t gemm_scale_group<double>(int, int, int, const double *, int, const double *,
+                                              int, const double *, int, int, double *, int,
+                                              cudaStream_t);
+template cudaError_t gemm_coef<double>(int, int, int, const double *, int, const double *, int,
+                                       const double *, int, double, double *, int, cudaStream_t);
+template cudaError_t gemm_field<double>(int, int, int, const double *, int, const double *, int,
+                                        const int *, double, double, double *, const double *,
+                                        int, cudaStream_t);
+template cudaError_t launch_jac_init<double>(int, int, int, const double *, const double *, int,
+                                             double *, cudaStream_t);
+template cudaError_t launch_broadcast<double>(int, size_t, const double *, double *,
+                                              cudaStream_t);
+#define DINO_INST_DRAW(T)                                                                     \
   template cudaError_t launch_prior_draw<T>(int, int, const T *, const T *, uint64_t,         \
                                             uint64_t, uint32_t, uint32_t, T *, int,           \
-                                            cudaStream_t, __nv_bfloat16 *, int, size_t, int); \
-  template cudaError_t launch_jac_init<T>(int, int, int, const T *, const T *, int, T *,      \
-                                          cudaStream_t);                                      \
-  template cudaError_t launch_broadcast<T>(int, size_t, const T *, T *, cudaStream_t);
-
-DINO_INST(double)
-DINO_INST(float)
+                                            cudaStream_t, __nv_bfloat16 *, int, size_t, int);
+DINO_INST_DRAW(double)
+DINO_INST_DRAW(float)
 
 }  // namespace dino
