@@ -168,8 +168,15 @@ __global__ void __launch_bounds__(kPriorThreads)
   T *Y = Ss + NN;
   const int c = blockIdx.x, N = n * n;
   const uint32_t chain = (uint32_t)(id_base + (uint64_t)c);
+  // q / d for 0 <= q < d^2 + 4d, d <= 256, from the FP32 reciprocal: (q + 1/2) / d
+  // stays at least 1/(2d) away from an integer, far beyond the rounding error
+  // (rounded operations, no contraction)
+  const float inv_ld = 1.0f / (float)ld, inv_n = 1.0f / (float)n;
+  auto quot = [](int q, float inv) {
+    return (int)__fmul_rn(__fadd_rn((float)q, 0.5f), inv);
+  };
   for (int e = threadIdx.x; e < NN; e += blockDim.x) {
-    const int row = e / ld, col = e % ld;
+    const int row = quot(e, inv_ld), col = e - row * ld;
     const bool in = row < n && col < n;
     X[e] = T(0);
     Ss[e] = in ? S[row * n + col] : T(0);
@@ -185,7 +192,10 @@ __global__ void __launch_bounds__(kPriorThreads)
     }
     for (int q = 0; q < 4; ++q) {
       const int m = 4 * blk + q;
-      if (m < N) X[(m / n) * ld + m % n] = sqrtlam[m] * z[q];
+      if (m < N) {
+        const int j = quot(m, inv_n);
+        X[j * ld + (m - j * n)] = sqrtlam[m] * z[q];
+      }
     }
   }
   __syncthreads();
