@@ -393,8 +393,14 @@ __device__ __forceinline__ void strip_advance(StripPos &p, int step, int w) {
     ++p.ii;
   }
   if (p.jj >= w) {
-    p.ii += p.jj / w;
-    p.jj %= w;
+    if (w == kNB) {  // a full panel strip: shifts instead of a runtime division
+      static_assert(kNB == 8, "strip width is a power of two");
+      p.ii += p.jj >> 3;
+      p.jj &= kNB - 1;
+    } else {
+      p.ii += p.jj / w;
+      p.jj %= w;
+    }
   }
 }
 
