@@ -48,3 +48,15 @@ def test_binding_covers_every_symbol_and_loads_without_gpu():
         assert hasattr(L, n)
         assert n in dino.exported_symbols()
     assert dino.dino_version() >= 100
+
+
+def test_no_gpu_means_an_error_not_a_fallback():
+    """Without a CUDA device the library refuses to create a context (ECUDA):
+    there is no host fallback for any step of the path."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_2403_08220_gb300 as dino
+    with pytest.raises(dino.DinoError) as ei:
+        dino.dino_init(0)
+    assert ei.value.code == dino.DINO_ECUDA
