@@ -174,7 +174,8 @@ def load_surrogate(dino, ctx, w):
     sid = dino.dino_load_surrogate(
         ctx, n_grid=w.n_grid, prior_gamma=w.prior_gamma, prior_delta=w.prior_delta, r=w.r,
         widths=w.widths, activation=w.activation, W=inp["Ws"], b=inp["bs"],
-        basis_kind=w.basis_kind, basis_gauss=inp["G"], precision=prec)
+        basis_kind=w.basis_kind, basis_gauss=inp["G"], precision=prec,
+        noise_map={"auto": 0, "cholesky": 1, "perturbation": 2}[w.noise_map])
     twin = dino.dino_load_surrogate(
         ctx, n_grid=w.n_grid, prior_gamma=w.prior_gamma, prior_delta=w.prior_delta, r=w.r,
         widths=w.widths, activation=w.activation, W=inp["Ws"], b=inp["bs"],
@@ -514,8 +515,10 @@ def cpu_baseline(args, sample_chains=None, sample_steps=None):
     sur = mmala.Surrogate(Ws=inp["Ws"], bs=inp["bs"], act=w.activation, y=y, noise_var=nv)
     C = sample_chains or 64
     K = sample_steps or 2
+    if w.noise_map not in ("cholesky", "perturbation"):
+        raise ValueError(f"workload {w.name} must name its proposal noise map")
     och = OracleChains(sur, E, D, w.n_grid, w.prior_gamma, w.prior_delta, C, w.dt,
-                       seed=SEED_CHAINS)
+                       seed=SEED_CHAINS, noise=w.noise_map)
     t0 = time.perf_counter()
     och.step(K)
     el = time.perf_counter() - t0

@@ -72,6 +72,19 @@ extern "C" {
                                  slices); Cholesky, solves and log-acceptance
                                  FP64-accurate (double-float); field in FP32 */
 
+/* Proposal noise map (Sec. 5.3, eq:reduced_space_sampling).  Both maps give
+ * the proposal law N(mu, (1 - s^2)(I + H)^-1); a given set of normals maps to
+ * different samples, so a parity check must use the map the library reports
+ * (dino_surrogate_query).
+ *   CHOLESKY      zeta = L^-T xi, L L^T = I + H (r normals per proposal);
+ *   PERTURBATION  zeta = (I + H)^-1 (xi + K^T xi2), K = J / sigma, with d_y
+ *                 further normals xi2: only the d_y x d_y matrix I + K K^T is
+ *                 factored (needs d_y < r and d_y <= 192);
+ *   AUTO          PERTURBATION when it applies, else CHOLESKY. */
+#define DINO_NOISE_AUTO         0
+#define DINO_NOISE_CHOLESKY     1
+#define DINO_NOISE_PERTURBATION 2
+
 #define DINO_FLAG_TIMING 1u   /* record per-kernel CUDA-event times */
 #define DINO_FLAG_NO_DIRECT_HOST 2u /* copy host fields with cudaMemcpy even where
                                        the device reads pageable host memory */
@@ -98,7 +111,7 @@ int dino_destroy(dino_ctx *ctx);
 const char *dino_last_error(const dino_ctx *ctx);
 
 /* ABI version (major*100 + minor). */
-int dino_version(void);
+int dino_version(void);  /* 101 */
 
 /* Block until all work issued on the context's stream has finished. */
 int dino_sync(dino_ctx *ctx);
@@ -125,8 +138,9 @@ int dino_sync(dino_ctx *ctx);
  *   each operand of the MLP-forward / Jacobian GEMMs (1..3; 0 = default 3 and
  *   2).  k terms use the k(k+1)/2 leading cross products, so 2 is the
  *   "bf16x3" scheme and 3 reaches FP32-level accuracy.
- * Errors: EINVAL (shapes, r > N, NULL arrays, noise_var <= 0), ENUMERIC
- *   (E D != I, non-finite data), ENOMEM. */
+ * noise_map: DINO_NOISE_* (0 = AUTO).
+ * Errors: EINVAL (shapes, r > N, NULL arrays, noise_var <= 0, a noise map
+ *   that does not apply), ENUMERIC (E D != I, non-finite data), ENOMEM. */
 typedef struct {
   int n_grid;
   double prior_gamma, prior_delta;
@@ -145,9 +159,23 @@ typedef struct {
   int precision;
   int fwd_slices;
   int jac_slices;
+  int noise_map;
 } dino_surrogate_desc;
 
 int dino_load_surrogate(dino_ctx *ctx, const dino_surrogate_desc *desc, int *surrogate_id);
+
+/* What the library made of a loaded surrogate: sizes, precision, the noise
+ * map its chains use (DINO_NOISE_CHOLESKY or DINO_NOISE_PERTURBATION),
+ * whether the Gram matrices J J^T come from the tensor cores, and the bf16
+ * slice counts (0 on the FP64 path).  Errors: ENOTFOUND, EINVAL (NULL). */
+typedef struct {
+  int N, r, d_y, n_layers, precision;
+  int noise_map;
+  int gram_on_tensor_cores;
+  int fwd_slices, jac_slices;
+} dino_surrogate_info;
+
+int dino_surrogate_query(dino_ctx *ctx, int surrogate_id, dino_surrogate_info *info);
 
 /* Replace the data y (d_y host values) and noise variance of a surrogate.
  * Pools created later use the new data; existing pools are unaffected
@@ -172,7 +200,10 @@ int dino_surrogate_eval(dino_ctx *ctx, int surrogate_id, int n, const double *m_
 
 /* ---- chain pools ------------------------------------------------------- */
 
-/* Create n_chains chains of surrogate `surrogate_id` with step size dt > 0.
+/* Create n_chains chains of surrogate `surrogate_id` with step size dt > 0
+ * (s = (4 - dt)/(4 + dt), eq:mmala), each at the "Known at m_j" state of
+ * Algorithm 1: m_r = Psi_r^* m0 (eq:projector, Sec. 4.1) and the surrogate
+ * misfit, gradient and Gauss-Newton factor at m_r (Sec. 5.1).
  * Chain k has global id chain_id_base + k; its random numbers are
  * Philox4x32-10 with key = seed and counter = (block, step, global id,
  * stream), stream 0 = reduced noise xi, 1 = accept uniform, 2 = complement
@@ -206,8 +237,13 @@ typedef struct {
  * stats (may be NULL) receives the totals of this call (it synchronises). */
 int dino_chains_step(dino_ctx *ctx, int pool_id, int n_steps, dino_step_stats *stats);
 
-/* Copy the current state to host buffers (any may be NULL):
- * m (n_chains x N), m_r (n_chains x r), phi (n_chains), accepts (n_chains). */
+/* Copy the current chain positions m_j of Algorithm 1 to host buffers (any
+ * may be NULL): the field m (n_chains x N, row-major), its reduced
+ * coordinates m_r = Psi_r^* m (n_chains x r, eq:projector), the surrogate
+ * misfit Phi(m_r) (n_chains; Sec. 5.1 with Gamma = noise_var I) and the
+ * accepts per chain (n_chains).  Synchronises the pool's stream.
+ * Errors: ENOTFOUND; ETIMEOUT if a bounded device wait gave up in an earlier
+ * step (the pool state is then invalid and should be destroyed). */
 int dino_chains_read(dino_ctx *ctx, int pool_id, double *m, double *m_r, double *phi,
                      uint64_t *accepts);
 
@@ -217,6 +253,27 @@ int dino_chains_read(dino_ctx *ctx, int pool_id, double *m, double *m_r, double 
 int dino_chains_read_last(dino_ctx *ctx, int pool_id, double *b, double *mu,
                           double *log_rho, double *log_u, int *accepted);
 
+/* Test hook: the noise of the pool's NEXT transition from the caller instead
+ * of Philox, so that an independent implementation of Algorithm 1 can be
+ * fed exactly the same draws (Algorithm 1 lines 1 and 6, Prop. 5.1):
+ *   xi    n_chains x r   reduced normals (xi_r);
+ *   xi2   n_chains x d_y observation-space normals of the perturbation map
+ *                        (EINVAL on a pool with the Cholesky map);
+ *   z     n_chains x N   the standard normals of the complement prior draw
+ *                        M = sum_q sqrt(lambda_q) z_q eta_q (full KLE, mode
+ *                        q = (kx-1) + n_grid (ky-1));
+ *   log_u n_chains       the log of the accept uniform (accept iff
+ *                        log_u <= min(0, log rho)).
+ * Any pointer may be NULL (that stream stays Philox).  Host arrays, copied
+ * before return; they apply to exactly one transition, after which every
+ * stream is Philox again.  The first call allocates a device buffer of
+ * n_chains (r + d_y + N + 1) doubles for the pool.
+ * Errors: ENOTFOUND, EINVAL, ENOMEM. */
+int dino_chains_set_noise(dino_ctx *ctx, int pool_id, const double *xi, const double *xi2,
+                          const double *z, const double *log_u);
+
+/* Free a chain pool's device memory (after its stream has drained); the
+ * pool id is invalid afterwards.  Errors: ENOTFOUND. */
 int dino_chains_destroy(dino_ctx *ctx, int pool_id);
 
 /* ---- serving: continuous batching of chain ensembles -------------------- */
@@ -278,6 +335,13 @@ int dino_serve_status(dino_ctx *ctx, int *queued, int *active, int *peak_active,
                       size_t *hbm_used, size_t *peak_hbm_used);
 
 /* ---- instrumentation --------------------------------------------------- */
+
+/* Bound on the polls of the Cholesky's diagonal-block flag (a wait between
+ * the warps of one CTA) before the kernel gives up, raises its error word and
+ * returns; dino_chains_step (with stats) and dino_chains_read then report
+ * DINO_ETIMEOUT.  0 restores the default (2^22 polls).  Applies to launches
+ * issued after the call.  For tests of the timeout path. */
+int dino_set_wait_limit(dino_ctx *ctx, uint32_t flag_spins);
 
 /* Number of kernels this context has launched since creation. */
 uint64_t dino_launch_count(const dino_ctx *ctx);

@@ -11,8 +11,10 @@ the target is the surrogate posterior.
 Random numbers (see `philox`): step j of chain c uses XI(j, c) for the r
 reduced normals, U(j, c) for the accept uniform and Z(j, c) for the N normals
 of the complement prior draw; the initial prior draw uses INIT(0, c).  With
-the perturbation noise map (`mmala.noise_map`: d_y < r) the d_y further
-normals come from XI2(j, c).
+the perturbation noise map the d_y further normals come from XI2(j, c).
+The noise map ("cholesky" or "perturbation", see `mmala.NOISE_MAPS`) is an
+explicit argument.  `step(noise=...)` replaces the draws of one transition by
+given arrays (xi, xi2, z, log_u), any of which may be absent.
 """
 from __future__ import annotations
 
@@ -23,12 +25,14 @@ from . import mmala, philox, prior
 
 class OracleChains:
     def __init__(self, sur: mmala.Surrogate, E, D, n_grid: int, gamma: float, delta: float,
-                 n_chains: int, dt: float, seed: int, m0=None, chain_ids=None,
-                 noise: str = "auto"):
+                 n_chains: int, dt: float, seed: int, m0=None, chain_ids=None, *,
+                 noise: str):
+        if noise not in mmala.NOISE_MAPS:
+            raise ValueError(f"noise map must be one of {mmala.NOISE_MAPS}, got {noise!r}")
         self.sur, self.E, self.D = sur, np.asarray(E), np.asarray(D)
         self.n_grid, self.gamma, self.delta = n_grid, gamma, delta
         self.dt, self.seed = float(dt), int(seed)
-        self.noise = mmala.noise_map(sur.r, sur.d_y) if noise == "auto" else noise
+        self.noise = noise
         self.ids = (np.arange(n_chains, dtype=np.uint64) if chain_ids is None
                     else np.asarray(chain_ids, dtype=np.uint64))
         C = len(self.ids)
@@ -43,19 +47,29 @@ class OracleChains:
         self.accepts = np.zeros(C, dtype=np.int64)
         self.last = None
 
-    def step(self, n_steps: int = 1):
-        for _ in range(n_steps):
-            self._step()
+    def step(self, n_steps: int = 1, noise=None):
+        for k in range(n_steps):
+            self._step(noise if k == 0 else None)
 
-    def _step(self):
+    def _step(self, given=None):
         j = self.step_index
         sur, dt, r = self.sur, self.dt, self.sur.r
         N = self.m.shape[1]
-        xi = philox.normals(self.seed, philox.STREAM_XI, j, self.ids, r)
-        u = philox.uniform(self.seed, philox.STREAM_U, j, self.ids)
+        given = given or {}
+
+        def draw(name, stream, width):
+            if given.get(name) is not None:
+                return np.asarray(given[name], dtype=np.float64)
+            return philox.normals(self.seed, stream, j, self.ids, width)
+
+        xi = draw("xi", philox.STREAM_XI, r)
+        if given.get("log_u") is not None:
+            log_u = np.asarray(given["log_u"], dtype=np.float64)
+        else:
+            log_u = np.log(philox.uniform(self.seed, philox.STREAM_U, j, self.ids))
         a, geo_a = self.m_r, self.geo
         if self.noise == "perturbation":
-            xi2 = philox.normals(self.seed, philox.STREAM_XI2, j, self.ids, sur.d_y)
+            xi2 = draw("xi2", philox.STREAM_XI2, sur.d_y)
             mu, b = mmala.reduced_proposal_perturbation(a, geo_a, xi, xi2, sur.noise_var, dt)
         else:
             mu, b = mmala.reduced_proposal(a, geo_a, xi, dt)
@@ -65,9 +79,8 @@ class OracleChains:
         lr_scale = (np.abs(geo_a.phi) + np.abs(geo_b.phi)
                     + np.abs(mmala.log_rho0(a, b, geo_a, dt))
                     + np.abs(mmala.log_rho0(b, a, geo_b, dt)))
-        log_u = np.log(u)
         acc = mmala.accept(log_u, lr)
-        z = philox.normals(self.seed, philox.STREAM_Z, j, self.ids, N)
+        z = draw("z", philox.STREAM_Z, N)
         M = prior.prior_sample(self.n_grid, self.gamma, self.delta, z)
         m_new = mmala.field_proposal(self.m, b, M, self.E, self.D, dt)
         self.last = dict(mu=mu, b=b, log_rho=lr, log_rho_scale=lr_scale, log_u=log_u, accepted=acc.copy(),

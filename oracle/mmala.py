@@ -21,10 +21,13 @@ Readings of the paper taken here (each also listed in the design notes):
   factor).  It has the law of the eigen form of eq:reduced_space_sampling
   (covariance (1 - s^2)(I + H)^-1); `reduced_proposal_eigen` keeps the
   paper's map for distribution checks.
-* When d_y < r (and d_y <= 192) the noise is drawn instead as zeta = (I + H)^-1 (xi1 + K^T xi2)
-  with K = J / sqrt(noise_var) and d_y further normals xi2: the same law
+* The noise may instead be drawn as zeta = (I + H)^-1 (xi1 + K^T xi2) with
+  K = J / sqrt(noise_var) and d_y further normals xi2: the same law
   (`reduced_proposal_perturbation`), which needs only the d_y x d_y matrix
-  I + K K^T to be factored (`noise_map`).
+  I + K K^T to be factored.  Which of the two maps a chain uses is an explicit
+  argument of the chain driver (`NOISE_MAPS`); both give the proposal law of
+  eq:reduced_space_sampling, so the choice is a property of the sampler being
+  compared against, not of the method.
 * Accept iff log u <= min(0, log rho) (Alg. 1 rejects iff alpha < u);
   a non-finite log rho is a reject.
 """
@@ -113,15 +116,7 @@ def reduced_proposal(a, geo: Geometry, xi, dt: float):
     return mu, mu + np.sqrt(1.0 - s * s) * eta
 
 
-WOODBURY_MAX_DY = 192
-
-
-def noise_map(r: int, d_y: int) -> str:
-    """The proposal noise map used for a surrogate with reduced dimension r and
-    d_y observables: "perturbation" when d_y < r and d_y <= WOODBURY_MAX_DY
-    (the d_y x d_y factor is then the smaller one and fits on chip), else
-    "cholesky"."""
-    return "perturbation" if d_y < r and d_y <= WOODBURY_MAX_DY else "cholesky"
+NOISE_MAPS = ("cholesky", "perturbation")
 
 
 def reduced_proposal_perturbation(a, geo: Geometry, xi1, xi2, noise_var: float, dt: float):

@@ -34,6 +34,8 @@ DINO_ESTATE = -8
 DINO_ACT_IDENTITY, DINO_ACT_TANH, DINO_ACT_GELU = 0, 1, 2
 DINO_BASIS_KLE, DINO_BASIS_DIS, DINO_BASIS_EXPLICIT = 0, 1, 2
 DINO_PREC_FP64, DINO_PREC_BF16 = 0, 1
+DINO_NOISE_AUTO, DINO_NOISE_CHOLESKY, DINO_NOISE_PERTURBATION = 0, 1, 2
+NOISE_MAP_NAMES = {DINO_NOISE_CHOLESKY: "cholesky", DINO_NOISE_PERTURBATION: "perturbation"}
 DINO_FLAG_TIMING = 1
 DINO_FLAG_NO_DIRECT_HOST = 2
 
@@ -55,6 +57,13 @@ class _Desc(ct.Structure):
                 ("basis_gauss", ct.POINTER(ct.c_double)), ("E", ct.POINTER(ct.c_double)),
                 ("D", ct.POINTER(ct.c_double)), ("y", ct.POINTER(ct.c_double)),
                 ("noise_var", ct.c_double), ("precision", ct.c_int), ("fwd_slices", ct.c_int),
+                ("jac_slices", ct.c_int), ("noise_map", ct.c_int)]
+
+
+class _Info(ct.Structure):
+    _fields_ = [("N", ct.c_int), ("r", ct.c_int), ("d_y", ct.c_int), ("n_layers", ct.c_int),
+                ("precision", ct.c_int), ("noise_map", ct.c_int),
+                ("gram_on_tensor_cores", ct.c_int), ("fwd_slices", ct.c_int),
                 ("jac_slices", ct.c_int)]
 
 
@@ -97,6 +106,9 @@ _SIGNATURES = {
     "dino_chains_read": ([_P, _I, _D, _D, _D, ct.POINTER(ct.c_uint64)], _I),
     "dino_chains_read_last": ([_P, _I, _D, _D, _D, _D, ct.POINTER(_I)], _I),
     "dino_chains_destroy": ([_P, _I], _I),
+    "dino_surrogate_query": ([_P, _I, ct.POINTER(_Info)], _I),
+    "dino_chains_set_noise": ([_P, _I, _D, _D, _D, _D], _I),
+    "dino_set_wait_limit": ([_P, ct.c_uint32], _I),
     "dino_launch_count": ([_P], ct.c_uint64),
     "dino_kernel_times": ([_P, ct.c_char_p, _D, ct.POINTER(ct.c_uint64), _I, ct.POINTER(_I), _I],
                           _I),
@@ -194,7 +206,7 @@ def dino_sync(ctx: Ctx):
 def dino_load_surrogate(ctx: Ctx, *, n_grid, prior_gamma, prior_delta, r, widths, activation,
                         W, b, basis_kind, basis_gauss=None, E=None, D=None, y=None,
                         noise_var=0.0, precision=DINO_PREC_FP64, fwd_slices=0,
-                        jac_slices=0) -> int:
+                        jac_slices=0, noise_map=DINO_NOISE_AUTO) -> int:
     L = len(W)
     wid = (ct.c_int * (L + 1))(*[int(x) for x in widths])
     Ws = [_f64(w) for w in W]
@@ -207,7 +219,7 @@ def dino_load_surrogate(ctx: Ctx, *, n_grid, prior_gamma, prior_delta, r, widths
     ya = _f64(y) if y is not None else None
     d = _Desc(n_grid, prior_gamma, prior_delta, r, L, wid, activation, Wp, bp, basis_kind,
               _dptr(G), _dptr(Ea), _dptr(Da), _dptr(ya), float(noise_var), precision,
-              fwd_slices, jac_slices)
+              fwd_slices, jac_slices, int(noise_map))
     sid = _I()
     _check(ctx, lib().dino_load_surrogate(ctx.ptr, ct.byref(d), ct.byref(sid)))
     return sid.value
@@ -281,6 +293,25 @@ def dino_chains_read_last(ctx: Ctx, pool: int, C: int, r: int) -> dict:
 
 def dino_chains_destroy(ctx: Ctx, pool: int):
     _check(ctx, lib().dino_chains_destroy(ctx.ptr, pool))
+
+
+def dino_surrogate_query(ctx: Ctx, sid: int) -> dict:
+    """Sizes, precision, noise map ("cholesky" / "perturbation") and paths of a surrogate."""
+    info = _Info()
+    _check(ctx, lib().dino_surrogate_query(ctx.ptr, sid, ct.byref(info)))
+    out = {k: getattr(info, k) for k, _ in _Info._fields_}
+    out["noise_map"] = NOISE_MAP_NAMES[info.noise_map]
+    return out
+
+
+def dino_chains_set_noise(ctx: Ctx, pool: int, xi=None, xi2=None, z=None, log_u=None):
+    """Caller noise for the pool's next transition (None keeps Philox for that stream)."""
+    arrs = [None if a is None else _f64(a) for a in (xi, xi2, z, log_u)]
+    _check(ctx, lib().dino_chains_set_noise(ctx.ptr, pool, *[_dptr(a) for a in arrs]))
+
+
+def dino_set_wait_limit(ctx: Ctx, flag_spins: int):
+    _check(ctx, lib().dino_set_wait_limit(ctx.ptr, int(flag_spins)))
 
 
 def dino_launch_count(ctx: Ctx) -> int:

@@ -482,11 +482,12 @@ __device__ __noinline__ void trailing_update(typename A::T *Ls, int r, int kb, i
 // column-at-a-time algorithm.  A non-positive pivot produces NaN, which the
 // caller turns into a reject.
 constexpr int kChunk = 128;                // trailing-update entries per warp grab
-constexpr uint32_t kFlagSpins = 1u << 22;  // polls of the diagonal-block flag
 
-// `ctr` is six ints of shared memory.
+// `ctr` is six ints of shared memory; a warp gives up waiting for the flag
+// after `max_spins` polls.
 template <class A>
-__device__ void cta_cholesky(typename A::T *Ls, typename A::T *inv, int r, int *ctr, int *err) {
+__device__ void cta_cholesky(typename A::T *Ls, typename A::T *inv, int r, int *ctr, int *err,
+                             uint32_t max_spins) {
   const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid < 6) ctr[tid] = 0;
   if (warp == 0) warp_factor_diag<A>(Ls, inv, 0, min(kNB, r), lane);
@@ -534,7 +535,7 @@ __device__ void cta_cholesky(typename A::T *Ls, typename A::T *inv, int r, int *
       } else if (job == 2) {
         trailing_update<A>(Ls, r, kb, kNB, j0, r, base, base + kChunk, lane, 32);
       } else {
-        if (++spins > kFlagSpins) {
+        if (++spins > max_spins) {
           if (lane == 0) atomicOr(err, 8);
           break;
         }
@@ -612,10 +613,15 @@ __device__ void form_gram_f64(const double *X, int m, int n, int ldx, double inv
 }
 
 // From an FP32 X into double-float entries: each thread accumulates up to
-// kHMaxTiles 4 x 4 tiles in FP32 registers over all m reduction rows (chunks
-// of kJChunkF rows staged in shared memory, padded to a multiple of 4
-// columns), then writes its entries once, the product with 1 / noise_var
-// taken exactly as a double-float.  Large n takes several rounds of tiles.
+// kHMaxTiles 4 x 4 tiles in FP32 registers (chunks of kJChunkF reduction rows
+// staged in shared memory, padded to a multiple of 4 columns); every
+// kGramFlush rows the FP32 tile sums are added exactly into double-float sums
+// held in Ls (each entry owned by one thread) and restart from zero, so the
+// FP32 rounding error grows with kGramFlush rather than with m.  At the end
+// each entry is multiplied by 1 / noise_var as a double-float and 1 is added
+// on the diagonal.  Large n takes several rounds of tiles.
+constexpr int kGramFlush = 2 * kJChunkF;
+
 template <bool kRedContig>
 __device__ void form_gram_f32(const float *X, int m, int n, int ldx, double inv_nv, float2 *Ls,
                               float *Jc) {
@@ -647,6 +653,7 @@ __device__ void form_gram_f32(const float *X, int m, int n, int ldx, double inv_
 #pragma unroll
         for (int q = 0; q < kHT; ++q) acc[s][p][q] = 0.0f;
     }
+    bool first = true;
     for (int i0 = 0; i0 < dy; i0 += kJChunkF) {
       const int nr = min(kJChunkF, dy - i0);
       // unrolled so that each thread has several independent loads in flight
@@ -679,7 +686,27 @@ __device__ void form_gram_f32(const float *X, int m, int n, int ldx, double inv_
         }
       }
       __syncthreads();
+      if ((i0 + nr) % kGramFlush == 0 || i0 + nr >= dy) {
+#pragma unroll
+        for (int s = 0; s < kHMaxTiles; ++s) {
+          if (ti[s] < 0) continue;
+#pragma unroll
+          for (int p = 0; p < kHT; ++p)
+#pragma unroll
+            for (int q = 0; q < kHT; ++q) {
+              const int i = kHT * ti[s] + p, j = kHT * tj[s] + q;
+              if (i < r && j <= i) {
+                float2 *e = Ls + tri(i) + j;
+                const float2 x = make_float2(acc[s][p][q], 0.0f);
+                *e = first ? x : DF::add(*e, x);
+              }
+              acc[s][p][q] = 0.0f;
+            }
+        }
+        first = false;
+      }
     }
+    // scale by 1 / noise_var and add the identity (the entries this thread owns)
 #pragma unroll
     for (int s = 0; s < kHMaxTiles; ++s) {
       if (ti[s] < 0) continue;
@@ -689,17 +716,9 @@ __device__ void form_gram_f32(const float *X, int m, int n, int ldx, double inv_
         for (int q = 0; q < kHT; ++q) {
           const int i = kHT * ti[s] + p, j = kHT * tj[s] + q;
           if (i < r && j <= i) {
-            const float x = acc[s][p][q], ph = __fmul_rn(x, nh);
-            float e = __fmaf_rn(x, nh, -ph);
-            e = __fmaf_rn(x, nl, e);
-            float h, l;
-            fast_two_sum(ph, e, h, l);
-            if (i == j) {
-              float s1, q1;
-              two_sum(1.0f, h, s1, q1);
-              fast_two_sum(s1, __fadd_rn(q1, l), h, l);
-            }
-            Ls[tri(i) + j] = make_float2(h, l);
+            float2 v = DF::mul(Ls[tri(i) + j], make_float2(nh, nl));
+            if (i == j) v = DF::add(make_float2(1.0f, 0.0f), v);
+            Ls[tri(i) + j] = v;
           }
         }
     }
@@ -711,7 +730,9 @@ __device__ void form_gram_f32(const float *X, int m, int n, int ldx, double inv_
 // counters, and the scalar state of an accepted chain.  Thread 0 only.
 __device__ bool accept_test(const ReducedArgs &a, int c, double lr, double phi_b, double hld_b) {
   const uint32_t chain = (uint32_t)(a.id_base + (uint64_t)c);
-  const double log_u = log(word_to_uniform(philox_block(a.seed, STREAM_U, a.step, chain, 0).x));
+  const double log_u =
+      a.ext_log_u ? a.ext_log_u[c]
+                  : log(word_to_uniform(philox_block(a.seed, STREAM_U, a.step, chain, 0).x));
   const bool finite = isfinite(lr);
   const bool accept = finite && log_u <= fmin(0.0, lr);
   a.log_rho[c] = lr;

@@ -79,6 +79,12 @@ struct ReducedArgs {
   unsigned long long *counters = nullptr;  // [0] accepts, [1] nan rejects
   double *sum_alpha = nullptr;
   int *err = nullptr;  // set (bit 4) when a bounded device wait gives up
+  // polls of the Cholesky diagonal-block flag before giving up (bit 8 of err)
+  uint32_t flag_spins = 1u << 22;
+  // caller-supplied noise of this transition (nullptr: Philox): reduced
+  // normals (C x r), observation-space normals of the perturbation map
+  // (C x d_y) and the log of the accept uniform (C)
+  const double *ext_xi = nullptr, *ext_xi2 = nullptr, *ext_log_u = nullptr;
   // tensor-core path: the proposal as bf16 slice planes (row pitch b_ld,
   // plane pitch b_plane elements); nullptr when unused
   __nv_bfloat16 *b_bf16 = nullptr;
@@ -138,12 +144,14 @@ size_t prior_draw_smem_bytes(int n, int elem);
 // Z_c from Philox stream `stream` at `step` for chain id_base + c.  With `ms`
 // (FP32 only) the draw is also written as ms_slices bf16 slice planes
 // (row pitch ldms, plane stride ms_plane) for the tensor-core projections.
+// With ext_z (C x N doubles, nullptr for Philox) the normals Z_c are the
+// caller's, indexed like the Philox ones.
 template <typename T>
 cudaError_t launch_prior_draw(int C, int n, const T *sqrtlam, const T *S, uint64_t seed,
                               uint64_t id_base, uint32_t stream, uint32_t step, T *out,
                               int ldo, cudaStream_t st,
                               __nv_bfloat16 *ms = nullptr, int ldms = 0, size_t ms_plane = 0,
-                              int ms_slices = 0);
+                              int ms_slices = 0, const double *ext_z = nullptr);
 // P[(c d_y + i) w + k] = WL[i w + k] * der[c ldd + k]
 template <typename T>
 cudaError_t launch_jac_init(int C, int d_y, int w, const T *WL, const T *der, int ldd, T *P,

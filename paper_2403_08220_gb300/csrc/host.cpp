@@ -97,6 +97,8 @@ struct dino_ctx {
   std::unique_ptr<dino::Server> server;
   // the device reads pageable host memory coherently (Grace: over NVLink-C2C)
   bool pageable_access = false;
+  // polls of the Cholesky diagonal-block flag before a kernel gives up
+  uint32_t flag_spins = 1u << 22;
 };
 
 namespace dino {
@@ -507,7 +509,18 @@ static int load_surrogate(dino_ctx *ctx, const dino_surrogate_desc *d) {
   if (geometry_smem_bytes(s->r, s->d_y, 1) > kSmemLimit ||
       geometry_smem_bytes(s->r, s->d_y, 0) > kSmemLimit)
     fail(DINO_EINVAL, "r=%d, d_y=%d exceed the per-chain shared-memory budget", s->r, s->d_y);
-  s->wb = s->d_y < s->r && s->d_y <= kMaxWbDy;
+  if (d->noise_map == DINO_NOISE_AUTO)
+    s->wb = s->d_y < s->r && s->d_y <= kMaxWbDy;
+  else if (d->noise_map == DINO_NOISE_CHOLESKY)
+    s->wb = false;
+  else if (d->noise_map == DINO_NOISE_PERTURBATION) {
+    if (!(s->d_y < s->r && s->d_y <= kMaxWbDy))
+      fail(DINO_EINVAL, "the perturbation noise map needs d_y < r and d_y <= %d (d_y=%d, r=%d)",
+           kMaxWbDy, s->d_y, s->r);
+    s->wb = true;
+  } else {
+    fail(DINO_EINVAL, "unknown noise map %d", d->noise_map);
+  }
   s->tc_gram = s->wb && s->precision == DINO_PREC_BF16 && s->L >= 2 && s->d_y <= 128;
   if (s->wb && (wb_smem_bytes(s->r, s->d_y, 1) > kSmemLimit ||
                 wb_smem_bytes(s->r, s->d_y, 0) > kSmemLimit))
@@ -886,6 +899,12 @@ struct Pool {
   // tensor path: bf16 slice planes of the prior draw (C x ldE) and of coef2 (C x ldD)
   __nv_bfloat16 *Ms = nullptr, *coef2s = nullptr;
   Work w;
+  // caller-supplied noise of the next transition (dino_chains_set_noise):
+  // one device buffer [xi C x r | xi2 C x d_y | z C x N | log_u C], and which
+  // parts are set
+  double *ext = nullptr;
+  size_t ext_bytes = 0;
+  bool ext_xi = false, ext_xi2 = false, ext_z = false, ext_log_u = false;
 };
 
 static void layout_pool(Pool &p, bool assign) {
@@ -973,6 +992,12 @@ static ReducedArgs reduced_args(const Pool &p) {
   a.counters = p.counters;
   a.sum_alpha = p.sum_alpha;
   a.err = p.err;
+  if (p.ext) {
+    const size_t C = p.C;
+    a.ext_xi = p.ext_xi ? p.ext : nullptr;
+    a.ext_xi2 = p.ext_xi2 ? p.ext + C * s->r : nullptr;
+    a.ext_log_u = p.ext_log_u ? p.ext + C * (s->r + s->d_y + (size_t)s->N) : nullptr;
+  }
   if (s->precision == DINO_PREC_FP64) {
     a.J = p.w.J64;
     a.f = p.w.f64;
@@ -1062,6 +1087,7 @@ static Pool *create_pool_on(dino_ctx *ctx, int sid, int C, double dt, uint64_t s
       });
     eval_surrogate(ctx, s, p->w, p->b, st);
     ReducedArgs ra = reduced_args(*p);
+    ra.flag_spins = ctx->flag_spins;
     launch(ctx, st, "geometry_init", [&] {
       return p->wb ? launch_wb_geometry(ra, 0, st) : launch_geometry(ra, 0, st);
     });
@@ -1100,6 +1126,9 @@ static void step_pool(dino_ctx *ctx, Pool &p) {
   cudaStream_t st = p.st;
   const double cs = std::sqrt(1.0 - p.sc * p.sc);
   ReducedArgs ra = reduced_args(p);
+  ra.flag_spins = ctx->flag_spins;
+  const double *ext_z =
+      p.ext && p.ext_z ? p.ext + (size_t)C * (r + s->d_y) : nullptr;
   launch(ctx, st, "propose", [&] {
     return p.wb ? launch_wb_propose(ra, st) : launch_propose(ra, st);
   });
@@ -1112,7 +1141,7 @@ static void step_pool(dino_ctx *ctx, Pool &p) {
     double *Mf = (double *)p.Mf, *coef2 = (double *)p.coef2, *m = (double *)p.m;
     launch(ctx, st, "prior_draw_f64", [&] {
       return launch_prior_draw<double>(C, s->n_grid, s->dSqrtLam, s->dS, p.seed, p.id_base,
-                                       STREAM_Z_ID, p.step, Mf, N, st);
+                                       STREAM_Z_ID, p.step, Mf, N, st, nullptr, 0, 0, 0, ext_z);
     });
     launch(ctx, st, "field_coef_f64", [&] {
       return gemm_coef<double>(C, r, N, Mf, N, s->dE, N, p.coef, r, cs, coef2, r, st);
@@ -1127,7 +1156,7 @@ static void step_pool(dino_ctx *ctx, Pool &p) {
     launch(ctx, st, "prior_draw_f32", [&] {
       return launch_prior_draw<float>(C, s->n_grid, s->fSqrtLam, s->fS, p.seed, p.id_base,
                                       STREAM_Z_ID, p.step, Mf, N, st, p.Ms, s->ldE,
-                                      (size_t)C * s->ldE, kFieldSlices);
+                                      (size_t)C * s->ldE, kFieldSlices, ext_z);
     });
     launch(ctx, st, "field_coef_tc", [&] {
       // coef2 (C x r) = coef - cs M E^T, written as bf16 slices
@@ -1180,10 +1209,16 @@ static void step_pool(dino_ctx *ctx, Pool &p) {
     });
   }
   p.step += 1;
+  p.ext_xi = p.ext_xi2 = p.ext_z = p.ext_log_u = false;  // caller noise is one-shot
 }
 
 static void destroy_pool(dino_ctx *ctx, int id) {
   Pool *p = get_pool(ctx, id);
+  if (p->ext) {
+    cudaStreamSynchronize(p->st);
+    dev_free(ctx, p->ext, p->ext_bytes);
+    p->ext = nullptr;
+  }
   if (p->async_mem) {
     dev_free_async(ctx, p->ar.base, p->ar.bytes, p->st);
   } else {
@@ -1228,6 +1263,7 @@ static void surrogate_eval(dino_ctx *ctx, int sid, int n, const double *x_host, 
     eval_surrogate(ctx, s, p.w, p.b, st);
     ReducedArgs ra = reduced_args(p);
     ra.noise_var = s->has_data ? s->noise_var : 1.0;
+    ra.flag_spins = ctx->flag_spins;
     launch(ctx, st, "geometry_init", [&] { return launch_geometry(ra, 0, st); });
     CK(cudaStreamSynchronize(st));
     std::vector<double> tmp;
@@ -1314,6 +1350,14 @@ struct Server {
   int steps_per_round = 8;
   int max_active = 32;
   size_t max_queue = 100000;
+  // first-fit admission may pass over the queue head only while it has
+  // waited less than this; after that nothing is admitted before it
+  double head_bypass_s = 2.0;
+  // an internal error outside any one request stops the server: every
+  // resident and queued request fails with it and submit refuses new ones
+  bool broken = false;
+  int broken_code = DINO_OK;
+  std::string broken_msg;
   uint64_t next_ticket = 1;
   int peak_active = 0;
   size_t peak_used = 0;
@@ -1452,11 +1496,19 @@ struct Server {
         ++k;
       }
     }
-    // admission in arrival order while the head fits the budget
-    while (!queue.empty() && (int)active.size() < max_active) {
-      Request *r = queue.front();
-      if (ctx->used + r->footprint > ctx->budget) break;
-      queue.pop_front();
+    // admission, first fit in arrival order: a request whose footprint fits
+    // the free budget is admitted even if an earlier, larger one does not
+    // fit yet, unless the queue head has waited longer than head_bypass_s
+    const double tnow = now_s();
+    for (auto it = queue.begin(); it != queue.end() && (int)active.size() < max_active;) {
+      Request *r = *it;
+      const bool head = it == queue.begin();
+      if (ctx->used + r->footprint > ctx->budget) {
+        if (head && tnow - r->t_submit > head_bypass_s) break;  // the head goes next
+        ++it;
+        continue;
+      }
+      it = queue.erase(it);
       int k = 0;
       for (size_t j = 1; j < streams.size(); ++j)
         if (load[j] < load[k]) k = (int)j;
@@ -1486,12 +1538,12 @@ struct Server {
       const int k = std::min(steps_per_round, r->req.n_steps - r->issued);
       try {
         for (int s = 0; s < k; ++s) step_pool(ctx, *r->pool);
+        CK(cudaEventRecord(r->ev[r->next_ev], r->pool->st));
       } catch (const Error &e) {
         fail_request(r, e.code, e.msg);
         continue;
       }
       r->issued += k;
-      CK(cudaEventRecord(r->ev[r->next_ev], r->pool->st));
       r->next_ev ^= 1;
       r->in_flight += 1;
       stream_rounds[sj] += 1;
@@ -1505,15 +1557,38 @@ struct Server {
     return did;
   }
 
+  // Fails every resident and queued request with `code` and stops admission.
+  void break_down(int code, const std::string &msg) {
+    broken = true;
+    broken_code = code;
+    broken_msg = msg;
+    for (Request *r : active)
+      if (r->state == 1) fail_request(r, code, "serving stopped: " + msg);
+    active.clear();
+    for (Request *r : queue) {
+      r->state = 3;
+      r->status = code;
+      r->err = "serving stopped before admission: " + msg;
+      r->t_done = now_s();
+    }
+    queue.clear();
+  }
+
   void loop() {
     std::unique_lock<std::recursive_mutex> lk(ctx->mu);
     cudaSetDevice(ctx->device);
     while (!stop) {
       bool did = false;
-      try {
-        did = pass();
-      } catch (...) {
-        did = false;
+      if (!broken) {
+        try {
+          did = pass();
+        } catch (const Error &e) {
+          break_down(e.code, e.msg);
+        } catch (const std::exception &e) {
+          break_down(DINO_ECUDA, std::string("internal error: ") + e.what());
+        } catch (...) {
+          break_down(DINO_ECUDA, "unknown internal error");
+        }
       }
       if (!did) {
         cv.wait_for(lk, std::chrono::microseconds(200));
@@ -1567,7 +1642,7 @@ static int guarded(dino_ctx *ctx, F &&fn) {
 
 extern "C" {
 
-int dino_version(void) { return 100; }
+int dino_version(void) { return 101; }
 
 int dino_init(dino_ctx **out, int device, size_t hbm_budget_bytes, void *stream,
               unsigned flags) {
@@ -1612,7 +1687,10 @@ int dino_destroy(dino_ctx *ctx) {
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
-    for (auto &kv : ctx->pools) dev_free(ctx, kv.second->ar.base, kv.second->ar.bytes);
+    for (auto &kv : ctx->pools) {
+      dev_free(ctx, kv.second->ar.base, kv.second->ar.bytes);
+      dev_free(ctx, kv.second->ext, kv.second->ext_bytes);
+    }
     ctx->pools.clear();
     for (auto &kv : ctx->surrogates) free_surrogate(ctx, kv.second.get());
     ctx->surrogates.clear();
@@ -1767,6 +1845,55 @@ int dino_chains_read_last(dino_ctx *ctx, int pool_id, double *b, double *mu, dou
   });
 }
 
+int dino_surrogate_query(dino_ctx *ctx, int surrogate_id, dino_surrogate_info *info) {
+  return guarded(ctx, [&] {
+    if (!info) fail(DINO_EINVAL, "info is NULL");
+    const Surrogate *s = get_surrogate(ctx, surrogate_id);
+    info->N = s->N;
+    info->r = s->r;
+    info->d_y = s->d_y;
+    info->n_layers = s->L;
+    info->precision = s->precision;
+    info->noise_map = s->wb ? DINO_NOISE_PERTURBATION : DINO_NOISE_CHOLESKY;
+    info->gram_on_tensor_cores = s->tc_gram ? 1 : 0;
+    info->fwd_slices = s->precision == DINO_PREC_BF16 ? s->fwd_slices : 0;
+    info->jac_slices = s->precision == DINO_PREC_BF16 ? s->jac_slices : 0;
+  });
+}
+
+int dino_chains_set_noise(dino_ctx *ctx, int pool_id, const double *xi, const double *xi2,
+                          const double *z, const double *log_u) {
+  return guarded(ctx, [&] {
+    cudaSetDevice(ctx->device);
+    Pool *p = get_pool(ctx, pool_id);
+    const Surrogate *s = p->s;
+    if (xi2 && !p->wb)
+      fail(DINO_EINVAL, "xi2 is only drawn by the perturbation noise map (this pool: Cholesky)");
+    const size_t C = p->C, r = s->r, dy = s->d_y, N = s->N;
+    const size_t bytes = C * (r + dy + N + 1) * sizeof(double);
+    if (!p->ext) {
+      p->ext = (double *)dev_alloc(ctx, bytes);
+      p->ext_bytes = bytes;
+    }
+    auto put = [&](const double *src, size_t off, size_t n) {
+      CK(cudaMemcpyAsync(p->ext + off, src, n * sizeof(double), cudaMemcpyHostToDevice, p->st));
+    };
+    if (xi) put(xi, 0, C * r);
+    if (xi2) put(xi2, C * r, C * dy);
+    if (z) put(z, C * (r + dy), C * N);
+    if (log_u) put(log_u, C * (r + dy + N), C);
+    CK(cudaStreamSynchronize(p->st));  // host arrays are not used after return
+    p->ext_xi = xi != nullptr;
+    p->ext_xi2 = xi2 != nullptr;
+    p->ext_z = z != nullptr;
+    p->ext_log_u = log_u != nullptr;
+  });
+}
+
+int dino_set_wait_limit(dino_ctx *ctx, uint32_t flag_spins) {
+  return guarded(ctx, [&] { ctx->flag_spins = flag_spins ? flag_spins : (1u << 22); });
+}
+
 int dino_chains_destroy(dino_ctx *ctx, int pool_id) {
   return guarded(ctx, [&] {
     cudaSetDevice(ctx->device);
@@ -1816,6 +1943,8 @@ int dino_serve_submit(dino_ctx *ctx, const dino_request *req, uint64_t *ticket) 
     cudaSetDevice(ctx->device);
     if (!ctx->server) ctx->server.reset(new Server(ctx, 4, 8, 32));
     Server &sv = *ctx->server;
+    if (sv.broken)
+      fail(sv.broken_code, "serving stopped after an internal error: %s", sv.broken_msg.c_str());
     if (sv.queue.size() >= sv.max_queue) fail(DINO_EBUSY, "serving queue is full");
     auto r = std::make_unique<Request>();
     r->ticket = sv.next_ticket++;

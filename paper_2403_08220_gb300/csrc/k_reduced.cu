@@ -122,7 +122,12 @@ __global__ void __launch_bounds__(kThreads) k_propose(ReducedArgs a) {
   const uint32_t chain = (uint32_t)(a.id_base + (uint64_t)c);
   for (int blk = threadIdx.x; blk < (r + 3) / 4; blk += blockDim.x) {
     double n4[4];
-    normals4_f64(philox_block(a.seed, STREAM_XI, a.step, chain, blk), n4);
+    if (a.ext_xi) {
+      for (int q = 0; q < 4; ++q)
+        n4[q] = 4 * blk + q < r ? a.ext_xi[(size_t)c * r + 4 * blk + q] : 0.0;
+    } else {
+      normals4_f64(philox_block(a.seed, STREAM_XI, a.step, chain, blk), n4);
+    }
     for (int q = 0; q < 4; ++q)
       if (4 * blk + q < r) vx[4 * blk + q] = z2[4 * blk + q] = n4[q];
   }
@@ -218,7 +223,12 @@ __global__ void __launch_bounds__(32 * kPropWarps) k_propose_warp(ReducedArgs a)
   const uint32_t chain = (uint32_t)(a.id_base + (uint64_t)c);
   for (int blk = lane; blk < (r + 3) / 4; blk += 32) {
     double n4[4];
-    normals4_f64(philox_block(a.seed, STREAM_XI, a.step, chain, blk), n4);
+    if (a.ext_xi) {
+      for (int q = 0; q < 4; ++q)
+        n4[q] = 4 * blk + q < r ? a.ext_xi[(size_t)c * r + 4 * blk + q] : 0.0;
+    } else {
+      normals4_f64(philox_block(a.seed, STREAM_XI, a.step, chain, blk), n4);
+    }
     for (int q = 0; q < 4; ++q)
       if (4 * blk + q < r) xi_s[w][4 * blk + q] = n4[q];
   }
@@ -341,7 +351,8 @@ __global__ void __launch_bounds__(kThreads) k_geometry(ReducedArgs a, int mode) 
   vv = block_sum(vv, red);
   if (threadIdx.x == 0) Ls[tri(r) + r] = A::from(1.0 + vv);
   __syncthreads();
-  cta_cholesky<A>(Ls, inv, r + 1, reinterpret_cast<int *>(red + 100), a.err);
+  cta_cholesky<A>(Ls, inv, r + 1, reinterpret_cast<int *>(red + 100), a.err,
+                  a.flag_spins);
   double ld = 0.0;
   for (int i = threadIdx.x; i < r; i += blockDim.x) ld += log(A::to(Ls[tri(i) + i]));
   const double hld_b = block_sum(ld, red);

@@ -160,7 +160,8 @@ template <typename T>
 __global__ void __launch_bounds__(kPriorThreads)
     k_prior_draw(int n, const T *__restrict__ sqrtlam, const T *__restrict__ S, uint64_t seed,
                  uint64_t id_base, uint32_t stream, uint32_t step, T *out, int ldo,
-                 __nv_bfloat16 *ms, int ldms, size_t ms_plane, int ms_slices) {
+                 __nv_bfloat16 *ms, int ldms, size_t ms_plane, int ms_slices,
+                 const double *__restrict__ ext_z) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int ld = prior_ld(n), nt = ld / 4, NN = ld * ld;
   T *X = reinterpret_cast<T *>(smraw);
@@ -183,12 +184,17 @@ __global__ void __launch_bounds__(kPriorThreads)
   }
   __syncthreads();
   for (int blk = threadIdx.x; blk < (N + 3) / 4; blk += blockDim.x) {
-    const uint4 w = philox_block(seed, stream, step, chain, blk);
     T z[4];
-    if constexpr (sizeof(T) == 8) {
-      normals4_f64(w, z);
+    if (ext_z) {
+      for (int q = 0; q < 4; ++q)
+        z[q] = 4 * blk + q < N ? (T)ext_z[(size_t)c * N + 4 * blk + q] : T(0);
     } else {
-      normals4_f32(w, z);
+      const uint4 w = philox_block(seed, stream, step, chain, blk);
+      if constexpr (sizeof(T) == 8) {
+        normals4_f64(w, z);
+      } else {
+        normals4_f32(w, z);
+      }
     }
     for (int q = 0; q < 4; ++q) {
       const int m = 4 * blk + q;
@@ -334,7 +340,7 @@ template <typename T>
 cudaError_t launch_prior_draw(int C, int n, const T *sqrtlam, const T *S, uint64_t seed,
                               uint64_t id_base, uint32_t stream, uint32_t step, T *out, int ldo,
                               cudaStream_t st, __nv_bfloat16 *ms, int ldms, size_t ms_plane,
-                              int ms_slices) {
+                              int ms_slices, const double *ext_z) {
   if (C <= 0) return cudaSuccess;
   if (ms && (sizeof(T) != 4 || ms_slices < 1 || ldms < n * n)) return cudaErrorInvalidValue;
   const size_t smem = prior_draw_smem_bytes(n, (int)sizeof(T));
@@ -342,7 +348,7 @@ cudaError_t launch_prior_draw(int C, int n, const T *sqrtlam, const T *S, uint64
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_prior_draw<T><<<C, kPriorThreads, smem, st>>>(n, sqrtlam, S, seed, id_base, stream, step, out,
-                                                   ldo, ms, ldms, ms_plane, ms_slices);
+                                                   ldo, ms, ldms, ms_plane, ms_slices, ext_z);
   return cudaGetLastError();
 }
 
@@ -390,7 +396,8 @@ template cudaError_t launch_broadcast<double>(int, size_t, const double *, doubl
 #define DINO_INST_DRAW(T)                                                                     \
   template cudaError_t launch_prior_draw<T>(int, int, const T *, const T *, uint64_t,         \
                                             uint64_t, uint32_t, uint32_t, T *, int,           \
-                                            cudaStream_t, __nv_bfloat16 *, int, size_t, int);
+                                            cudaStream_t, __nv_bfloat16 *, int, size_t, int, \
+                                            const double *);
 DINO_INST_DRAW(double)
 DINO_INST_DRAW(float)
 

@@ -414,7 +414,8 @@ __global__ void __launch_bounds__(kWbThreads, kWbMinBlocks) k_wb_geometry(Reduce
   for (int i = threadIdx.x; i < dy; i += blockDim.x) Ms[tri(dy) + i] = A::from(u[i]);
   if (threadIdx.x == 0) Ms[tri(dy) + dy] = A::from(1.0 + uu);
   __syncthreads();
-  cta_cholesky<A>(Ms, inv, dy + 1, reinterpret_cast<int *>(red + 100), a.err);
+  cta_cholesky<A>(Ms, inv, dy + 1, reinterpret_cast<int *>(red + 100), a.err,
+                  a.flag_spins);
   double ld = 0.0, ss = 0.0;
   for (int i = threadIdx.x; i < dy; i += blockDim.x) {
     ld += log(A::to(Ms[tri(i) + i]));
@@ -523,10 +524,20 @@ __global__ void __launch_bounds__(kWbThreads, kWbMinBlocks) k_wb_propose(Reduced
       for (int q = 0; q < 4; ++q) e4[q] = A::from(n4[q]);
     }
   };
+  // caller-supplied normals (FP64) instead of Philox
+  auto ext4 = [&](const double *x, int n, int blk, double n4[4], E e4[4]) {
+    for (int q = 0; q < 4; ++q) {
+      n4[q] = 4 * blk + q < n ? x[(size_t)c * n + 4 * blk + q] : 0.0;
+      e4[q] = A::from(n4[q]);
+    }
+  };
   for (int blk = threadIdx.x; blk < (r + 3) / 4; blk += blockDim.x) {
     double n4[4];
     E e4[4];
-    normals4(philox_block(a.seed, STREAM_XI, a.step, chain, blk), n4, e4);
+    if (a.ext_xi)
+      ext4(a.ext_xi, r, blk, n4, e4);
+    else
+      normals4(philox_block(a.seed, STREAM_XI, a.step, chain, blk), n4, e4);
     for (int q = 0; q < 4; ++q)
       if (4 * blk + q < r) {
         xi1[4 * blk + q] = n4[q];
@@ -536,7 +547,10 @@ __global__ void __launch_bounds__(kWbThreads, kWbMinBlocks) k_wb_propose(Reduced
   for (int blk = threadIdx.x; blk < (dy + 3) / 4; blk += blockDim.x) {
     double n4[4];
     E e4[4];
-    normals4(philox_block(a.seed, STREAM_XI2, a.step, chain, blk), n4, e4);
+    if (a.ext_xi2)
+      ext4(a.ext_xi2, dy, blk, n4, e4);
+    else
+      normals4(philox_block(a.seed, STREAM_XI2, a.step, chain, blk), n4, e4);
     for (int q = 0; q < 4; ++q)
       if (4 * blk + q < dy) xi2[4 * blk + q] = n4[q];
   }

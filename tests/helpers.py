@@ -11,11 +11,13 @@ import dataclasses
 import numpy as np
 
 from oracle import mlp, mmala, prior
-from workloads import (BASIS_DIS, BASIS_KLE, Workload, make_data, surrogate_inputs)
+from workloads import (BASIS_DIS, BASIS_KLE, SEED_CHAINS, Workload, make_data,
+                       surrogate_inputs)
 
 
 def variant(w: Workload, **kw) -> Workload:
-    return dataclasses.replace(w, **kw)
+    """A reshaped workload; unless given, its noise map is the library's choice."""
+    return dataclasses.replace(w, **{"noise_map": "auto", **kw})
 
 
 def oracle_setup(w: Workload):
@@ -30,6 +32,9 @@ def oracle_setup(w: Workload):
     return sur, E, D
 
 
+NOISE_CODES = {"auto": 0, "cholesky": 1, "perturbation": 2}
+
+
 def gpu_setup(dino, ctx, w: Workload, precision=None, fwd_slices=0, jac_slices=0):
     inp = surrogate_inputs(w)
     prec = precision if precision is not None else (
@@ -38,7 +43,7 @@ def gpu_setup(dino, ctx, w: Workload, precision=None, fwd_slices=0, jac_slices=0
         ctx, n_grid=w.n_grid, prior_gamma=w.prior_gamma, prior_delta=w.prior_delta, r=w.r,
         widths=w.widths, activation=w.activation, W=inp["Ws"], b=inp["bs"],
         basis_kind=w.basis_kind, basis_gauss=inp["G"], precision=prec,
-        fwd_slices=fwd_slices, jac_slices=jac_slices)
+        fwd_slices=fwd_slices, jac_slices=jac_slices, noise_map=NOISE_CODES[w.noise_map])
     # the library's own FP64 forward gives its copy of the noiseless data (an
     # FP64 twin with the same weights; the basis does not enter f)
     twin = dino.dino_load_surrogate(
@@ -50,6 +55,18 @@ def gpu_setup(dino, ctx, w: Workload, precision=None, fwd_slices=0, jac_slices=0
     y, nv = make_data(ev["f"][0], inp["eps"], w.noise_frac)
     dino.dino_set_data(ctx, sid, y, nv)
     return sid
+
+
+def noise_of(dino, ctx, sid) -> str:
+    """The proposal noise map the library reports for a loaded surrogate."""
+    return dino.dino_surrogate_query(ctx, sid)["noise_map"]
+
+
+def oracle_chains(dino, ctx, sid, w: Workload, sur, E, D, C, dt, **kw):
+    """Oracle chains of workload `w` with the noise map the library uses for `sid`."""
+    from oracle.chains import OracleChains
+    return OracleChains(sur, E, D, w.n_grid, w.prior_gamma, w.prior_delta, C, dt,
+                        seed=kw.pop("seed", SEED_CHAINS), noise=noise_of(dino, ctx, sid), **kw)
 
 
 def rel_err(a, b):

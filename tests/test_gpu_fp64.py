@@ -6,7 +6,8 @@ max(1, |b|)), accept decisions identical except within 1e-8 of the threshold.
 import numpy as np
 import pytest
 
-from helpers import gpu_setup, oracle_setup, rel_err, step_and_compare, variant
+from helpers import (gpu_setup, oracle_chains, oracle_setup, rel_err, step_and_compare,
+                     variant)
 from oracle import mmala, prior
 from oracle.chains import OracleChains
 from workloads import (ACT_GELU, ACT_IDENTITY, ACT_TANH, BASIS_DIS, BASIS_KLE, CONFIGS,
@@ -30,9 +31,8 @@ def ctx(dino):
     c.close()
 
 
-def _oracle_chains(w, sur, E, D, C, dt, ids=None):
-    return OracleChains(sur, E, D, w.n_grid, w.prior_gamma, w.prior_delta, C, dt,
-                        seed=SEED_CHAINS, chain_ids=ids)
+def _oracle_chains(dino, ctx, sid, w, sur, E, D, C, dt, ids=None):
+    return oracle_chains(dino, ctx, sid, w, sur, E, D, C, dt, chain_ids=ids)
 
 
 @pytest.mark.parametrize("kind", [BASIS_KLE, BASIS_DIS])
@@ -70,7 +70,7 @@ def test_chains_small_config_match_oracle(dino, ctx, dt, steps):
     sur, E, D = oracle_setup(w)
     pool = dino.dino_chains_create(ctx, sid, w.n_chains, dt, SEED_CHAINS)
     st = dino.dino_chains_read(ctx, pool, w.n_chains, w.r, w.N)
-    och = _oracle_chains(w, sur, E, D, w.n_chains, dt)
+    och = _oracle_chains(dino, ctx, sid, w, sur, E, D, w.n_chains, dt)
     assert rel_err(st["m"], och.m) <= TOL
     assert rel_err(st["m_r"], och.m_r) <= TOL
     assert rel_err(st["phi"], och.geo.phi) <= TOL
@@ -90,7 +90,7 @@ def test_chains_r200_match_oracle(dino, ctx, dt):
     sid = gpu_setup(dino, ctx, w)
     sur, E, D = oracle_setup(w)
     pool = dino.dino_chains_create(ctx, sid, C, dt, SEED_CHAINS)
-    och = _oracle_chains(w, sur, E, D, C, dt)
+    och = _oracle_chains(dino, ctx, sid, w, sur, E, D, C, dt)
     step_and_compare(dino, ctx, pool, och, w, C, 3, tol=TOL)
     dino.dino_chains_destroy(ctx, pool)
     dino.dino_unload_surrogate(ctx, sid)
@@ -104,7 +104,7 @@ def test_full_size_fp64_sampled_chains(dino, ctx):
     sid = gpu_setup(dino, ctx, w)
     sur, E, D = oracle_setup(w)
     pool = dino.dino_chains_create(ctx, sid, C, w.dt, SEED_CHAINS)
-    och = _oracle_chains(w, sur, E, D, len(sample), w.dt, ids=sample)
+    och = _oracle_chains(dino, ctx, sid, w, sur, E, D, len(sample), w.dt, ids=sample)
     step_and_compare(dino, ctx, pool, och, w, C, 2, tol=TOL, sample=sample)
     dino.dino_chains_destroy(ctx, pool)
     dino.dino_unload_surrogate(ctx, sid)
@@ -118,7 +118,7 @@ def test_ragged_sizes_and_single_chain(dino, ctx):
     sur, E, D = oracle_setup(w)
     for C, dt in [(1, 0.05), (37, 0.01)]:
         pool = dino.dino_chains_create(ctx, sid, C, dt, SEED_CHAINS)
-        och = _oracle_chains(w, sur, E, D, C, dt)
+        och = _oracle_chains(dino, ctx, sid, w, sur, E, D, C, dt)
         step_and_compare(dino, ctx, pool, och, w, C, 5, tol=TOL)
         dino.dino_chains_destroy(ctx, pool)
     dino.dino_unload_surrogate(ctx, sid)
@@ -144,7 +144,7 @@ def test_single_layer_surrogate(dino, ctx):
     sid = gpu_setup(dino, ctx, w)
     sur, E, D = oracle_setup(w)
     pool = dino.dino_chains_create(ctx, sid, 8, 0.3, SEED_CHAINS)
-    och = _oracle_chains(w, sur, E, D, 8, 0.3)
+    och = _oracle_chains(dino, ctx, sid, w, sur, E, D, 8, 0.3)
     step_and_compare(dino, ctx, pool, och, w, 8, 4, tol=TOL)
     dino.dino_chains_destroy(ctx, pool)
     dino.dino_unload_surrogate(ctx, sid)
@@ -158,8 +158,7 @@ def test_given_initial_field(dino, ctx):
     m0 = prior.prior_sample(w.n_grid, w.prior_gamma, w.prior_delta,
                             np.random.default_rng(9).standard_normal((C, w.N)))
     pool = dino.dino_chains_create(ctx, sid, C, 0.002, SEED_CHAINS, 0, m0)
-    och = OracleChains(sur, E, D, w.n_grid, w.prior_gamma, w.prior_delta, C, 0.002,
-                       seed=SEED_CHAINS, m0=m0)
+    och = oracle_chains(dino, ctx, sid, w, sur, E, D, C, 0.002, m0=m0)
     step_and_compare(dino, ctx, pool, och, w, C, 10, tol=TOL)
     dino.dino_chains_destroy(ctx, pool)
     dino.dino_unload_surrogate(ctx, sid)
@@ -221,7 +220,7 @@ def test_r1_and_zero_steps(dino, ctx):
     st = dino.dino_chains_step(ctx, pool, 0)
     after = dino.dino_chains_read(ctx, pool, 9, w.r, w.N)
     assert st["proposals"] == 0 and np.array_equal(before["m_r"], after["m_r"])
-    och = _oracle_chains(w, sur, E, D, 9, 0.7)
+    och = _oracle_chains(dino, ctx, sid, w, sur, E, D, 9, 0.7)
     acc, _, _ = step_and_compare(dino, ctx, pool, och, w, 9, 40, tol=TOL)
     assert 0.0 < np.mean(acc) <= 1.0
     dino.dino_chains_destroy(ctx, pool)
@@ -257,14 +256,15 @@ def test_zero_jacobian_reduces_to_pcn(dino, ctx):
 def test_noise_map_boundary_matches_oracle(dino, ctx, dy):
     """r = 200: d_y = 192 runs the Woodbury path (perturbation noise), d_y = 193
     the r-sized path (Cholesky noise); both follow the oracle's rule at 1e-10."""
-    from oracle import mmala as om
     w = variant(CONFIGS["small_fp64"], n_grid=15, r=200, widths=[200, 64, dy],
                 activation=ACT_TANH, noise_frac=0.2)
-    assert om.noise_map(w.r, dy) == ("perturbation" if dy == 192 else "cholesky")
     sid = gpu_setup(dino, ctx, w)
+    info = dino.dino_surrogate_query(ctx, sid)
+    assert info["noise_map"] == ("perturbation" if dy == 192 else "cholesky")
+    assert (info["r"], info["d_y"], info["N"]) == (w.r, dy, w.N)
     sur, E, D = oracle_setup(w)
     pool = dino.dino_chains_create(ctx, sid, 3, 2e-4, SEED_CHAINS)
-    och = _oracle_chains(w, sur, E, D, 3, 2e-4)
+    och = _oracle_chains(dino, ctx, sid, w, sur, E, D, 3, 2e-4)
     step_and_compare(dino, ctx, pool, och, w, 3, 3, tol=TOL)
     dino.dino_chains_destroy(ctx, pool)
     dino.dino_unload_surrogate(ctx, sid)

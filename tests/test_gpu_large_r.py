@@ -7,7 +7,8 @@ Shapes follow the largest posteriors of the heterogeneous workload
 import numpy as np
 import pytest
 
-from helpers import gpu_setup, oracle_setup, rel_err, step_and_compare, variant
+from helpers import (gpu_setup, oracle_chains, oracle_setup, rel_err, step_and_compare,
+                     variant)
 from oracle import mmala
 from oracle.chains import OracleChains
 from workloads import BASIS_DIS, CONFIGS, SEED_CHAINS, heterogeneous_workloads
@@ -41,8 +42,7 @@ def test_fp64_r256_global_factor_matches_oracle(dino, ctx):
         assert rel_err(g[k], ref) <= 1e-10, k
     for dt in (0.5, 1e-3):
         pool = dino.dino_chains_create(ctx, sid, 5, dt, SEED_CHAINS)
-        och = OracleChains(sur, E, D, w.n_grid, w.prior_gamma, w.prior_delta, 5, dt,
-                           seed=SEED_CHAINS)
+        och = oracle_chains(dino, ctx, sid, w, sur, E, D, 5, dt)
         step_and_compare(dino, ctx, pool, och, w, 5, 3, tol=1e-10)
         dino.dino_chains_destroy(ctx, pool)
     dino.dino_unload_surrogate(ctx, sid)
@@ -61,18 +61,16 @@ def test_bf16_large_r_meets_precision_bars(dino, ctx, idx):
     assert rel_err(g["f"], o.f) <= 1e-4
     C = 4
     pool = dino.dino_chains_create(ctx, sid, C, w.dt, SEED_CHAINS)
-    och = OracleChains(sur, E, D, w.n_grid, w.prior_gamma, w.prior_delta, C, w.dt,
-                       seed=SEED_CHAINS)
+    och = oracle_chains(dino, ctx, sid, w, sur, E, D, C, w.dt)
     dino.dino_chains_step(ctx, pool, 1, stats=False)
     och.step()
     last = dino.dino_chains_read_last(ctx, pool, C, w.r)
     mu_err = np.linalg.norm(last["mu"] - och.last["mu"], axis=1) / np.linalg.norm(
         och.last["mu"], axis=1)
-    # the FP32-accumulated Gauss-Newton product and forward pass bound the mean
-    # error by ~1e-8 cond(I + H) (measured: 2.7e-4 at cond 4.9e4, r = 256;
-    # 1.2e-3 at cond 1.2e5, r = 400); the 1e-3 bar holds up to cond ~ 5e4
-    cond = max(np.linalg.cond(np.eye(w.r) + h) for h in mmala.geometry(sur, och.m_r).H)
-    assert mu_err.max() <= max(1e-3, 2e-8 * cond)
+    # the bar as stated, at the conditioning of prior-draw starts (cond(I + H)
+    # about 1e5 at r = 400): J^T J is accumulated in FP32 over chunks of 64
+    # rows and the chunk sums in double-float
+    assert mu_err.max() <= 1e-3, mu_err
     scale = np.maximum(1.0, och.last["log_rho_scale"])
     assert np.max(np.abs(last["log_rho"] - och.last["log_rho"]) / scale) <= 1e-3
     dino.dino_chains_destroy(ctx, pool)

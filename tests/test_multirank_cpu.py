@@ -41,7 +41,7 @@ def _worker(rank, world, port, out):
     base = bench.shard_base(rank, C_PER_RANK)
     ids = np.arange(base, base + C_PER_RANK)
     och = OracleChains(sur, E, D, w.n_grid, w.prior_gamma, w.prior_delta, C_PER_RANK, 0.01,
-                       seed=77, chain_ids=ids)
+                       seed=77, chain_ids=ids, noise="cholesky")
     och.step(STEPS)
     mine = torch.tensor(och.m_r)
     gathered = [torch.zeros_like(mine) for _ in range(world)]
@@ -75,7 +75,7 @@ def test_two_gloo_ranks_reproduce_one_process():
     from oracle.chains import OracleChains
     w, (sur, E, D) = _setup()
     ref = OracleChains(sur, E, D, w.n_grid, w.prior_gamma, w.prior_delta, world * C_PER_RANK,
-                       0.01, seed=77)
+                       0.01, seed=77, noise="cholesky")
     ref.step(STEPS)
     assert np.allclose(m_r, ref.m_r, rtol=0, atol=1e-12)
     assert tmax == float(world)

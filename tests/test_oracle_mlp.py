@@ -68,3 +68,31 @@ def test_identity_network_is_composed_affine_map():
     c = Ws[1] @ bs[0] + bs[1]
     assert np.allclose(f, W @ x + c, atol=1e-14)
     assert np.allclose(mlp.jacobian_reverse(Ws, mlp.ACT_IDENTITY, zs), W, atol=1e-14)
+
+
+# Known values of a hand-written 2 -> 2 -> 1 network: W1 = [[1, -1], [0.5, 2]],
+# b1 = [0.1, -0.2], W2 = [[2, -3]], b2 = [0.25] at x = (0.3, 0.7), so the hidden
+# pre-activations are z = (-0.3, 1.35) and f = 2 s(-0.3) - 3 s(1.35) + 0.25,
+# J = W2 diag(s'(z)) W1.  The numbers were evaluated once from these closed
+# forms at 30 significant digits (arbitrary-precision tanh and erf); a bias
+# added after the activation, a dropped bias or a transposed weight changes
+# them in the second digit.
+_KNOWN = {
+    mlp.ACT_TANH: (-2.954785088561202874551505, [1.47622764874976700790838,
+                                                 -3.246459023267223999740097]),
+    mlp.ACT_GELU: (-3.670795781365150178026406, [-1.156669784365503845580935,
+                                                 -7.303401469190916752434359]),
+}
+
+
+@pytest.mark.parametrize("kind", [mlp.ACT_TANH, mlp.ACT_GELU])
+def test_nonlinear_forward_and_jacobian_known_values(kind):
+    Ws = [np.array([[1.0, -1.0], [0.5, 2.0]]), np.array([[2.0, -3.0]])]
+    bs = [np.array([0.1, -0.2]), np.array([0.25])]
+    x = np.array([[0.3, 0.7]])
+    f, zs = mlp.forward(Ws, bs, kind, x)
+    f_ref, J_ref = _KNOWN[kind]
+    assert abs(f[0, 0] - f_ref) <= 1e-15 * abs(f_ref)
+    assert np.allclose(zs[0][0], [-0.3, 1.35], rtol=0, atol=1e-15)
+    for J in (mlp.jacobian_reverse(Ws, kind, zs), mlp.jacobian_forward(Ws, kind, zs)):
+        assert np.allclose(J[0, 0], J_ref, rtol=1e-15, atol=0)

@@ -81,7 +81,7 @@ def test_p2_linear_surrogate_chain_is_exact_ar1():
     dt = 0.5
     s = mmala.s_of_dt(dt)
     m0 = np.zeros(n * n)
-    ch = OracleChains(sur, E, D, n, GAMMA, DELTA, C, dt, seed=31, m0=m0)
+    ch = OracleChains(sur, E, D, n, GAMMA, DELTA, C, dt, seed=31, m0=m0, noise="cholesky")
     W = sur.Ws[1] @ sur.Ws[0]
     c = sur.Ws[1] @ sur.bs[0] + sur.bs[1]
     Cpost = np.linalg.inv(np.eye(r) + W.T @ W / sur.noise_var)
@@ -204,7 +204,7 @@ def test_p8_r1_chain_moments_match_quadrature():
     mean_q = np.trapezoid(x * p, x)
     var_q = np.trapezoid((x - mean_q) ** 2 * p, x)
     C = 3000
-    ch = OracleChains(sur, E, D, n, GAMMA, DELTA, C, dt, seed=77)
+    ch = OracleChains(sur, E, D, n, GAMMA, DELTA, C, dt, seed=77, noise="cholesky")
     ch.step(60)
     acc = []
     samples = []
@@ -237,8 +237,6 @@ def test_p9_perturbation_map_has_the_proposal_covariance():
     # dropping the observation-space normals (or mis-scaling K) breaks the law
     T1 = T[:, :r]
     assert np.abs(T1 @ T1.T - cov_ref).max() > 1e-3 * np.abs(cov_ref).max()
-    assert mmala.noise_map(r, dy) == "perturbation" and mmala.noise_map(dy, r) == "cholesky"
-    assert mmala.noise_map(400, 192) == "perturbation" and mmala.noise_map(400, 193) == "cholesky"
 
 
 def test_p9_perturbation_chain_is_exact_ar1_for_linear_surrogate():
@@ -247,8 +245,8 @@ def test_p9_perturbation_chain_is_exact_ar1_for_linear_surrogate():
     E, D = prior.kle_basis(n, GAMMA, DELTA, r)
     C, dt = 4000, 0.5
     s = mmala.s_of_dt(dt)
-    ch = OracleChains(sur, E, D, n, GAMMA, DELTA, C, dt, seed=32, m0=np.zeros(n * n))
-    assert ch.noise == "perturbation"
+    ch = OracleChains(sur, E, D, n, GAMMA, DELTA, C, dt, seed=32, m0=np.zeros(n * n),
+                      noise="perturbation")
     W = sur.Ws[1] @ sur.Ws[0]
     c = sur.Ws[1] @ sur.bs[0] + sur.bs[1]
     Cpost = np.linalg.inv(np.eye(r) + W.T @ W / sur.noise_var)
@@ -261,3 +259,30 @@ def test_p9_perturbation_chain_is_exact_ar1_for_linear_surrogate():
         w = np.linalg.solve(np.linalg.cholesky(cov), (ch.m_r - mean).T).T
         assert np.all(np.abs(w.mean(0)) < 5 / np.sqrt(C))
         assert np.abs(np.cov(w.T) - np.eye(r)).max() < 7 / np.sqrt(C)
+
+
+def test_given_noise_reproduces_the_philox_step():
+    """Feeding a step the arrays the chain would draw itself changes nothing;
+    feeding other arrays changes the proposal."""
+    from oracle import philox
+    n, r, dy = 3, 5, 2
+    sur = _surrogate([r, 4, dy], mlp.ACT_TANH, noise_var=0.3)
+    E, D = prior.kle_basis(n, GAMMA, DELTA, r)
+    C, dt = 6, 0.3
+    for noise in ("cholesky", "perturbation"):
+        a = OracleChains(sur, E, D, n, GAMMA, DELTA, C, dt, seed=5, noise=noise)
+        b = OracleChains(sur, E, D, n, GAMMA, DELTA, C, dt, seed=5, noise=noise)
+        ids = np.arange(C, dtype=np.uint64)
+        given = dict(xi=philox.normals(5, philox.STREAM_XI, 0, ids, r),
+                     xi2=philox.normals(5, philox.STREAM_XI2, 0, ids, dy),
+                     z=philox.normals(5, philox.STREAM_Z, 0, ids, n * n),
+                     log_u=np.log(philox.uniform(5, philox.STREAM_U, 0, ids)))
+        a.step()
+        b.step(noise=given)
+        for k in ("b", "log_rho", "log_u", "m_new"):
+            assert np.array_equal(a.last[k], b.last[k]), k
+        b.step(noise=dict(xi=np.zeros((C, r))))
+        a.step()
+        assert not np.allclose(a.last["b"], b.last["b"])
+    with pytest.raises(ValueError):
+        OracleChains(sur, E, D, n, GAMMA, DELTA, C, dt, seed=5, noise="auto")

@@ -56,6 +56,10 @@ class Workload:
     noise_frac: float = 0.01    # sigma = noise_frac * RMS(noiseless observables)
     precision: str = "fp64"
     seed_offset: int = 0        # added to every seed (serving requests)
+    # proposal noise map the chains use: "cholesky" (L^-T xi), "perturbation"
+    # ((I + H)^-1 (xi + K^T xi2)) or "auto" (the library's choice, reported by
+    # dino_surrogate_query); both are the same proposal law
+    noise_map: str = "auto"
 
     @property
     def N(self) -> int:
@@ -70,13 +74,14 @@ class Workload:
 CONFIGS = {
     "small_fp64": Workload("small_fp64", n_grid=33, r=16, widths=[16, 64, 64, 49],
                            activation=ACT_TANH, basis_kind=BASIS_KLE,
-                           n_chains=64, n_steps=200),
+                           n_chains=64, n_steps=200, noise_map="cholesky"),
     "r200_kle_fp64": Workload("r200_kle_fp64", n_grid=65, r=200, widths=[200, 400, 400, 100],
                               activation=ACT_GELU, basis_kind=BASIS_KLE,
-                              n_chains=4096, n_steps=1000),
+                              n_chains=4096, n_steps=1000, noise_map="perturbation"),
     "r200_dis_bf16": Workload("r200_dis_bf16", n_grid=65, r=200, widths=[200, 400, 400, 100],
                               activation=ACT_GELU, basis_kind=BASIS_DIS,
-                              n_chains=16384, n_steps=1000, precision="bf16"),
+                              n_chains=16384, n_steps=1000, precision="bf16",
+                              noise_map="perturbation"),
 }
 
 
