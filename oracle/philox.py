@@ -19,7 +19,8 @@ normals 4k .. 4k+3.
 Streams: XI (reduced proposal noise of Algorithm 1), U (the uniform of its
 accept test), Z (prior draw for the complement, Prop. 5.1), INIT (prior draw
 of the initial state), XI2 (the d_y observation-space normals of the
-perturbation noise map, see `mmala.reduced_proposal_perturbation`).
+perturbation noise map, see `mmala.reduced_proposal_perturbation`), U2 (the
+uniform of the second, true-model stage of delayed acceptance, Algorithm 1).
 """
 from __future__ import annotations
 
@@ -30,6 +31,7 @@ STREAM_U = 1
 STREAM_Z = 2
 STREAM_INIT = 3
 STREAM_XI2 = 4
+STREAM_U2 = 5
 
 _M0 = np.uint64(0xD2511F53)
 _M1 = np.uint64(0xCD9E8D57)
