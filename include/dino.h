@@ -173,6 +173,7 @@ typedef struct {
   int noise_map;
   int gram_on_tensor_cores;
   int fwd_slices, jac_slices;
+  int true_model_rank;  /* r_t of an attached true map, 0 if none */
 } dino_surrogate_info;
 
 int dino_surrogate_query(dino_ctx *ctx, int surrogate_id, dino_surrogate_info *info);
@@ -224,7 +225,10 @@ typedef struct {
   uint64_t proposals;   /* chain-steps performed */
   uint64_t accepts;
   uint64_t nan_rejects; /* proposals rejected because log rho was not finite */
-  double sum_alpha;     /* sum over proposals of min(1, rho) */
+  double sum_alpha;     /* sum over proposals of min(1, rho) (first stage) */
+  uint64_t stage1_accepts; /* proposals accepted by the first (surrogate) stage;
+                              equals accepts unless the surrogate has a true
+                              model (delayed acceptance) */
 } dino_step_stats;
 
 /* Advance every chain of the pool by n_steps transitions.  Each transition:
@@ -263,14 +267,55 @@ int dino_chains_read_last(dino_ctx *ctx, int pool_id, double *b, double *mu,
  *                        M = sum_q sqrt(lambda_q) z_q eta_q (full KLE, mode
  *                        q = (kx-1) + n_grid (ky-1));
  *   log_u n_chains       the log of the accept uniform (accept iff
- *                        log_u <= min(0, log rho)).
+ *                        log_u <= min(0, log rho));
+ *   log_u2 n_chains      the log of the second-stage uniform of delayed
+ *                        acceptance (EINVAL without a true model).
  * Any pointer may be NULL (that stream stays Philox).  Host arrays, copied
  * before return; they apply to exactly one transition, after which every
  * stream is Philox again.  The first call allocates a device buffer of
- * n_chains (r + d_y + N + 1) doubles for the pool.
+ * n_chains (r + d_y + N + 2) doubles for the pool.
  * Errors: ENOTFOUND, EINVAL, ENOMEM. */
 int dino_chains_set_noise(dino_ctx *ctx, int pool_id, const double *xi, const double *xi2,
-                          const double *z, const double *log_u);
+                          const double *z, const double *log_u, const double *log_u2);
+
+/* ---- delayed acceptance (Algorithm 1, lines 7-13) ----------------------- */
+
+/* The true parameter-to-observable map of the second stage.  The paper's are
+ * PDE solves; this library takes a stand-in of the same role that also sees
+ * the field outside the surrogate's reduced basis: G(m) = f_t(E_t m), with
+ * E_t an r_t x N encoder (host, row-major, r_t <= N) and f_t an MLP
+ * (n_layers affine layers, widths[0] = r_t, widths[n_layers] = d_y, the
+ * activation on every hidden layer).  Its data misfit uses the surrogate's
+ * data: Phi(m) = |G(m) - y|^2 / (2 noise_var). */
+typedef struct {
+  int r_t;
+  const double *E_t;
+  int n_layers;
+  const int *widths;
+  int activation;
+  const double *const *W;
+  const double *const *b;
+} dino_true_model_desc;
+
+/* Attach a true map to a surrogate (desc == NULL detaches it).  Pools created
+ * afterwards run the two-stage transition of Algorithm 1: the first stage
+ * tests rho_r^(1) (eq:da_dino_trr_1) as before; a chain that passes draws
+ * its complement (only then), evaluates Phi at the full proposal m^dagger
+ * (Prop. 5.1) and moves only if log u2 <= min(0, log rho^(2)) with
+ * log rho^(2) = Phi(m_j) - Phi(m^dagger) + Phi~(m_r^dagger) - Phi~(m_r,j)
+ * (eq:da_dino_trr_2), u2 from its own Philox stream (5).  The chain state
+ * adds E_t m and Phi(m).  Copied before return; the precision of the
+ * surrogate applies (BF16: three bf16 slices per operand, FP32 accumulation).
+ * Errors: ENOTFOUND, ESTATE (pools of the surrogate exist), EINVAL,
+ * ENUMERIC, ENOMEM. */
+int dino_set_true_model(dino_ctx *ctx, int surrogate_id, const dino_true_model_desc *desc);
+
+/* What the last transition of a delayed-acceptance pool computed in its
+ * second stage (any output may be NULL, each n_chains long): Phi(m) of the
+ * current state, log rho^(2) (NaN where the first stage rejected), log u2
+ * and the first-stage flags (0/1).  Errors: ENOTFOUND, ESTATE (no true model). */
+int dino_chains_read_da(dino_ctx *ctx, int pool_id, double *phi_true, double *log_rho2,
+                        double *log_u2, int *stage1);
 
 /* Free a chain pool's device memory (after its stream has drained); the
  * pool id is invalid afterwards.  Errors: ENOTFOUND. */

@@ -64,12 +64,20 @@ class _Info(ct.Structure):
     _fields_ = [("N", ct.c_int), ("r", ct.c_int), ("d_y", ct.c_int), ("n_layers", ct.c_int),
                 ("precision", ct.c_int), ("noise_map", ct.c_int),
                 ("gram_on_tensor_cores", ct.c_int), ("fwd_slices", ct.c_int),
-                ("jac_slices", ct.c_int)]
+                ("jac_slices", ct.c_int), ("true_model_rank", ct.c_int)]
 
 
 class _Stats(ct.Structure):
     _fields_ = [("proposals", ct.c_uint64), ("accepts", ct.c_uint64),
-                ("nan_rejects", ct.c_uint64), ("sum_alpha", ct.c_double)]
+                ("nan_rejects", ct.c_uint64), ("sum_alpha", ct.c_double),
+                ("stage1_accepts", ct.c_uint64)]
+
+
+class _TrueDesc(ct.Structure):
+    _fields_ = [("r_t", ct.c_int), ("E_t", ct.POINTER(ct.c_double)), ("n_layers", ct.c_int),
+                ("widths", ct.POINTER(ct.c_int)), ("activation", ct.c_int),
+                ("W", ct.POINTER(ct.POINTER(ct.c_double))),
+                ("b", ct.POINTER(ct.POINTER(ct.c_double)))]
 
 
 class _Request(ct.Structure):
@@ -107,7 +115,9 @@ _SIGNATURES = {
     "dino_chains_read_last": ([_P, _I, _D, _D, _D, _D, ct.POINTER(_I)], _I),
     "dino_chains_destroy": ([_P, _I], _I),
     "dino_surrogate_query": ([_P, _I, ct.POINTER(_Info)], _I),
-    "dino_chains_set_noise": ([_P, _I, _D, _D, _D, _D], _I),
+    "dino_chains_set_noise": ([_P, _I, _D, _D, _D, _D, _D], _I),
+    "dino_set_true_model": ([_P, _I, ct.POINTER(_TrueDesc)], _I),
+    "dino_chains_read_da": ([_P, _I, _D, _D, _D, ct.POINTER(_I)], _I),
     "dino_set_wait_limit": ([_P, ct.c_uint32], _I),
     "dino_launch_count": ([_P], ct.c_uint64),
     "dino_kernel_times": ([_P, ct.c_char_p, _D, ct.POINTER(ct.c_uint64), _I, ct.POINTER(_I), _I],
@@ -269,7 +279,7 @@ def dino_chains_step(ctx: Ctx, pool: int, n_steps: int, stats: bool = True):
     if not stats:
         return None
     return dict(proposals=st.proposals, accepts=st.accepts, nan_rejects=st.nan_rejects,
-                sum_alpha=st.sum_alpha)
+                sum_alpha=st.sum_alpha, stage1_accepts=st.stage1_accepts)
 
 
 def dino_chains_read(ctx: Ctx, pool: int, C: int, r: int, N: int, field: bool = True) -> dict:
@@ -304,10 +314,38 @@ def dino_surrogate_query(ctx: Ctx, sid: int) -> dict:
     return out
 
 
-def dino_chains_set_noise(ctx: Ctx, pool: int, xi=None, xi2=None, z=None, log_u=None):
+def dino_chains_set_noise(ctx: Ctx, pool: int, xi=None, xi2=None, z=None, log_u=None,
+                          log_u2=None):
     """Caller noise for the pool's next transition (None keeps Philox for that stream)."""
-    arrs = [None if a is None else _f64(a) for a in (xi, xi2, z, log_u)]
+    arrs = [None if a is None else _f64(a) for a in (xi, xi2, z, log_u, log_u2)]
     _check(ctx, lib().dino_chains_set_noise(ctx.ptr, pool, *[_dptr(a) for a in arrs]))
+
+
+def dino_set_true_model(ctx: Ctx, sid: int, E_t=None, W=None, b=None, activation=0):
+    """Attach the true map G(m) = f_t(E_t m) of delayed acceptance (E_t None detaches)."""
+    if E_t is None:
+        _check(ctx, lib().dino_set_true_model(ctx.ptr, sid, None))
+        return
+    Et = _f64(E_t)
+    Ws = [_f64(w) for w in W]
+    bs = [_f64(x) for x in b]
+    L = len(Ws)
+    widths = [Et.shape[0]] + [w.shape[0] for w in Ws]
+    wid = (ct.c_int * (L + 1))(*widths)
+    Wp = (ct.POINTER(ct.c_double) * L)(*[_dptr(w) for w in Ws])
+    bp = (ct.POINTER(ct.c_double) * L)(*[_dptr(x) for x in bs])
+    d = _TrueDesc(Et.shape[0], _dptr(Et), L, wid, int(activation), Wp, bp)
+    _check(ctx, lib().dino_set_true_model(ctx.ptr, sid, ct.byref(d)))
+
+
+def dino_chains_read_da(ctx: Ctx, pool: int, C: int) -> dict:
+    out = dict(phi_true=np.empty(C), log_rho2=np.empty(C), log_u2=np.empty(C),
+               stage1=np.empty(C, dtype=np.int32))
+    _check(ctx, lib().dino_chains_read_da(ctx.ptr, pool, _dptr(out["phi_true"]),
+                                          _dptr(out["log_rho2"]), _dptr(out["log_u2"]),
+                                          out["stage1"].ctypes.data_as(ct.POINTER(_I))))
+    out["stage1"] = out["stage1"].astype(bool)
+    return out
 
 
 def dino_set_wait_limit(ctx: Ctx, flag_spins: int):
@@ -386,7 +424,8 @@ def dino_serve_submit(ctx: Ctx, sid: int, n_chains: int, n_steps: int, dt: float
 def _result(ctx, ticket, res):
     out = _SERVE_OUT.pop((ctx.ptr.value, ticket))
     out.update(stats=dict(proposals=res.stats.proposals, accepts=res.stats.accepts,
-                          nan_rejects=res.stats.nan_rejects, sum_alpha=res.stats.sum_alpha),
+                          nan_rejects=res.stats.nan_rejects, sum_alpha=res.stats.sum_alpha,
+                          stage1_accepts=res.stats.stage1_accepts),
                queue_s=res.queue_s, latency_s=res.latency_s)
     return out
 

@@ -727,7 +727,9 @@ __device__ void form_gram_f32(const float *X, int m, int n, int ldx, double inv_
 }
 
 // The accept test log u <= min(0, log rho) (Algorithm 1; NaN rejects), the
-// counters, and the scalar state of an accepted chain.  Thread 0 only.
+// counters ([0] accepts, [1] non-finite rejects, [2] first-stage accepts),
+// and the scalar state of an accepted chain, or with delayed acceptance its
+// staging for the second stage.  Thread 0 only.
 __device__ bool accept_test(const ReducedArgs &a, int c, double lr, double phi_b, double hld_b) {
   const uint32_t chain = (uint32_t)(a.id_base + (uint64_t)c);
   const double log_u =
@@ -739,11 +741,17 @@ __device__ bool accept_test(const ReducedArgs &a, int c, double lr, double phi_b
   a.log_u[c] = log_u;
   a.acc[c] = accept ? 1 : 0;
   if (accept) {
-    a.acc_count[c] += 1;
-    atomicAdd(&a.counters[0], 1ull);
-    a.phi[c] = phi_b;
-    a.hld[c] = hld_b;
-    a.cur[c] ^= 1;
+    atomicAdd(&a.counters[2], 1ull);  // first-stage accepts
+    if (a.da) {  // delayed acceptance: staged for the second stage
+      a.phi_st[c] = phi_b;
+      a.hld_st[c] = hld_b;
+    } else {
+      a.acc_count[c] += 1;
+      atomicAdd(&a.counters[0], 1ull);
+      a.phi[c] = phi_b;
+      a.hld[c] = hld_b;
+      a.cur[c] ^= 1;
+    }
   }
   if (!finite) atomicAdd(&a.counters[1], 1ull);
   atomicAdd(a.sum_alpha, finite ? exp(fmin(0.0, lr)) : 0.0);

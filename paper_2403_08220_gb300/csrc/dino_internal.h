@@ -23,7 +23,7 @@ constexpr size_t kSmemLimit = 227 * 1024;   // opt-in shared memory per CTA
 // prior draw, initial prior draw, observation-space noise of the
 // perturbation map (d_y < r).
 constexpr uint32_t STREAM_XI_ID = 0, STREAM_U_ID = 1, STREAM_Z_ID = 2, STREAM_INIT_ID = 3,
-                   STREAM_XI2_ID = 4;
+                   STREAM_XI2_ID = 4, STREAM_U2_ID = 5;
 
 inline __host__ __device__ size_t tri_size(int r) { return (size_t)r * (r + 1) / 2; }
 // Per-chain factor slot in global memory: the packed lower Cholesky factor
@@ -85,6 +85,11 @@ struct ReducedArgs {
   // normals (C x r), observation-space normals of the perturbation map
   // (C x d_y) and the log of the accept uniform (C)
   const double *ext_xi = nullptr, *ext_xi2 = nullptr, *ext_log_u = nullptr;
+  // delayed acceptance: the first stage only stages an accepted proposal
+  // (its factor in the spare slot, Phi, half log det and, r-sized path, g in
+  // the *_st buffers); the second stage (launch_da_decide) commits it
+  int da = 0;
+  double *phi_st = nullptr, *hld_st = nullptr, *g_st = nullptr;
   // tensor-core path: the proposal as bf16 slice planes (row pitch b_ld,
   // plane pitch b_plane elements); nullptr when unused
   __nv_bfloat16 *b_bf16 = nullptr;
@@ -145,13 +150,15 @@ size_t prior_draw_smem_bytes(int n, int elem);
 // (FP32 only) the draw is also written as ms_slices bf16 slice planes
 // (row pitch ldms, plane stride ms_plane) for the tensor-core projections.
 // With ext_z (C x N doubles, nullptr for Philox) the normals Z_c are the
-// caller's, indexed like the Philox ones.
+// caller's, indexed like the Philox ones.  With `only`, chains c with
+// only[c] == 0 draw nothing (their rows keep earlier contents).
 template <typename T>
 cudaError_t launch_prior_draw(int C, int n, const T *sqrtlam, const T *S, uint64_t seed,
                               uint64_t id_base, uint32_t stream, uint32_t step, T *out,
                               int ldo, cudaStream_t st,
                               __nv_bfloat16 *ms = nullptr, int ldms = 0, size_t ms_plane = 0,
-                              int ms_slices = 0, const double *ext_z = nullptr);
+                              int ms_slices = 0, const double *ext_z = nullptr,
+                              const int *only = nullptr);
 // P[(c d_y + i) w + k] = WL[i w + k] * der[c ldd + k]
 template <typename T>
 cudaError_t launch_jac_init(int C, int d_y, int w, const T *WL, const T *der, int ldd, T *P,
@@ -163,6 +170,45 @@ cudaError_t launch_f64_to_f32(size_t n, const double *src, float *dst, cudaStrea
 // dst[i] = src[i]; src may be pageable host memory on a device that reads it
 // coherently (cudaDevAttrPageableMemoryAccess)
 cudaError_t launch_copy_f64(size_t n, const double *src, double *dst, cudaStream_t st);
+
+// ---- delayed acceptance: the true-model stage (Algorithm 1) -------------
+// xt = s mt + cs EtM + EtDc (C x r_t; EtM, EtDc FP64 or, with in_f32, FP32;
+// either may be nullptr for 0), and with xb its nslice bf16 slice planes
+// (row pitch ldx, plane stride plane).
+cudaError_t launch_da_assemble(int C, int r_t, double s, double cs, const double *mt,
+                               const void *EtM, const void *EtDc, int in_f32, double *xt,
+                               __nv_bfloat16 *xb, int ldx, size_t plane, int nslice,
+                               cudaStream_t st);
+// phi_t[c] = |ft[c] - y|^2 / (2 noise_var) (ft FP64, or FP32 with f32)
+cudaError_t launch_da_misfit(int C, int d_y, const void *ft, int f32, const double *y,
+                             double noise_var, double *phi_t, cudaStream_t st);
+struct DaArgs {
+  int C = 0, r = 0, d_y = 0, r_t = 0;
+  double noise_var = 1;
+  uint64_t seed = 0, id_base = 0;
+  uint32_t step = 0;
+  int *acc = nullptr;                    // first-stage flags in, final flags out
+  int *stage1 = nullptr;                 // copy of the first-stage flags
+  double *mt = nullptr, *phi_t = nullptr;  // E_t m and Phi(m) of the chain state
+  const double *xt = nullptr;            // E_t m^dagger
+  const void *ft = nullptr;              // true map at m^dagger (C x d_y)
+  int ft_f32 = 0;
+  const double *y = nullptr;
+  double *mr = nullptr, *phi = nullptr, *hld = nullptr, *g = nullptr;
+  const double *b = nullptr, *phi_st = nullptr, *hld_st = nullptr, *g_st = nullptr;
+  int *cur = nullptr;
+  const void *J = nullptr;               // Woodbury path: J at b, copied into Js
+  void *Js = nullptr;
+  int j_f32 = 0;
+  const float2 *b_df = nullptr;          // BF16 Woodbury path: b -> a_df
+  float2 *a_df = nullptr;
+  unsigned long long *acc_count = nullptr, *counters = nullptr;
+  double *log_rho2 = nullptr, *log_u2 = nullptr;
+  const double *ext_log_u2 = nullptr;
+};
+// Phi(m^dagger), log rho^(2) (eq:da_dino_trr_2), the second accept test and
+// the commit of a chain that passes both stages; CTA per chain.
+cudaError_t launch_da_decide(const DaArgs &a, cudaStream_t st);
 
 // ---- tcgen05 BF16 GEMM (sm_103a) -----------------------------------------
 // Operands are bf16 "slice planes": X ~= sum_s X_s, plane s at X + s * plane.

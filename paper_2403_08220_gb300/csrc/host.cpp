@@ -420,7 +420,28 @@ struct Surrogate {
   std::vector<int> ldW, ldWT;
   std::vector<size_t> plW, plWT;
   int widest = 0;  // max hidden/output width used by the Jacobian buffers
+  // delayed acceptance (Algorithm 1's second stage): the true map
+  // G(m) = f_t(E_t m), an MLP on an r_t-dimensional encoding of the field
+  struct TrueModel {
+    bool on = false;
+    int r_t = 0, L = 0, act = 0, widest = 0;
+    std::vector<int> widths;
+    std::vector<std::pair<void *, size_t>> allocs;
+    double *dEt = nullptr, *dEtD = nullptr;  // E_t (r_t x N), E_t D (r_t x r)
+    std::vector<double *> dW, db;
+    // tensor path: three bf16 slices of E_t (r_t x ldE), E_t D (r_t x ldD)
+    // and of each W_l (pitch ldW[l]); FP32 biases
+    __nv_bfloat16 *bEt = nullptr, *bEtD = nullptr;
+    size_t plEt = 0, plEtD = 0;
+    std::vector<__nv_bfloat16 *> bW;
+    std::vector<int> ldW;
+    std::vector<size_t> plW;
+    std::vector<float *> fb;
+  } tm;
 };
+
+// bf16 slices of the true model's operands (FP32-level, like the surrogate's forward)
+constexpr int kTrueSlices = 3;
 
 template <typename T>
 static T *sur_alloc(dino_ctx *ctx, Surrogate *s, size_t n) {
@@ -465,10 +486,97 @@ static void upload_data(dino_ctx *ctx, Surrogate *s) {
   CK(cudaStreamSynchronize(ctx->stream));
 }
 
+static void free_true_model(dino_ctx *ctx, Surrogate *s) {
+  cudaStreamSynchronize(ctx->stream);
+  for (auto &a : s->tm.allocs) dev_free(ctx, a.first, a.second);
+  s->tm = Surrogate::TrueModel{};
+}
+
 static void free_surrogate(dino_ctx *ctx, Surrogate *s) {
   cudaStreamSynchronize(ctx->stream);
   for (auto &a : s->allocs) dev_free(ctx, a.first, a.second);
   s->allocs.clear();
+  free_true_model(ctx, s);
+}
+
+template <typename T>
+static T *tm_upload(dino_ctx *ctx, Surrogate *s, const T *host, size_t n) {
+  T *p = (T *)dev_alloc(ctx, n * sizeof(T));
+  s->tm.allocs.push_back({p, n * sizeof(T)});
+  CK(cudaMemcpyAsync(p, host, n * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+  return p;
+}
+
+// Attach (or with d == nullptr detach) the true map of delayed acceptance.
+static void set_true_model(dino_ctx *ctx, Surrogate *s, const dino_true_model_desc *d) {
+  if (s->pools > 0) fail(DINO_ESTATE, "surrogate has live chain pools");
+  free_true_model(ctx, s);
+  if (!d) return;
+  const int N = s->N, r = s->r;
+  if (d->r_t < 1 || d->r_t > N || !d->E_t || d->n_layers < 1 || !d->widths || !d->W || !d->b)
+    fail(DINO_EINVAL, "true model: 1 <= r_t <= N, n_layers >= 1, non-NULL E_t, widths, W, b");
+  if (d->activation < 0 || d->activation > 2) fail(DINO_EINVAL, "unknown activation");
+  auto &t = s->tm;
+  t.r_t = d->r_t;
+  t.L = d->n_layers;
+  t.act = d->activation;
+  t.widths.assign(d->widths, d->widths + d->n_layers + 1);
+  if (t.widths[0] != t.r_t || t.widths.back() != s->d_y)
+    fail(DINO_EINVAL, "true model widths must run from r_t=%d to d_y=%d", t.r_t, s->d_y);
+  for (int w : t.widths)
+    if (w < 1) fail(DINO_EINVAL, "every width must be >= 1");
+  std::vector<double> Et(d->E_t, d->E_t + (size_t)t.r_t * N);
+  for (double v : Et)
+    if (!std::isfinite(v)) fail(DINO_ENUMERIC, "non-finite entry of E_t");
+  // E_t D (r_t x r), the map of the complement coefficient into E_t coordinates
+  std::vector<double> EtD((size_t)t.r_t * r, 0.0);
+  for (int i = 0; i < t.r_t; ++i)
+    for (int p = 0; p < N; ++p) {
+      const double e = Et[(size_t)i * N + p];
+      if (e == 0.0) continue;
+      const double *Dp = &s->D[(size_t)p * r];
+      double *o = &EtD[(size_t)i * r];
+      for (int j = 0; j < r; ++j) o[j] += e * Dp[j];
+    }
+  std::vector<std::vector<double>> W, b;
+  for (int l = 0; l < t.L; ++l) {
+    if (!d->W[l] || !d->b[l]) fail(DINO_EINVAL, "true model W[%d] or b[%d] is NULL", l, l);
+    const size_t nw = (size_t)t.widths[l + 1] * t.widths[l];
+    W.emplace_back(d->W[l], d->W[l] + nw);
+    b.emplace_back(d->b[l], d->b[l] + t.widths[l + 1]);
+    for (double v : W.back())
+      if (!std::isfinite(v)) fail(DINO_ENUMERIC, "non-finite weight in true layer %d", l);
+    if (l >= 1) t.widest = std::max(t.widest, t.widths[l]);
+  }
+  try {
+    t.dEt = tm_upload(ctx, s, Et.data(), Et.size());
+    t.dEtD = tm_upload(ctx, s, EtD.data(), EtD.size());
+    for (int l = 0; l < t.L; ++l) {
+      t.dW.push_back(tm_upload(ctx, s, W[l].data(), W[l].size()));
+      t.db.push_back(tm_upload(ctx, s, b[l].data(), b[l].size()));
+      if (s->precision == DINO_PREC_BF16) {
+        const int wo = t.widths[l + 1], wi = t.widths[l], ldw = pad8(wi);
+        size_t pl = 0;
+        const auto bw = split_planes(W[l], wo, wi, ldw, kTrueSlices, pl);
+        t.bW.push_back(tm_upload(ctx, s, bw.data(), bw.size()));
+        t.ldW.push_back(ldw);
+        t.plW.push_back(pl);
+        const auto fb = to_f32(b[l]);
+        t.fb.push_back(tm_upload(ctx, s, fb.data(), fb.size()));
+      }
+    }
+    if (s->precision == DINO_PREC_BF16) {
+      const auto be = split_planes(Et, t.r_t, N, s->ldE, kTrueSlices, t.plEt);
+      const auto bd = split_planes(EtD, t.r_t, r, s->ldD, kTrueSlices, t.plEtD);
+      t.bEt = tm_upload(ctx, s, be.data(), be.size());
+      t.bEtD = tm_upload(ctx, s, bd.data(), bd.size());
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+  } catch (...) {
+    free_true_model(ctx, s);
+    throw;
+  }
+  t.on = true;
 }
 
 static Surrogate *get_surrogate(dino_ctx *ctx, int id) {
@@ -904,7 +1012,22 @@ struct Pool {
   // parts are set
   double *ext = nullptr;
   size_t ext_bytes = 0;
-  bool ext_xi = false, ext_xi2 = false, ext_z = false, ext_log_u = false;
+  bool ext_xi = false, ext_xi2 = false, ext_z = false, ext_log_u = false, ext_log_u2 = false;
+  // delayed acceptance (the surrogate has a true model): chain state E_t m
+  // (C x r_t) and Phi(m); the first stage's staging (Phi~, half log det, g);
+  // E_t m^dagger and its pieces; the true map's output and work buffers;
+  // log rho^(2), log u2 and the first-stage flags of the last transition
+  bool da = false;
+  double *mt = nullptr, *phi_t = nullptr, *phi_st = nullptr, *hld_st = nullptr,
+         *g_st = nullptr, *xt = nullptr, *lr2 = nullptr, *lu2 = nullptr;
+  int *st1 = nullptr;
+  void *EtM = nullptr, *EtDc = nullptr, *ft = nullptr;
+  std::vector<double *> tact64;              // FP64: hidden activations of f_t
+  __nv_bfloat16 *xtb = nullptr;              // tensor path: slices of xt
+  int ldxt = 0;
+  std::vector<__nv_bfloat16 *> tactb;        // tensor path: hidden activations as slices
+  std::vector<int> ldtact;
+  float *tder = nullptr;                     // tensor path: derivative scratch of f_t
 };
 
 static void layout_pool(Pool &p, bool assign) {
@@ -934,7 +1057,7 @@ static void layout_pool(Pool &p, bool assign) {
   p.log_u = (double *)take((size_t)C * 8);
   p.acc = (int *)take((size_t)C * 4);
   p.acc_count = (unsigned long long *)take((size_t)C * 8);
-  p.counters = (unsigned long long *)take(2 * 8);
+  p.counters = (unsigned long long *)take(4 * 8);
   p.sum_alpha = (double *)take(8);
   p.err = (int *)take(16);
   // FP64 at init even on the FP32 path; also holds a zero data vector in surrogate_eval
@@ -946,6 +1069,37 @@ static void layout_pool(Pool &p, bool assign) {
     p.coef2s = (__nv_bfloat16 *)take((size_t)C * s->ldD * kFieldSlices * 2);
   }
   layout_work(s, C, ar, p.w, assign, p.wb && s->tc_gram);
+  p.da = s->tm.on;
+  if (p.da) {
+    const auto &t = s->tm;
+    const size_t rt = t.r_t, dy = s->d_y;
+    p.mt = (double *)take(C * rt * 8);
+    p.phi_t = (double *)take((size_t)C * 8);
+    p.phi_st = (double *)take((size_t)C * 8);
+    p.hld_st = (double *)take((size_t)C * 8);
+    p.g_st = p.wb ? nullptr : (double *)take((size_t)C * r * 8);
+    p.xt = (double *)take(C * rt * 8);
+    p.lr2 = (double *)take((size_t)C * 8);
+    p.lu2 = (double *)take((size_t)C * 8);
+    p.st1 = (int *)take((size_t)C * 4);
+    p.EtM = take(C * rt * fe);
+    p.EtDc = take(C * rt * fe);
+    p.ft = take(C * dy * fe);
+    p.tact64.assign(t.L, nullptr);
+    p.tactb.assign(t.L, nullptr);
+    p.ldtact.assign(t.L, 0);
+    if (s->precision == DINO_PREC_FP64) {
+      for (int l = 0; l + 1 < t.L; ++l) p.tact64[l] = (double *)take((size_t)C * t.widths[l + 1] * 8);
+    } else {
+      p.ldxt = pad8(t.r_t);
+      p.xtb = (__nv_bfloat16 *)take((size_t)C * p.ldxt * kTrueSlices * 2);
+      for (int l = 0; l + 1 < t.L; ++l) {
+        p.ldtact[l] = pad8(t.widths[l + 1]);
+        p.tactb[l] = (__nv_bfloat16 *)take((size_t)C * p.ldtact[l] * kTrueSlices * 2);
+      }
+      p.tder = (float *)take((size_t)C * std::max(1, t.widest) * 4);
+    }
+  }
 }
 
 static Pool *get_pool(dino_ctx *ctx, int id) {
@@ -998,6 +1152,12 @@ static ReducedArgs reduced_args(const Pool &p) {
     a.ext_xi2 = p.ext_xi2 ? p.ext + C * s->r : nullptr;
     a.ext_log_u = p.ext_log_u ? p.ext + C * (s->r + s->d_y + (size_t)s->N) : nullptr;
   }
+  if (p.da) {
+    a.da = 1;
+    a.phi_st = p.phi_st;
+    a.hld_st = p.hld_st;
+    a.g_st = p.g_st;
+  }
   if (s->precision == DINO_PREC_FP64) {
     a.J = p.w.J64;
     a.f = p.w.f64;
@@ -1023,6 +1183,167 @@ static void split_input(dino_ctx *ctx, const Surrogate *s, Work &w, const double
 }
 
 static size_t pool_footprint(const Surrogate *s, int C);
+
+// The true map f_t at the C points x_t = p.xt (FP64 path) or its slices
+// p.xtb (tensor path), into p.ft.
+static void true_forward(dino_ctx *ctx, const Surrogate *s, Pool &p, cudaStream_t st) {
+  const auto &t = s->tm;
+  const int C = p.C, L = t.L, dy = s->d_y;
+  if (s->precision == DINO_PREC_FP64) {
+    const double *a = p.xt;
+    int lda = t.r_t;
+    for (int l = 0; l < L; ++l) {
+      const int wo = t.widths[l + 1], wi = t.widths[l];
+      const bool last = l + 1 == L;
+      double *out = last ? (double *)p.ft : p.tact64[l];
+      launch(ctx, st, "true_mlp_f64", [&] {
+        return gemm_bias_act<double>(C, wo, wi, a, lda, t.dW[l], wi, t.db[l], last ? 0 : t.act,
+                                     out, nullptr, wo, st);
+      });
+      a = out;
+      lda = wo;
+    }
+    return;
+  }
+  const __nv_bfloat16 *a = p.xtb;
+  int lda = p.ldxt;
+  for (int l = 0; l < L; ++l) {
+    const bool last = l + 1 == L;
+    TcGemmArgs g;
+    g.M = C;
+    g.N = t.widths[l + 1];
+    g.K = t.widths[l];
+    g.A = a;
+    g.lda = lda;
+    g.a_plane = (size_t)C * lda;
+    g.B = t.bW[l];
+    g.ldb = t.ldW[l];
+    g.b_plane = t.plW[l];
+    g.nslice = kTrueSlices;
+    g.bias = t.fb[l];
+    if (last) {
+      g.epi = TC_EPI_BIAS_F32;
+      g.outf = (float *)p.ft;
+      g.ldo = dy;
+    } else {
+      g.epi = TC_EPI_BIAS_ACT;
+      g.act = t.act;
+      g.out_bf = p.tactb[l];
+      g.ldo = p.ldtact[l];
+      g.out_plane = (size_t)C * p.ldtact[l];
+      g.out_slices = kTrueSlices;
+      g.der = p.tder;
+    }
+    launch(ctx, st, "true_mlp_tc", [&] { return launch_tc_gemm(g, st); });
+    if (!last) {
+      a = p.tactb[l];
+      lda = p.ldtact[l];
+    }
+  }
+}
+
+// E_t m^dagger = s E_t m + cs E_t M + (E_t D) coef2, the true map there,
+// log rho^(2), the second test and the commit (Algorithm 1's second stage).
+static void da_stage(dino_ctx *ctx, Pool &p, double cs, cudaStream_t st) {
+  const Surrogate *s = p.s;
+  const auto &t = s->tm;
+  const int C = p.C, r = s->r, N = s->N, rt = t.r_t;
+  const bool tc = s->precision != DINO_PREC_FP64;
+  if (!tc) {
+    launch(ctx, st, "da_proj_f64", [&] {
+      return gemm_store<double>(C, rt, N, (const double *)p.Mf, N, t.dEt, N, (double *)p.EtM, rt,
+                                st);
+    });
+    launch(ctx, st, "da_proj_f64", [&] {
+      return gemm_store<double>(C, rt, r, (const double *)p.coef2, r, t.dEtD, r,
+                                (double *)p.EtDc, rt, st);
+    });
+  } else {
+    auto proj = [&](const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, size_t bpl, int K,
+                    void *out) {
+      TcGemmArgs g;
+      g.M = C;
+      g.N = rt;
+      g.K = K;
+      g.A = A;
+      g.lda = lda;
+      g.a_plane = (size_t)C * lda;
+      g.B = B;
+      g.ldb = lda;
+      g.b_plane = bpl;
+      g.nslice = kFieldSlices;
+      g.epi = TC_EPI_STORE_F32;
+      g.outf = (float *)out;
+      g.ldo = rt;
+      launch(ctx, st, "da_proj_tc", [&] { return launch_tc_gemm(g, st); });
+    };
+    proj(p.Ms, s->ldE, t.bEt, t.plEt, N, p.EtM);          // E_t M
+    proj(p.coef2s, s->ldD, t.bEtD, t.plEtD, r, p.EtDc);   // (E_t D) coef2
+  }
+  launch(ctx, st, "da_assemble", [&] {
+    return launch_da_assemble(C, rt, p.sc, cs, p.mt, p.EtM, p.EtDc, tc ? 1 : 0, p.xt, p.xtb,
+                              p.ldxt, (size_t)C * p.ldxt, kTrueSlices, st);
+  });
+  true_forward(ctx, s, p, st);
+  DaArgs a;
+  a.C = C;
+  a.r = r;
+  a.d_y = s->d_y;
+  a.r_t = rt;
+  a.noise_var = s->noise_var;
+  a.seed = p.seed;
+  a.id_base = p.id_base;
+  a.step = p.step;
+  a.acc = p.acc;
+  a.stage1 = p.st1;
+  a.mt = p.mt;
+  a.phi_t = p.phi_t;
+  a.xt = p.xt;
+  a.ft = p.ft;
+  a.ft_f32 = tc ? 1 : 0;
+  a.y = s->dy;
+  a.mr = p.mr;
+  a.phi = p.phi;
+  a.hld = p.hld;
+  a.g = p.g;
+  a.b = p.b;
+  a.phi_st = p.phi_st;
+  a.hld_st = p.hld_st;
+  a.g_st = p.g_st;
+  a.cur = p.cur;
+  if (p.wb) {
+    a.J = tc ? (const void *)p.w.J32 : (const void *)p.w.J64;
+    a.Js = p.Js;
+    a.j_f32 = tc ? 1 : 0;
+    a.b_df = p.w.b_df;
+    a.a_df = p.w.a_df;
+  }
+  a.acc_count = p.acc_count;
+  a.counters = p.counters;
+  a.log_rho2 = p.lr2;
+  a.log_u2 = p.lu2;
+  a.ext_log_u2 = p.ext && p.ext_log_u2 ? p.ext + (size_t)C * (r + s->d_y + (size_t)N + 1) : nullptr;
+  launch(ctx, st, "da_decide", [&] { return launch_da_decide(a, st); });
+}
+
+// Initial true-model state of a DA pool from its FP64 initial field m64.
+static void da_init(dino_ctx *ctx, Pool &p, const double *m64, cudaStream_t st) {
+  const Surrogate *s = p.s;
+  const auto &t = s->tm;
+  const int C = p.C, N = s->N, rt = t.r_t;
+  const bool tc = s->precision != DINO_PREC_FP64;
+  launch(ctx, st, "da_encode_f64", [&] {
+    return gemm_store<double>(C, rt, N, m64, N, t.dEt, N, p.mt, rt, st);
+  });
+  launch(ctx, st, "da_assemble", [&] {
+    return launch_da_assemble(C, rt, 1.0, 0.0, p.mt, nullptr, nullptr, tc ? 1 : 0, p.xt, p.xtb,
+                              p.ldxt, (size_t)C * p.ldxt, kTrueSlices, st);
+  });
+  true_forward(ctx, s, p, st);
+  launch(ctx, st, "da_misfit", [&] {
+    return launch_da_misfit(C, s->d_y, p.ft, tc ? 1 : 0, s->dy, s->noise_var, p.phi_t, st);
+  });
+}
 
 static Pool *create_pool_on(dino_ctx *ctx, int sid, int C, double dt, uint64_t seed,
                             uint64_t id_base, const double *m0, cudaStream_t st,
@@ -1050,7 +1371,7 @@ static Pool *create_pool_on(dino_ctx *ctx, int sid, int C, double dt, uint64_t s
     layout_pool(*p, true);
     const int r = s->r, N = s->N;
     CK(cudaMemsetAsync(p->acc_count, 0, (size_t)C * 8, st));
-    CK(cudaMemsetAsync(p->counters, 0, 16, st));
+    CK(cudaMemsetAsync(p->counters, 0, 32, st));
     CK(cudaMemsetAsync(p->sum_alpha, 0, 8, st));
     CK(cudaMemsetAsync(p->err, 0, 16, st));
     CK(cudaMemsetAsync(p->cur, 0, (size_t)C * 4, st));
@@ -1091,6 +1412,7 @@ static Pool *create_pool_on(dino_ctx *ctx, int sid, int C, double dt, uint64_t s
     launch(ctx, st, "geometry_init", [&] {
       return p->wb ? launch_wb_geometry(ra, 0, st) : launch_geometry(ra, 0, st);
     });
+    if (p->da) da_init(ctx, *p, m64, st);
     if (!serving) CK(cudaStreamSynchronize(st));
   } catch (...) {
     if (serving)
@@ -1141,11 +1463,13 @@ static void step_pool(dino_ctx *ctx, Pool &p) {
     double *Mf = (double *)p.Mf, *coef2 = (double *)p.coef2, *m = (double *)p.m;
     launch(ctx, st, "prior_draw_f64", [&] {
       return launch_prior_draw<double>(C, s->n_grid, s->dSqrtLam, s->dS, p.seed, p.id_base,
-                                       STREAM_Z_ID, p.step, Mf, N, st, nullptr, 0, 0, 0, ext_z);
+                                       STREAM_Z_ID, p.step, Mf, N, st, nullptr, 0, 0, 0, ext_z,
+                                       p.da ? p.acc : nullptr);
     });
     launch(ctx, st, "field_coef_f64", [&] {
       return gemm_coef<double>(C, r, N, Mf, N, s->dE, N, p.coef, r, cs, coef2, r, st);
     });
+    if (p.da) da_stage(ctx, p, cs, st);
     launch(ctx, st, "field_update_f64", [&] {
       return gemm_field<double>(C, N, r, coef2, r, s->dD, r, p.acc, p.sc, cs, m, Mf, N, st);
     });
@@ -1156,7 +1480,8 @@ static void step_pool(dino_ctx *ctx, Pool &p) {
     launch(ctx, st, "prior_draw_f32", [&] {
       return launch_prior_draw<float>(C, s->n_grid, s->fSqrtLam, s->fS, p.seed, p.id_base,
                                       STREAM_Z_ID, p.step, Mf, N, st, p.Ms, s->ldE,
-                                      (size_t)C * s->ldE, kFieldSlices, ext_z);
+                                      (size_t)C * s->ldE, kFieldSlices, ext_z,
+                                      p.da ? p.acc : nullptr);
     });
     launch(ctx, st, "field_coef_tc", [&] {
       // coef2 (C x r) = coef - cs M E^T, written as bf16 slices
@@ -1185,6 +1510,7 @@ static void step_pool(dino_ctx *ctx, Pool &p) {
       g.out_slices = kFieldSlices;
       return launch_tc_gemm(g, st);
     });
+    if (p.da) da_stage(ctx, p, cs, st);
     launch(ctx, st, "field_update_tc", [&] {
       // (D coef2^T) (N x C), added where accepted: m <- s m + cs M + D coef2
       TcGemmArgs g;
@@ -1209,7 +1535,7 @@ static void step_pool(dino_ctx *ctx, Pool &p) {
     });
   }
   p.step += 1;
-  p.ext_xi = p.ext_xi2 = p.ext_z = p.ext_log_u = false;  // caller noise is one-shot
+  p.ext_xi = p.ext_xi2 = p.ext_z = p.ext_log_u = p.ext_log_u2 = false;  // one-shot
 }
 
 static void destroy_pool(dino_ctx *ctx, int id) {
@@ -1425,10 +1751,10 @@ struct Server {
     Pool *p = r->pool;
     const int C = p->C, rr = p->s->r, N = p->s->N;
     CK(cudaStreamSynchronize(p->st));
-    unsigned long long c[2];
+    unsigned long long c[3];
     double a = 0;
     int err = 0;
-    CK(cudaMemcpy(c, p->counters, 16, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(c, p->counters, 24, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(&a, p->sum_alpha, 8, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(&err, p->err, 4, cudaMemcpyDeviceToHost));
     if (err) fail(DINO_ETIMEOUT, "a device wait gave up (code %d)", err);
@@ -1450,6 +1776,7 @@ struct Server {
     r->stats.accepts = c[0];
     r->stats.nan_rejects = c[1];
     r->stats.sum_alpha = a;
+    r->stats.stage1_accepts = c[2];
     const int id = p->id;
     for (size_t k = 0; k < streams.size(); ++k)
       if (streams[k] == p->st) load[k] -= 1;
@@ -1780,18 +2107,18 @@ int dino_chains_step(dino_ctx *ctx, int pool_id, int n_steps, dino_step_stats *s
     if (n_steps < 0) fail(DINO_EINVAL, "n_steps must be >= 0");
     cudaSetDevice(ctx->device);
     Pool *p = get_pool(ctx, pool_id);
-    unsigned long long c0[2] = {0, 0};
+    unsigned long long c0[3] = {0, 0, 0};
     double a0 = 0;
     if (stats) {
-      CK(cudaMemcpyAsync(c0, p->counters, 16, cudaMemcpyDeviceToHost, p->st));
+      CK(cudaMemcpyAsync(c0, p->counters, 24, cudaMemcpyDeviceToHost, p->st));
       CK(cudaMemcpyAsync(&a0, p->sum_alpha, 8, cudaMemcpyDeviceToHost, p->st));
     }
     for (int k = 0; k < n_steps; ++k) step_pool(ctx, *p);
     if (stats) {
-      unsigned long long c1[2];
+      unsigned long long c1[3];
       double a1 = 0;
       int err = 0;
-      CK(cudaMemcpyAsync(c1, p->counters, 16, cudaMemcpyDeviceToHost, p->st));
+      CK(cudaMemcpyAsync(c1, p->counters, 24, cudaMemcpyDeviceToHost, p->st));
       CK(cudaMemcpyAsync(&a1, p->sum_alpha, 8, cudaMemcpyDeviceToHost, p->st));
       CK(cudaMemcpyAsync(&err, p->err, 4, cudaMemcpyDeviceToHost, p->st));
       CK(cudaStreamSynchronize(p->st));
@@ -1800,6 +2127,7 @@ int dino_chains_step(dino_ctx *ctx, int pool_id, int n_steps, dino_step_stats *s
       stats->accepts = c1[0] - c0[0];
       stats->nan_rejects = c1[1] - c0[1];
       stats->sum_alpha = a1 - a0;
+      stats->stage1_accepts = c1[2] - c0[2];
     }
     collect_times(ctx);
   });
@@ -1858,11 +2186,12 @@ int dino_surrogate_query(dino_ctx *ctx, int surrogate_id, dino_surrogate_info *i
     info->gram_on_tensor_cores = s->tc_gram ? 1 : 0;
     info->fwd_slices = s->precision == DINO_PREC_BF16 ? s->fwd_slices : 0;
     info->jac_slices = s->precision == DINO_PREC_BF16 ? s->jac_slices : 0;
+    info->true_model_rank = s->tm.on ? s->tm.r_t : 0;
   });
 }
 
 int dino_chains_set_noise(dino_ctx *ctx, int pool_id, const double *xi, const double *xi2,
-                          const double *z, const double *log_u) {
+                          const double *z, const double *log_u, const double *log_u2) {
   return guarded(ctx, [&] {
     cudaSetDevice(ctx->device);
     Pool *p = get_pool(ctx, pool_id);
@@ -1870,7 +2199,9 @@ int dino_chains_set_noise(dino_ctx *ctx, int pool_id, const double *xi, const do
     if (xi2 && !p->wb)
       fail(DINO_EINVAL, "xi2 is only drawn by the perturbation noise map (this pool: Cholesky)");
     const size_t C = p->C, r = s->r, dy = s->d_y, N = s->N;
-    const size_t bytes = C * (r + dy + N + 1) * sizeof(double);
+    if (log_u2 && !p->da)
+      fail(DINO_EINVAL, "log_u2 is only drawn by delayed acceptance (no true model)");
+    const size_t bytes = C * (r + dy + N + 2) * sizeof(double);
     if (!p->ext) {
       p->ext = (double *)dev_alloc(ctx, bytes);
       p->ext_bytes = bytes;
@@ -1882,11 +2213,35 @@ int dino_chains_set_noise(dino_ctx *ctx, int pool_id, const double *xi, const do
     if (xi2) put(xi2, C * r, C * dy);
     if (z) put(z, C * (r + dy), C * N);
     if (log_u) put(log_u, C * (r + dy + N), C);
+    if (log_u2) put(log_u2, C * (r + dy + N + 1), C);
     CK(cudaStreamSynchronize(p->st));  // host arrays are not used after return
     p->ext_xi = xi != nullptr;
     p->ext_xi2 = xi2 != nullptr;
     p->ext_z = z != nullptr;
     p->ext_log_u = log_u != nullptr;
+    p->ext_log_u2 = log_u2 != nullptr;
+  });
+}
+
+int dino_set_true_model(dino_ctx *ctx, int surrogate_id, const dino_true_model_desc *desc) {
+  return guarded(ctx, [&] {
+    cudaSetDevice(ctx->device);
+    set_true_model(ctx, get_surrogate(ctx, surrogate_id), desc);
+  });
+}
+
+int dino_chains_read_da(dino_ctx *ctx, int pool_id, double *phi_true, double *log_rho2,
+                        double *log_u2, int *stage1) {
+  return guarded(ctx, [&] {
+    cudaSetDevice(ctx->device);
+    Pool *p = get_pool(ctx, pool_id);
+    if (!p->da) fail(DINO_ESTATE, "pool %d does not run delayed acceptance", pool_id);
+    const size_t C = p->C;
+    CK(cudaStreamSynchronize(p->st));
+    if (phi_true) CK(cudaMemcpy(phi_true, p->phi_t, C * 8, cudaMemcpyDeviceToHost));
+    if (log_rho2) CK(cudaMemcpy(log_rho2, p->lr2, C * 8, cudaMemcpyDeviceToHost));
+    if (log_u2) CK(cudaMemcpy(log_u2, p->lu2, C * 8, cudaMemcpyDeviceToHost));
+    if (stage1) CK(cudaMemcpy(stage1, p->st1, C * 4, cudaMemcpyDeviceToHost));
   });
 }
 

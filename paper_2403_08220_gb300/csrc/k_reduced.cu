@@ -401,8 +401,12 @@ __global__ void __launch_bounds__(kThreads) k_geometry(ReducedArgs a, int mode) 
   for (int i = threadIdx.x; i < r; i += blockDim.x) {
     a.coef[(size_t)c * r + i] = vb[i] - s * va[i];
     if (accept) {
-      a.mr[(size_t)c * r + i] = vb[i];
-      a.g[(size_t)c * r + i] = vg[i];
+      if (a.da) {
+        a.g_st[(size_t)c * r + i] = vg[i];
+      } else {
+        a.mr[(size_t)c * r + i] = vb[i];
+        a.g[(size_t)c * r + i] = vg[i];
+      }
       Lg[lsz + i] = vp[i];
     }
   }

@@ -161,7 +161,8 @@ __global__ void __launch_bounds__(kPriorThreads)
     k_prior_draw(int n, const T *__restrict__ sqrtlam, const T *__restrict__ S, uint64_t seed,
                  uint64_t id_base, uint32_t stream, uint32_t step, T *out, int ldo,
                  __nv_bfloat16 *ms, int ldms, size_t ms_plane, int ms_slices,
-                 const double *__restrict__ ext_z) {
+                 const double *__restrict__ ext_z, const int *__restrict__ only) {
+  if (only && !only[blockIdx.x]) return;  // the whole CTA: this chain draws nothing
   extern __shared__ __align__(16) unsigned char smraw[];
   const int ld = prior_ld(n), nt = ld / 4, NN = ld * ld;
   T *X = reinterpret_cast<T *>(smraw);
@@ -340,7 +341,7 @@ template <typename T>
 cudaError_t launch_prior_draw(int C, int n, const T *sqrtlam, const T *S, uint64_t seed,
                               uint64_t id_base, uint32_t stream, uint32_t step, T *out, int ldo,
                               cudaStream_t st, __nv_bfloat16 *ms, int ldms, size_t ms_plane,
-                              int ms_slices, const double *ext_z) {
+                              int ms_slices, const double *ext_z, const int *only) {
   if (C <= 0) return cudaSuccess;
   if (ms && (sizeof(T) != 4 || ms_slices < 1 || ldms < n * n)) return cudaErrorInvalidValue;
   const size_t smem = prior_draw_smem_bytes(n, (int)sizeof(T));
@@ -348,7 +349,8 @@ cudaError_t launch_prior_draw(int C, int n, const T *sqrtlam, const T *S, uint64
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_prior_draw<T><<<C, kPriorThreads, smem, st>>>(n, sqrtlam, S, seed, id_base, stream, step, out,
-                                                   ldo, ms, ldms, ms_plane, ms_slices, ext_z);
+                                                   ldo, ms, ldms, ms_plane, ms_slices, ext_z,
+                                                   only);
   return cudaGetLastError();
 }
 
@@ -397,7 +399,7 @@ template cudaError_t launch_broadcast<double>(int, size_t, const double *, doubl
   template cudaError_t launch_prior_draw<T>(int, int, const T *, const T *, uint64_t,         \
                                             uint64_t, uint32_t, uint32_t, T *, int,           \
                                             cudaStream_t, __nv_bfloat16 *, int, size_t, int, \
-                                            const double *);
+                                            const double *, const int *);
 DINO_INST_DRAW(double)
 DINO_INST_DRAW(float)
 

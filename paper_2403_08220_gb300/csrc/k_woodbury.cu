@@ -474,7 +474,7 @@ __global__ void __launch_bounds__(kWbThreads, kWbMinBlocks) k_wb_geometry(Reduce
   if (accept) {
     const double *vv = solve_v();
     wb_store_factor<TJ, A>(Lg, Ms, inv, u, vv, t1, dy);
-    take_state();
+    if (!a.da) take_state();  // delayed acceptance: the second stage commits
   }
 }
 

@@ -10,7 +10,9 @@
 
 namespace dino {
 
-enum : uint32_t { STREAM_XI = 0, STREAM_U = 1, STREAM_Z = 2, STREAM_INIT = 3, STREAM_XI2 = 4 };
+enum : uint32_t {
+  STREAM_XI = 0, STREAM_U = 1, STREAM_Z = 2, STREAM_INIT = 3, STREAM_XI2 = 4, STREAM_U2 = 5
+};
 
 __host__ __device__ __forceinline__ uint32_t mulhi32(uint32_t a, uint32_t b) {
 #ifdef __CUDA_ARCH__

@@ -10,7 +10,7 @@ arithmetic lives here.  It produces
   (noise standard deviation = a fraction of its RMS).
 
 Seeds follow one convention: basis=11, weights=12, truth=13, data noise=14,
-chains=15 (plus a request index for serving workloads).
+chains=15, true-model weights=16 (plus a request index for serving workloads).
 
 The workloads mirror the shapes of the paper's experiments (Secs. 7-8: a
 reduced basis of rank 200, GELU MLPs of width 400, tens to hundreds of
@@ -37,6 +37,7 @@ SEED_WEIGHTS = 12
 SEED_TRUTH = 13
 SEED_DATA_NOISE = 14
 SEED_CHAINS = 15
+SEED_TRUE = 16
 
 
 @dataclass
@@ -139,3 +140,15 @@ def surrogate_inputs(w: Workload):
     m_true_r = truth_reduced(w.r, SEED_TRUTH + w.seed_offset)
     eps = data_noise(w.d_y, SEED_DATA_NOISE + w.seed_offset)
     return dict(Ws=Ws, bs=bs, G=G, m_true_r=m_true_r, eps=eps)
+
+
+def true_model_weights(w: Workload, r_c: int, eps: float):
+    """Weights of the true-map stand-in f_t of delayed acceptance for workload
+    `w`: the surrogate's network whose first layer also reads r_c further
+    coordinates (the encoder's extra rows) through eps V, V seeded
+    N(0, 1/r_c), so that f_t(x, x_c) = f(x) + O(eps)."""
+    inp = surrogate_inputs(w)
+    V = np.random.default_rng(SEED_TRUE + w.seed_offset).standard_normal(
+        (w.widths[1], r_c)) / np.sqrt(r_c)
+    Ws = [np.hstack([inp["Ws"][0], eps * V])] + [x.copy() for x in inp["Ws"][1:]]
+    return Ws, [x.copy() for x in inp["bs"]]
