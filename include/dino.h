@@ -317,6 +317,49 @@ int dino_set_true_model(dino_ctx *ctx, int surrogate_id, const dino_true_model_d
 int dino_chains_read_da(dino_ctx *ctx, int pool_id, double *phi_true, double *log_rho2,
                         double *log_u2, int *stage1);
 
+/* ---- chain diagnostics (Sec. 6.2) ---------------------------------------- */
+
+/* A device trajectory of n_chains chains x n_dof degrees of freedom (at most
+ * max_samples samples), and the diagnostics the paper uses to judge a pool
+ * of chains, computed on the device from it:
+ *   ESS% per degree of freedom (eq:ess): 1 / (1 + 2 sum_{t=1}^{2n'+1} MACT(t)),
+ *     MACT(t) = 1 - (w - mean_k AC(t, k)) / v with w, v the 1D covariance
+ *     estimators and AC(t, k) the lag-t autocovariance of chain k; n' ends the
+ *     initial positive sequence (MACT(0) = 1, pairs MACT(2i) + MACT(2i+1) > 0);
+ *     returned as a fraction;
+ *   the Wasserstein MPSRF Tr(W + V - 2 (W^1/2 V W^1/2)^1/2) of the within-
+ *     chain and pooled covariance estimators (eq:covariance_estimator), with
+ *     the symmetric square roots from a one-sided Jacobi eigensolver
+ *     (n_dof <= 1024);
+ *   the mean squared jump MSJ = 1/(n_s - 1) sum_j |x_{j+1} - x_j|^2, averaged
+ *     over chains (the acceptance rate comes with dino_chains_step's stats).
+ * The trajectory takes n_dof n_chains max_samples doubles of device memory. */
+#define DINO_DIAG_REDUCED 0   /* record m_r (n_dof = r) */
+#define DINO_DIAG_FIELD   1   /* record the field m (n_dof = N) */
+
+typedef struct {
+  int n_samples;
+  double ess_median;     /* median over degrees of freedom of ESS% (fraction) */
+  double msj;
+  double mpsrf_w;        /* NaN unless requested */
+  double trace_w, trace_v;
+  int jacobi_sweeps;     /* sweeps of the last eigensolve */
+} dino_diag_result;
+
+/* Errors: EINVAL (n_chains < 2 or > 6144, n_dof < 1, max_samples < 2), ENOMEM. */
+int dino_diag_create(dino_ctx *ctx, int n_chains, int n_dof, int max_samples, int *diag_id);
+/* Append the current state of chains chain0 .. chain0 + n_chains - 1 of a
+ * pool (what = DINO_DIAG_REDUCED or DINO_DIAG_FIELD), after the work already
+ * issued on the pool's stream.  Errors: ENOTFOUND, EINVAL (shape), ENOMEM (full). */
+int dino_diag_record(dino_ctx *ctx, int diag_id, int pool_id, int what, int chain0);
+/* Append a caller sample (host, n_chains x n_dof, row-major). */
+int dino_diag_push(dino_ctx *ctx, int diag_id, const double *sample);
+/* Compute the diagnostics of the samples recorded so far; ess (host, n_dof)
+ * and result may be NULL.  Errors: ENOTFOUND, ESTATE (< 2 samples), EINVAL. */
+int dino_diag_compute(dino_ctx *ctx, int diag_id, int want_mpsrf, double *ess,
+                      dino_diag_result *result);
+int dino_diag_destroy(dino_ctx *ctx, int diag_id);
+
 /* Free a chain pool's device memory (after its stream has drained); the
  * pool id is invalid afterwards.  Errors: ENOTFOUND. */
 int dino_chains_destroy(dino_ctx *ctx, int pool_id);

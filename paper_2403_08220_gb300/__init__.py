@@ -36,6 +36,7 @@ DINO_BASIS_KLE, DINO_BASIS_DIS, DINO_BASIS_EXPLICIT = 0, 1, 2
 DINO_PREC_FP64, DINO_PREC_BF16 = 0, 1
 DINO_NOISE_AUTO, DINO_NOISE_CHOLESKY, DINO_NOISE_PERTURBATION = 0, 1, 2
 NOISE_MAP_NAMES = {DINO_NOISE_CHOLESKY: "cholesky", DINO_NOISE_PERTURBATION: "perturbation"}
+DINO_DIAG_REDUCED, DINO_DIAG_FIELD = 0, 1
 DINO_FLAG_TIMING = 1
 DINO_FLAG_NO_DIRECT_HOST = 2
 
@@ -65,6 +66,12 @@ class _Info(ct.Structure):
                 ("precision", ct.c_int), ("noise_map", ct.c_int),
                 ("gram_on_tensor_cores", ct.c_int), ("fwd_slices", ct.c_int),
                 ("jac_slices", ct.c_int), ("true_model_rank", ct.c_int)]
+
+
+class _DiagResult(ct.Structure):
+    _fields_ = [("n_samples", ct.c_int), ("ess_median", ct.c_double), ("msj", ct.c_double),
+                ("mpsrf_w", ct.c_double), ("trace_w", ct.c_double), ("trace_v", ct.c_double),
+                ("jacobi_sweeps", ct.c_int)]
 
 
 class _Stats(ct.Structure):
@@ -119,6 +126,11 @@ _SIGNATURES = {
     "dino_set_true_model": ([_P, _I, ct.POINTER(_TrueDesc)], _I),
     "dino_chains_read_da": ([_P, _I, _D, _D, _D, ct.POINTER(_I)], _I),
     "dino_set_wait_limit": ([_P, ct.c_uint32], _I),
+    "dino_diag_create": ([_P, _I, _I, _I, ct.POINTER(_I)], _I),
+    "dino_diag_record": ([_P, _I, _I, _I, _I], _I),
+    "dino_diag_push": ([_P, _I, _D], _I),
+    "dino_diag_compute": ([_P, _I, _I, _D, ct.POINTER(_DiagResult)], _I),
+    "dino_diag_destroy": ([_P, _I], _I),
     "dino_launch_count": ([_P], ct.c_uint64),
     "dino_kernel_times": ([_P, ct.c_char_p, _D, ct.POINTER(ct.c_uint64), _I, ct.POINTER(_I), _I],
                           _I),
@@ -346,6 +358,36 @@ def dino_chains_read_da(ctx: Ctx, pool: int, C: int) -> dict:
                                           out["stage1"].ctypes.data_as(ct.POINTER(_I))))
     out["stage1"] = out["stage1"].astype(bool)
     return out
+
+
+def dino_diag_create(ctx: Ctx, n_chains: int, n_dof: int, max_samples: int) -> int:
+    i = _I()
+    _check(ctx, lib().dino_diag_create(ctx.ptr, n_chains, n_dof, max_samples, ct.byref(i)))
+    return i.value
+
+
+def dino_diag_record(ctx: Ctx, diag: int, pool: int, what: int = DINO_DIAG_REDUCED,
+                     chain0: int = 0):
+    _check(ctx, lib().dino_diag_record(ctx.ptr, diag, pool, what, chain0))
+
+
+def dino_diag_push(ctx: Ctx, diag: int, sample):
+    x = _f64(sample)
+    _check(ctx, lib().dino_diag_push(ctx.ptr, diag, _dptr(x)))
+
+
+def dino_diag_compute(ctx: Ctx, diag: int, n_dof: int, mpsrf: bool = True) -> dict:
+    ess = np.empty(n_dof)
+    r = _DiagResult()
+    _check(ctx, lib().dino_diag_compute(ctx.ptr, diag, 1 if mpsrf else 0, _dptr(ess),
+                                        ct.byref(r)))
+    out = {k: getattr(r, k) for k, _ in _DiagResult._fields_}
+    out["ess"] = ess
+    return out
+
+
+def dino_diag_destroy(ctx: Ctx, diag: int):
+    _check(ctx, lib().dino_diag_destroy(ctx.ptr, diag))
 
 
 def dino_set_wait_limit(ctx: Ctx, flag_spins: int):

@@ -210,6 +210,26 @@ struct DaArgs {
 // the commit of a chain that passes both stages; CTA per chain.
 cudaError_t launch_da_decide(const DaArgs &a, cudaStream_t st);
 
+// ---- chain diagnostics (Sec. 6.2) ----------------------------------------
+// traj[(i n_c + k) max_s + j] = src[k ld_src + i] for k < n_c, i < d
+cudaError_t launch_diag_record(int n_c, int d, const void *src, int src_f32, int ld_src,
+                               double *traj, int max_s, int j, cudaStream_t st);
+// per degree of freedom: chain means (d x n_c), ESS fraction, sum of squared jumps
+cudaError_t launch_diag_ess(int d, int n_c, int n_s, const double *traj, int max_s, double *means,
+                            double *ess, double *sqjump, cudaStream_t st);
+// centred samples Xc (d x n_c n_s) and centred chain means Mc (d x n_c)
+cudaError_t launch_diag_center(int d, int n_c, int n_s, const double *traj, int max_s,
+                               const double *means, double *Xc, double *Mc, cudaStream_t st);
+cudaError_t launch_diag_wv(int d, int n_c, int n_s, const double *Wr, const double *Br, double *W,
+                           double *V, cudaStream_t st);
+// one-sided Jacobi on the d columns of G (in place); Q (optional) gets the
+// accumulated rotations, sig the column norms, *sweeps the sweeps taken
+cudaError_t launch_jacobi(int d, double *G, double *Q, double *sig, int *sweeps, cudaStream_t st);
+cudaError_t launch_sym_sqrt(int d, const double *Q, const double *lam, double *S, cudaStream_t st);
+cudaError_t launch_small_mm(int d, const double *A, const double *B, double *C, cudaStream_t st);
+cudaError_t launch_mpsrf_final(int d, const double *W, const double *V, const double *sig,
+                               double *out, cudaStream_t st);
+
 // ---- tcgen05 BF16 GEMM (sm_103a) -----------------------------------------
 // Operands are bf16 "slice planes": X ~= sum_s X_s, plane s at X + s * plane.
 // D = sum over slice pairs (i, j), i + j < nslice, of A_i B_j^T, FP32 accum.

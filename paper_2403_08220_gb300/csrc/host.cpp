@@ -68,6 +68,7 @@ struct Arena {
 struct Surrogate;
 struct Pool;
 struct Server;
+struct Diag;
 
 }  // namespace dino
 
@@ -95,6 +96,7 @@ struct dino_ctx {
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> event_pool;
   std::unique_ptr<dino::Server> server;
+  std::map<int, std::unique_ptr<dino::Diag>> diags;
   // the device reads pageable host memory coherently (Grace: over NVLink-C2C)
   bool pageable_access = false;
   // polls of the Cholesky diagonal-block flag before a kernel gives up
@@ -1629,6 +1631,172 @@ static void surrogate_eval(dino_ctx *ctx, int sid, int n, const double *x_host, 
 }
 
 // ---------------------------------------------------------------------------
+// chain diagnostics: a device trajectory of n_c chains x d degrees of freedom
+
+struct Diag {
+  int id = 0, n_c = 0, d = 0, max_s = 0, n_s = 0;
+  double *traj = nullptr, *means = nullptr, *ess = nullptr, *sqjump = nullptr;
+  size_t bytes = 0;
+  cudaEvent_t ready = nullptr;  // recorded after the last append
+};
+
+static Diag *get_diag(dino_ctx *ctx, int id) {
+  auto it = ctx->diags.find(id);
+  if (it == ctx->diags.end()) fail(DINO_ENOTFOUND, "unknown diagnostics id %d", id);
+  return it->second.get();
+}
+
+static void free_diag(dino_ctx *ctx, Diag *g) {
+  if (g->ready) {
+    cudaEventSynchronize(g->ready);
+    cudaEventDestroy(g->ready);
+  }
+  dev_free(ctx, g->traj, g->bytes);
+}
+
+static int diag_create(dino_ctx *ctx, int n_c, int d, int max_s) {
+  if (n_c < 2 || d < 1 || max_s < 2 || n_c > 6144)
+    fail(DINO_EINVAL, "diagnostics need 2 <= n_chains <= 6144, n_dof >= 1, max_samples >= 2");
+  auto g = std::make_unique<Diag>();
+  g->id = ctx->next_id++;
+  g->n_c = n_c;
+  g->d = d;
+  g->max_s = max_s;
+  const size_t nt = (size_t)d * n_c * max_s, nm = (size_t)d * n_c;
+  g->bytes = (nt + nm + 2 * (size_t)d) * sizeof(double);
+  g->traj = (double *)dev_alloc(ctx, g->bytes);
+  g->means = g->traj + nt;
+  g->ess = g->means + nm;
+  g->sqjump = g->ess + d;
+  if (cudaEventCreateWithFlags(&g->ready, cudaEventDisableTiming) != cudaSuccess) {
+    dev_free(ctx, g->traj, g->bytes);
+    fail(DINO_ECUDA, "cudaEventCreate failed");
+  }
+  const int id = g->id;
+  ctx->diags[id] = std::move(g);
+  return id;
+}
+
+// Append the current state of chains [chain0, chain0 + n_c) of a pool.
+static void diag_record(dino_ctx *ctx, Diag *g, Pool *p, int what, int chain0) {
+  const Surrogate *s = p->s;
+  if (g->n_s >= g->max_s) fail(DINO_ENOMEM, "diagnostics trajectory is full (%d samples)", g->max_s);
+  if (chain0 < 0 || chain0 + g->n_c > p->C) fail(DINO_EINVAL, "chains out of the pool's range");
+  const void *src;
+  int f32 = 0, ld;
+  if (what == DINO_DIAG_REDUCED) {
+    if (g->d != s->r) fail(DINO_EINVAL, "n_dof %d != r %d", g->d, s->r);
+    src = p->mr + (size_t)chain0 * s->r;
+    ld = s->r;
+  } else if (what == DINO_DIAG_FIELD) {
+    if (g->d != s->N) fail(DINO_EINVAL, "n_dof %d != N %d", g->d, s->N);
+    f32 = s->precision == DINO_PREC_FP64 ? 0 : 1;
+    src = (const char *)p->m + (size_t)chain0 * s->N * (f32 ? 4 : 8);
+    ld = s->N;
+  } else {
+    fail(DINO_EINVAL, "unknown record kind %d", what);
+  }
+  launch(ctx, p->st, "diag_record", [&] {
+    return launch_diag_record(g->n_c, g->d, src, f32, ld, g->traj, g->max_s, g->n_s, p->st);
+  });
+  CK(cudaEventRecord(g->ready, p->st));
+  g->n_s += 1;
+}
+
+static void diag_push(dino_ctx *ctx, Diag *g, const double *sample) {
+  if (!sample) fail(DINO_EINVAL, "sample is NULL");
+  if (g->n_s >= g->max_s) fail(DINO_ENOMEM, "diagnostics trajectory is full (%d samples)", g->max_s);
+  const size_t n = (size_t)g->n_c * g->d;
+  double *tmp = (double *)dev_alloc(ctx, n * 8);
+  try {
+    CK(cudaMemcpyAsync(tmp, sample, n * 8, cudaMemcpyHostToDevice, ctx->stream));
+    launch(ctx, ctx->stream, "diag_record", [&] {
+      return launch_diag_record(g->n_c, g->d, tmp, 0, g->d, g->traj, g->max_s, g->n_s,
+                                ctx->stream);
+    });
+    CK(cudaStreamSynchronize(ctx->stream));
+  } catch (...) {
+    dev_free(ctx, tmp, n * 8);
+    throw;
+  }
+  dev_free(ctx, tmp, n * 8);
+  g->n_s += 1;
+}
+
+static void diag_compute(dino_ctx *ctx, Diag *g, int want_mpsrf, double *ess_out,
+                         dino_diag_result *res) {
+  const int n_c = g->n_c, d = g->d, n_s = g->n_s;
+  if (n_s < 2) fail(DINO_ESTATE, "need at least 2 recorded samples (have %d)", n_s);
+  if (want_mpsrf && d > 1024) fail(DINO_EINVAL, "MPSRF needs n_dof <= 1024 (have %d)", d);
+  cudaStream_t st = ctx->stream;
+  CK(cudaStreamWaitEvent(st, g->ready, 0));
+  launch(ctx, st, "diag_ess", [&] {
+    return launch_diag_ess(d, n_c, n_s, g->traj, g->max_s, g->means, g->ess, g->sqjump, st);
+  });
+  std::vector<double> ess(d), sj(d);
+  CK(cudaMemcpyAsync(ess.data(), g->ess, d * 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(sj.data(), g->sqjump, d * 8, cudaMemcpyDeviceToHost, st));
+  double out[3] = {0, 0, 0};
+  int sweeps = 0;
+  if (want_mpsrf) {
+    const size_t K = (size_t)n_c * n_s, dd = (size_t)d * d;
+    const size_t bytes = ((size_t)d * K + (size_t)d * n_c + 9 * dd + d + 4) * 8;
+    double *w = (double *)dev_alloc(ctx, bytes);
+    try {
+      double *Xc = w, *Mc = Xc + (size_t)d * K, *Wr = Mc + (size_t)d * n_c, *Br = Wr + dd,
+             *W = Br + dd, *V = W + dd, *G = V + dd, *Q = G + dd, *Wh = Q + dd, *T = Wh + dd,
+             *M = T + dd, *sig = M + dd, *o = sig + d;
+      launch(ctx, st, "diag_center", [&] {
+        return launch_diag_center(d, n_c, n_s, g->traj, g->max_s, g->means, Xc, Mc, st);
+      });
+      launch(ctx, st, "diag_gram", [&] {
+        return gemm_store<double>(d, d, (int)K, Xc, (int)K, Xc, (int)K, Wr, d, st);
+      });
+      launch(ctx, st, "diag_gram", [&] {
+        return gemm_store<double>(d, d, n_c, Mc, n_c, Mc, n_c, Br, d, st);
+      });
+      launch(ctx, st, "diag_wv", [&] { return launch_diag_wv(d, n_c, n_s, Wr, Br, W, V, st); });
+      // W = Q diag(lam) Q^T (W symmetric: its rows are its columns)
+      CK(cudaMemcpyAsync(G, W, dd * 8, cudaMemcpyDeviceToDevice, st));
+      launch(ctx, st, "jacobi", [&] { return launch_jacobi(d, G, Q, sig, nullptr, st); });
+      launch(ctx, st, "sym_sqrt", [&] { return launch_sym_sqrt(d, Q, sig, Wh, st); });
+      launch(ctx, st, "small_mm", [&] { return launch_small_mm(d, Wh, V, T, st); });
+      launch(ctx, st, "small_mm", [&] { return launch_small_mm(d, T, Wh, M, st); });
+      // eigenvalues of W^1/2 V W^1/2 (symmetric positive semidefinite)
+      launch(ctx, st, "jacobi", [&] {
+        return launch_jacobi(d, M, nullptr, sig, reinterpret_cast<int *>(o + 3), st);
+      });
+      launch(ctx, st, "mpsrf_final", [&] { return launch_mpsrf_final(d, W, V, sig, o, st); });
+      CK(cudaMemcpyAsync(out, o, 24, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(&sweeps, o + 3, 4, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+    } catch (...) {
+      cudaStreamSynchronize(st);
+      dev_free(ctx, w, bytes);
+      throw;
+    }
+    dev_free(ctx, w, bytes);
+  }
+  CK(cudaStreamSynchronize(st));
+  if (ess_out) std::memcpy(ess_out, ess.data(), d * 8);
+  if (res) {
+    double msj = 0.0;
+    for (double x : sj) msj += x;
+    res->n_samples = n_s;
+    res->msj = msj / ((double)n_c * (n_s - 1));
+    res->mpsrf_w = want_mpsrf ? out[0] : std::nan("");
+    res->trace_w = want_mpsrf ? out[1] : std::nan("");
+    res->trace_v = want_mpsrf ? out[2] : std::nan("");
+    res->jacobi_sweeps = sweeps;
+    double e = 0.0;
+    std::vector<double> sorted(ess);
+    std::sort(sorted.begin(), sorted.end());
+    e = d % 2 ? sorted[d / 2] : 0.5 * (sorted[d / 2 - 1] + sorted[d / 2]);
+    res->ess_median = e;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // serving: continuous batching of chain ensembles
 //
 // A background thread owns admission and issue.  Requests wait in a FIFO
@@ -2019,6 +2187,8 @@ int dino_destroy(dino_ctx *ctx) {
       dev_free(ctx, kv.second->ext, kv.second->ext_bytes);
     }
     ctx->pools.clear();
+    for (auto &kv : ctx->diags) free_diag(ctx, kv.second.get());
+    ctx->diags.clear();
     for (auto &kv : ctx->surrogates) free_surrogate(ctx, kv.second.get());
     ctx->surrogates.clear();
     for (auto &p : ctx->pending) {
@@ -2242,6 +2412,44 @@ int dino_chains_read_da(dino_ctx *ctx, int pool_id, double *phi_true, double *lo
     if (log_rho2) CK(cudaMemcpy(log_rho2, p->lr2, C * 8, cudaMemcpyDeviceToHost));
     if (log_u2) CK(cudaMemcpy(log_u2, p->lu2, C * 8, cudaMemcpyDeviceToHost));
     if (stage1) CK(cudaMemcpy(stage1, p->st1, C * 4, cudaMemcpyDeviceToHost));
+  });
+}
+
+int dino_diag_create(dino_ctx *ctx, int n_chains, int n_dof, int max_samples, int *diag_id) {
+  return guarded(ctx, [&] {
+    if (!diag_id) fail(DINO_EINVAL, "diag_id is NULL");
+    cudaSetDevice(ctx->device);
+    *diag_id = diag_create(ctx, n_chains, n_dof, max_samples);
+  });
+}
+
+int dino_diag_record(dino_ctx *ctx, int diag_id, int pool_id, int what, int chain0) {
+  return guarded(ctx, [&] {
+    cudaSetDevice(ctx->device);
+    diag_record(ctx, get_diag(ctx, diag_id), get_pool(ctx, pool_id), what, chain0);
+  });
+}
+
+int dino_diag_push(dino_ctx *ctx, int diag_id, const double *sample) {
+  return guarded(ctx, [&] {
+    cudaSetDevice(ctx->device);
+    diag_push(ctx, get_diag(ctx, diag_id), sample);
+  });
+}
+
+int dino_diag_compute(dino_ctx *ctx, int diag_id, int want_mpsrf, double *ess,
+                      dino_diag_result *result) {
+  return guarded(ctx, [&] {
+    cudaSetDevice(ctx->device);
+    diag_compute(ctx, get_diag(ctx, diag_id), want_mpsrf, ess, result);
+  });
+}
+
+int dino_diag_destroy(dino_ctx *ctx, int diag_id) {
+  return guarded(ctx, [&] {
+    cudaSetDevice(ctx->device);
+    free_diag(ctx, get_diag(ctx, diag_id));
+    ctx->diags.erase(diag_id);
   });
 }
 
