@@ -317,6 +317,23 @@ int dino_set_true_model(dino_ctx *ctx, int surrogate_id, const dino_true_model_d
 int dino_chains_read_da(dino_ctx *ctx, int pool_id, double *phi_true, double *log_rho2,
                         double *log_u2, int *stage1);
 
+/* ---- derivative-informed subspace from the surrogate ------------------- */
+
+/* The DIS eigenproblem (eq:jtj_eigenvalue) restricted to the span of the
+ * surrogate's basis, with the Monte Carlo estimate of the expected ppGNH
+ * (eq:mc_ppgnh): at n_samples encoded prior draws m_r,i ~ N(0, I_r) (Philox
+ * stream 6, step 0, chain i; Lemma of Sec. 5.3) the surrogate's Jacobians give
+ *   H_mc = (1/n) sum_i J(m_r,i)^T J(m_r,i) / noise_var   (r x r),
+ * eigendecomposed on the device (one-sided Jacobi) as P diag(lambda) P^T with
+ * lambda decreasing.  Outputs (host, any may be NULL): eigvals (r), P (r x
+ * r_new, the leading eigenvectors, signs arbitrary), E_new = P^T E (r_new x N)
+ * and D_new = D P (N x r_new), a C_pr^-1-orthonormal basis with
+ * E_new D_new = I.  A surrogate on the new basis takes the first-layer
+ * weights W_1 P (coordinates outside the r_new leading directions set to 0).
+ * Errors: ENOTFOUND, EINVAL (n_samples < 1, r_new outside 1..r), ENOMEM. */
+int dino_dis_from_surrogate(dino_ctx *ctx, int surrogate_id, int n_samples, uint64_t seed,
+                            int r_new, double *eigvals, double *P, double *E_new, double *D_new);
+
 /* ---- chain diagnostics (Sec. 6.2) ---------------------------------------- */
 
 /* A device trajectory of n_chains chains x n_dof degrees of freedom (at most

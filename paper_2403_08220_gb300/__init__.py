@@ -126,6 +126,7 @@ _SIGNATURES = {
     "dino_set_true_model": ([_P, _I, ct.POINTER(_TrueDesc)], _I),
     "dino_chains_read_da": ([_P, _I, _D, _D, _D, ct.POINTER(_I)], _I),
     "dino_set_wait_limit": ([_P, ct.c_uint32], _I),
+    "dino_dis_from_surrogate": ([_P, _I, _I, ct.c_uint64, _I, _D, _D, _D, _D], _I),
     "dino_diag_create": ([_P, _I, _I, _I, ct.POINTER(_I)], _I),
     "dino_diag_record": ([_P, _I, _I, _I, _I], _I),
     "dino_diag_push": ([_P, _I, _D], _I),
@@ -357,6 +358,16 @@ def dino_chains_read_da(ctx: Ctx, pool: int, C: int) -> dict:
                                           _dptr(out["log_rho2"]), _dptr(out["log_u2"]),
                                           out["stage1"].ctypes.data_as(ct.POINTER(_I))))
     out["stage1"] = out["stage1"].astype(bool)
+    return out
+
+
+def dino_dis_from_surrogate(ctx: Ctx, sid: int, n_samples: int, seed: int, r_new: int, r: int,
+                            N: int) -> dict:
+    out = dict(eigvals=np.empty(r), P=np.empty((r, r_new)), E=np.empty((r_new, N)),
+               D=np.empty((N, r_new)))
+    _check(ctx, lib().dino_dis_from_surrogate(ctx.ptr, sid, n_samples, int(seed), r_new,
+                                              _dptr(out["eigvals"]), _dptr(out["P"]),
+                                              _dptr(out["E"]), _dptr(out["D"])))
     return out
 
 

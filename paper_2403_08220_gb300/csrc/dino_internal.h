@@ -229,6 +229,13 @@ cudaError_t launch_sym_sqrt(int d, const double *Q, const double *lam, double *S
 cudaError_t launch_small_mm(int d, const double *A, const double *B, double *C, cudaStream_t st);
 cudaError_t launch_mpsrf_final(int d, const double *W, const double *V, const double *sig,
                                double *out, cudaStream_t st);
+// out (n x r) = standard normals of Philox (seed, stream, step 0, chain i)
+cudaError_t launch_normals(uint64_t seed, uint32_t stream, int n, int r, double *out,
+                           cudaStream_t st);
+// dst (cols x rows, FP64) = scale * src^T, src rows x cols (row pitch ld, FP64 or FP32)
+cudaError_t launch_transpose(int rows, int cols, const void *src, int src_f32, int ld,
+                             double scale, double *dst, cudaStream_t st);
+constexpr uint32_t STREAM_DIS_ID = 6;  // Monte Carlo draws of the surrogate DIS
 
 // ---- tcgen05 BF16 GEMM (sm_103a) -----------------------------------------
 // Operands are bf16 "slice planes": X ~= sum_s X_s, plane s at X + s * plane.

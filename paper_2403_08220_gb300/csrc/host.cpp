@@ -1631,6 +1631,85 @@ static void surrogate_eval(dino_ctx *ctx, int sid, int n, const double *x_host, 
 }
 
 // ---------------------------------------------------------------------------
+// derivative-informed subspace from the surrogate's Jacobians (setup)
+
+static void dis_from_surrogate(dino_ctx *ctx, int sid, int n, uint64_t seed, int r_new,
+                               double *eig, double *P_out, double *E_out, double *D_out) {
+  Surrogate *s = get_surrogate(ctx, sid);
+  const int r = s->r, dy = s->d_y, N = s->N;
+  if (n < 1 || r_new < 1 || r_new > r) fail(DINO_EINVAL, "need n >= 1 and 1 <= r_new <= r");
+  cudaStream_t st = ctx->stream;
+  Pool p;  // scratch pool-shaped workspace for the surrogate evaluation at n points
+  p.s = s;
+  p.C = n;
+  p.dt = 1.0;
+  p.sc = 0.6;
+  layout_pool(p, false);
+  p.ar.bytes = p.ar.off;
+  const size_t K = (size_t)n * dy, rr = (size_t)r * r;
+  const size_t wbytes = (K * r + 4 * rr + r + (size_t)N * r + 2 * (size_t)N * r_new +
+                         (size_t)r_new * r) * 8;
+  p.ar.base = (char *)dev_alloc(ctx, p.ar.bytes);
+  double *w = nullptr;
+  try {
+    w = (double *)dev_alloc(ctx, wbytes);
+    layout_pool(p, true);
+    double *At = w, *H = At + K * r, *G = H + rr, *Q = G + rr, *sig = Q + rr, *Et = sig + r + rr,
+           *Dn = Et + (size_t)N * r, *En = Dn + (size_t)N * r_new, *PrT = En + (size_t)N * r_new;
+    // encoded prior draws m_r ~ N(0, I_r) and the surrogate's Jacobian there
+    launch(ctx, st, "normals", [&] { return launch_normals(seed, STREAM_DIS_ID, n, r, p.b, st); });
+    split_input(ctx, s, p.w, p.b, st);
+    eval_surrogate(ctx, s, p.w, p.b, st);
+    const bool tc = s->precision == DINO_PREC_BF16;
+    // H_mc = (1/n) sum_i J_i^T J_i / noise_var = At At^T, At = J^T / sqrt(n noise_var)
+    launch(ctx, st, "transpose", [&] {
+      return launch_transpose((int)K, r, tc ? (const void *)p.w.J32 : (const void *)p.w.J64,
+                              tc ? 1 : 0, r, 1.0 / std::sqrt((double)n * s->noise_var), At, st);
+    });
+    launch(ctx, st, "dis_gram", [&] {
+      return gemm_store<double>(r, r, (int)K, At, (int)K, At, (int)K, H, r, st);
+    });
+    CK(cudaMemcpyAsync(G, H, rr * 8, cudaMemcpyDeviceToDevice, st));
+    launch(ctx, st, "jacobi", [&] { return launch_jacobi(r, G, Q, sig, nullptr, st); });
+    std::vector<double> lam(r), Qh(rr);
+    CK(cudaMemcpyAsync(lam.data(), sig, r * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(Qh.data(), Q, rr * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    // decreasing eigenvalues (H_mc is positive semidefinite: column norms = eigenvalues)
+    std::vector<int> order(r);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lam[a] > lam[b]; });
+    std::vector<double> prt((size_t)r_new * r);
+    for (int i = 0; i < r_new; ++i)
+      for (int k = 0; k < r; ++k) prt[(size_t)i * r + k] = Qh[(size_t)order[i] * r + k];
+    if (eig)
+      for (int i = 0; i < r; ++i) eig[i] = lam[order[i]];
+    if (P_out)
+      for (int k = 0; k < r; ++k)
+        for (int i = 0; i < r_new; ++i) P_out[(size_t)k * r_new + i] = prt[(size_t)i * r + k];
+    CK(cudaMemcpyAsync(PrT, prt.data(), prt.size() * 8, cudaMemcpyHostToDevice, st));
+    // D' = D P_r' and E' = P_r'^T E
+    launch(ctx, st, "dis_basis", [&] {
+      return gemm_store<double>(N, r_new, r, s->dD, r, PrT, r, Dn, r_new, st);
+    });
+    launch(ctx, st, "transpose", [&] { return launch_transpose(r, N, s->dE, 0, N, 1.0, Et, st); });
+    launch(ctx, st, "dis_basis", [&] {
+      return gemm_store<double>(r_new, N, r, PrT, r, Et, r, En, N, st);
+    });
+    if (D_out) CK(cudaMemcpyAsync(D_out, Dn, (size_t)N * r_new * 8, cudaMemcpyDeviceToHost, st));
+    if (E_out) CK(cudaMemcpyAsync(E_out, En, (size_t)N * r_new * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  } catch (...) {
+    cudaStreamSynchronize(st);
+    if (w) dev_free(ctx, w, wbytes);
+    dev_free(ctx, p.ar.base, p.ar.bytes);
+    throw;
+  }
+  dev_free(ctx, w, wbytes);
+  dev_free(ctx, p.ar.base, p.ar.bytes);
+}
+
+// ---------------------------------------------------------------------------
 // chain diagnostics: a device trajectory of n_c chains x d degrees of freedom
 
 struct Diag {
@@ -2412,6 +2491,14 @@ int dino_chains_read_da(dino_ctx *ctx, int pool_id, double *phi_true, double *lo
     if (log_rho2) CK(cudaMemcpy(log_rho2, p->lr2, C * 8, cudaMemcpyDeviceToHost));
     if (log_u2) CK(cudaMemcpy(log_u2, p->lu2, C * 8, cudaMemcpyDeviceToHost));
     if (stage1) CK(cudaMemcpy(stage1, p->st1, C * 4, cudaMemcpyDeviceToHost));
+  });
+}
+
+int dino_dis_from_surrogate(dino_ctx *ctx, int surrogate_id, int n_samples, uint64_t seed,
+                            int r_new, double *eigvals, double *P, double *E_new, double *D_new) {
+  return guarded(ctx, [&] {
+    cudaSetDevice(ctx->device);
+    dis_from_surrogate(ctx, surrogate_id, n_samples, seed, r_new, eigvals, P, E_new, D_new);
   });
 }
 

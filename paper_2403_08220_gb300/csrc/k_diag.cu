@@ -23,7 +23,10 @@
 //                   eigenvectors;
 //   k_sym_sqrt, k_mm  the square root Q diag(sqrt(lambda)) Q^T and the small
 //                   products of the Wasserstein MPSRF
-//                   Tr(W + V - 2 (W^1/2 V W^1/2)^1/2).
+//                   Tr(W + V - 2 (W^1/2 V W^1/2)^1/2);
+//   k_normals, k_transpose  the encoded prior draws and the stacked transposed
+//                   Jacobian of the surrogate-driven DIS basis (eq:mc_ppgnh),
+//                   whose eigenproblem the same Jacobi kernel solves.
 // Every loop is bounded by the sizes (lags by n_s, Jacobi sweeps by
 // kMaxSweeps); no kernel waits on another CTA.
 #include <algorithm>
@@ -284,6 +287,30 @@ __global__ void k_mpsrf_final(int d, const double *__restrict__ W, const double 
 
 int grid_for(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 8) + 0; }
 
+// out[i r + q] = normal q of Philox (seed, stream, step 0, "chain" i), i < n
+__global__ void k_normals(uint64_t seed, uint32_t stream, int n, int r, double *__restrict__ out) {
+  const int nb = (r + 3) / 4;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)n * nb;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / nb), blk = (int)(e - (size_t)i * nb);
+    double z[4];
+    normals4_f64(philox_block(seed, stream, 0, (uint32_t)i, blk), z);
+    for (int q = 0; q < 4; ++q)
+      if (4 * blk + q < r) out[(size_t)i * r + 4 * blk + q] = z[q];
+  }
+}
+
+// dst[c rows + i] = scale * src[i ld + c]  (rows x cols -> cols x rows, FP64)
+template <typename T>
+__global__ void k_transpose(int rows, int cols, const T *__restrict__ src, int ld, double scale,
+                            double *__restrict__ dst) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)rows * cols;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const size_t c = e / rows, i = e - c * rows;
+    dst[e] = scale * (double)src[i * ld + c];
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_diag_record(int n_c, int d, const void *src, int src_f32, int ld_src,
@@ -340,6 +367,25 @@ cudaError_t launch_sym_sqrt(int d, const double *Q, const double *lam, double *S
 
 cudaError_t launch_small_mm(int d, const double *A, const double *B, double *C, cudaStream_t st) {
   k_mm<<<grid_for((size_t)d * d), 256, 0, st>>>(d, A, B, C);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_normals(uint64_t seed, uint32_t stream, int n, int r, double *out,
+                           cudaStream_t st) {
+  if (n <= 0 || r <= 0) return cudaSuccess;
+  k_normals<<<grid_for((size_t)n * ((r + 3) / 4)), 256, 0, st>>>(seed, stream, n, r, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transpose(int rows, int cols, const void *src, int src_f32, int ld,
+                             double scale, double *dst, cudaStream_t st) {
+  const size_t n = (size_t)rows * cols;
+  if (n == 0) return cudaSuccess;
+  if (src_f32)
+    k_transpose<float><<<grid_for(n), 256, 0, st>>>(rows, cols, (const float *)src, ld, scale, dst);
+  else
+    k_transpose<double><<<grid_for(n), 256, 0, st>>>(rows, cols, (const double *)src, ld, scale,
+                                                     dst);
   return cudaGetLastError();
 }
 
