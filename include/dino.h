@@ -174,6 +174,8 @@ typedef struct {
   int gram_on_tensor_cores;
   int fwd_slices, jac_slices;
   int true_model_rank;  /* r_t of an attached true map, 0 if none */
+  int jac_forward;      /* 1: the Jacobian is accumulated in forward mode (r < d_y
+                           and fewer flops, Sec. 4.3's min{d_y, r} rule), 0: reverse */
 } dino_surrogate_info;
 
 int dino_surrogate_query(dino_ctx *ctx, int surrogate_id, dino_surrogate_info *info);

@@ -65,7 +65,8 @@ class _Info(ct.Structure):
     _fields_ = [("N", ct.c_int), ("r", ct.c_int), ("d_y", ct.c_int), ("n_layers", ct.c_int),
                 ("precision", ct.c_int), ("noise_map", ct.c_int),
                 ("gram_on_tensor_cores", ct.c_int), ("fwd_slices", ct.c_int),
-                ("jac_slices", ct.c_int), ("true_model_rank", ct.c_int)]
+                ("jac_slices", ct.c_int), ("true_model_rank", ct.c_int),
+                ("jac_forward", ct.c_int)]
 
 
 class _DiagResult(ct.Structure):

@@ -167,6 +167,9 @@ cudaError_t launch_jac_init(int C, int d_y, int w, const T *WL, const T *der, in
 template <typename T>
 cudaError_t launch_broadcast(int C, size_t n, const T *src, T *out, cudaStream_t st);
 cudaError_t launch_f64_to_f32(size_t n, const double *src, float *dst, cudaStream_t st);
+// dst[c][i][j] = src[c][j][i]: C blocks of a x b (src) into b x a (dst), FP64 or FP32 (f32)
+cudaError_t launch_batched_transpose(int C, int a, int b, const void *src, int f32, void *dst,
+                                     cudaStream_t st);
 // dst[i] = src[i]; src may be pageable host memory on a device that reads it
 // coherently (cudaDevAttrPageableMemoryAccess)
 cudaError_t launch_copy_f64(size_t n, const double *src, double *dst, cudaStream_t st);

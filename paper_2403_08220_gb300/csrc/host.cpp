@@ -406,6 +406,15 @@ struct Surrogate {
   // Woodbury path on the tensor path with d_y <= 128 and a hidden layer: the
   // d_y x d_y Gram matrices J J^T come from the tensor cores
   bool tc_gram = false;
+  // Jacobian order: forward mode (push the r input directions) when r < d_y
+  // and it takes fewer flops than reverse mode (pull the d_y outputs), the
+  // min{d_y, r} rule of Sec. 4.3; the tensor path then keeps FP32 W_0^T and
+  // jac_slices bf16 planes of W_1 .. W_{L-1} (pitch ldWj)
+  bool jac_fwd = false;
+  float *fW0T = nullptr;
+  std::vector<__nv_bfloat16 *> bWj;
+  std::vector<int> ldWj;
+  std::vector<size_t> plWj;
   int pools = 0;
   // device
   std::vector<std::pair<void *, size_t>> allocs;
@@ -707,6 +716,31 @@ static int load_surrogate(dino_ctx *ctx, const dino_surrogate_desc *d) {
       s->plWT.push_back(plt);
     }
   }
+  {
+    // flops per chain of one slice product: reverse 2 d_y sum_{l=0}^{L-2} w_l w_{l+1},
+    // forward 2 r sum_{l=1}^{L-1} w_l w_{l+1}
+    double rev = 0.0, fwd = 0.0;
+    for (int l = 0; l + 1 < s->L; ++l) rev += 2.0 * s->d_y * s->widths[l] * s->widths[l + 1];
+    for (int l = 1; l < s->L; ++l) fwd += 2.0 * s->r * s->widths[l] * s->widths[l + 1];
+    s->jac_fwd = s->L >= 2 && !s->wb && s->r < s->d_y && fwd < rev;
+  }
+  if (s->jac_fwd && s->precision == DINO_PREC_BF16) {
+    const int w1 = s->widths[1];
+    std::vector<double> W0T((size_t)r * w1);
+    for (int i = 0; i < w1; ++i)
+      for (int j = 0; j < r; ++j) W0T[(size_t)j * w1 + i] = s->W[0][(size_t)i * r + j];
+    const auto f0t = to_f32(W0T);
+    s->fW0T = sur_upload(ctx, s.get(), f0t.data(), f0t.size());
+    s->bWj.assign(s->L, nullptr);
+    s->ldWj.assign(s->L, 0);
+    s->plWj.assign(s->L, 0);
+    for (int l = 1; l < s->L; ++l) {
+      const int wo = s->widths[l + 1], wi = s->widths[l];
+      s->ldWj[l] = pad8(wi);
+      const auto bw = split_planes(s->W[l], wo, wi, s->ldWj[l], s->jac_slices, s->plWj[l]);
+      s->bWj[l] = sur_upload(ctx, s.get(), bw.data(), bw.size());
+    }
+  }
   if (s->precision == DINO_PREC_BF16) {
     const auto fS = to_f32(S), fL = to_f32(sqrtlam);
     s->fS = sur_upload(ctx, s.get(), fS.data(), fS.size());
@@ -748,6 +782,8 @@ struct Work {
   std::vector<size_t> plact;
   std::vector<float *> der32;
   float *f32 = nullptr, *J32 = nullptr;
+  // forward-mode Jacobian: J^T per chain (C x r x d_y), FP64 or FP32
+  void *Jt = nullptr;
   __nv_bfloat16 *Pb[2] = {nullptr, nullptr};
   int ldp = 0;
   size_t plp = 0;
@@ -772,6 +808,8 @@ static void layout_work(const Surrogate *s, int C, Arena &ar, Work &w, bool assi
   w.C = C;
   const int L = s->L, dy = s->d_y;
   const size_t rows = (size_t)C * dy;
+  // rows of the stacked Jacobian accumulation: d_y per chain in reverse mode, r in forward
+  const size_t prows = s->jac_fwd ? (size_t)C * std::max(dy, s->r) : rows;
   w.act64.assign(L, nullptr);
   w.der64.assign(L, nullptr);
   w.der32.assign(L, nullptr);
@@ -785,10 +823,11 @@ static void layout_work(const Surrogate *s, int C, Arena &ar, Work &w, bool assi
     }
     w.f64 = (double *)take((size_t)C * dy * 8);
     if (L >= 2) {
-      w.P64[0] = (double *)take(rows * s->widest * 8);
-      w.P64[1] = (double *)take(rows * s->widest * 8);
+      w.P64[0] = (double *)take(prows * s->widest * 8);
+      w.P64[1] = (double *)take(prows * s->widest * 8);
     }
     w.J64 = (double *)take(rows * s->r * 8);
+    if (s->jac_fwd) w.Jt = take(rows * s->r * 8);
   } else {
     w.ldx = pad8(s->r);
     w.plx = (size_t)C * w.ldx;
@@ -803,11 +842,12 @@ static void layout_work(const Surrogate *s, int C, Arena &ar, Work &w, bool assi
     w.f32 = (float *)take((size_t)C * dy * 4);
     if (L >= 2) {
       w.ldp = pad8(s->widest);
-      w.plp = rows * w.ldp;
+      w.plp = prows * w.ldp;
       w.Pb[0] = (__nv_bfloat16 *)take(w.plp * s->jac_slices * 2);
       w.Pb[1] = (__nv_bfloat16 *)take(w.plp * s->jac_slices * 2);
     }
     w.J32 = (float *)take(rows * s->r * 4);
+    if (s->jac_fwd) w.Jt = take(rows * s->r * 4);
     if (gram) {
       w.ldjb = pad8(s->r);
       w.pljb = rows * w.ldjb;
@@ -848,6 +888,32 @@ static void eval_surrogate(dino_ctx *ctx, const Surrogate *s, Work &w, const dou
     if (L == 1) {
       launch(ctx, st, "jac_broadcast", [&] {
         return launch_broadcast<double>(C, (size_t)dy * r, s->dW[0], w.J64, st);
+      });
+      return;
+    }
+    if (s->jac_fwd) {
+      // forward mode on J^T: T = W_0^T .* d_0 (r x w_1 per chain);
+      // T <- (T W_l^T) .* d_l; J^T = T W_{L-1}^T, then J per chain
+      const int w1 = s->widths[1];
+      launch(ctx, st, "jac_init_f64", [&] {
+        return launch_jac_init<double>(C, r, w1, s->dWT[0], w.der64[0], w1, w.P64[0], st);
+      });
+      int cur = 0;
+      for (int l = 1; l + 1 < L; ++l) {
+        const int wi = s->widths[l], wo = s->widths[l + 1];
+        launch(ctx, st, "jac_gemm_f64", [&] {
+          return gemm_scale_group<double>(C * r, wo, wi, w.P64[cur], wi, s->dW[l], wi,
+                                          w.der64[l], wo, r, w.P64[1 - cur], wo, st);
+        });
+        cur = 1 - cur;
+      }
+      const int wl = s->widths[L - 1];
+      launch(ctx, st, "jac_gemm_f64", [&] {
+        return gemm_store<double>(C * r, dy, wl, w.P64[cur], wl, s->dW[L - 1], wl,
+                                  (double *)w.Jt, dy, st);
+      });
+      launch(ctx, st, "jac_transpose", [&] {
+        return launch_batched_transpose(C, r, dy, w.Jt, 0, w.J64, st);
       });
       return;
     }
@@ -917,6 +983,49 @@ static void eval_surrogate(dino_ctx *ctx, const Surrogate *s, Work &w, const dou
     g.outf = w.f32;
     g.ldo = dy;
     launch(ctx, st, "mlp_tc", [&] { return launch_tc_gemm(g, st); });
+  }
+  if (s->jac_fwd) {
+    // forward mode on J^T (see the FP64 path), bf16 slices of T, W_l as B
+    const int w1 = s->widths[1];
+    launch(ctx, st, "jac_init_tc", [&] {
+      return launch_jac_init_bf16(C, r, w1, s->fW0T, w.der32[0], w1, w.Pb[0], w.ldp, w.plp,
+                                  s->jac_slices, st);
+    });
+    int cur = 0;
+    for (int l = 1; l < L; ++l) {
+      const bool last = l + 1 == L;
+      TcGemmArgs g;
+      g.M = C * r;
+      g.N = s->widths[l + 1];
+      g.K = s->widths[l];
+      g.A = w.Pb[cur];
+      g.lda = w.ldp;
+      g.a_plane = w.plp;
+      g.B = s->bWj[l];
+      g.ldb = s->ldWj[l];
+      g.b_plane = s->plWj[l];
+      g.nslice = s->jac_slices;
+      if (last) {
+        g.epi = TC_EPI_STORE_F32;
+        g.outf = (float *)w.Jt;
+        g.ldo = dy;
+      } else {
+        g.epi = TC_EPI_SCALE_GROUP;
+        g.scale = w.der32[l];
+        g.lds = s->widths[l + 1];
+        g.group = r;
+        g.out_bf = w.Pb[1 - cur];
+        g.ldo = w.ldp;
+        g.out_plane = w.plp;
+        g.out_slices = s->jac_slices;
+      }
+      launch(ctx, st, "jac_tc", [&] { return launch_tc_gemm(g, st); });
+      cur = 1 - cur;
+    }
+    launch(ctx, st, "jac_transpose", [&] {
+      return launch_batched_transpose(C, r, dy, w.Jt, 1, w.J32, st);
+    });
+    return;
   }
   const int wl = s->widths[L - 1];
   launch(ctx, st, "jac_init_tc", [&] {
@@ -2436,6 +2545,7 @@ int dino_surrogate_query(dino_ctx *ctx, int surrogate_id, dino_surrogate_info *i
     info->fwd_slices = s->precision == DINO_PREC_BF16 ? s->fwd_slices : 0;
     info->jac_slices = s->precision == DINO_PREC_BF16 ? s->jac_slices : 0;
     info->true_model_rank = s->tm.on ? s->tm.r_t : 0;
+    info->jac_forward = s->jac_fwd ? 1 : 0;
   });
 }
 

@@ -333,6 +333,30 @@ cudaError_t gemm_field(int M, int N, int K, const T *A, int lda, const T *B, int
   return run_gemm(M, N, K, A, lda, B, ldb, EpiField<T>{acc_flag, s, c, m, Mf, ldm}, st);
 }
 
+template <typename T>
+__global__ void k_batched_transpose(int C, int a, int b, const T *__restrict__ src,
+                                    T *__restrict__ dst) {
+  const size_t blk = (size_t)a * b, n = (size_t)C * blk;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const size_t c = e / blk, rem = e - c * blk, i = rem / a, j = rem - i * a;
+    dst[e] = src[c * blk + j * b + i];  // dst (c, i < b, j < a) = src (c, j, i)
+  }
+}
+
+cudaError_t launch_batched_transpose(int C, int a, int b, const void *src, int f32, void *dst,
+                                     cudaStream_t st) {
+  const size_t n = (size_t)C * a * b;
+  if (n == 0) return cudaSuccess;
+  const int grid = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
+  if (f32)
+    k_batched_transpose<float><<<grid, 256, 0, st>>>(C, a, b, (const float *)src, (float *)dst);
+  else
+    k_batched_transpose<double><<<grid, 256, 0, st>>>(C, a, b, (const double *)src,
+                                                      (double *)dst);
+  return cudaGetLastError();
+}
+
 size_t prior_draw_smem_bytes(int n, int elem) {
   return 3 * (size_t)prior_ld(n) * prior_ld(n) * elem;
 }

@@ -83,6 +83,16 @@ CONFIGS = {
                               activation=ACT_GELU, basis_kind=BASIS_DIS,
                               n_chains=16384, n_steps=1000, precision="bf16",
                               noise_map="perturbation"),
+    # the paper's network shape (Sec. 7-8: six hidden layers of 400 GELU units,
+    # r = 200 DIS; d_y = 25 and 64 observations, N of about 1681 and 2145)
+    "paper_ndr_bf16": Workload("paper_ndr_bf16", n_grid=41, r=200,
+                               widths=[200] + [400] * 6 + [25], activation=ACT_GELU,
+                               basis_kind=BASIS_DIS, n_chains=16384, n_steps=1000,
+                               precision="bf16", noise_map="perturbation"),
+    "paper_hyper_bf16": Workload("paper_hyper_bf16", n_grid=46, r=200,
+                                 widths=[200] + [400] * 6 + [64], activation=ACT_GELU,
+                                 basis_kind=BASIS_DIS, n_chains=16384, n_steps=1000,
+                                 precision="bf16", noise_map="perturbation"),
 }
 
 
