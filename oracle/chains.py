@@ -81,6 +81,8 @@ class OracleChains:
         if self.noise == "perturbation":
             xi2 = draw("xi2", philox.STREAM_XI2, sur.d_y)
             mu, b = mmala.reduced_proposal_perturbation(a, geo_a, xi, xi2, sur.noise_var, dt)
+        elif self.noise == "eigen":
+            mu, b = mmala.reduced_proposal_sqrt(a, geo_a, xi, dt)
         else:
             mu, b = mmala.reduced_proposal(a, geo_a, xi, dt)
         geo_b = mmala.geometry(sur, b)

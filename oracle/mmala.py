@@ -21,6 +21,8 @@ Readings of the paper taken here (each also listed in the design notes):
   factor).  It has the law of the eigen form of eq:reduced_space_sampling
   (covariance (1 - s^2)(I + H)^-1); `reduced_proposal_eigen` keeps the
   paper's map for distribution checks.
+* The paper's own eigen map, in its symmetric form P diag((d+1)^-1/2) P^T xi
+  (`reduced_proposal_sqrt`), is a third choice with the same law.
 * The noise may instead be drawn as zeta = (I + H)^-1 (xi1 + K^T xi2) with
   K = J / sqrt(noise_var) and d_y further normals xi2: the same law
   (`reduced_proposal_perturbation`), which needs only the d_y x d_y matrix
@@ -116,7 +118,7 @@ def reduced_proposal(a, geo: Geometry, xi, dt: float):
     return mu, mu + np.sqrt(1.0 - s * s) * eta
 
 
-NOISE_MAPS = ("cholesky", "perturbation")
+NOISE_MAPS = ("cholesky", "perturbation", "eigen")
 
 
 def reduced_proposal_perturbation(a, geo: Geometry, xi1, xi2, noise_var: float, dt: float):
@@ -134,6 +136,24 @@ def reduced_proposal_perturbation(a, geo: Geometry, xi1, xi2, noise_var: float, 
     rhs = (np.asarray(xi1, dtype=np.float64)
            + np.einsum("...ij,...i->...j", K, np.asarray(xi2, dtype=np.float64)))
     zeta = _solve(np.eye(r) + geo.H, rhs)
+    return mu, mu + np.sqrt(1.0 - s * s) * zeta
+
+
+def reduced_proposal_sqrt(a, geo: Geometry, xi, dt: float):
+    """m_r^dagger = mu + sqrt(1 - s^2) (I + H)^-1/2 xi with the symmetric root
+    (I + H)^-1/2 = P diag((d + 1)^-1/2) P^T, H = P diag(d) P^T.
+
+    This is the eigen form of eq:reduced_space_sampling written so that it
+    does not depend on the signs or the order of the eigenvectors: the
+    paper's P diag(...) Xi with Xi = P^T xi (the same law, since P^T xi is
+    again standard normal).  Returns (mu, b).
+    """
+    s = s_of_dt(dt)
+    mu = proposal_mean(a, geo, dt)
+    d, P = np.linalg.eigh(geo.H)
+    Pt = np.swapaxes(P, -1, -2)
+    y = np.einsum("...ij,...j->...i", Pt, np.asarray(xi, dtype=np.float64))
+    zeta = np.einsum("...ij,...j->...i", P, y / np.sqrt(d + 1.0))
     return mu, mu + np.sqrt(1.0 - s * s) * zeta
 
 

@@ -286,3 +286,24 @@ def test_given_noise_reproduces_the_philox_step():
         assert not np.allclose(a.last["b"], b.last["b"])
     with pytest.raises(ValueError):
         OracleChains(sur, E, D, n, GAMMA, DELTA, C, dt, seed=5, noise="auto")
+
+
+def test_eigen_map_law_and_the_papers_form():
+    """The symmetric eigen map has covariance (1 - s^2)(I + H)^-1 exactly, and
+    equals the paper's P diag(sqrt((1 - s^2)/(d + 1))) Xi of
+    eq:reduced_space_sampling for Xi = P^T xi."""
+    r, dt = 6, 0.4
+    s = mmala.s_of_dt(dt)
+    sur = _surrogate([r, 9, 4], mlp.ACT_GELU, noise_var=0.2)
+    a = np.random.default_rng(12).standard_normal(r)
+    geo = mmala.geometry(sur, a)
+    mu, b0 = mmala.reduced_proposal_sqrt(a, geo, np.zeros(r), dt)
+    assert np.allclose(b0, mu, atol=1e-14)
+    T = np.array([mmala.reduced_proposal_sqrt(a, geo, e, dt)[1] - b0 for e in np.eye(r)]).T
+    cov = (1 - s * s) * np.linalg.inv(np.eye(r) + geo.H)
+    assert np.allclose(T @ T.T, cov, atol=1e-12 * np.abs(cov).max())
+    assert np.allclose(T, T.T, atol=1e-13)                # a symmetric root
+    xi = np.random.default_rng(13).standard_normal(r)
+    d, P = np.linalg.eigh(geo.H)
+    paper = mmala.reduced_proposal_eigen(a, geo.H, geo.g, P.T @ xi, dt)
+    assert np.allclose(mmala.reduced_proposal_sqrt(a, geo, xi, dt)[1], paper, atol=1e-12)
