@@ -175,7 +175,7 @@ def load_surrogate(dino, ctx, w):
         ctx, n_grid=w.n_grid, prior_gamma=w.prior_gamma, prior_delta=w.prior_delta, r=w.r,
         widths=w.widths, activation=w.activation, W=inp["Ws"], b=inp["bs"],
         basis_kind=w.basis_kind, basis_gauss=inp["G"], precision=prec,
-        noise_map={"auto": 0, "cholesky": 1, "perturbation": 2}[w.noise_map])
+        noise_map={"auto": 0, "cholesky": 1, "perturbation": 2, "eigen": 3}[w.noise_map])
     twin = dino.dino_load_surrogate(
         ctx, n_grid=w.n_grid, prior_gamma=w.prior_gamma, prior_delta=w.prior_delta, r=w.r,
         widths=w.widths, activation=w.activation, W=inp["Ws"], b=inp["bs"],

@@ -80,10 +80,16 @@ extern "C" {
  *   PERTURBATION  zeta = (I + H)^-1 (xi + K^T xi2), K = J / sigma, with d_y
  *                 further normals xi2: only the d_y x d_y matrix I + K K^T is
  *                 factored (needs d_y < r and d_y <= 192);
+ *   EIGEN         zeta = (I + H)^-1/2 xi = P diag((d + 1)^-1/2) P^T xi with
+ *                 H = P diag(d) P^T: the paper's eigen form, written with the
+ *                 symmetric root so that it does not depend on eigenvector
+ *                 signs; the d_y x d_y matrix I + K K^T is eigendecomposed
+ *                 per chain (one-sided Jacobi, FP64; needs d_y < r, d_y <= 64);
  *   AUTO          PERTURBATION when it applies, else CHOLESKY. */
 #define DINO_NOISE_AUTO         0
 #define DINO_NOISE_CHOLESKY     1
 #define DINO_NOISE_PERTURBATION 2
+#define DINO_NOISE_EIGEN        3
 
 #define DINO_FLAG_TIMING 1u   /* record per-kernel CUDA-event times */
 #define DINO_FLAG_NO_DIRECT_HOST 2u /* copy host fields with cudaMemcpy even where

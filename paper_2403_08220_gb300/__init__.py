@@ -34,8 +34,9 @@ DINO_ESTATE = -8
 DINO_ACT_IDENTITY, DINO_ACT_TANH, DINO_ACT_GELU = 0, 1, 2
 DINO_BASIS_KLE, DINO_BASIS_DIS, DINO_BASIS_EXPLICIT = 0, 1, 2
 DINO_PREC_FP64, DINO_PREC_BF16 = 0, 1
-DINO_NOISE_AUTO, DINO_NOISE_CHOLESKY, DINO_NOISE_PERTURBATION = 0, 1, 2
-NOISE_MAP_NAMES = {DINO_NOISE_CHOLESKY: "cholesky", DINO_NOISE_PERTURBATION: "perturbation"}
+DINO_NOISE_AUTO, DINO_NOISE_CHOLESKY, DINO_NOISE_PERTURBATION, DINO_NOISE_EIGEN = 0, 1, 2, 3
+NOISE_MAP_NAMES = {DINO_NOISE_CHOLESKY: "cholesky", DINO_NOISE_PERTURBATION: "perturbation",
+                   DINO_NOISE_EIGEN: "eigen"}
 DINO_DIAG_REDUCED, DINO_DIAG_FIELD = 0, 1
 DINO_FLAG_TIMING = 1
 DINO_FLAG_NO_DIRECT_HOST = 2

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libdino.so")
 SOURCES = ["host.cpp", "k_reduced.cu", "k_woodbury.cu", "k_simt.cu", "k_tc.cu", "k_da.cu",
-           "k_diag.cu", "noalloc.cu"]
+           "k_diag.cu", "k_eig.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(HERE, "..", "include")]

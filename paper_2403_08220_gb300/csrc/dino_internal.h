@@ -118,6 +118,13 @@ cudaError_t launch_geometry(const ReducedArgs &a, int mode, cudaStream_t st);
 size_t wb_smem_bytes(int r, int d_y, int jf_f32);
 cudaError_t launch_wb_propose(const ReducedArgs &a, cudaStream_t st);
 cudaError_t launch_wb_geometry(const ReducedArgs &a, int mode, cudaStream_t st);
+// The eigen map (d_y < r, d_y <= kMaxEigDy): the same two steps with the
+// eigendecomposition of I + K K^T and the noise (I + H)^-1/2 xi.
+constexpr int kMaxEigDy = 64;
+size_t eig_slot_stride(int d_y);
+size_t eig_smem_bytes(int r, int d_y);
+cudaError_t launch_eig_propose(const ReducedArgs &a, cudaStream_t st);
+cudaError_t launch_eig_geometry(const ReducedArgs &a, int mode, cudaStream_t st);
 
 // ---- SIMT GEMMs: out = epilogue(A B^T), A: M x K (lda), B: N x K (ldb) ----
 template <typename T>

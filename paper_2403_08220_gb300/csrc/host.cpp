@@ -406,6 +406,9 @@ struct Surrogate {
   // Woodbury path on the tensor path with d_y <= 128 and a hidden layer: the
   // d_y x d_y Gram matrices J J^T come from the tensor cores
   bool tc_gram = false;
+  // eigen map (d_y < r): I + K K^T eigendecomposed instead of factored; the
+  // pools keep the perturbation path's J state (wb is set too)
+  bool eig = false;
   // Jacobian order: forward mode (push the r input directions) when r < d_y
   // and it takes fewer flops than reverse mode (pull the d_y outputs), the
   // min{d_y, r} rule of Sec. 4.3; the tensor path then keeps FP32 W_0^T and
@@ -632,7 +635,15 @@ static int load_surrogate(dino_ctx *ctx, const dino_surrogate_desc *d) {
     s->wb = s->d_y < s->r && s->d_y <= kMaxWbDy;
   else if (d->noise_map == DINO_NOISE_CHOLESKY)
     s->wb = false;
-  else if (d->noise_map == DINO_NOISE_PERTURBATION) {
+  else if (d->noise_map == DINO_NOISE_EIGEN) {
+    if (!(s->d_y < s->r && s->d_y <= kMaxEigDy))
+      fail(DINO_EINVAL, "the eigen noise map needs d_y < r and d_y <= %d (d_y=%d, r=%d)",
+           kMaxEigDy, s->d_y, s->r);
+    if (eig_smem_bytes(s->r, s->d_y) > kSmemLimit)
+      fail(DINO_EINVAL, "r=%d, d_y=%d exceed the eigen map's shared-memory budget", s->r, s->d_y);
+    s->wb = true;
+    s->eig = true;
+  } else if (d->noise_map == DINO_NOISE_PERTURBATION) {
     if (!(s->d_y < s->r && s->d_y <= kMaxWbDy))
       fail(DINO_EINVAL, "the perturbation noise map needs d_y < r and d_y <= %d (d_y=%d, r=%d)",
            kMaxWbDy, s->d_y, s->r);
@@ -1101,6 +1112,7 @@ struct Pool {
   uint64_t seed = 0, id_base = 0;
   uint32_t step = 0;
   Arena ar;
+  bool eig = false;  // eigen map (with wb: the J state of the d_y-sized path)
   bool wb = false;  // Woodbury path (the surrogate's d_y < r); scratch pools of
                     // surrogate_eval always take the r-sized path
   // state
@@ -1155,7 +1167,8 @@ static void layout_pool(Pool &p, bool assign) {
   p.g = (double *)take((size_t)C * r * 8);
   p.phi = (double *)take((size_t)C * 8);
   p.hld = (double *)take((size_t)C * 8);
-  const size_t ss = p.wb ? wb_slot_stride(s->d_y) : slot_stride(r);
+  const size_t ss = p.eig ? eig_slot_stride(s->d_y)
+                          : p.wb ? wb_slot_stride(s->d_y) : slot_stride(r);
   p.L = (double *)take(2 * (size_t)C * ss * 8);  // two slots
   p.cur = (int *)take((size_t)C * 4);
   p.Js = p.wb ? take((size_t)C * s->d_y * r * fe) : nullptr;
@@ -1237,7 +1250,8 @@ static ReducedArgs reduced_args(const Pool &p) {
   a.hld = p.hld;
   a.L = p.L;
   a.cur = p.cur;
-  a.L_slot = (size_t)p.C * (p.wb ? wb_slot_stride(s->d_y) : slot_stride(s->r));
+  a.L_slot = (size_t)p.C * (p.eig  ? eig_slot_stride(s->d_y)
+                           : p.wb ? wb_slot_stride(s->d_y) : slot_stride(s->r));
   a.Js = p.Js;
   a.G = p.w.G;
   a.ldg = p.w.ldg;
@@ -1474,6 +1488,7 @@ static Pool *create_pool_on(dino_ctx *ctx, int sid, int C, double dt, uint64_t s
   p->st = st;
   p->async_mem = serving;
   p->wb = s->wb;
+  p->eig = s->eig;
   layout_pool(*p, false);
   p->ar.bytes = p->ar.off;
   p->ar.base = (char *)(serving ? dev_alloc_async(ctx, p->ar.bytes, st)
@@ -1521,7 +1536,8 @@ static Pool *create_pool_on(dino_ctx *ctx, int sid, int C, double dt, uint64_t s
     ReducedArgs ra = reduced_args(*p);
     ra.flag_spins = ctx->flag_spins;
     launch(ctx, st, "geometry_init", [&] {
-      return p->wb ? launch_wb_geometry(ra, 0, st) : launch_geometry(ra, 0, st);
+      return p->eig ? launch_eig_geometry(ra, 0, st)
+             : p->wb ? launch_wb_geometry(ra, 0, st) : launch_geometry(ra, 0, st);
     });
     if (p->da) da_init(ctx, *p, m64, st);
     if (!serving) CK(cudaStreamSynchronize(st));
@@ -1548,6 +1564,7 @@ static size_t pool_footprint(const Surrogate *s, int C) {
   p.s = const_cast<Surrogate *>(s);
   p.C = C;
   p.wb = s->wb;
+  p.eig = s->eig;
   layout_pool(p, false);
   return p.ar.off;
 }
@@ -1563,11 +1580,13 @@ static void step_pool(dino_ctx *ctx, Pool &p) {
   const double *ext_z =
       p.ext && p.ext_z ? p.ext + (size_t)C * (r + s->d_y) : nullptr;
   launch(ctx, st, "propose", [&] {
-    return p.wb ? launch_wb_propose(ra, st) : launch_propose(ra, st);
+    return p.eig ? launch_eig_propose(ra, st) : p.wb ? launch_wb_propose(ra, st)
+                                                     : launch_propose(ra, st);
   });
   eval_surrogate(ctx, s, p.w, p.b, st, true);
   launch(ctx, st, "geometry", [&] {
-    return p.wb ? launch_wb_geometry(ra, 1, st) : launch_geometry(ra, 1, st);
+    return p.eig ? launch_eig_geometry(ra, 1, st)
+           : p.wb ? launch_wb_geometry(ra, 1, st) : launch_geometry(ra, 1, st);
   });
   // complement (Prop. 5.1): M prior draw, coef2 = (b - s a) - cs E M, m <- s m + cs M + D coef2
   if (s->precision == DINO_PREC_FP64) {
@@ -2540,7 +2559,8 @@ int dino_surrogate_query(dino_ctx *ctx, int surrogate_id, dino_surrogate_info *i
     info->d_y = s->d_y;
     info->n_layers = s->L;
     info->precision = s->precision;
-    info->noise_map = s->wb ? DINO_NOISE_PERTURBATION : DINO_NOISE_CHOLESKY;
+    info->noise_map = s->eig ? DINO_NOISE_EIGEN
+                      : s->wb ? DINO_NOISE_PERTURBATION : DINO_NOISE_CHOLESKY;
     info->gram_on_tensor_cores = s->tc_gram ? 1 : 0;
     info->fwd_slices = s->precision == DINO_PREC_BF16 ? s->fwd_slices : 0;
     info->jac_slices = s->precision == DINO_PREC_BF16 ? s->jac_slices : 0;

@@ -32,7 +32,7 @@ def oracle_setup(w: Workload):
     return sur, E, D
 
 
-NOISE_CODES = {"auto": 0, "cholesky": 1, "perturbation": 2}
+NOISE_CODES = {"auto": 0, "cholesky": 1, "perturbation": 2, "eigen": 3}
 
 
 def gpu_setup(dino, ctx, w: Workload, precision=None, fwd_slices=0, jac_slices=0):

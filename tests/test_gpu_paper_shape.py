@@ -14,7 +14,7 @@ import pytest
 
 from helpers import gpu_setup, oracle_chains, oracle_setup, rel_err, step_and_compare, variant
 from oracle import mmala
-from workloads import CONFIGS, SEED_CHAINS
+from workloads import BASIS_DIS, CONFIGS, SEED_CHAINS
 
 pytestmark = pytest.mark.gpu
 
@@ -96,4 +96,47 @@ def test_forward_mode_jacobian(dino, ctx, precision):
     else:
         jrel = np.linalg.norm(g["J"] - o.J, axis=(1, 2)) / np.linalg.norm(o.J, axis=(1, 2))
         assert jrel.max() <= 1e-4
+    dino.dino_unload_surrogate(ctx, sid)
+
+
+PERT = variant(CONFIGS["small_fp64"], n_grid=9, r=45, widths=[45, 33, 17, 20],
+               basis_kind=BASIS_DIS, activation=2, noise_frac=0.2, noise_map="eigen")
+
+
+@pytest.mark.parametrize("dt", [0.01, 0.5])
+def test_eigen_map_fp64_matches_oracle(dino, ctx, dt):
+    """The paper's eigen map (symmetric root), per-chain Jacobi eigensolver."""
+    w = PERT
+    sid = gpu_setup(dino, ctx, w)
+    assert dino.dino_surrogate_query(ctx, sid)["noise_map"] == "eigen"
+    sur, E, D = oracle_setup(w)
+    pool = dino.dino_chains_create(ctx, sid, 16, dt, SEED_CHAINS)
+    och = oracle_chains(dino, ctx, sid, w, sur, E, D, 16, dt)
+    assert och.noise == "eigen"
+    acc, _, _ = step_and_compare(dino, ctx, pool, och, w, 16, 12, tol=1e-10)
+    if dt < 0.1:
+        assert np.mean(acc) > 0
+    dino.dino_chains_destroy(ctx, pool)
+    dino.dino_unload_surrogate(ctx, sid)
+
+
+def test_eigen_map_bf16_paper_shape(dino, ctx):
+    """d_y = 25, 6 x 400 GELU on the tensor path with the eigen map."""
+    w = variant(CONFIGS["paper_ndr_bf16"], noise_map="eigen")
+    sid = gpu_setup(dino, ctx, w)
+    sur, E, D = oracle_setup(w)
+    C = 24
+    pool = dino.dino_chains_create(ctx, sid, C, w.dt, SEED_CHAINS)
+    och = oracle_chains(dino, ctx, sid, w, sur, E, D, C, w.dt)
+    for _ in range(2):
+        dino.dino_chains_step(ctx, pool, 1, stats=False)
+        och.step()
+        last = dino.dino_chains_read_last(ctx, pool, C, w.r)
+        err = np.linalg.norm(last["mu"] - och.last["mu"], axis=1) / np.linalg.norm(
+            och.last["mu"], axis=1)
+        assert err.max() <= 1e-3
+        bdiff = np.linalg.norm(last["b"] - och.last["b"], axis=1) / np.linalg.norm(
+            och.last["b"], axis=1)
+        assert bdiff.max() <= 1e-3
+    dino.dino_chains_destroy(ctx, pool)
     dino.dino_unload_surrogate(ctx, sid)
