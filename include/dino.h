@@ -249,6 +249,14 @@ typedef struct {
  * stats (may be NULL) receives the totals of this call (it synchronises). */
 int dino_chains_step(dino_ctx *ctx, int pool_id, int n_steps, dino_step_stats *stats);
 
+/* Advance several pools by n_steps transitions each, concurrently: every
+ * pool runs on a stream of its own (up to 16, created by the context on
+ * first use) after the work already issued on its stream, and its stream
+ * waits for the result, so the call returns without synchronising.  The
+ * results are those of dino_chains_step on each pool.  Errors: ENOTFOUND,
+ * EINVAL (a pool listed twice, a serving pool). */
+int dino_chains_step_many(dino_ctx *ctx, int n_pools, const int *pool_ids, int n_steps);
+
 /* Copy the current chain positions m_j of Algorithm 1 to host buffers (any
  * may be NULL): the field m (n_chains x N, row-major), its reduced
  * coordinates m_r = Psi_r^* m (n_chains x r, eq:projector), the surrogate
@@ -455,6 +463,11 @@ int dino_serve_status(dino_ctx *ctx, int *queued, int *active, int *peak_active,
  * DINO_ETIMEOUT.  0 restores the default (2^22 polls).  Applies to launches
  * issued after the call.  For tests of the timeout path. */
 int dino_set_wait_limit(dino_ctx *ctx, uint32_t flag_spins);
+
+/* Measured FP32 fused-multiply-add throughput of the context's device in
+ * TFLOP/s (2 flops per FMA; independent FMA chains on every SM, best of three
+ * timed launches).  The denominator of the double-float kernels' roofline. */
+int dino_measure_fp32_peak(dino_ctx *ctx, double *tflops);
 
 /* Number of kernels this context has launched since creation. */
 uint64_t dino_launch_count(const dino_ctx *ctx);

@@ -128,6 +128,8 @@ _SIGNATURES = {
     "dino_set_true_model": ([_P, _I, ct.POINTER(_TrueDesc)], _I),
     "dino_chains_read_da": ([_P, _I, _D, _D, _D, ct.POINTER(_I)], _I),
     "dino_set_wait_limit": ([_P, ct.c_uint32], _I),
+    "dino_chains_step_many": ([_P, _I, ct.POINTER(_I), _I], _I),
+    "dino_measure_fp32_peak": ([_P, _D], _I),
     "dino_dis_from_surrogate": ([_P, _I, _I, ct.c_uint64, _I, _D, _D, _D, _D], _I),
     "dino_diag_create": ([_P, _I, _I, _I, ct.POINTER(_I)], _I),
     "dino_diag_record": ([_P, _I, _I, _I, _I], _I),
@@ -401,6 +403,17 @@ def dino_diag_compute(ctx: Ctx, diag: int, n_dof: int, mpsrf: bool = True) -> di
 
 def dino_diag_destroy(ctx: Ctx, diag: int):
     _check(ctx, lib().dino_diag_destroy(ctx.ptr, diag))
+
+
+def dino_chains_step_many(ctx: Ctx, pools, n_steps: int):
+    ids = (_I * len(pools))(*[int(p) for p in pools])
+    _check(ctx, lib().dino_chains_step_many(ctx.ptr, len(pools), ids, n_steps))
+
+
+def dino_measure_fp32_peak(ctx: Ctx) -> float:
+    t = ct.c_double()
+    _check(ctx, lib().dino_measure_fp32_peak(ctx.ptr, ct.byref(t)))
+    return t.value
 
 
 def dino_set_wait_limit(ctx: Ctx, flag_spins: int):

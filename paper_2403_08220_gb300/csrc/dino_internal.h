@@ -220,6 +220,11 @@ struct DaArgs {
 // the commit of a chain that passes both stages; CTA per chain.
 cudaError_t launch_da_decide(const DaArgs &a, cudaStream_t st);
 
+// FP32 fused multiply-add throughput of the device: runs a kernel of
+// independent FMA chains on every SM and returns its time and its flops
+// (2 per FMA); the best of a few launches after a warm-up.
+cudaError_t measure_fma_peak(cudaStream_t st, float *ms, double *flops);
+
 // ---- chain diagnostics (Sec. 6.2) ----------------------------------------
 // traj[(i n_c + k) max_s + j] = src[k ld_src + i] for k < n_c, i < d
 cudaError_t launch_diag_record(int n_c, int d, const void *src, int src_f32, int ld_src,

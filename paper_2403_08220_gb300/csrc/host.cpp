@@ -97,6 +97,8 @@ struct dino_ctx {
   std::vector<cudaEvent_t> event_pool;
   std::unique_ptr<dino::Server> server;
   std::map<int, std::unique_ptr<dino::Diag>> diags;
+  // streams that dino_chains_step_many spreads pools over (created on first use)
+  std::vector<cudaStream_t> aux_streams;
   // the device reads pageable host memory coherently (Grace: over NVLink-C2C)
   bool pageable_access = false;
   // polls of the Cholesky diagonal-block flag before a kernel gives up
@@ -2403,6 +2405,10 @@ int dino_destroy(dino_ctx *ctx) {
       cudaEventDestroy(p.e1);
     }
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
+    for (auto st : ctx->aux_streams) {
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+    }
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   }
   delete ctx;
@@ -2507,6 +2513,75 @@ int dino_chains_step(dino_ctx *ctx, int pool_id, int n_steps, dino_step_stats *s
       stats->stage1_accepts = c1[2] - c0[2];
     }
     collect_times(ctx);
+  });
+}
+
+int dino_chains_step_many(dino_ctx *ctx, int n_pools, const int *pool_ids, int n_steps) {
+  return guarded(ctx, [&] {
+    if (n_pools < 1 || !pool_ids || n_steps < 0) fail(DINO_EINVAL, "need pools and n_steps >= 0");
+    cudaSetDevice(ctx->device);
+    std::vector<Pool *> ps;
+    for (int i = 0; i < n_pools; ++i) {
+      Pool *p = get_pool(ctx, pool_ids[i]);
+      if (p->async_mem) fail(DINO_EINVAL, "pool %d belongs to the serving loop", pool_ids[i]);
+      for (Pool *q : ps)
+        if (q == p) fail(DINO_EINVAL, "pool %d listed twice", pool_ids[i]);
+      ps.push_back(p);
+    }
+    constexpr int kMaxAux = 16;
+    while ((int)ctx->aux_streams.size() < std::min(n_pools, kMaxAux)) {
+      cudaStream_t st;
+      CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+      ctx->aux_streams.push_back(st);
+    }
+    // each pool moves to its own stream after the work already on its stream,
+    // steps there (issue interleaved over pools so that all streams fill), and
+    // its own stream waits for the result
+    std::vector<cudaStream_t> home(n_pools);
+    std::vector<cudaEvent_t> evs;
+    auto event_on = [&](cudaStream_t st) {
+      cudaEvent_t e;
+      CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      evs.push_back(e);
+      CK(cudaEventRecord(e, st));
+      return e;
+    };
+    try {
+      for (int i = 0; i < n_pools; ++i) {
+        home[i] = ps[i]->st;
+        cudaStream_t aux = ctx->aux_streams[i % ctx->aux_streams.size()];
+        CK(cudaStreamWaitEvent(aux, event_on(home[i]), 0));
+        ps[i]->st = aux;
+      }
+      for (int k = 0; k < n_steps; ++k)
+        for (Pool *p : ps) step_pool(ctx, *p);
+    } catch (...) {
+      for (int i = 0; i < n_pools; ++i)
+        if (home[i]) {
+          cudaStreamWaitEvent(home[i], event_on(ps[i]->st), 0);
+          ps[i]->st = home[i];
+        }
+      for (cudaEvent_t e : evs) cudaEventDestroy(e);
+      throw;
+    }
+    for (int i = 0; i < n_pools; ++i) {
+      CK(cudaStreamWaitEvent(home[i], event_on(ps[i]->st), 0));
+      ps[i]->st = home[i];
+    }
+    for (cudaEvent_t e : evs) cudaEventDestroy(e);
+    collect_times(ctx);
+  });
+}
+
+int dino_measure_fp32_peak(dino_ctx *ctx, double *tflops) {
+  return guarded(ctx, [&] {
+    if (!tflops) fail(DINO_EINVAL, "tflops is NULL");
+    cudaSetDevice(ctx->device);
+    float ms = 0;
+    double f = 0;
+    CK(measure_fma_peak(ctx->stream, &ms, &f));
+    if (!(ms > 0)) fail(DINO_ECUDA, "the FMA timing returned no time");
+    *tflops = f / (ms * 1e-3) / 1e12;
   });
 }
 
