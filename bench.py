@@ -93,18 +93,28 @@ def load_peaks() -> dict:
         return {}
 
 
-def jacobian_flops(w) -> float:
-    """Tensor-core flops per chain of the reverse-mode Jacobian GEMMs.
-
-    For layers l = L-2 .. 1 the product of the running d_y x w_{l+1} block
-    with W_l^T (2 d_y w_l w_{l+1}), then the last with W_0^T (2 d_y r w_1),
-    each once per slice pair (three pairs for two slices).
-    """
+def jacobian_flops(w, slice_products: int = 1) -> float:
+    """Flops per chain of the Jacobian GEMMs in the order the library picks
+    (Sec. 4.3's min{d_y, r} rule): reverse 2 d_y sum_{l=0}^{L-2} w_l w_{l+1},
+    forward 2 r sum_{l=1}^{L-1} w_l w_{l+1}, the smaller (reverse on a tie or
+    when d_y < r).  slice_products = 1 gives the algorithmic work, 3 the
+    products the default two-slice scheme issues."""
     ws = list(w.widths)
     L = len(ws) - 1
-    per_term = sum(2.0 * w.d_y * ws[l] * ws[l + 1] for l in range(1, L - 1))
-    per_term += 2.0 * w.d_y * w.r * ws[1]
-    return 3.0 * per_term
+    rev = sum(2.0 * w.d_y * ws[l] * ws[l + 1] for l in range(0, L - 1))
+    fwd = sum(2.0 * w.r * ws[l] * ws[l + 1] for l in range(1, L))
+    use = fwd if (w.r < w.d_y and fwd < rev) else rev
+    return slice_products * use
+
+
+def tensor_flops_per_proposal(w) -> float:
+    """Algorithmic dense-contraction flops of one proposal: MLP forward,
+    Jacobian, the Gauss-Newton Gram product (the smaller of J^T J and J J^T)
+    and the two complement projections (E M and D coef2)."""
+    ws = list(w.widths)
+    fwd = sum(2.0 * ws[l] * ws[l + 1] for l in range(len(ws) - 1))
+    gram = 2.0 * min(w.r, w.d_y) ** 2 * max(w.r, w.d_y)
+    return fwd + jacobian_flops(w) + gram + 2 * 2.0 * w.N * w.r
 
 
 def fp64_flops_geometry(r: int, d_y: int) -> float:
@@ -193,6 +203,12 @@ def shard_base(rank: int, chains_per_rank: int) -> int:
     return rank * chains_per_rank
 
 
+def timed_repeats(dino, ctx, pool, steps, st, barrier, repeats):
+    """Device times of `repeats` passes of `steps` transitions; the median pass."""
+    times = [timed_steps(dino, ctx, pool, steps, st, barrier) for _ in range(repeats)]
+    return statistics.median(times), times
+
+
 def timed_steps(dino, ctx, pool, steps, st, barrier):
     """Device time of `steps` transitions (CUDA events on the stream the library launches on)."""
     import torch
@@ -236,15 +252,17 @@ def run_ours(args, rank, world, device):
     stream = torch.cuda.Stream(device=device)
     assert stream.cuda_stream != 0
     ctx = dino.dino_init(device, 0, stream.cuda_stream, 0)
+    fp32_peak = dino.dino_measure_fp32_peak(ctx)
     sid = load_surrogate(dino, ctx, w)
+    info = dino.dino_surrogate_query(ctx, sid)
     base = shard_base(rank, C)            # weak scaling: each rank owns its chain range
     pool = dino.dino_chains_create(ctx, sid, C, w.dt, SEED_CHAINS, base)
     dino.dino_chains_step(ctx, pool, args.warmup, stats=False)
     dino.dino_sync(ctx)
     n0 = dino.dino_launch_count(ctx)
     with ClockSampler(device) as clk:
-        secs = timed_steps(dino, ctx, pool, args.steps, stream, barrier)
-    launches = dino.dino_launch_count(ctx) - n0
+        secs, rep_secs = timed_repeats(dino, ctx, pool, args.steps, stream, barrier, args.repeats)
+    launches = (dino.dino_launch_count(ctx) - n0) // args.repeats
     stats = dino.dino_chains_step(ctx, pool, 1)
     secs = max_over_ranks(secs)
     value = world * C * args.steps / secs
@@ -261,36 +279,65 @@ def run_ours(args, rank, world, device):
     dino.dino_chains_destroy(ctx_t, pool_t)
     ctx_t.close()
     total = sum(v[0] for v in kt.values()) or 1.0
-    dom = max(kt.items(), key=lambda kv: kv[1][0])
-    geo = kt.get("geometry", dom[1])
+    geo = kt.get("geometry", max(kt.values(), key=lambda v: v[0]))
     geo_ms = geo[0] / max(1, geo[1])
-    tc_gram = w.precision == "bf16" and w.d_y < w.r and w.d_y <= 128 and len(w.widths) >= 3
+    tc_gram = bool(info["gram_on_tensor_cores"])
     work = geometry_work(w.r, w.d_y, tc_gram)
     achieved = work["fp32_charge"] * C / (geo_ms * 1e-3) / 1e12
     tpc = geometry_traffic_per_chain(args.workload)
     roofline = {"bound": "alu", "pipe": "fp32", "kernel": "geometry",
-                "achieved": round(achieved, 4), "peak": round(FP32_PEAK_TFLOPS, 2),
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz x 2 flops; "
-                               "double-float multiply-adds charged at 12 FP32 instructions",
-                "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
+                "achieved": round(achieved, 4), "peak": round(fp32_peak, 2),
+                "peak_source": "measured: dino_measure_fp32_peak (independent FMA chains on "
+                               "every SM, CUDA events); double-float multiply-adds charged at "
+                               "12 FP32 instructions",
+                "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 4),
                 "work_per_chain": {"fp32_flops": work["fp32"], "df_flops": work["df"]},
                 "traffic": tpc * C if tpc else None,
                 "traffic_note": "dram bytes per launch scaled from a 1216-chain ncu capture",
                 "share_of_step": round(geo[0] / total, 4)}
-    # the largest tensor-core kernel beside it: the Jacobian GEMMs (two
-    # launches per step), against the measured sustained bf16 peak
+    peaks = load_peaks()
+    bf16_sus = peaks.get("bf16_tflops_sustained")
+    hbm = peaks.get("hbm_gbs")
+    # the largest tensor-core kernel beside it: the Jacobian GEMMs, against
+    # the measured sustained bf16 peak; algorithmic flops (one product) and
+    # the slice products the default two-slice scheme issues
     roofline_tensor = None
     jt = kt.get("jac_tc")
     if jt and w.precision == "bf16":
-        peak = load_peaks().get("bf16_tflops_sustained")
-        flops = jacobian_flops(w) * C * n_pass
-        ach = flops / (jt[0] * 1e-3) / 1e12
+        alg = jacobian_flops(w) * C * n_pass / (jt[0] * 1e-3) / 1e12
+        iss = jacobian_flops(w, 3) * C * n_pass / (jt[0] * 1e-3) / 1e12
         roofline_tensor = {"bound": "tensor", "kernel": "jac_tc (k_tc_gemm, Jacobian)",
-                           "achieved": round(ach, 2), "peak": peak, "unit": "TFLOP/s",
+                           "achieved": round(alg, 2), "achieved_issued": round(iss, 2),
+                           "peak": bf16_sus, "unit": "TFLOP/s",
                            "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained",
-                           "frac": round(ach / peak, 4) if peak else None,
+                           "frac": round(alg / bf16_sus, 4) if bf16_sus else None,
+                           "frac_issued": round(iss / bf16_sus, 4) if bf16_sus else None,
                            "flops_per_chain": jacobian_flops(w),
+                           "flops_per_chain_issued": jacobian_flops(w, 3),
                            "share_of_step": round(jt[0] / total, 4)}
+    # the whole step against the per-proposal algorithmic work of the hot
+    # path (tensor: MLP, Jacobian, Gram, projections; HBM: 249 KB of chain
+    # state per proposal at r = 200)
+    tpp = tensor_flops_per_proposal(w)
+    step_fractions = {
+        "tensor_mflop_per_proposal": round(tpp / 1e6, 2),
+        "tensor_frac_of_sustained_bf16": round(tpp * value / world / (bf16_sus * 1e12), 4)
+        if bf16_sus else None,
+        "hbm_kb_per_proposal": 249.0,
+        "hbm_frac": round(249e3 * value / world / (hbm * 1e9), 4) if hbm else None}
+
+    # a step size that mixes (prior-draw starts, dt = 2e-5: about a sixth of
+    # the proposals accepted), so that the accept path's stores are timed
+    mix = None
+    if not args.skip_mixing:
+        pm = dino.dino_chains_create(ctx, sid, C, 2e-5, SEED_CHAINS, base)
+        dino.dino_chains_step(ctx, pm, args.warmup, stats=False)
+        sm_, _ = timed_repeats(dino, ctx, pm, args.steps, stream, barrier, 3)
+        st_m = dino.dino_chains_step(ctx, pm, args.steps)
+        mix = {"dt": 2e-5, "proposals_per_s": world * C * args.steps / max_over_ranks(sm_),
+               "ms_per_step": 1e3 * sm_ / args.steps,
+               "acceptance_rate": st_m["accepts"] / max(1, st_m["proposals"])}
+        dino.dino_chains_destroy(ctx, pm)
 
     # FP64 plain step beside it (fewer steps: it runs its GEMMs in FP64)
     fp64_line = None
@@ -299,7 +346,7 @@ def run_ours(args, rank, world, device):
         sid64 = load_surrogate(dino, ctx, w64)
         p64 = dino.dino_chains_create(ctx, sid64, w64.n_chains, w64.dt, SEED_CHAINS)
         dino.dino_chains_step(ctx, p64, 1, stats=False)
-        k64 = max(1, min(3, args.steps))
+        k64 = max(1, min(5, args.steps))
         s64 = timed_steps(dino, ctx, p64, k64, stream, lambda: None)
         fp64_line = {"workload": "r200_kle_fp64", "chains": w64.n_chains, "steps": k64,
                      "proposals_per_s": w64.n_chains * k64 / s64,
@@ -329,23 +376,29 @@ def run_ours(args, rank, world, device):
 
     line = None
     if rank == 0:
+        slots = state_bytes(w, C, info)
         line = {
             "metric": METRIC, "value": value, "unit": "proposals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f64",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 GEMMs (fp32 accumulation) + double-float (fp32 pairs) Cholesky and "
+                     "solves + f64 log-ratio",
             "data": "synthetic (seeded weights, DIS basis, data from the surrogate at a seeded truth)",
             "config": {"workload": f"{args.workload}: {C} chains/GPU, r={w.r} "
                                    f"{'DIS' if w.basis_kind else 'KLE'}, MLP "
                                    f"{'-'.join(map(str, w.widths))} GELU, N={w.N}, dt={w.dt}",
-                       "l2": "inputs larger than L2 (Cholesky factors %.1f GB)"
-                             % (C * w.r * (w.r + 1) / 2 * 8 / 1e9),
+                       "l2": "inputs larger than L2 (chain state %.2f GB: %s)"
+                             % (slots["total"] / 1e9, slots["what"]),
+                       "repeats": f"median of {args.repeats} timed passes of {args.steps} steps",
                        "parallelism": f"chains sharded over {world} GPU(s)"},
             "roofline": roofline, "roofline_tensor": roofline_tensor,
+            "step_fractions": step_fractions,
             "gpu_launches": int(launches),
             "acceptance_rate": stats["accepts"] / max(1, stats["proposals"]),
+            "repeat_ms_per_step": [round(1e3 * t / args.steps, 4) for t in rep_secs],
             "kernel_share": {k: round(v[0] / total, 4) for k, v in kt.items()},
-            "fp64_plain": fp64_line, "e2e": e2e,
+            "mixing": mix, "fp64_plain": fp64_line, "e2e": e2e,
             "clocks": clk.result,
         }
     if dist is not None:
@@ -353,45 +406,176 @@ def run_ours(args, rank, world, device):
     return line
 
 
+def state_bytes(w, C, info) -> dict:
+    """Device bytes of the chain state a step reads: the two factor slots,
+    the Jacobian state of the d_y-sized paths and the field."""
+    r, dy = w.r, w.d_y
+    fe = 4 if w.precision == "bf16" else 8
+    if info["noise_map"] == "perturbation":
+        slot = ((dy + 1) * (dy + 2) // 2 + (dy + 1) + 2 * dy + 2) * 8
+        js = C * dy * r * fe
+        what = "perturbation-map factor slots and J state"
+    elif info["noise_map"] == "eigen":
+        slot = (dy * dy + 3 * dy + 2) * 8
+        js = C * dy * r * fe
+        what = "eigen-map slots and J state"
+    else:
+        slot = ((r + 1) * (r + 2) // 2 + r + 1) * 8
+        js = 0
+        what = "Cholesky factor slots"
+    total = 2 * C * slot + js + C * w.N * fe
+    return {"total": total, "what": what + " + field"}
+
+
 def run_hetero(args, device=0):
     """Eight posteriors of different size (r = 32 ... 400) stepped together.
 
-    One step = one transition of every chain of all eight pools (their kernels
-    are issued back to back on one stream).  Returns total proposals/s and the
-    per-posterior step time.
+    One step = one transition of every chain of all eight pools, issued by
+    dino_chains_step_many, which runs each pool on a stream of its own so
+    that their kernels overlap.  The same steps issued pool after pool on one
+    stream are timed beside it.
     """
     import torch
     import paper_2403_08220_gb300 as dino
     from workloads import heterogeneous_workloads
     torch.cuda.set_device(device)
     stream = torch.cuda.Stream(device=device)
-    ctx = dino.dino_init(device, 0, stream.cuda_stream, dino.DINO_FLAG_TIMING)
+    ctx = dino.dino_init(device, 0, stream.cuda_stream, 0)
+    fp32_peak = dino.dino_measure_fp32_peak(ctx)
     ws = heterogeneous_workloads()
-    pools = []
-    for k, w in enumerate(ws):
+    pools, infos = [], []
+    for w in ws:
         sid = load_surrogate(dino, ctx, w)
-        pools.append((w, dino.dino_chains_create(ctx, sid, w.n_chains, w.dt, SEED_CHAINS)))
-    for w, p in pools:
-        dino.dino_chains_step(ctx, p, 1, stats=False)
-    dino.dino_kernel_times(ctx, reset=True)
-    steps = max(1, min(args.steps, 3))
-    per = []
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(steps):
-        for w, p in pools:
-            dino.dino_chains_step(ctx, p, 1, stats=False)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    secs = e0.elapsed_time(e1) / 1e3
-    total = sum(w.n_chains for w, _ in pools) * steps
-    for w, p in pools:
+        infos.append(dino.dino_surrogate_query(ctx, sid))
+        pools.append(dino.dino_chains_create(ctx, sid, w.n_chains, w.dt, SEED_CHAINS))
+    dino.dino_chains_step_many(ctx, pools, 2)
+    steps = max(1, min(args.steps, 10))
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    conc = statistics.median(timed(lambda: dino.dino_chains_step_many(ctx, pools, steps))
+                             for _ in range(3))
+
+    def sequential():
+        for _ in range(steps):
+            for p in pools:
+                dino.dino_chains_step(ctx, p, 1, stats=False)
+    seq = timed(sequential)
+    total = sum(w.n_chains for w in ws) * steps
+    tflops = sum(w.n_chains * tensor_flops_per_proposal(w) for w in ws) * steps / conc / 1e12
+    charge = sum(w.n_chains * geometry_work(w.r, w.d_y, bool(i["gram_on_tensor_cores"]))
+                 ["fp32_charge"] for w, i in zip(ws, infos)) * steps / conc / 1e12
+    peaks = load_peaks()
+    bf16_sus = peaks.get("bf16_tflops_sustained")
+    for p in pools:
         dino.dino_chains_destroy(ctx, p)
     ctx.close()
-    return {"workload": "8 posteriors, r in {32,...,400}, d_y in {50,...,400}, 512-8192 chains",
-            "proposals_per_s": total / secs, "ms_per_step": 1e3 * secs / steps,
-            "chains": [w.n_chains for w in ws], "r": [w.r for w in ws]}
+    return {"workload": "8 posteriors, r in {32,...,400}, d_y in {50,...,400}, MLP r-2r-2r-d_y "
+                        "GELU, 512-8192 chains, N=4225, dt=0.5, stepped concurrently",
+            "proposals_per_s": total / conc, "ms_per_step": 1e3 * conc / steps,
+            "sequential_ms_per_step": 1e3 * seq / steps,
+            "chains": [w.n_chains for w in ws], "r": [w.r for w in ws], "d_y": [w.d_y for w in ws],
+            "jacobian_mode": ["forward" if i["jac_forward"] else "reverse" for i in infos],
+            "noise_map": [i["noise_map"] for i in infos],
+            "roofline": {
+                "tensor_achieved_tflops": round(tflops, 2),
+                "tensor_frac_of_sustained_bf16": round(tflops / bf16_sus, 4) if bf16_sus else None,
+                "fp32_pipe_charge_tflops": round(charge, 2),
+                "fp32_frac_of_measured": round(charge / fp32_peak, 4),
+                "note": "whole-step rates: algorithmic tensor flops (MLP, Jacobian, Gram, "
+                        "projections) and the geometry kernels' FP32-pipe charge over the step time"}}
+
+
+def library_kle_rows(dino, ctx, w, lo, hi):
+    """Rows lo .. hi - 1 of the library's own KLE encoder on w's grid."""
+    Ws = [np.zeros((2, hi)), np.zeros((2, 2))]
+    sid = dino.dino_load_surrogate(
+        ctx, n_grid=w.n_grid, prior_gamma=w.prior_gamma, prior_delta=w.prior_delta, r=hi,
+        widths=[hi, 2, 2], activation=1, W=Ws, b=[np.zeros(2), np.zeros(2)],
+        basis_kind=BASIS_KLE)
+    E, _ = dino.dino_read_basis(ctx, sid, hi, w.N)
+    dino.dino_unload_surrogate(ctx, sid)
+    return E[lo:hi]
+
+
+def run_da(args, device=0):
+    """Delayed acceptance (Algorithm 1's second stage) on the r = 200 workload.
+
+    True map: the surrogate's network reading 200 further KLE coordinates of
+    the field (E_t = [E; KLE rows 200..399], weights from
+    workloads.true_model_weights, eps = 0.05).  dt = 2e-5 from prior draws,
+    where the first stage accepts about a sixth of the proposals.
+    """
+    import torch
+    import paper_2403_08220_gb300 as dino
+    from workloads import true_model_weights
+    torch.cuda.set_device(device)
+    stream = torch.cuda.Stream(device=device)
+    ctx = dino.dino_init(device, 0, stream.cuda_stream, 0)
+    w = CONFIGS["r200_dis_bf16"]
+    C, dt = w.n_chains, 2e-5
+    out = {"workload": f"r200_dis_bf16 + true map on a 400-dim encoding, {C} chains, dt={dt}"}
+    for da in (False, True):
+        sid = load_surrogate(dino, ctx, w)
+        if da:
+            E, _ = dino.dino_read_basis(ctx, sid, w.r, w.N)
+            Et = np.vstack([E, library_kle_rows(dino, ctx, w, w.r, 2 * w.r)])
+            Wt, bt = true_model_weights(w, w.r, 0.05)
+            dino.dino_set_true_model(ctx, sid, E_t=Et, W=Wt, b=bt, activation=w.activation)
+        pool = dino.dino_chains_create(ctx, sid, C, dt, SEED_CHAINS)
+        dino.dino_chains_step(ctx, pool, 3, stats=False)
+        secs, _ = timed_repeats(dino, ctx, pool, args.steps, stream, lambda: None, 3)
+        st = dino.dino_chains_step(ctx, pool, args.steps)
+        key = "two_stage" if da else "surrogate_only"
+        out[key] = {"proposals_per_s": C * args.steps / secs,
+                    "ms_per_step": 1e3 * secs / args.steps,
+                    "stage1_acceptance": st["stage1_accepts"] / max(1, st["proposals"]),
+                    "acceptance": st["accepts"] / max(1, st["proposals"])}
+        dino.dino_chains_destroy(ctx, pool)
+        dino.dino_unload_surrogate(ctx, sid)
+    s1 = out["two_stage"]["stage1_acceptance"]
+    out["two_stage"]["stage2_acceptance_given_stage1"] = (
+        out["two_stage"]["acceptance"] / s1 if s1 else None)
+    ctx.close()
+    return out
+
+
+def run_paper_shape(args, device=0):
+    """The paper's network (6 x 400 GELU, r = 200 DIS, d_y = 25, N = 1681):
+    proposals/s with the perturbation map (Cholesky of I + K K^T) and with the
+    paper's eigen map (per-chain Jacobi eigendecomposition)."""
+    import torch
+    import dataclasses
+    import paper_2403_08220_gb300 as dino
+    torch.cuda.set_device(device)
+    stream = torch.cuda.Stream(device=device)
+    ctx = dino.dino_init(device, 0, stream.cuda_stream, 0)
+    out = {}
+    for name, noise, C in (("paper_ndr_bf16", "perturbation", 16384),
+                           ("paper_ndr_bf16", "eigen", 4096),
+                           ("paper_hyper_bf16", "perturbation", 16384)):
+        w = dataclasses.replace(CONFIGS[name], noise_map=noise)
+        sid = load_surrogate(dino, ctx, w)
+        info = dino.dino_surrogate_query(ctx, sid)
+        pool = dino.dino_chains_create(ctx, sid, C, w.dt, SEED_CHAINS)
+        dino.dino_chains_step(ctx, pool, 3, stats=False)
+        k = max(2, min(args.steps, 10))
+        secs, _ = timed_repeats(dino, ctx, pool, k, stream, lambda: None, 3)
+        out[f"{name}/{noise}"] = {"chains": C, "proposals_per_s": C * k / secs,
+                                  "ms_per_step": 1e3 * secs / k,
+                                  "jacobian_mode": "forward" if info["jac_forward"] else "reverse",
+                                  "d_y": w.d_y, "N": w.N}
+        dino.dino_chains_destroy(ctx, pool)
+        dino.dino_unload_surrogate(ctx, sid)
+    ctx.close()
+    return out
 
 
 def serving_workload(n_surrogates=16, seed=2024):
@@ -413,13 +597,16 @@ def run_serving(args, device=0):
 
     Latency is measured on the host: from the submit call to the poll that
     returns the request's outputs.  Two runs on the same resident surrogates:
-    * stable load: steps uniform in [10, 100], chains log-uniform in
-      [256, 2048], arrivals at 0.7 of the capacity measured just before on a
-      batch of such requests; all requests drain;
+    * stable load: chains log-uniform in [256, 8192] as written, steps uniform
+      in [10, 100] (the written 1k-10k scaled down 100 times so that the run
+      drains), arrivals at 0.7 of the capacity measured just before on a
+      batch of such requests;
     * written load: 20 requests/s, chains log-uniform in [256, 8192], steps
-      uniform in [1000, 10000], for a fixed window.  The offered work is far
-      above one GPU's capacity, so the queue grows; completed requests, queue
-      length and the offered GPU-seconds per second are reported.
+      uniform in [1000, 10000], for a fixed window (60 s by default).  The
+      offered work is far above one GPU's capacity, so the queue grows; the
+      latencies of completed requests are reported with the ages of the ones
+      still queued or running when the window closes (lower bounds of their
+      latency), the queue length and the offered GPU-seconds per second.
     """
     import torch
     import paper_2403_08220_gb300 as dino
@@ -457,42 +644,50 @@ def run_serving(args, device=0):
             time.sleep(0.001)
         return done, outstanding, time.perf_counter() - t_start, n
 
+    def pct(x, q):
+        return float(np.percentile(x, q)) if len(x) else None
+
     ctx = dino.dino_init(device, 0, None, 0)
     t0 = time.perf_counter()
     sids = [load_surrogate(dino, ctx, w) for w in ws]
     setup_s = time.perf_counter() - t0
     dino.dino_serve_config(ctx, n_streams=8, steps_per_round=4, max_active=32)
     # capacity on a batch of stable-size requests submitted at once
-    cal, _, cal_s, _ = run(ctx, sids, 1e9, 1e9, 256, 2048, 10, 100, 16, True)
+    cal, _, cal_s, _ = run(ctx, sids, 1e9, 1e9, 256, 8192, 10, 100, 24, True)
     capacity = sum(wk for _, wk in cal) / cal_s
     mean_work = float(np.mean([wk for _, wk in cal]))
     rate = 0.7 * capacity / mean_work
-    st, _, st_s, _ = run(ctx, sids, rate, args.serve_window, 256, 2048, 10, 100, 10 ** 6, True)
+    st, _, st_s, _ = run(ctx, sids, rate, args.serve_window, 256, 8192, 10, 100, 10 ** 6, True)
     lat = np.array([l for l, _ in st])
     stable = {"offered_load_of_capacity": 0.7, "rate_per_s": rate, "requests": len(st),
-              "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+              "p50_s": pct(lat, 50), "p99_s": pct(lat, 99),
               "proposals_per_s": sum(wk for _, wk in st) / st_s,
               "capacity_proposals_per_s": capacity,
-              "request": "chains log-uniform [256, 2048], steps U[10, 100]"}
+              "request": "chains log-uniform [256, 8192], steps U[10, 100] (written 1k-10k / 100)"}
     ctx.close()
 
     ctx = dino.dino_init(device, 0, None, 0)
     sids = [load_surrogate(dino, ctx, w) for w in ws]
     dino.dino_serve_config(ctx, n_streams=8, steps_per_round=2, max_active=32)
-    wr, left, wr_s, n = run(ctx, sids, 20.0, args.serve_window, 256, 8192, 1000, 10000, 600,
-                            False)
+    window = args.serve_written_window
+    wr, left, wr_s, n = run(ctx, sids, 20.0, window, 256, 8192, 1000, 10000, 10 ** 6, False)
+    t_end = time.perf_counter()
     status = dino.dino_serve_status(ctx)
     lat_w = np.array([l for l, _ in wr])
+    ages = np.array([t_end - t0 for t0, _ in left.values()])
     works = [wk for _, wk in wr] + [wk for _, wk in left.values()]
-    written = {"rate_per_s": 20.0, "window_s": args.serve_window, "submitted": n,
+    written = {"rate_per_s": 20.0, "window_s": window, "submitted": n,
                "completed": len(wr), "queued_at_end": status["queued"],
-               "resident_at_end": status["active"],
-               "peak_resident": status["peak_active"],
+               "resident_at_end": status["active"], "peak_resident": status["peak_active"],
                "peak_hbm_gb": status["peak_hbm_used"] / 1e9,
-               "p50_s": float(np.percentile(lat_w, 50)) if len(lat_w) else None,
-               "p99_s": float(np.percentile(lat_w, 99)) if len(lat_w) else None,
+               "p50_s": pct(lat_w, 50), "p99_s": pct(lat_w, 99),
+               "completed_proposals_per_s": sum(wk for _, wk in wr) / wr_s,
+               "unfinished_age_p50_s": pct(ages, 50), "unfinished_age_p99_s": pct(ages, 99),
+               "unfinished_age_max_s": float(ages.max()) if len(ages) else None,
                "offered_gpu_s_per_s": float(20.0 * np.mean(works) / capacity) if works else 0.0,
-               "request": "chains log-uniform [256, 8192], steps U[1000, 10000]"}
+               "request": "chains log-uniform [256, 8192], steps U[1000, 10000]",
+               "note": "latencies of completed requests; unfinished requests' ages are lower "
+                       "bounds of their latencies (censored at the window's end)"}
     t_close = time.perf_counter()
     ctx.close()   # cancels what is still queued; lets resident rounds finish
     written["close_s"] = time.perf_counter() - t_close
@@ -541,13 +736,18 @@ def main():
     ap.add_argument("--chains", type=int, default=0)
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-mixing", action="store_true")
+    ap.add_argument("--repeats", type=int, default=5)
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-chains", type=int, default=512)
     ap.add_argument("--cpu-steps", type=int, default=4)
-    ap.add_argument("--hetero", action="store_true",
-                    help="also time the eight-posterior heterogeneous batch")
+    ap.add_argument("--no-hetero", action="store_true",
+                    help="skip the eight-posterior heterogeneous batch")
+    ap.add_argument("--no-da", action="store_true", help="skip the delayed-acceptance line")
+    ap.add_argument("--no-paper", action="store_true", help="skip the paper-shaped network line")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving load test")
     ap.add_argument("--serve-window", type=float, default=10.0)
+    ap.add_argument("--serve-written-window", type=float, default=60.0)
     ap.add_argument("--serve-surrogates", type=int, default=16)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -582,8 +782,12 @@ def main():
         return
 
     line = run_ours(args, rank, world, local)
-    if rank == 0 and args.hetero and world == 1:
+    if rank == 0 and not args.no_hetero and world == 1:
         line["hetero"] = run_hetero(args, local)
+    if rank == 0 and not args.no_da and world == 1:
+        line["delayed_acceptance"] = run_da(args, local)
+    if rank == 0 and not args.no_paper and world == 1:
+        line["paper_shape"] = run_paper_shape(args, local)
     if rank == 0 and not args.no_serve and world == 1:
         line["serving"] = run_serving(args, local)
     if rank == 0:

@@ -9,13 +9,33 @@ from workloads import CONFIGS
 
 
 def test_jacobian_flops_r200():
-    # d_y x w times W_2^T (w x w), then d_y x w times W_1^T (w x r), 2 flops per
-    # multiply-add, three slice products with two slices
+    # reverse mode (d_y < r): d_y x w times W_2^T (w x w), then d_y x w times
+    # W_1^T (w x r), 2 flops per multiply-add; three slice products issued
     w = CONFIGS["r200_dis_bf16"]
     d_y, width, r = 100, 400, 200
     assert (w.d_y, w.r, list(w.widths)) == (d_y, r, [r, width, width, d_y])
-    assert bench.jacobian_flops(w) == 3 * (2 * d_y * width * width + 2 * d_y * r * width)
-    assert bench.jacobian_flops(w) == 144e6
+    assert bench.jacobian_flops(w) == 2 * d_y * width * width + 2 * d_y * r * width == 48e6
+    assert bench.jacobian_flops(w, 3) == 144e6
+
+
+def test_jacobian_order_follows_the_cheaper_mode():
+    # the paper's network with d_y = 25: reverse mode, 44 MFLOP against 324
+    # MFLOP forward
+    w = CONFIGS["paper_ndr_bf16"]
+    rev = 2 * 25 * (200 * 400 + 5 * 400 * 400)
+    assert bench.jacobian_flops(w) == rev
+    from workloads import heterogeneous_workloads
+    h = heterogeneous_workloads()[1]             # r = 64 < d_y = 100: forward is cheaper
+    fwd = 2 * 64 * (128 * 128 + 128 * 100)
+    assert bench.jacobian_flops(h) == fwd < 2 * 100 * (64 * 128 + 128 * 128)
+
+
+def test_tensor_flops_per_proposal_r200():
+    # forward 2(200*400 + 400*400 + 400*100) + Jacobian 48e6 + Gram 2*100^2*200
+    # + two projections 2*2*4225*200
+    w = CONFIGS["r200_dis_bf16"]
+    ref = 2 * (200 * 400 + 400 * 400 + 400 * 100) + 48e6 + 2 * 100 ** 2 * 200 + 4 * 4225 * 200
+    assert bench.tensor_flops_per_proposal(w) == ref
 
 
 def test_geometry_work_woodbury_with_tensor_core_gram():
