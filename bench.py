@@ -668,7 +668,7 @@ def run_serving(args, device=0):
 
     ctx = dino.dino_init(device, 0, None, 0)
     sids = [load_surrogate(dino, ctx, w) for w in ws]
-    dino.dino_serve_config(ctx, n_streams=8, steps_per_round=2, max_active=32)
+    dino.dino_serve_config(ctx, n_streams=8, steps_per_round=4, max_active=32)
     window = args.serve_written_window
     wr, left, wr_s, n = run(ctx, sids, 20.0, window, 256, 8192, 1000, 10000, 10 ** 6, False)
     t_end = time.perf_counter()

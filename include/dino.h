@@ -434,9 +434,14 @@ typedef struct {
 int dino_serve_config(dino_ctx *ctx, int n_streams, int steps_per_round, int max_active);
 
 /* Queue a request; returns immediately with a ticket.  A background thread
- * admits queued requests in arrival order as soon as their device footprint
- * (the pool's arena) fits in the HBM budget, so requests arriving while
- * others run are batched with them, each on its own stream.
+ * admits queued requests as soon as their device footprint (the pool's
+ * arena) fits in the HBM budget, so requests arriving while others run are
+ * batched with them, each on its own stream.  Among the requests that fit,
+ * the one with the least estimated work (chains x steps x per-proposal cost)
+ * goes first; a request that has waited longer than 20 s goes before all
+ * others, in arrival order, and is not passed over while it does not fit.
+ * Of the resident requests, as many as there are streams progress at a time:
+ * those with the least remaining work (shortest remaining work first).
  * Errors: ENOTFOUND (surrogate), ESTATE (no data), EINVAL, EBUSY (queue full),
  * ENOMEM (the request alone exceeds the whole budget). */
 int dino_serve_submit(dino_ctx *ctx, const dino_request *req, uint64_t *ticket);

@@ -2008,8 +2008,9 @@ static void diag_compute(dino_ctx *ctx, Diag *g, int want_mpsrf, double *ess_out
 // ---------------------------------------------------------------------------
 // serving: continuous batching of chain ensembles
 //
-// A background thread owns admission and issue.  Requests wait in a FIFO
-// until their pool's device footprint fits the context's HBM budget; each
+// A background thread owns admission and issue.  Requests wait in a queue
+// until their pool's device footprint fits the context's HBM budget (the
+// least estimated work first, requests older than starve_s before all); each
 // admitted request gets its own pool on one of several CUDA streams, and its
 // transitions are issued in rounds of `steps_per_round` with at most two
 // rounds in flight, so requests that arrive while others run join between
@@ -2027,6 +2028,7 @@ struct Request {
   dino_request req{};
   std::vector<double> m0;
   size_t footprint = 0;
+  double work = 0;  // estimated cost: proposals x per-proposal work of the surrogate
   double t_submit = 0, t_admit = 0, t_done = 0;
   int state = 0;  // 0 queued, 1 active, 2 done, 3 failed
   int status = DINO_OK;
@@ -2053,9 +2055,9 @@ struct Server {
   int steps_per_round = 8;
   int max_active = 32;
   size_t max_queue = 100000;
-  // first-fit admission may pass over the queue head only while it has
-  // waited less than this; after that nothing is admitted before it
-  double head_bypass_s = 2.0;
+  // admission order: requests that have waited longer than starve_s first
+  // (oldest first), then the others by estimated work, smallest first
+  double starve_s = 20.0;
   // an internal error outside any one request stops the server: every
   // resident and queued request fails with it and submit refuses new ones
   bool broken = false;
@@ -2200,19 +2202,25 @@ struct Server {
         ++k;
       }
     }
-    // admission, first fit in arrival order: a request whose footprint fits
-    // the free budget is admitted even if an earlier, larger one does not
-    // fit yet, unless the queue head has waited longer than head_bypass_s
+    // admission: shortest estimated job first among the requests that fit
+    // the free budget (first fit), except that requests waiting longer than
+    // starve_s go first in arrival order, and while the oldest of them does
+    // not fit nothing else is admitted (it cannot be passed over forever)
     const double tnow = now_s();
-    for (auto it = queue.begin(); it != queue.end() && (int)active.size() < max_active;) {
-      Request *r = *it;
-      const bool head = it == queue.begin();
+    std::vector<Request *> order(queue.begin(), queue.end());
+    std::stable_sort(order.begin(), order.end(), [&](const Request *a, const Request *b) {
+      const bool sa = tnow - a->t_submit > starve_s, sb = tnow - b->t_submit > starve_s;
+      if (sa != sb) return sa;
+      if (sa) return a->ticket < b->ticket;
+      return a->work < b->work;
+    });
+    for (Request *r : order) {
+      if ((int)active.size() >= max_active) break;
       if (ctx->used + r->footprint > ctx->budget) {
-        if (head && tnow - r->t_submit > head_bypass_s) break;  // the head goes next
-        ++it;
+        if (tnow - r->t_submit > starve_s) break;  // the starved request goes next
         continue;
       }
-      it = queue.erase(it);
+      queue.erase(std::find(queue.begin(), queue.end(), r));
       int k = 0;
       for (size_t j = 1; j < streams.size(); ++j)
         if (load[j] < load[k]) k = (int)j;
@@ -2232,9 +2240,22 @@ struct Server {
       did = true;
     }
     // issue rounds: at most two in flight per request and per stream, so the
-    // launch queues stay short and this thread never blocks in a launch
-    for (Request *r : active) {
-      if (r->in_flight >= 2 || r->issued >= r->req.n_steps) continue;
+    // launch queues stay short and this thread never blocks in a launch.
+    // Only as many residents as there are streams progress at a time, those
+    // with the least remaining work (under overload this lets short requests
+    // finish instead of sharing the device evenly with long ones).
+    std::vector<Request *> prog(active.begin(), active.end());
+    auto remaining = [](const Request *r) {
+      return r->work * (double)(r->req.n_steps - r->issued) / std::max(1, r->req.n_steps);
+    };
+    std::stable_sort(prog.begin(), prog.end(), [&](const Request *a, const Request *b) {
+      return remaining(a) < remaining(b);
+    });
+    int progressing = 0;
+    for (Request *r : prog) {
+      if (r->issued >= r->req.n_steps) continue;
+      if (progressing++ >= (int)streams.size()) break;
+      if (r->in_flight >= 2) continue;
       size_t sj = 0;
       for (size_t j = 0; j < streams.size(); ++j)
         if (streams[j] == r->pool->st) sj = j;
@@ -2805,6 +2826,15 @@ int dino_serve_submit(dino_ctx *ctx, const dino_request *req, uint64_t *ticket) 
     r->ticket = sv.next_ticket++;
     r->req = *req;
     r->footprint = pool_footprint(s, req->n_chains);
+    {
+      // per proposal: the factorisation of the smaller Gauss-Newton system
+      // and the Jacobian GEMMs (orders of magnitude, for ordering only)
+      const double k = std::min(s->r, s->d_y) + 1.0;
+      double jac = 0.0;
+      for (int l = 0; l + 1 < s->L; ++l) jac += 2.0 * s->widths[l] * s->widths[l + 1];
+      r->work = (double)req->n_chains * req->n_steps *
+                (12.0 * k * k * k / 3.0 + jac * std::min(s->r, s->d_y) / 50.0);
+    }
     if (r->footprint > ctx->budget)
       fail(DINO_ENOMEM, "request needs %zu bytes, more than the whole HBM budget %zu",
            r->footprint, ctx->budget);

@@ -288,8 +288,8 @@ __global__ void __launch_bounds__(32 * kPropWarps) k_propose_warp(ReducedArgs a)
 // an accepted chain to b: its factor slot (written only then, into the other
 // slot, which becomes current) and its state vectors.  The complement
 // coefficient b - s a is written for every chain.
-template <typename TJ, bool G>
-__global__ void __launch_bounds__(kThreads) k_geometry(ReducedArgs a, int mode) {
+template <typename TJ, bool G, int NT>
+__global__ void __launch_bounds__(NT) k_geometry(ReducedArgs a, int mode) {
   // FP32 Jacobian (tensor-core path): double-float Cholesky; FP64 Jacobian: FP64
   using A = std::conditional_t<sizeof(TJ) == 4, DF, F64>;
   using E = typename A::T;
@@ -451,14 +451,24 @@ cudaError_t launch_propose(const ReducedArgs &a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <typename TJ, bool G, int NT>
+static cudaError_t launch_geometry_nt(const ReducedArgs &a, int mode, size_t smem,
+                                      cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_geometry<TJ, G, NT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_geometry<TJ, G, NT><<<a.C, NT, smem, st>>>(a, mode);
+  return cudaGetLastError();
+}
+
+// CTA size by r: a small factor keeps few threads busy, and smaller CTAs let
+// more chains share an SM (the kernel's loops stride over blockDim).
 template <typename TJ, bool G>
 static cudaError_t launch_geometry_t(const ReducedArgs &a, int mode, size_t smem,
                                      cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(k_geometry<TJ, G>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_geometry<TJ, G><<<a.C, kThreads, smem, st>>>(a, mode);
-  return cudaGetLastError();
+  if (a.r <= 64) return launch_geometry_nt<TJ, G, 128>(a, mode, smem, st);
+  if (a.r <= 128) return launch_geometry_nt<TJ, G, 256>(a, mode, smem, st);
+  return launch_geometry_nt<TJ, G, kThreads>(a, mode, smem, st);
 }
 
 cudaError_t launch_geometry(const ReducedArgs &a, int mode, cudaStream_t st) {
