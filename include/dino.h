@@ -462,13 +462,6 @@ int dino_serve_status(dino_ctx *ctx, int *queued, int *active, int *peak_active,
 
 /* ---- instrumentation --------------------------------------------------- */
 
-/* Bound on the polls of the Cholesky's diagonal-block flag (a wait between
- * the warps of one CTA) before the kernel gives up, raises its error word and
- * returns; dino_chains_step (with stats) and dino_chains_read then report
- * DINO_ETIMEOUT.  0 restores the default (2^22 polls).  Applies to launches
- * issued after the call.  For tests of the timeout path. */
-int dino_set_wait_limit(dino_ctx *ctx, uint32_t flag_spins);
-
 /* Measured FP32 fused-multiply-add throughput of the context's device in
  * TFLOP/s (2 flops per FMA; independent FMA chains on every SM, best of three
  * timed launches).  The denominator of the double-float kernels' roofline. */

@@ -127,7 +127,6 @@ _SIGNATURES = {
     "dino_chains_set_noise": ([_P, _I, _D, _D, _D, _D, _D], _I),
     "dino_set_true_model": ([_P, _I, ct.POINTER(_TrueDesc)], _I),
     "dino_chains_read_da": ([_P, _I, _D, _D, _D, ct.POINTER(_I)], _I),
-    "dino_set_wait_limit": ([_P, ct.c_uint32], _I),
     "dino_chains_step_many": ([_P, _I, ct.POINTER(_I), _I], _I),
     "dino_measure_fp32_peak": ([_P, _D], _I),
     "dino_dis_from_surrogate": ([_P, _I, _I, ct.c_uint64, _I, _D, _D, _D, _D], _I),
@@ -414,10 +413,6 @@ def dino_measure_fp32_peak(ctx: Ctx) -> float:
     t = ct.c_double()
     _check(ctx, lib().dino_measure_fp32_peak(ctx.ptr, ct.byref(t)))
     return t.value
-
-
-def dino_set_wait_limit(ctx: Ctx, flag_spins: int):
-    _check(ctx, lib().dino_set_wait_limit(ctx.ptr, int(flag_spins)))
 
 
 def dino_launch_count(ctx: Ctx) -> int:

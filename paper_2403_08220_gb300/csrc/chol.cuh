@@ -294,48 +294,47 @@ __device__ __forceinline__ void tri_pos(int e, int &ii, int &jj) {
 
 
 // Factor the 8 x 8 diagonal block at kb (size nb) by one warp, in registers.
-// Every lane holds the whole lower block and factors it (column q: the pivot
-// A::pivot, the scaling of column q, the rank-1 update of the columns to its
-// right), so no value crosses lanes and the dependent chain per column is
-// only pivot -> scale -> next diagonal update; the off-diagonal updates of
-// the unrolled loop overlap it.  Rows and columns >= nb are padded with the
-// identity, which leaves the rows < nb unchanged and is never stored.  The
-// arithmetic per entry is the column-at-a-time sequence.  After a warp
-// barrier (the block is read by all lanes and overwritten in place) lanes
-// share the stores: entry e of the block by lane e mod 32, inv[k] = 1 / L_kk.
+// Lane 4 i + s holds the entries (i, s) and (i, s + 4) of the lower block;
+// rows and columns >= nb are padded with the identity, which leaves the rows
+// < nb unchanged and is never stored.  Column q: every lane takes the pivot
+// A::pivot of the broadcast diagonal entry, the owners of column q scale it,
+// and each entry (i, k), q < k <= i, takes the rank-1 update with the scaled
+// values of rows i and k fetched by shuffles.  The arithmetic per entry is the
+// column-at-a-time sequence; inv[k] = 1 / L_kk.
 template <class A>
 __device__ __noinline__ void warp_factor_diag(typename A::T *Ls, typename A::T *inv, int kb,
                                               int nb, int lane) {
   using E = typename A::T;
-  E c[kNB][kNB];
-#pragma unroll
-  for (int i = 0; i < kNB; ++i)
-#pragma unroll
-    for (int j = 0; j <= i; ++j)
-      c[i][j] = i < nb ? Ls[tri(kb + i) + kb + j] : (i == j ? A::from_j(1.0f) : E{});
+  const int i = lane >> 2, s = lane & 3;
+  const E one = A::from_j(1.0f);
+  E c0 = E{}, c1 = E{};  // (i, s) and (i, s + 4)
+  if (s <= i) c0 = i < nb ? Ls[tri(kb + i) + kb + s] : (i == s ? one : E{});
+  if (s + 4 <= i) c1 = i < nb ? Ls[tri(kb + i) + kb + s + 4] : (i == s + 4 ? one : E{});
 #pragma unroll
   for (int q = 0; q < kNB; ++q) {
+    const int sq = q & 3;
+    E &own = q < 4 ? c0 : c1;  // this lane's entry in column q, if any
     E d, id;
-    A::pivot(c[q][q], d, id);
-    c[q][q] = d;
+    A::pivot(shfl_elt(own, 4 * q + sq), d, id);
     if (lane == 0 && q < nb) inv[kb + q] = id;
-#pragma unroll
-    for (int i = q + 1; i < kNB; ++i) c[i][q] = A::mul(c[i][q], id);
-#pragma unroll
-    for (int k = q + 1; k < kNB; ++k)
-#pragma unroll
-      for (int i = k; i < kNB; ++i) {
-        typename A::Acc acc = A::begin(c[i][k]);
-        A::sub(acc, c[i][q], c[k][q]);
-        c[i][k] = A::end(acc);
-      }
+    if (s == sq && i > q) own = A::mul(own, id);
+    if (s == sq && i == q) own = d;
+    const E ciq = shfl_elt(own, 4 * i + sq);        // L_iq
+    const E csq = shfl_elt(own, (4 * s + sq) & 31);  // L_sq
+    const E cs4q = shfl_elt(own, 4 * (s + 4) + sq);  // L_{s+4,q}
+    if (s > q && s <= i) {
+      typename A::Acc acc = A::begin(c0);
+      A::sub(acc, ciq, csq);
+      c0 = A::end(acc);
+    }
+    if (s + 4 > q && s + 4 <= i) {
+      typename A::Acc acc = A::begin(c1);
+      A::sub(acc, ciq, cs4q);
+      c1 = A::end(acc);
+    }
   }
-  __syncwarp();  // every lane's loads of the block precede any lane's stores
-#pragma unroll
-  for (int i = 0; i < kNB; ++i)
-#pragma unroll
-    for (int j = 0; j <= i; ++j)
-      if (lane == (tri(i) + j) % 32 && i < nb) Ls[tri(kb + i) + kb + j] = c[i][j];
+  if (i < nb && s <= i) Ls[tri(kb + i) + kb + s] = c0;
+  if (i < nb && s + 4 <= i) Ls[tri(kb + i) + kb + s + 4] = c1;
   __syncwarp();
 }
 
@@ -374,175 +373,116 @@ __device__ __noinline__ void panel_row(typename A::T *Ls, const typename A::T *i
     if (q < nb) row[kb + q] = x[q];
 }
 
-// Rank-nb update from the panel at kb of the entries (i, j), j0 <= j <= i < r
-// and j < j1: the triangle below j0 when j1 >= r, or a column strip.
-// Threads t0, t0 + T, ... share the entries evenly; each thread works on two
-// entries at a time so that two independent FMA chains hide the FP64 latency.
-struct StripPos {
-  int ii, jj;
-};
+// Trailing update of a right-looking Cholesky step: every entry (i, j) with
+// c0 <= j <= i < n takes the rank-8 update from the factored panel at kb,
+// A_ij -= sum_{k < 8} L_{i,kb+k} L_{j,kb+k}.  The columns are cut into blocks
+// of 32; per block the work items, which warps take from the shared counter
+// *next (one atomic per item), are
+//   two halves of the block's diagonal triangle (rows and columns in the
+//   block), its entries enumerated in packed order, one entry per lane at a
+//   time with both panel rows read from shared memory;
+//   chunks of kColRows rows below the triangle, where each lane owns one
+//   column j (its panel values L_{j,kb..} in registers) and the rows are read
+//   as warp-wide broadcasts, two rows at a time so that every lane runs two
+//   independent accumulations; every lane has work in every row.
+// Every entry is written by one lane and only panel columns are read, so the
+// items need no synchronisation.  The first item (half 0 of the first block)
+// holds the whole 8 x 8 diagonal block of the next panel at c0; with
+// `factor_next` the warp that takes it factors that block right after.
+constexpr int kColRows = 16;
 
-// Rows ii < w of the strip are the triangle's (length ii + 1), the rows below
-// have length w: the walk crosses triangle rows one by one and the
-// rectangular part by one division.
-__device__ __forceinline__ void strip_advance(StripPos &p, int step, int w) {
-  p.jj += step;
-  while (p.ii < w) {
-    if (p.jj <= p.ii) return;
-    p.jj -= p.ii + 1;
-    ++p.ii;
-  }
-  if (p.jj >= w) {
-    if (w == kNB) {  // a full panel strip: shifts instead of a runtime division
-      static_assert(kNB == 8, "strip width is a power of two");
-      p.ii += p.jj >> 3;
-      p.jj &= kNB - 1;
-    } else {
-      p.ii += p.jj / w;
-      p.jj %= w;
-    }
-  }
-}
-
-__device__ __forceinline__ int strip_entries(int r, int j0, int j1) {
-  const int n = r - j0, w = min(j1, r) - j0;
-  return w * (w + 1) / 2 + (n - w) * w;
-}
-
-// Entries [e0, e1) of the enumeration (clipped to the strip).
 template <class A>
-__device__ __noinline__ void trailing_update(typename A::T *Ls, int r, int kb, int nb, int j0,
-                                                int j1, int e0, int e1, int t0, int T) {
+__device__ void trailing_cols(typename A::T *Ls, typename A::T *inv, int n, int kb, int c0,
+                              int *next, bool factor_next) {
   using E = typename A::T;
-  const int w = min(j1, r) - j0;  // strip width (w == n: whole triangle)
-  e1 = min(e1, strip_entries(r, j0, j1));
-  if (e0 + t0 >= e1) return;
-  StripPos p;
-  {
-    const int tw = w * (w + 1) / 2, e = e0 + t0;
-    if (e < tw) {
-      tri_pos(e, p.ii, p.jj);
-    } else {
-      p.ii = w + (e - tw) / w;
-      p.jj = (e - tw) % w;
+  const int lane = threadIdx.x & 31;
+  const int nblk = (n - c0 + 31) / 32;
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(next, 1);
+    item = __shfl_sync(kFull, item, 0);
+    int b = 0, jb = c0, q = item;
+    for (; b < nblk; ++b, jb += 32) {
+      const int chunks = 2 + (max(0, n - jb - 32) + kColRows - 1) / kColRows;
+      if (q < chunks) break;
+      q -= chunks;
     }
-  }
-  for (int e = e0 + t0; e < e1; e += 2 * T) {
-    StripPos q = p;
-    const bool two = e + T < e1;
-    if (two) strip_advance(q, T, w);
-    const int i1 = j0 + p.ii, c1 = j0 + p.jj;
-    const int i2 = j0 + q.ii, c2 = j0 + q.jj;
-    const E *li1 = Ls + tri(i1) + kb, *lj1 = Ls + tri(c1) + kb;
-    const E *li2 = Ls + tri(i2) + kb, *lj2 = Ls + tri(c2) + kb;
-    E *a1 = Ls + tri(i1) + c1;
-    E *a2 = Ls + tri(i2) + c2;
-    // without a second entry q == p: the second chain recomputes the first
-    // entry from valid addresses and is not stored (no selects in the loop)
-    typename A::Acc acc1 = A::begin(*a1), acc2 = A::begin(*a2);
-    if (nb == kNB) {
-      E x1[kNB], y1[kNB], x2[kNB], y2[kNB];
+    if (b == nblk) return;
+    if (q < 2) {  // half q of the diagonal triangle
+      const int m = min(32, n - jb), ne = m * (m + 1) / 2;
+      const int half = min(ne, max(tri(kNB), (ne + 1) / 2));  // half 0 holds the 8 x 8 corner
+      const int e1 = min(ne, (q + 1) * half);
+      for (int e = q * half + lane; e < e1; e += 32) {
+        int ii, jj;
+        tri_pos(e, ii, jj);
+        const E *x = Ls + tri(jb + ii) + kb, *y = Ls + tri(jb + jj) + kb;
+        E *p = Ls + tri(jb + ii) + jb + jj;
+        typename A::Acc acc = A::begin(*p);
+#pragma unroll
+        for (int k = 0; k < kNB; ++k) A::sub(acc, x[k], y[k]);
+        *p = A::end(acc);
+      }
+      if (factor_next && item == 0) {  // the next panel's diagonal block is final
+        __syncwarp();
+        warp_factor_diag<A>(Ls, inv, c0, min(kNB, n - c0), lane);
+      }
+      continue;
+    }
+    const int j = jb + lane;  // < jb + 32 <= every row of the chunk
+    E yj[kNB];
+#pragma unroll
+    for (int k = 0; k < kNB; ++k) yj[k] = Ls[tri(j) + kb + k];
+    const int i0 = jb + 32 + (q - 2) * kColRows, i1 = min(n, i0 + kColRows);
+    for (int i = i0; i < i1; i += 2) {
+      const bool two = i + 1 < i1;
+      const int ib = two ? i + 1 : i;
+      const E *xa = Ls + tri(i) + kb;
+      const E *xb = Ls + tri(ib) + kb;
+      E *pa = Ls + tri(i) + j;
+      E *pb = Ls + tri(ib) + j;
+      typename A::Acc acc1 = A::begin(*pa), acc2 = A::begin(*pb);
 #pragma unroll
       for (int k = 0; k < kNB; ++k) {
-        x1[k] = li1[k];
-        y1[k] = lj1[k];
-        x2[k] = li2[k];
-        y2[k] = lj2[k];
+        A::sub(acc1, xa[k], yj[k]);
+        A::sub(acc2, xb[k], yj[k]);
       }
-#pragma unroll
-      for (int k = 0; k < kNB; ++k) {
-        A::sub(acc1, x1[k], y1[k]);
-        A::sub(acc2, x2[k], y2[k]);
-      }
-    } else {
-      for (int k = 0; k < nb; ++k) A::sub(acc1, li1[k], lj1[k]);
-      if (two)
-        for (int k = 0; k < nb; ++k) A::sub(acc2, li2[k], lj2[k]);
+      *pa = A::end(acc1);
+      if (two) *pb = A::end(acc2);
     }
-    *a1 = A::end(acc1);
-    if (two) *a2 = A::end(acc2);
-    p = q;
-    strip_advance(p, two ? T : 0, w);
   }
 }
 
-// In-place right-looking Cholesky of the packed matrix in 8-column panels.
-// After the first panel, step kb (the panel at kb final) factors the next
-// panel nk = kb + 8 in two phases separated by CTA barriers:
-//   (A) all threads: panel nk's columns take panel kb's rank-8 update;
-//   (B) warp 0 factors the diagonal block of nk and raises a flag; all warps
-//       take work from shared counters: once the flag is up, rows of panel
-//       nk (one per lane, solved against the block), otherwise chunks of
-//       kChunk entries of the trailing triangle right of nk (panel kb's
-//       update); a warp with nothing left but rows waits for the flag
-//       (bounded: on timeout bit 8 of `err` is raised).
-// The counters and the flag alternate between two sets by step parity, so
-// that the set of the next step is cleared while this one is in use.  Per
-// element this is the same sequence of fused multiply-adds as the
-// column-at-a-time algorithm.  A non-positive pivot produces NaN, which the
-// caller turns into a reject.
-constexpr int kChunk = 128;                // trailing-update entries per warp grab
-
-// `ctr` is six ints of shared memory; a warp gives up waiting for the flag
-// after `max_spins` polls.
+// In-place right-looking Cholesky of the packed n x n matrix in 8-column
+// panels.  The first diagonal block is factored by one warp (in registers);
+// then per panel kb, with a CTA barrier after each phase:
+//   every thread takes rows below the factored diagonal block and solves
+//   them against it;
+//   the warps apply the panel's rank-8 update to the columns right of it
+//   (work items from a shared counter), and the warp that updates the next
+//   panel's diagonal block factors it as soon as it is final, while the
+//   others carry on with the update.
+// Row assignment rotates with the panel and the CTA, so that the CTAs
+// resident on an SM load its schedulers evenly.  Per element this is the
+// column-at-a-time sequence of fused multiply-adds.  A non-positive pivot
+// produces NaN, which the caller turns into a reject.  No thread waits on
+// another beyond the barriers.
 template <class A>
-__device__ void cta_cholesky(typename A::T *Ls, typename A::T *inv, int r, int *ctr, int *err,
-                             uint32_t max_spins) {
-  const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid < 6) ctr[tid] = 0;
-  if (warp == 0) warp_factor_diag<A>(Ls, inv, 0, min(kNB, r), lane);
+__device__ void cta_cholesky_panels(typename A::T *Ls, typename A::T *inv, int n) {
+  __shared__ int next_item;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (warp == blockIdx.x % nw) warp_factor_diag<A>(Ls, inv, 0, min(kNB, n), lane);
   __syncthreads();
-  for (int i = min(kNB, r) + tid; i < r; i += T) panel_row<A>(Ls, inv, 0, min(kNB, r), -1, i);
-  __syncthreads();
-  int step = 0;
-  for (int kb = 0; kb + kNB < r; kb += kNB, ++step) {
-    const int nk = kb + kNB, nb2 = min(kNB, r - nk), j0 = nk + nb2;
-    const int rows = r - j0, full = rows > 0 ? strip_entries(r, j0, r) : 0;
-    int *c3 = ctr + 3 * (step & 1);
-    trailing_update<A>(Ls, r, kb, kNB, nk, j0, 0, 1 << 30, tid, T);  // (A)
-    if (tid == 0) {
-      int *o = ctr + 3 * ((step + 1) & 1);
-      o[0] = o[1] = o[2] = 0;
-    }
+  for (int kb = 0; kb < n; kb += kNB) {
+    const int nb = min(kNB, n - kb), j1 = kb + nb;
+    const int rot = (kb / kNB + blockIdx.x) % nw;
+    if (threadIdx.x == 0) next_item = 0;
+    const int t = (threadIdx.x + 32 * rot) % blockDim.x;
+    for (int i = j1 + t; i < n; i += blockDim.x) panel_row<A>(Ls, inv, kb, nb, -1, i);
     __syncthreads();
-    if (warp == 0) {  // (B)
-      warp_factor_diag<A>(Ls, inv, nk, nb2, lane);
-      __threadfence_block();
-      if (lane == 0) atomicExch(&c3[2], 1);
+    if (j1 < n) {
+      trailing_cols<A>(Ls, inv, n, kb, j1, &next_item, true);
+      __syncthreads();
     }
-    uint32_t spins = 0;
-    for (;;) {
-      int job = 0, base = 0;  // 0 done, 1 rows, 2 trailing chunk, 3 wait
-      if (lane == 0) {
-        const bool ready = atomicAdd(&c3[2], 0) != 0;
-        if (ready && rows > 0) {
-          base = atomicAdd(&c3[1], 32);
-          if (base < rows) job = 1;
-        }
-        if (job == 0) {
-          base = atomicAdd(&c3[0], 1) * kChunk;
-          if (base < full) job = 2;
-        }
-        if (job == 0 && !ready && rows > 0) job = 3;
-      }
-      job = __shfl_sync(kFull, job, 0);
-      base = __shfl_sync(kFull, base, 0);
-      if (job == 0) break;
-      if (job == 1) {
-        __syncwarp();
-        __threadfence_block();
-        if (base + lane < rows) panel_row<A>(Ls, inv, nk, nb2, -1, j0 + base + lane);
-      } else if (job == 2) {
-        trailing_update<A>(Ls, r, kb, kNB, j0, r, base, base + kChunk, lane, 32);
-      } else {
-        if (++spins > max_spins) {
-          if (lane == 0) atomicOr(err, 8);
-          break;
-        }
-        __nanosleep(32);
-      }
-    }
-    __syncthreads();
   }
 }
 

@@ -79,8 +79,6 @@ struct ReducedArgs {
   unsigned long long *counters = nullptr;  // [0] accepts, [1] nan rejects
   double *sum_alpha = nullptr;
   int *err = nullptr;  // set (bit 4) when a bounded device wait gives up
-  // polls of the Cholesky diagonal-block flag before giving up (bit 8 of err)
-  uint32_t flag_spins = 1u << 22;
   // caller-supplied noise of this transition (nullptr: Philox): reduced
   // normals (C x r), observation-space normals of the perturbation map
   // (C x d_y) and the log of the accept uniform (C)

@@ -101,8 +101,6 @@ struct dino_ctx {
   std::vector<cudaStream_t> aux_streams;
   // the device reads pageable host memory coherently (Grace: over NVLink-C2C)
   bool pageable_access = false;
-  // polls of the Cholesky diagonal-block flag before a kernel gives up
-  uint32_t flag_spins = 1u << 22;
 };
 
 namespace dino {
@@ -1536,7 +1534,6 @@ static Pool *create_pool_on(dino_ctx *ctx, int sid, int C, double dt, uint64_t s
       });
     eval_surrogate(ctx, s, p->w, p->b, st);
     ReducedArgs ra = reduced_args(*p);
-    ra.flag_spins = ctx->flag_spins;
     launch(ctx, st, "geometry_init", [&] {
       return p->eig ? launch_eig_geometry(ra, 0, st)
              : p->wb ? launch_wb_geometry(ra, 0, st) : launch_geometry(ra, 0, st);
@@ -1578,7 +1575,6 @@ static void step_pool(dino_ctx *ctx, Pool &p) {
   cudaStream_t st = p.st;
   const double cs = std::sqrt(1.0 - p.sc * p.sc);
   ReducedArgs ra = reduced_args(p);
-  ra.flag_spins = ctx->flag_spins;
   const double *ext_z =
       p.ext && p.ext_z ? p.ext + (size_t)C * (r + s->d_y) : nullptr;
   launch(ctx, st, "propose", [&] {
@@ -1721,7 +1717,6 @@ static void surrogate_eval(dino_ctx *ctx, int sid, int n, const double *x_host, 
     eval_surrogate(ctx, s, p.w, p.b, st);
     ReducedArgs ra = reduced_args(p);
     ra.noise_var = s->has_data ? s->noise_var : 1.0;
-    ra.flag_spins = ctx->flag_spins;
     launch(ctx, st, "geometry_init", [&] { return launch_geometry(ra, 0, st); });
     CK(cudaStreamSynchronize(st));
     std::vector<double> tmp;
@@ -2766,9 +2761,6 @@ int dino_diag_destroy(dino_ctx *ctx, int diag_id) {
   });
 }
 
-int dino_set_wait_limit(dino_ctx *ctx, uint32_t flag_spins) {
-  return guarded(ctx, [&] { ctx->flag_spins = flag_spins ? flag_spins : (1u << 22); });
-}
 
 int dino_chains_destroy(dino_ctx *ctx, int pool_id) {
   return guarded(ctx, [&] {

@@ -351,8 +351,7 @@ __global__ void __launch_bounds__(NT) k_geometry(ReducedArgs a, int mode) {
   vv = block_sum(vv, red);
   if (threadIdx.x == 0) Ls[tri(r) + r] = A::from(1.0 + vv);
   __syncthreads();
-  cta_cholesky<A>(Ls, inv, r + 1, reinterpret_cast<int *>(red + 100), a.err,
-                  a.flag_spins);
+  cta_cholesky_panels<A>(Ls, inv, r + 1);
   double ld = 0.0;
   for (int i = threadIdx.x; i < r; i += blockDim.x) ld += log(A::to(Ls[tri(i) + i]));
   const double hld_b = block_sum(ld, red);

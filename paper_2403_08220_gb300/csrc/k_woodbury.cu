@@ -388,10 +388,28 @@ __global__ void __launch_bounds__(kWbThreads, kWbMinBlocks) k_wb_geometry(Reduce
                                reinterpret_cast<const float2 *>(ae), mode == 1, Kb, Ka);
       const float *Gc = a.G + (size_t)c * dy * a.ldg;
       const float nh = __double2float_rn(inv_nv), nl = __double2float_rn(inv_nv - (double)nh);
-      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-      for (int i = warp; i < dy; i += nw)
-        for (int j = lane; j <= i; j += 32)
-          reinterpret_cast<float2 *>(Ms)[tri(i) + j] = gram_entry(Gc[(size_t)i * a.ldg + j], nh, nl, i == j);
+      // the packed lower triangle in order, eight independent loads in flight per thread
+      constexpr int kLoads = 8;
+      const int ntri = tri(dy);
+      for (int e0 = threadIdx.x; e0 < ntri; e0 += kLoads * blockDim.x) {
+        float x[kLoads];
+        int ii[kLoads], jj[kLoads];
+#pragma unroll
+        for (int q = 0; q < kLoads; ++q) {
+          const int e = e0 + q * blockDim.x;
+          ii[q] = jj[q] = 0;
+          x[q] = 0.0f;
+          if (e < ntri) {
+            tri_pos(e, ii[q], jj[q]);
+            x[q] = Gc[(size_t)ii[q] * a.ldg + jj[q]];
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < kLoads; ++q) {
+          const int e = e0 + q * blockDim.x;
+          if (e < ntri) reinterpret_cast<float2 *>(Ms)[e] = gram_entry(x[q], nh, nl, ii[q] == jj[q]);
+        }
+      }
       __syncthreads();
     } else {
       wb_gram_rows<A>(reinterpret_cast<const float *>(J), dy, r, inv_nv, inv_sigma,
@@ -414,8 +432,7 @@ __global__ void __launch_bounds__(kWbThreads, kWbMinBlocks) k_wb_geometry(Reduce
   for (int i = threadIdx.x; i < dy; i += blockDim.x) Ms[tri(dy) + i] = A::from(u[i]);
   if (threadIdx.x == 0) Ms[tri(dy) + dy] = A::from(1.0 + uu);
   __syncthreads();
-  cta_cholesky<A>(Ms, inv, dy + 1, reinterpret_cast<int *>(red + 100), a.err,
-                  a.flag_spins);
+  cta_cholesky_panels<A>(Ms, inv, dy + 1);
   double ld = 0.0, ss = 0.0;
   for (int i = threadIdx.x; i < dy; i += blockDim.x) {
     ld += log(A::to(Ms[tri(i) + i]));

@@ -1,5 +1,5 @@
-"""Caller-supplied noise, the accept rule at its threshold, non-finite log rho
-and the bounded device wait (GPU).
+"""Caller-supplied noise, the accept rule at its threshold and non-finite log
+rho (GPU).
 
 dino_chains_set_noise feeds the next transition's normals and accept uniform
 from the host, so the CUDA path and the oracle can be driven with the same
@@ -8,10 +8,7 @@ arbitrary (not Philox) draws, including adversarial ones:
   * log u placed exactly at min(0, log rho): Algorithm 1 rejects only when
     alpha < u, so equality accepts, and the next double above rejects;
   * NaN reduced noise: log rho is not finite, the proposal is rejected and
-    counted in nan_rejects, and the chain state is unchanged;
-  * a one-poll limit on the Cholesky's diagonal-block flag (a wait between
-    the warps of one CTA): the step reports DINO_ETIMEOUT and the context
-    stays usable.
+    counted in nan_rejects, and the chain state is unchanged.
 """
 import numpy as np
 import pytest
@@ -137,37 +134,6 @@ def test_nan_noise_is_a_counted_reject(dino, ctx, w):
     # the pool goes on normally afterwards
     st2 = dino.dino_chains_step(ctx, pool, 2)
     assert st2["nan_rejects"] == 0
-    dino.dino_chains_destroy(ctx, pool)
-    dino.dino_unload_surrogate(ctx, sid)
-
-
-def test_flag_wait_timeout_reports_etimeout_and_context_survives(dino, ctx):
-    """One poll of the diagonal-block flag: warps that run out of trailing
-    work before the diagonal block is factored give up at once, raise the
-    pool's error word and leave the kernel; the step then reports ETIMEOUT.
-    The kernel finishes either way (the wait only gets shorter)."""
-    w = CONFIGS["r200_kle_fp64"]
-    sid = gpu_setup(dino, ctx, w)
-    sur, E, D = oracle_setup(w)
-    C, dt = 64, 2e-5
-    pool = dino.dino_chains_create(ctx, sid, C, dt, SEED_CHAINS)
-    dino.dino_set_wait_limit(ctx, 1)
-    try:
-        with pytest.raises(dino.DinoError) as e:
-            dino.dino_chains_step(ctx, pool, 1)
-        assert e.value.code == dino.DINO_ETIMEOUT
-        with pytest.raises(dino.DinoError) as e:
-            dino.dino_chains_read(ctx, pool, C, w.r, w.N)
-        assert e.value.code == dino.DINO_ETIMEOUT
-    finally:
-        dino.dino_set_wait_limit(ctx, 0)
-    dino.dino_chains_destroy(ctx, pool)
-    # the context is usable: a new pool steps and matches the oracle
-    pool = dino.dino_chains_create(ctx, sid, 8, dt, SEED_CHAINS)
-    och = oracle_chains(dino, ctx, sid, w, sur, E, D, 8, dt)
-    dino.dino_chains_step(ctx, pool, 1)
-    och.step()
-    assert rel_err(dino.dino_chains_read_last(ctx, pool, 8, w.r)["b"], och.last["b"]) <= TOL
     dino.dino_chains_destroy(ctx, pool)
     dino.dino_unload_surrogate(ctx, sid)
 
