@@ -19,7 +19,7 @@ constexpr int kJChunkF = 32;   // rows of an FP32 matrix staged per pass
 constexpr int kNB = 8;         // Cholesky panel width
 constexpr int kHT = 4;         // FP32 register tile edge of the Gram products
 constexpr int kHMaxTiles = 3;  // tiles per thread: ceil(52*53/2 / 512) for n <= 208
-constexpr int kRed = 104;      // reduction scratch (doubles): block_sum3 [0, 99), Cholesky counters [100, 103)
+constexpr int kRed = 104;      // reduction scratch (doubles): block_sum3 uses [0, 99)
 
 __device__ __forceinline__ int tri(int i) { return i * (i + 1) / 2; }
 // Sum over the CTA; `red` holds >= 33 doubles.  Every thread gets the sum.
@@ -319,14 +319,17 @@ __device__ __noinline__ void warp_factor_diag(typename A::T *Ls, typename A::T *
     if (lane == 0 && q < nb) inv[kb + q] = id;
     if (s == sq && i > q) own = A::mul(own, id);
     if (s == sq && i == q) own = d;
-    const E ciq = shfl_elt(own, 4 * i + sq);        // L_iq
-    const E csq = shfl_elt(own, (4 * s + sq) & 31);  // L_sq
-    const E cs4q = shfl_elt(own, 4 * (s + 4) + sq);  // L_{s+4,q}
-    if (s > q && s <= i) {
-      typename A::Acc acc = A::begin(c0);
-      A::sub(acc, ciq, csq);
-      c0 = A::end(acc);
+    if (q == kNB - 1) break;  // nothing right of the last column
+    const E ciq = shfl_elt(own, 4 * i + sq);  // L_iq
+    if (q < 3) {                              // entries (i, s) with s > q exist
+      const E csq = shfl_elt(own, 4 * s + sq);  // L_sq
+      if (s > q && s <= i) {
+        typename A::Acc acc = A::begin(c0);
+        A::sub(acc, ciq, csq);
+        c0 = A::end(acc);
+      }
     }
+    const E cs4q = shfl_elt(own, 4 * (s + 4) + sq);  // L_{s+4,q}
     if (s + 4 > q && s + 4 <= i) {
       typename A::Acc acc = A::begin(c1);
       A::sub(acc, ciq, cs4q);
@@ -378,17 +381,19 @@ __device__ __noinline__ void panel_row(typename A::T *Ls, const typename A::T *i
 // A_ij -= sum_{k < 8} L_{i,kb+k} L_{j,kb+k}.  The columns are cut into blocks
 // of 32; per block the work items, which warps take from the shared counter
 // *next (one atomic per item), are
-//   two halves of the block's diagonal triangle (rows and columns in the
-//   block), its entries enumerated in packed order, one entry per lane at a
-//   time with both panel rows read from shared memory;
+//   the block's diagonal triangle (rows and columns in the block) in three
+//   items, its 8 x 8 corner and two halves of the rest, entries enumerated in
+//   packed order, one entry per lane at a time with both panel rows read
+//   from shared memory;
 //   chunks of kColRows rows below the triangle, where each lane owns one
 //   column j (its panel values L_{j,kb..} in registers) and the rows are read
 //   as warp-wide broadcasts, two rows at a time so that every lane runs two
 //   independent accumulations; every lane has work in every row.
 // Every entry is written by one lane and only panel columns are read, so the
-// items need no synchronisation.  The first item (half 0 of the first block)
-// holds the whole 8 x 8 diagonal block of the next panel at c0; with
-// `factor_next` the warp that takes it factors that block right after.
+// items need no synchronisation.  The first item (the corner of the first
+// block) is the 8 x 8 diagonal block of the next panel at c0; with
+// `factor_next` the warp that takes it factors that block right after, a
+// short serial path that the other warps' items overlap.
 constexpr int kColRows = 16;
 
 template <class A>
@@ -403,16 +408,17 @@ __device__ void trailing_cols(typename A::T *Ls, typename A::T *inv, int n, int 
     item = __shfl_sync(kFull, item, 0);
     int b = 0, jb = c0, q = item;
     for (; b < nblk; ++b, jb += 32) {
-      const int chunks = 2 + (max(0, n - jb - 32) + kColRows - 1) / kColRows;
+      const int chunks = 3 + (max(0, n - jb - 32) + kColRows - 1) / kColRows;
       if (q < chunks) break;
       q -= chunks;
     }
     if (b == nblk) return;
-    if (q < 2) {  // half q of the diagonal triangle
-      const int m = min(32, n - jb), ne = m * (m + 1) / 2;
-      const int half = min(ne, max(tri(kNB), (ne + 1) / 2));  // half 0 holds the 8 x 8 corner
-      const int e1 = min(ne, (q + 1) * half);
-      for (int e = q * half + lane; e < e1; e += 32) {
+    if (q < 3) {  // the diagonal triangle: its 8 x 8 corner, then two halves of the rest
+      const int m = min(32, n - jb), ne = m * (m + 1) / 2, nc = min(ne, tri(kNB));
+      const int half = (ne - nc + 1) / 2;
+      const int e0 = q == 0 ? 0 : nc + (q - 1) * half;
+      const int e1 = q == 0 ? nc : min(ne, nc + q * half);
+      for (int e = e0 + lane; e < e1; e += 32) {
         int ii, jj;
         tri_pos(e, ii, jj);
         const E *x = Ls + tri(jb + ii) + kb, *y = Ls + tri(jb + jj) + kb;
@@ -432,7 +438,7 @@ __device__ void trailing_cols(typename A::T *Ls, typename A::T *inv, int n, int 
     E yj[kNB];
 #pragma unroll
     for (int k = 0; k < kNB; ++k) yj[k] = Ls[tri(j) + kb + k];
-    const int i0 = jb + 32 + (q - 2) * kColRows, i1 = min(n, i0 + kColRows);
+    const int i0 = jb + 32 + (q - 3) * kColRows, i1 = min(n, i0 + kColRows);
     for (int i = i0; i < i1; i += 2) {
       const bool two = i + 1 < i1;
       const int ib = two ? i + 1 : i;
@@ -666,17 +672,26 @@ __device__ void form_gram_f32(const float *X, int m, int n, int ldx, double inv_
   __syncthreads();
 }
 
-// The accept test log u <= min(0, log rho) (Algorithm 1; NaN rejects), the
-// counters ([0] accepts, [1] non-finite rejects, [2] first-stage accepts),
-// and the scalar state of an accepted chain, or with delayed acceptance its
-// staging for the second stage.  Thread 0 only.
-__device__ bool accept_test(const ReducedArgs &a, int c, double lr, double phi_b, double hld_b) {
+// log u of the accept test: caller-supplied, or from the chain's Philox
+// stream STREAM_U at this step.
+__device__ double draw_log_u(const ReducedArgs &a, int c) {
   const uint32_t chain = (uint32_t)(a.id_base + (uint64_t)c);
-  const double log_u =
-      a.ext_log_u ? a.ext_log_u[c]
-                  : log(word_to_uniform(philox_block(a.seed, STREAM_U, a.step, chain, 0).x));
+  return a.ext_log_u ? a.ext_log_u[c]
+                     : log(word_to_uniform(philox_block(a.seed, STREAM_U, a.step, chain, 0).x));
+}
+
+// The accept test log u <= min(0, log rho) (Algorithm 1; NaN rejects).
+__device__ __forceinline__ bool accept_decide(double lr, double log_u) {
+  return isfinite(lr) && log_u <= fmin(0.0, lr);
+}
+
+// The record of the test: log rho, log u, the decision, the counters ([0]
+// accepts, [1] non-finite rejects, [2] first-stage accepts), the sum of the
+// acceptance probabilities, and the scalar state of an accepted chain, or
+// with delayed acceptance its staging for the second stage.  One thread.
+__device__ void accept_record(const ReducedArgs &a, int c, double lr, double log_u, bool accept,
+                              double phi_b, double hld_b) {
   const bool finite = isfinite(lr);
-  const bool accept = finite && log_u <= fmin(0.0, lr);
   a.log_rho[c] = lr;
   a.log_u[c] = log_u;
   a.acc[c] = accept ? 1 : 0;
@@ -695,6 +710,13 @@ __device__ bool accept_test(const ReducedArgs &a, int c, double lr, double phi_b
   }
   if (!finite) atomicAdd(&a.counters[1], 1ull);
   atomicAdd(a.sum_alpha, finite ? exp(fmin(0.0, lr)) : 0.0);
+}
+
+// Both at once (thread 0).
+__device__ bool accept_test(const ReducedArgs &a, int c, double lr, double phi_b, double hld_b) {
+  const double log_u = draw_log_u(a, c);
+  const bool accept = accept_decide(lr, log_u);
+  accept_record(a, c, lr, log_u, accept, phi_b, hld_b);
   return accept;
 }
 

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cstddef>
+#include <cmath>
 #include <cstdint>
 
 namespace dino {
@@ -44,6 +45,17 @@ inline __host__ __device__ size_t wb_slot_stride(int d_y) {
 struct ReducedArgs {
   int C = 0, r = 0, d_y = 0;
   double s = 0, dt = 0, noise_var = 1;
+  // constants of every chain, set by derive() before a launch (the kernels
+  // would otherwise each take FP64 divisions and square roots):
+  // 1 / noise_var, its square root, c_s = sqrt(1 - s^2), 1 / c_s, sqrt(dt)
+  double inv_nv = 1, inv_sigma = 1, cs = 1, inv_cs = 1, sqrt_dt = 0;
+  void derive() {
+    inv_nv = 1.0 / noise_var;
+    inv_sigma = std::sqrt(inv_nv);
+    cs = std::sqrt(1.0 - s * s);
+    inv_cs = 1.0 / cs;
+    sqrt_dt = std::sqrt(dt);
+  }
   uint64_t seed = 0, id_base = 0;
   uint32_t step = 0;
   // chain state

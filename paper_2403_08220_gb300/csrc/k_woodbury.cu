@@ -37,7 +37,8 @@ namespace dino {
 namespace {
 
 constexpr int kWbThreads = 128;
-constexpr int kWbMinBlocks = 4;  // CTAs per SM the register budget is sized for
+constexpr int kWbPreThreads = 256;  // geometry with the Gram matrix and K b, K a formed beforehand
+constexpr int kWbMinBlocks = 4;     // CTAs per SM the register budget is sized for
 
 // Slot offsets (8-byte elements).
 struct WbSlot {
@@ -53,11 +54,11 @@ struct WbSlot {
 
 // Shared-memory layout in 8-byte elements:
 //   Ms[tri(dy+1)] inv[dy+1] | r-vectors: vb va be ae | dy-vectors: Kb Ka u sv eE zE vE
-//   | red[kRed] flag | staging of J (FP64 geometry only)
+//   | red[kRed] flag lu | staging of J (FP64 geometry only)
 // On the tensor-core path J is staged inside Ms, which holds nothing until
 // the Gram tiles are written (wb_stage_fits).
 struct WbLayout {
-  size_t Ms, inv, vb, va, be, ae, Kb, Ka, u, sv, eE, zE, vE, red, flag, tail;
+  size_t Ms, inv, vb, va, be, ae, Kb, Ka, u, sv, eE, zE, vE, red, flag, lu, tail;
   __host__ __device__ WbLayout(int r, int dy) {
     Ms = 0;
     inv = (tri_size(dy + 1) + 1) & ~(size_t)1;
@@ -74,7 +75,8 @@ struct WbLayout {
     vE = zE + dy;
     red = vE + dy;
     flag = red + kRed;
-    tail = (flag + 1 + 1) & ~(size_t)1;
+    lu = flag + 1;  // log u of the accept test
+    tail = (lu + 1 + 1) & ~(size_t)1;
   }
 };
 
@@ -327,9 +329,12 @@ __device__ void wb_store_factor(double *Lg, const typename A::T *Ms, const typen
   if (threadIdx.x == 0) Lg[sl.t1] = t1;
 }
 
-// One CTA per chain at the point b (see the file comment).
-template <typename TJ>
-__global__ void __launch_bounds__(kWbThreads, kWbMinBlocks) k_wb_geometry(ReducedArgs a, int mode) {
+// One CTA of NT threads per chain at the point b (see the file comment).
+// kPre: the Gram matrix J J^T and K b, K a come formed (the tensor-core
+// path); this instantiation is kept lean in registers so that NT = 256
+// threads (64 registers each) fit four CTAs on an SM.
+template <typename TJ, bool kPre, int NT>
+__global__ void __launch_bounds__(NT, kWbMinBlocks) k_wb_geometry(ReducedArgs a, int mode) {
   using A = std::conditional_t<sizeof(TJ) == 4, DF, F64>;
   using E = typename A::T;
   static_assert(sizeof(E) == sizeof(double), "one factor element per double of the slot");
@@ -348,14 +353,17 @@ __global__ void __launch_bounds__(kWbThreads, kWbMinBlocks) k_wb_geometry(Reduce
   E *vE = reinterpret_cast<E *>(sm + lay.vE);
   double *red = sm + lay.red;
   int *flag = reinterpret_cast<int *>(sm + lay.flag);
+  double *log_u_s = sm + lay.lu;
   const TJ *J = reinterpret_cast<const TJ *>(a.J) + (size_t)c * dy * r;
   const TJ *f = reinterpret_cast<const TJ *>(a.f) + (size_t)c * dy;
-  const double inv_nv = 1.0 / a.noise_var, inv_sigma = sqrt(inv_nv);
+  const double inv_nv = a.inv_nv, inv_sigma = a.inv_sigma;
+  // log u, off the accept test's critical path (read after several barriers)
+  if (mode == 1 && threadIdx.x == blockDim.x - 1) *log_u_s = draw_log_u(a, c);
 
   for (int k = threadIdx.x; k < r; k += blockDim.x) {
     vb[k] = a.b[(size_t)c * r + k];
     va[k] = mode == 1 ? a.mr[(size_t)c * r + k] : 0.0;
-    if (!a.Kb_pre) {  // operands of this kernel's own K b, K a pass
+    if (!kPre && !a.Kb_pre) {  // operands of this kernel's own K b, K a pass
       be[k] = A::from(vb[k]);
       ae[k] = A::from(va[k]);
     }
@@ -370,25 +378,27 @@ __global__ void __launch_bounds__(kWbThreads, kWbMinBlocks) k_wb_geometry(Reduce
   if constexpr (sizeof(TJ) == 4) {  // M, K b and K a from one pass over J
     float *stage = wb_stage_fits(dy) ? reinterpret_cast<float *>(sm + lay.Ms)
                                      : reinterpret_cast<float *>(sm + lay.tail);
-    if (a.G) {  // Gram matrix formed on the tensor cores: K b, K a only, then M from G
-      if (a.Kb_pre) {  // ... and K b, K a too (the Jacobian GEMM's epilogue)
+    if (kPre || a.G) {  // Gram matrix formed on the tensor cores: K b, K a only, then M from G
+      if constexpr (kPre) {  // ... and K b, K a too (the Jacobian GEMM's epilogue)
         for (int i = threadIdx.x; i < dy; i += blockDim.x) {
           Kb[i] = a.Kb_pre[(size_t)c * dy + i];
           if (mode == 1) Ka[i] = a.Ka_pre[(size_t)c * dy + i];
         }
-      } else if (wb_ring4_fits(dy))
+      } else if (wb_ring4_fits(dy)) {
         wb_gram_rows<A, false, 4>(reinterpret_cast<const float *>(J), dy, r, inv_nv, inv_sigma,
                                   reinterpret_cast<float2 *>(Ms), stage,
                                   reinterpret_cast<const float2 *>(be),
                                   reinterpret_cast<const float2 *>(ae), mode == 1, Kb, Ka);
-      else
+      } else {
         wb_gram_rows<A, false>(reinterpret_cast<const float *>(J), dy, r, inv_nv, inv_sigma,
                                reinterpret_cast<float2 *>(Ms), stage,
                                reinterpret_cast<const float2 *>(be),
                                reinterpret_cast<const float2 *>(ae), mode == 1, Kb, Ka);
+      }
       const float *Gc = a.G + (size_t)c * dy * a.ldg;
       const float nh = __double2float_rn(inv_nv), nl = __double2float_rn(inv_nv - (double)nh);
-      // the packed lower triangle in order, eight independent loads in flight per thread
+      // the packed lower triangle in order, eight independent loads in
+      // flight per thread
       constexpr int kLoads = 8;
       const int ntri = tri(dy);
       for (int e0 = threadIdx.x; e0 < ntri; e0 += kLoads * blockDim.x) {
@@ -411,7 +421,7 @@ __global__ void __launch_bounds__(kWbThreads, kWbMinBlocks) k_wb_geometry(Reduce
         }
       }
       __syncthreads();
-    } else {
+    } else if constexpr (!kPre) {
       wb_gram_rows<A>(reinterpret_cast<const float *>(J), dy, r, inv_nv, inv_sigma,
                       reinterpret_cast<float2 *>(Ms), stage,
                       reinterpret_cast<const float2 *>(be), reinterpret_cast<const float2 *>(ae),
@@ -472,21 +482,23 @@ __global__ void __launch_bounds__(kWbThreads, kWbMinBlocks) k_wb_geometry(Reduce
     }
     return;
   }
-  const double s = a.s, cs = sqrt(1.0 - s * s);
+  const double s = a.s, inv_cs = a.inv_cs;
   double t2 = 0.0, t3 = 0.0, unused = 0.0;
   for (int i = threadIdx.x; i < dy; i += blockDim.x) {
-    const double km = (Ka[i] - s * Kb[i]) / cs;  // K mhat for b -> a
+    const double km = (Ka[i] - s * Kb[i]) * inv_cs;  // K mhat for b -> a
     t2 += km * u[i];
     t3 += km * km;
   }
   block_sum3(t2, t3, unused, red);
+  double lr = 0.0;
   if (threadIdx.x == 0) {
-    const double lq_rev = -a.dt / 8.0 * t1 + sqrt(a.dt) / 2.0 * t2 + hld_b - 0.5 * t3;
-    const double lr = a.phi[c] - phi_b + lq_rev - a.lq_fwd[c];
-    *flag = accept_test(a, c, lr, phi_b, hld_b) ? 1 : 0;
+    const double lq_rev = -a.dt / 8.0 * t1 + a.sqrt_dt / 2.0 * t2 + hld_b - 0.5 * t3;
+    lr = a.phi[c] - phi_b + lq_rev - a.lq_fwd[c];
+    *flag = accept_decide(lr, *log_u_s) ? 1 : 0;
   }
   __syncthreads();
   const bool accept = *flag != 0;
+  if (threadIdx.x == 0) accept_record(a, c, lr, *log_u_s, accept, phi_b, hld_b);
   for (int k = threadIdx.x; k < r; k += blockDim.x) a.coef[(size_t)c * r + k] = vb[k] - s * va[k];
   if (accept) {
     const double *vv = solve_v();
@@ -679,14 +691,23 @@ size_t wb_geometry_smem(int r, int dy) {
   return WbLayout(r, dy).tail * sizeof(double) + wb_stage_bytes<TJ>(r, dy);
 }
 
-template <typename TJ>
-cudaError_t launch_wb_geometry_t(const ReducedArgs &a, int mode, cudaStream_t st) {
+template <typename TJ, bool kPre, int NT>
+cudaError_t launch_wb_geometry_k(const ReducedArgs &a, int mode, cudaStream_t st) {
   const size_t smem = wb_geometry_smem<TJ>(a.r, a.d_y);
-  cudaError_t e = cudaFuncSetAttribute(k_wb_geometry<TJ>,
+  cudaError_t e = cudaFuncSetAttribute(k_wb_geometry<TJ, kPre, NT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_wb_geometry<TJ><<<a.C, kWbThreads, smem, st>>>(a, mode);
+  ReducedArgs b = a;
+  b.derive();
+  k_wb_geometry<TJ, kPre, NT><<<a.C, NT, smem, st>>>(b, mode);
   return cudaGetLastError();
+}
+
+template <typename TJ>
+cudaError_t launch_wb_geometry_t(const ReducedArgs &a, int mode, cudaStream_t st) {
+  if constexpr (sizeof(TJ) == 4)
+    if (a.G && a.Kb_pre) return launch_wb_geometry_k<TJ, true, kWbPreThreads>(a, mode, st);
+  return launch_wb_geometry_k<TJ, false, kWbThreads>(a, mode, st);
 }
 
 template <typename TJ>
@@ -695,7 +716,9 @@ cudaError_t launch_wb_propose_t(const ReducedArgs &a, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(k_wb_propose<TJ>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_wb_propose<TJ><<<a.C, kWbThreads, smem, st>>>(a);
+  ReducedArgs b = a;
+  b.derive();
+  k_wb_propose<TJ><<<a.C, kWbThreads, smem, st>>>(b);
   return cudaGetLastError();
 }
 
