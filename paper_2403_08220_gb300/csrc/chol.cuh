@@ -169,30 +169,27 @@ struct DF {
     return make_float2(h, l);
   }
   __device__ static T neg(T a) { return make_float2(-a.x, -a.y); }
-  // The same pivot on the FP32 pipe: the Newton step y <- y + y (1 - x y^2) / 2
-  // takes the residual 1 - x y^2 exactly (double-float product, two-sum
-  // against 1) and the small correction in FP32, so from an estimate with
-  // relative error e it reaches about 1.5 e^2.  x <= 0 gives NaN, as in FP64.
-  __device__ static void newton_rsqrt(T x, T &y) {
-    const T y2 = mul(y, y);
-    const T xy2 = mul(x, y2);
-    float s, q;
-    two_sum(1.0f, -xy2.x, s, q);
-    const float res = __fadd_rn(s, __fsub_rn(q, xy2.y));
-    const float c = __fmul_rn(__fmul_rn(0.5f, y.x), res);
-    float h, l;
-    two_sum(y.x, c, h, l);
-    fast_two_sum(h, __fadd_rn(l, y.y), y.x, y.y);
-  }
+  // The same pivot on the FP32 pipe: an FP32 estimate y of x^(-1/2), one
+  // FP32 Newton step (relative error ~2^-24), then one Newton step
+  // y <- y + y (1 - x y^2) / 2 whose residual is formed from exact pieces:
+  // y^2 = p + e and x.h p = hp + herr exactly, 1 - hp is exact (hp is within
+  // a factor 2 of 1), so r = 1 - x y^2 is accurate to ~2^-47 absolute and
+  // from an estimate with relative error e the step reaches about 1.5 e^2
+  // (~2^-45 from e ~ 2^-23).  The correction y r / 2 needs only FP32
+  // precision.  x <= 0 gives NaN, as in FP64.
   __device__ static void pivot(T x, T &d, T &id) {
-    // FP32 estimate, one FP32 Newton step (relative error ~2^-23), then one
-    // double-float step (~2^-45)
-    float y0 = rsqrtf(x.x);
-    y0 = y0 * (1.5f - 0.5f * x.x * y0 * y0);
-    T y = make_float2(y0, 0.0f);
-    newton_rsqrt(x, y);
-    id = y;
-    d = mul(x, y);
+    float y = rsqrtf(x.x);
+    y = y * (1.5f - 0.5f * x.x * y * y);
+    const float p = __fmul_rn(y, y);
+    const float e = __fmaf_rn(y, y, -p);
+    const float hp = __fmul_rn(x.x, p);
+    const float herr = __fmaf_rn(x.x, p, -hp);
+    float r = __fsub_rn(__fsub_rn(1.0f, hp), herr);
+    r = __fmaf_rn(-x.x, e, r);
+    r = __fmaf_rn(-x.y, p, r);
+    const float c = __fmul_rn(__fmul_rn(0.5f, y), r);
+    fast_two_sum(y, c, id.x, id.y);
+    d = mul(x, id);
   }
 };
 
@@ -300,14 +297,16 @@ __device__ __forceinline__ void tri_pos(int e, int &ii, int &jj) {
 // A::pivot of the broadcast diagonal entry, the owners of column q scale it,
 // and each entry (i, k), q < k <= i, takes the rank-1 update with the scaled
 // values of rows i and k fetched by shuffles.  The arithmetic per entry is the
-// column-at-a-time sequence; inv[k] = 1 / L_kk.
+// column-at-a-time sequence; inv[k] = 1 / L_kk, and lsc (packed, 8 x 8)
+// receives the strictly lower block scaled by row, L_ij / L_ii.
 template <class A>
 __device__ __noinline__ void warp_factor_diag(typename A::T *Ls, typename A::T *inv, int kb,
-                                              int nb, int lane) {
+                                              int nb, int lane, typename A::T *lsc) {
   using E = typename A::T;
   const int i = lane >> 2, s = lane & 3;
   const E one = A::from_j(1.0f);
   E c0 = E{}, c1 = E{};  // (i, s) and (i, s + 4)
+  E id_i = one;          // 1 / L_ii of this lane's row
   if (s <= i) c0 = i < nb ? Ls[tri(kb + i) + kb + s] : (i == s ? one : E{});
   if (s + 4 <= i) c1 = i < nb ? Ls[tri(kb + i) + kb + s + 4] : (i == s + 4 ? one : E{});
 #pragma unroll
@@ -317,6 +316,7 @@ __device__ __noinline__ void warp_factor_diag(typename A::T *Ls, typename A::T *
     E d, id;
     A::pivot(shfl_elt(own, 4 * q + sq), d, id);
     if (lane == 0 && q < nb) inv[kb + q] = id;
+    if (i == q) id_i = id;
     if (s == sq && i > q) own = A::mul(own, id);
     if (s == sq && i == q) own = d;
     if (q == kNB - 1) break;  // nothing right of the last column
@@ -338,37 +338,33 @@ __device__ __noinline__ void warp_factor_diag(typename A::T *Ls, typename A::T *
   }
   if (i < nb && s <= i) Ls[tri(kb + i) + kb + s] = c0;
   if (i < nb && s + 4 <= i) Ls[tri(kb + i) + kb + s + 4] = c1;
+  // the rows of the block scaled by their inverse pivots, L_ij / L_ii (j < i),
+  // for the row solves
+  if (s < i) lsc[tri(i) + s] = A::mul(c0, id_i);
+  if (s + 4 < i) lsc[tri(i) + s + 4] = A::mul(c1, id_i);
   __syncwarp();
 }
 
-// Row i of the panel at kb (width nb): when pk >= 0 its entries first take
-// the rank-8 update from the panel at pk, then L[i, kb:kb+nb] <- L[i, kb:kb+nb] L_bb^-T
-// against the factored diagonal block.
+// Row i of the panel at kb (width nb): L[i, kb:kb+nb] <- L[i, kb:kb+nb] L_bb^-T,
+// by forward substitution with the row-scaled block lsc (L_qp / L_qq):
+// x_q = b_q / L_qq - sum_{p<q} x_p (L_qp / L_qq), so that each step of the
+// dependent chain is one multiply-subtract.
 template <class A>
-__device__ __noinline__ void panel_row(typename A::T *Ls, const typename A::T *inv, int kb,
-                                       int nb, int pk, int i) {
+__device__ __noinline__ void panel_row(typename A::T *Ls, const typename A::T *inv,
+                                       const typename A::T *lsc, int kb, int nb, int i) {
   using E = typename A::T;
   E *row = Ls + tri(i);
-  typename A::Acc acc[kNB];
-#pragma unroll
-  for (int q = 0; q < kNB; ++q) acc[q] = A::begin(q < nb ? row[kb + q] : E{});
-  if (pk >= 0) {
-#pragma unroll
-    for (int p = 0; p < kNB; ++p) {
-      const E x = row[pk + p];
-#pragma unroll
-      for (int q = 0; q < kNB; ++q)
-        if (q < nb) A::sub(acc[q], x, Ls[tri(kb + q) + pk + p]);
-    }
-  }
   E x[kNB];
 #pragma unroll
-  for (int q = 0; q < kNB; ++q) {
-    if (q < nb) {
-      const E *lq = Ls + tri(kb + q) + kb;
+  for (int q = 0; q < kNB; ++q)
+    if (q < nb) x[q] = A::mul(row[kb + q], inv[kb + q]);
 #pragma unroll
-      for (int p = 0; p < q; ++p) A::sub(acc[q], x[p], lq[p]);
-      x[q] = A::mul(A::end(acc[q]), inv[kb + q]);
+  for (int q = 1; q < kNB; ++q) {
+    if (q < nb) {
+      typename A::Acc acc = A::begin(x[q]);
+#pragma unroll
+      for (int p = 0; p < q; ++p) A::sub(acc, x[p], lsc[tri(q) + p]);
+      x[q] = A::end(acc);
     }
   }
 #pragma unroll
@@ -397,8 +393,8 @@ __device__ __noinline__ void panel_row(typename A::T *Ls, const typename A::T *i
 constexpr int kColRows = 16;
 
 template <class A>
-__device__ void trailing_cols(typename A::T *Ls, typename A::T *inv, int n, int kb, int c0,
-                              int *next, bool factor_next) {
+__device__ void trailing_cols(typename A::T *Ls, typename A::T *inv, typename A::T *lsc, int n,
+                              int kb, int c0, int *next, bool factor_next) {
   using E = typename A::T;
   const int lane = threadIdx.x & 31;
   const int nblk = (n - c0 + 31) / 32;
@@ -430,7 +426,7 @@ __device__ void trailing_cols(typename A::T *Ls, typename A::T *inv, int n, int 
       }
       if (factor_next && item == 0) {  // the next panel's diagonal block is final
         __syncwarp();
-        warp_factor_diag<A>(Ls, inv, c0, min(kNB, n - c0), lane);
+        warp_factor_diag<A>(Ls, inv, c0, min(kNB, n - c0), lane, lsc);
       }
       continue;
     }
@@ -475,18 +471,19 @@ __device__ void trailing_cols(typename A::T *Ls, typename A::T *inv, int n, int 
 template <class A>
 __device__ void cta_cholesky_panels(typename A::T *Ls, typename A::T *inv, int n) {
   __shared__ int next_item;
+  __shared__ typename A::T lsc[kNB * (kNB + 1) / 2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (warp == blockIdx.x % nw) warp_factor_diag<A>(Ls, inv, 0, min(kNB, n), lane);
+  if (warp == blockIdx.x % nw) warp_factor_diag<A>(Ls, inv, 0, min(kNB, n), lane, lsc);
   __syncthreads();
   for (int kb = 0; kb < n; kb += kNB) {
     const int nb = min(kNB, n - kb), j1 = kb + nb;
     const int rot = (kb / kNB + blockIdx.x) % nw;
     if (threadIdx.x == 0) next_item = 0;
     const int t = (threadIdx.x + 32 * rot) % blockDim.x;
-    for (int i = j1 + t; i < n; i += blockDim.x) panel_row<A>(Ls, inv, kb, nb, -1, i);
+    for (int i = j1 + t; i < n; i += blockDim.x) panel_row<A>(Ls, inv, lsc, kb, nb, i);
     __syncthreads();
     if (j1 < n) {
-      trailing_cols<A>(Ls, inv, n, kb, j1, &next_item, true);
+      trailing_cols<A>(Ls, inv, lsc, n, kb, j1, &next_item, true);
       __syncthreads();
     }
   }

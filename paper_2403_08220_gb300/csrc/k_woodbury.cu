@@ -359,6 +359,19 @@ __global__ void __launch_bounds__(NT, kWbMinBlocks) k_wb_geometry(ReducedArgs a,
   const double inv_nv = a.inv_nv, inv_sigma = a.inv_sigma;
   // log u, off the accept test's critical path (read after several barriers)
   if (mode == 1 && threadIdx.x == blockDim.x - 1) *log_u_s = draw_log_u(a, c);
+  // kPre: this chain's Gram matrix (d_y x ldg FP32) streams into the top of
+  // the factor's region by 16-byte asynchronous copies while the state loads
+  // and the misfit below proceed
+  float *gstage = nullptr;
+  if constexpr (kPre) {
+    const int gbytes = dy * a.ldg * 4;
+    gstage = reinterpret_cast<float *>(reinterpret_cast<char *>(sm + lay.Ms) +
+                                       (lay.inv * sizeof(double) - gbytes));
+    const char *src = reinterpret_cast<const char *>(a.G + (size_t)c * dy * a.ldg);
+    for (int o = threadIdx.x * 16; o < gbytes; o += blockDim.x * 16)
+      cp_async16(reinterpret_cast<char *>(gstage) + o, src + o, 16);
+    cp_async_commit();
+  }
 
   for (int k = threadIdx.x; k < r; k += blockDim.x) {
     vb[k] = a.b[(size_t)c * r + k];
@@ -379,7 +392,7 @@ __global__ void __launch_bounds__(NT, kWbMinBlocks) k_wb_geometry(ReducedArgs a,
     float *stage = wb_stage_fits(dy) ? reinterpret_cast<float *>(sm + lay.Ms)
                                      : reinterpret_cast<float *>(sm + lay.tail);
     if (kPre || a.G) {  // Gram matrix formed on the tensor cores: K b, K a only, then M from G
-      if constexpr (kPre) {  // ... and K b, K a too (the Jacobian GEMM's epilogue)
+      if (kPre || a.Kb_pre) {  // ... and K b, K a too (the Jacobian GEMM's epilogue)
         for (int i = threadIdx.x; i < dy; i += blockDim.x) {
           Kb[i] = a.Kb_pre[(size_t)c * dy + i];
           if (mode == 1) Ka[i] = a.Ka_pre[(size_t)c * dy + i];
@@ -395,13 +408,45 @@ __global__ void __launch_bounds__(NT, kWbMinBlocks) k_wb_geometry(ReducedArgs a,
                                reinterpret_cast<const float2 *>(be),
                                reinterpret_cast<const float2 *>(ae), mode == 1, Kb, Ka);
       }
-      const float *Gc = a.G + (size_t)c * dy * a.ldg;
       const float nh = __double2float_rn(inv_nv), nl = __double2float_rn(inv_nv - (double)nh);
-      // the packed lower triangle in order, eight independent loads in
-      // flight per thread
       constexpr int kLoads = 8;
       const int ntri = tri(dy);
-      for (int e0 = threadIdx.x; e0 < ntri; e0 += kLoads * blockDim.x) {
+      if constexpr (kPre) {
+        // M in place from the staged G, bottom-up in chunks of kLoads
+        // entries per thread: a chunk's entries are all read before any is
+        // written, and its writes end below the staged rows of the chunks
+        // after it (wb_pre_stage_fits)
+        cp_async_wait<0>();
+        __syncthreads();
+        // the same number of passes in every thread (barriers inside)
+        for (int e00 = 0; e00 < ntri; e00 += kLoads * blockDim.x) {
+          const int e0 = e00 + threadIdx.x;
+          float x[kLoads];
+          int dg = 0;
+#pragma unroll
+          for (int q = 0; q < kLoads; ++q) {
+            const int e = e0 + q * blockDim.x;
+            x[q] = 0.0f;
+            if (e < ntri) {
+              int i, j;
+              tri_pos(e, i, j);
+              x[q] = gstage[(size_t)i * a.ldg + j];
+              dg |= (i == j) << q;
+            }
+          }
+          __syncthreads();
+#pragma unroll
+          for (int q = 0; q < kLoads; ++q) {
+            const int e = e0 + q * blockDim.x;
+            if (e < ntri) reinterpret_cast<float2 *>(Ms)[e] = gram_entry(x[q], nh, nl, (dg >> q) & 1);
+          }
+          __syncthreads();
+        }
+      }
+      // otherwise from global memory: the packed lower triangle in order,
+      // kLoads independent loads in flight per thread
+      const float *Gc = a.G + (size_t)c * dy * a.ldg;
+      for (int e0 = threadIdx.x; e0 < (kPre ? 0 : ntri); e0 += kLoads * blockDim.x) {
         float x[kLoads];
         int ii[kLoads], jj[kLoads];
 #pragma unroll
@@ -703,10 +748,30 @@ cudaError_t launch_wb_geometry_k(const ReducedArgs &a, int mode, cudaStream_t st
   return cudaGetLastError();
 }
 
+// The in-place conversion of the staged Gram matrix (kPre) is safe when, at
+// every chunk boundary E (entries of 8 per thread of kWbPreThreads), the
+// double-float writes below it (bytes [0, 8E)) end at or below the staged
+// FP32 entry E, the first one not yet read.
+bool wb_pre_stage_fits(int dy, int ldg) {
+  const size_t region = WbLayout(1, dy).inv * sizeof(double);
+  const size_t gbytes = (size_t)dy * ldg * 4;
+  if (gbytes > region || gbytes % 16) return false;
+  const size_t S = region - gbytes;
+  const long ntri = (long)dy * (dy + 1) / 2, step = 8L * kWbPreThreads;
+  for (long E = step; E < ntri; E += step) {
+    long i = 0;
+    while ((i + 1) * (i + 2) / 2 <= E) ++i;
+    const long j = E - i * (i + 1) / 2;
+    if ((size_t)(8 * E) > S + 4 * (size_t)(ldg * i + j)) return false;
+  }
+  return true;
+}
+
 template <typename TJ>
 cudaError_t launch_wb_geometry_t(const ReducedArgs &a, int mode, cudaStream_t st) {
   if constexpr (sizeof(TJ) == 4)
-    if (a.G && a.Kb_pre) return launch_wb_geometry_k<TJ, true, kWbPreThreads>(a, mode, st);
+    if (a.G && a.Kb_pre && wb_pre_stage_fits(a.d_y, a.ldg))
+      return launch_wb_geometry_k<TJ, true, kWbPreThreads>(a, mode, st);
   return launch_wb_geometry_k<TJ, false, kWbThreads>(a, mode, st);
 }
 
