@@ -216,9 +216,11 @@ __device__ __forceinline__ typename A::T warp_sum_elt(typename A::T v) {
 }
 
 // x <- L^-1 x over the leading n rows of a packed lower factor (x in shared
-// memory): 32-row diagonal blocks are solved by warp 0 with shuffles (every
-// lane computes, selects keep its own), the rows below each block are
-// updated by the whole CTA.
+// memory): 32-row diagonal blocks are solved by warp 0 with shuffles, the
+// rows below each block are updated by the whole CTA.  In a block, lane i
+// carries its running value scaled by 1 / L_ii, so that step k of the
+// dependent chain is one broadcast and one multiply-subtract with
+// L_ik / L_ii (formed off the chain): y_k is lane k's value as it stands.
 template <class A>
 __device__ void cta_lower_solve_t(const typename A::T *Ls, const typename A::T *inv, int n,
                                   typename A::T *x) {
@@ -227,15 +229,16 @@ __device__ void cta_lower_solve_t(const typename A::T *Ls, const typename A::T *
   for (int jb = 0; jb < n; jb += 32) {
     const int nb = min(32, n - jb);
     if (warp == 0) {
-      E xl = lane < nb ? x[jb + lane] : E{};
       const int row = jb + min(lane, nb - 1);
+      const E il = inv[row];
+      E xl = lane < nb ? A::mul(x[jb + lane], il) : E{};
       for (int k = 0; k < nb; ++k) {
-        const E yk = A::mul(shfl_elt(xl, k), inv[jb + k]);
-        const E l = Ls[tri(row) + jb + min(k, row - jb)];
+        const E yk = shfl_elt(xl, k);
+        const E l = A::mul(Ls[tri(row) + jb + min(k, row - jb)], il);
         typename A::Acc acc = A::begin(xl);
         A::sub(acc, l, yk);
         const E u = A::end(acc);
-        xl = lane == k ? yk : ((lane > k && lane < nb) ? u : xl);
+        xl = (lane > k && lane < nb) ? u : xl;
       }
       if (lane < nb) x[jb + lane] = xl;
     }
@@ -250,7 +253,8 @@ __device__ void cta_lower_solve_t(const typename A::T *Ls, const typename A::T *
   }
 }
 
-// x <- L^-T x (back substitution on the upper factor L^T), same scheme.
+// x <- L^-T x (back substitution on the upper factor L^T), same scheme
+// (lane i scaled by 1 / L_ii, coefficients L_ki / L_ii).
 template <class A>
 __device__ void cta_upper_solve_t(const typename A::T *Ls, const typename A::T *inv, int n,
                                   typename A::T *x) {
@@ -259,15 +263,16 @@ __device__ void cta_upper_solve_t(const typename A::T *Ls, const typename A::T *
   for (int jb = ((n - 1) / 32) * 32; jb >= 0; jb -= 32) {
     const int nb = min(32, n - jb);
     if (warp == 0) {
-      E xl = lane < nb ? x[jb + lane] : E{};
       const int col = jb + min(lane, nb - 1);
+      const E il = inv[col];
+      E xl = lane < nb ? A::mul(x[jb + lane], il) : E{};
       for (int k = nb - 1; k >= 0; --k) {
-        const E yk = A::mul(shfl_elt(xl, k), inv[jb + k]);
-        const E l = Ls[tri(jb + k) + min(col, jb + k)];
+        const E yk = shfl_elt(xl, k);
+        const E l = A::mul(Ls[tri(jb + k) + min(col, jb + k)], il);
         typename A::Acc acc = A::begin(xl);
         A::sub(acc, l, yk);
         const E u = A::end(acc);
-        xl = lane == k ? yk : (lane < k ? u : xl);
+        xl = lane < k ? u : xl;
       }
       if (lane < nb) x[jb + lane] = xl;
     }

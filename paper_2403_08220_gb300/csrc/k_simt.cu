@@ -152,12 +152,16 @@ cudaError_t run_gemm(int M, int N, int K, const T *A, int lda, const T *B, int l
 // (zero-filled).  Each product is computed in 4 x 4 register tiles: per step
 // of the reduction a tile reads one float4 (or double4-as-two-loads) row
 // segment of the right operand and four broadcast values of the left one.
+// FP32 draws with at most kPriorWide tiles use a CTA of kPriorWide threads
+// (four CTAs per SM), so that each product takes a single round; otherwise
+// kPriorThreads threads loop over the tiles.
 constexpr int kPriorThreads = 256;
+constexpr int kPriorWide = 320;
 
 __host__ __device__ inline int prior_ld(int n) { return (n + 3) / 4 * 4; }
 
-template <typename T>
-__global__ void __launch_bounds__(kPriorThreads)
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, NT == kPriorWide ? 4 : 1)
     k_prior_draw(int n, const T *__restrict__ sqrtlam, const T *__restrict__ S, uint64_t seed,
                  uint64_t id_base, uint32_t stream, uint32_t step, T *out, int ldo,
                  __nv_bfloat16 *ms, int ldms, size_t ms_plane, int ms_slices,
@@ -201,19 +205,20 @@ __global__ void __launch_bounds__(kPriorThreads)
       const int m = 4 * blk + q;
       if (m < N) {
         const int j = quot(m, inv_n);
-        X[j * ld + (m - j * n)] = sqrtlam[m] * z[q];
+        X[(m - j * n) * ld + j] = sqrtlam[m] * z[q];  // stored transposed
       }
     }
   }
   __syncthreads();
-  // Y[ky][i] = sum_kx X[ky][kx] S[kx][i]
+  // Y[ky][i] = sum_kx X[ky][kx] S[kx][i], with X held transposed (X[kx][ky]
+  // at kx * ld + ky) so that both operands are read as row segments
   for (int tt = threadIdx.x; tt < nt * nt; tt += blockDim.x) {
     const int r0 = 4 * (tt / nt), c0 = 4 * (tt % nt);
     T acc[4][4] = {};
     for (int k = 0; k < n; ++k) {
       T a[4], b[4];
 #pragma unroll
-      for (int p = 0; p < 4; ++p) a[p] = X[(r0 + p) * ld + k];
+      for (int p = 0; p < 4; ++p) a[p] = X[k * ld + r0 + p];
 #pragma unroll
       for (int q = 0; q < 4; ++q) b[q] = Ss[k * ld + c0 + q];
 #pragma unroll
@@ -417,13 +422,18 @@ cudaError_t launch_prior_draw(int C, int n, const T *sqrtlam, const T *S, uint64
   if (C <= 0) return cudaSuccess;
   if (ms && (sizeof(T) != 4 || ms_slices < 1 || ldms < n * n)) return cudaErrorInvalidValue;
   const size_t smem = prior_draw_smem_bytes(n, (int)sizeof(T));
-  cudaError_t e = cudaFuncSetAttribute(k_prior_draw<T>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_prior_draw<T><<<C, kPriorThreads, smem, st>>>(n, sqrtlam, S, seed, id_base, stream, step, out,
-                                                   ldo, ms, ldms, ms_plane, ms_slices, ext_z,
-                                                   only);
-  return cudaGetLastError();
+  const int nt = prior_ld(n) / 4;
+  auto go = [&](auto kernel, int threads) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    kernel<<<C, threads, smem, st>>>(n, sqrtlam, S, seed, id_base, stream, step, out, ldo, ms,
+                                     ldms, ms_plane, ms_slices, ext_z, only);
+    return cudaGetLastError();
+  };
+  if constexpr (sizeof(T) == 4)
+    if (nt * nt <= kPriorWide) return go(k_prior_draw<T, kPriorWide>, kPriorWide);
+  return go(k_prior_draw<T, kPriorThreads>, kPriorThreads);
 }
 
 template <typename T>

@@ -553,8 +553,8 @@ __global__ void __launch_bounds__(NT, kWbMinBlocks) k_wb_geometry(ReducedArgs a,
 }
 
 // One CTA per chain at the state x = m_r (see the file comment).
-template <typename TJ>
-__global__ void __launch_bounds__(kWbThreads, kWbMinBlocks) k_wb_propose(ReducedArgs a) {
+template <typename TJ, int NT>
+__global__ void __launch_bounds__(NT, kWbMinBlocks) k_wb_propose(ReducedArgs a) {
   using A = std::conditional_t<sizeof(TJ) == 4, DF, F64>;
   using E = typename A::T;
   extern __shared__ __align__(16) double sm[];
@@ -778,12 +778,14 @@ cudaError_t launch_wb_geometry_t(const ReducedArgs &a, int mode, cudaStream_t st
 template <typename TJ>
 cudaError_t launch_wb_propose_t(const ReducedArgs &a, cudaStream_t st) {
   const size_t smem = WbLayout(a.r, a.d_y).tail * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(k_wb_propose<TJ>,
+  // the double-float path at 256 threads (64 registers, 32 warps per SM)
+  constexpr int NT = sizeof(TJ) == 4 ? kWbPreThreads : kWbThreads;
+  cudaError_t e = cudaFuncSetAttribute(k_wb_propose<TJ, NT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   ReducedArgs b = a;
   b.derive();
-  k_wb_propose<TJ><<<a.C, kWbThreads, smem, st>>>(b);
+  k_wb_propose<TJ, NT><<<a.C, NT, smem, st>>>(b);
   return cudaGetLastError();
 }
 
