@@ -179,7 +179,8 @@ __host__ __device__ size_t wb_stage_bytes(int r, int dy) {
 
 // M = I + J J^T / noise_var (double-float entries, FP32 register tiles) and,
 // from the same pass over J, Kb = (J b) / sigma and Ka = (J a) / sigma
-// (double-float dot products, thread per row).  J (dy x r, row-major FP32)
+// (double-float dot products, a thread per row, or two per row taking
+// alternate columns when there are threads for it).  J (dy x r, row-major FP32)
 // streams through a ring of kDepth shared buffers in chunks of kWbKc columns
 // by asynchronous copies, kDepth - 1 chunks in flight while one is used;
 // rows are kept in natural order (padded to kWbLd floats) and read as float4
@@ -190,6 +191,7 @@ __device__ void wb_gram_rows(const float *J, int dy, int r, double inv_nv, doubl
                              float2 *Ms, float *stage, const float2 *be, const float2 *ae,
                              bool two, double *Kb, double *Ka) {
   const int tid = threadIdx.x, T = blockDim.x;
+  const bool split = 2 * dy <= T;  // two threads per row of the row products
   const int nt = (dy + kHT - 1) / kHT, dyp = nt * kHT;
   const int ntiles = nt * (nt + 1) / 2;
   const int nch = (r + kWbKc - 1) / kWbKc;
@@ -276,27 +278,50 @@ __device__ void wb_gram_rows(const float *J, int dy, int r, double inv_nv, doubl
           }
       }
     }
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int j = tid + h * T;
+    if (split) {  // row tid >> 1, columns of parity tid & 1 of the chunk
+      const int j = tid >> 1;
       if (j < dy) {
         const float *row = x + (size_t)j * kWbLd;
         const int kn = min(kWbKc, r - k0);
-        for (int k = 0; k < kn; ++k) {
+        for (int k = tid & 1; k < kn; k += 2) {
           const float2 jk = A::from_j(row[k]);
-          A::sub(kb[h], jk, A::neg(be[k0 + k]));
-          if (two) A::sub(ka[h], jk, A::neg(ae[k0 + k]));
+          A::sub(kb[0], jk, A::neg(be[k0 + k]));
+          if (two) A::sub(ka[0], jk, A::neg(ae[k0 + k]));
+        }
+      }
+    } else {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int j = tid + h * T;
+        if (j < dy) {
+          const float *row = x + (size_t)j * kWbLd;
+          const int kn = min(kWbKc, r - k0);
+          for (int k = 0; k < kn; ++k) {
+            const float2 jk = A::from_j(row[k]);
+            A::sub(kb[h], jk, A::neg(be[k0 + k]));
+            if (two) A::sub(ka[h], jk, A::neg(ae[k0 + k]));
+          }
         }
       }
     }
     __syncthreads();
   }
+  if (split) {  // the two halves of each row meet in adjacent lanes
+    const float2 b0 = A::end(kb[0]), b1 = shfl_xor_elt(b0, 1);
+    const float2 a0 = A::end(ka[0]), a1 = shfl_xor_elt(a0, 1);
+    const int j = tid >> 1;
+    if (j < dy && (tid & 1) == 0) {
+      Kb[j] = A::to(A::add(b0, b1)) * inv_sigma;
+      if (two) Ka[j] = A::to(A::add(a0, a1)) * inv_sigma;
+    }
+  } else {
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int j = tid + h * T;
-    if (j < dy) {
-      Kb[j] = A::to(A::end(kb[h])) * inv_sigma;
-      if (two) Ka[j] = A::to(A::end(ka[h])) * inv_sigma;
+    for (int h = 0; h < 2; ++h) {
+      const int j = tid + h * T;
+      if (j < dy) {
+        Kb[j] = A::to(A::end(kb[h])) * inv_sigma;
+        if (two) Ka[j] = A::to(A::end(ka[h])) * inv_sigma;
+      }
     }
   }
   const float nh = __double2float_rn(inv_nv), nl = __double2float_rn(inv_nv - (double)nh);
@@ -571,8 +596,8 @@ __global__ void __launch_bounds__(NT, kWbMinBlocks) k_wb_propose(ReducedArgs a) 
   E *zE = reinterpret_cast<E *>(sm + lay.zE), *vE = reinterpret_cast<E *>(sm + lay.vE);
   double *red = sm + lay.red;
   const TJ *J = reinterpret_cast<const TJ *>(a.Js) + (size_t)c * dy * r;
-  const double inv_sigma = sqrt(1.0 / a.noise_var);
-  const double s = a.s, cs = sqrt(1.0 - s * s);
+  const double inv_sigma = a.inv_sigma;
+  const double s = a.s, cs = a.cs;
 
   for (int i = threadIdx.x; i < dy; i += blockDim.x) {
     inv[i] = G[sl.inv + i];
@@ -670,7 +695,7 @@ __global__ void __launch_bounds__(NT, kWbMinBlocks) k_wb_propose(ReducedArgs a) 
     if (a.b_bf16) split_bf16_store(bk, a.b_bf16 + (size_t)c * a.b_ld + k, a.b_plane, a.b_slices);
   }
   double t2 = 0.0, t3 = 0.0, unused = 0.0;
-  const double inv_cs = 1.0 / cs;
+  const double inv_cs = a.inv_cs;
   for (int i = threadIdx.x; i < dy; i += blockDim.x) {
     const double km = Kxi[i] + (yv[i] - A::to(zE[i])) * inv_cs;  // K mhat
     t2 += km * u[i];
@@ -678,7 +703,7 @@ __global__ void __launch_bounds__(NT, kWbMinBlocks) k_wb_propose(ReducedArgs a) 
   }
   block_sum3(t2, t3, unused, red);
   if (threadIdx.x == 0)
-    a.lq_fwd[c] = -a.dt / 8.0 * Lg[sl.t1] + sqrt(a.dt) / 2.0 * t2 + a.hld[c] - 0.5 * t3;
+    a.lq_fwd[c] = -a.dt / 8.0 * Lg[sl.t1] + a.sqrt_dt / 2.0 * t2 + a.hld[c] - 0.5 * t3;
 }
 
 // K b and K a from the FP32 Jacobian: eight lanes per row (c, i), four rows
