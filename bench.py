@@ -443,6 +443,10 @@ def run_hetero(args, device=0):
     ctx = dino.dino_init(device, 0, stream.cuda_stream, 0)
     fp32_peak = dino.dino_measure_fp32_peak(ctx)
     ws = heterogeneous_workloads()
+    if args.hetero_r:  # one posterior of the eight (a small case for a profile)
+        ws = [w for w in ws if w.r == args.hetero_r]
+        if not ws:
+            raise SystemExit(f"no heterogeneous posterior with r = {args.hetero_r}")
     pools, infos = [], []
     for w in ws:
         sid = load_surrogate(dino, ctx, w)
@@ -743,6 +747,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-hetero", action="store_true",
                     help="skip the eight-posterior heterogeneous batch")
+    ap.add_argument("--hetero-r", type=int, default=0,
+                    help="step only the heterogeneous posterior with this r (profiling)")
     ap.add_argument("--no-da", action="store_true", help="skip the delayed-acceptance line")
     ap.add_argument("--no-paper", action="store_true", help="skip the paper-shaped network line")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving load test")
