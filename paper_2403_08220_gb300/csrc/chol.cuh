@@ -22,6 +22,35 @@ constexpr int kHMaxTiles = 3;  // tiles per thread: ceil(52*53/2 / 512) for n <=
 constexpr int kRed = 104;      // reduction scratch (doubles): block_sum3 uses [0, 99)
 
 __device__ __forceinline__ int tri(int i) { return i * (i + 1) / 2; }
+
+// Asynchronous copies global -> shared (cp.async, 16 or 4 bytes; bytes
+// beyond src_bytes are zero-filled), their commit groups and waits on the
+// thread's own groups.
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// 16-byte asynchronous copy global -> shared; bytes beyond `src_bytes` (0..16)
+// are zero-filled.  Both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src),
+               "r"(src_bytes)
+               : "memory");
+}
+// 4-byte variant (src_bytes 0 or 4).
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_addr(dst)), "l"(src),
+               "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Sum over the CTA; `red` holds >= 33 doubles.  Every thread gets the sum.
 __device__ double block_sum(double v, double *red) {
 #pragma unroll
@@ -584,6 +613,7 @@ __device__ void form_gram_f32(const float *X, int m, int n, int ldx, double inv_
     return;
   }
   const float nh = __double2float_rn(inv_nv), nl = __double2float_rn(inv_nv - (double)nh);
+  const bool vec16 = !kRedContig && (ldx & 3) == 0 && ((uintptr_t)X & 15) == 0;
   for (int t0 = 0; t0 < ntiles; t0 += kHMaxTiles * blockDim.x) {
     int ti[kHMaxTiles], tj[kHMaxTiles];
     float acc[kHMaxTiles][kHT][kHT];
@@ -611,6 +641,16 @@ __device__ void form_gram_f32(const float *X, int m, int n, int ldx, double inv_
           const int j = e / nr, k = e % nr;
           Jc[k * rp + j] = j < r ? X[(size_t)j * ldx + i0 + k] : 0.0f;
         }
+      } else if (vec16) {  // 16-byte rows: asynchronous 16-byte copies, all in flight at once
+        const int q4 = rp / 4;
+        for (int e = threadIdx.x; e < nr * q4; e += blockDim.x) {
+          const int k = e / q4, j = 4 * (e - k * q4);
+          const int left = r - j;
+          const int bytes = left >= 4 ? 16 : (left > 0 ? 4 * left : 0);
+          cp_async16(Jc + k * rp + j, X + (size_t)(i0 + k) * ldx + (left > 0 ? j : 0), bytes);
+        }
+        cp_async_commit();
+        cp_async_wait<0>();
       } else {
 #pragma unroll 8
         for (int e = threadIdx.x; e < nr * rp; e += blockDim.x) {

@@ -112,31 +112,6 @@ __device__ void rows_times(const TJ *J, int dy, int r, double inv_sigma, const t
 constexpr int kWbKc = 16;          // J columns per staged chunk (tensor-core path)
 constexpr int kWbLd = kWbKc + 4;   // padded row length (floats) of a staged chunk
 
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// 16-byte asynchronous copy global -> shared; bytes beyond `src_bytes` (0..16)
-// are zero-filled.  Both addresses 16-byte aligned.
-__device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src),
-               "r"(src_bytes)
-               : "memory");
-}
-// 4-byte variant (src_bytes 0 or 4).
-__device__ __forceinline__ void cp_async4(void *dst, const void *src, int src_bytes) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_addr(dst)), "l"(src),
-               "r"(src_bytes)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
 // Entry of M = I + G / noise_var in double-float from the FP32 Gram value x:
 // x (nh + nl) with (nh, nl) = 1 / noise_var as a double-float pair, and 1
 // added on the diagonal.
