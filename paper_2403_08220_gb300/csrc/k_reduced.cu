@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(32 * kPropWarps) k_propose_warp(ReducedArgs a)
 // slot, which becomes current) and its state vectors.  The complement
 // coefficient b - s a is written for every chain.
 template <typename TJ, bool G, int NT>
-__global__ void __launch_bounds__(NT) k_geometry(ReducedArgs a, int mode) {
+__global__ void __launch_bounds__(NT, NT <= 128 ? 4 : (NT <= 256 ? 2 : 1)) k_geometry(ReducedArgs a, int mode) {
   // FP32 Jacobian (tensor-core path): double-float Cholesky; FP64 Jacobian: FP64
   using A = std::conditional_t<sizeof(TJ) == 4, DF, F64>;
   using E = typename A::T;
@@ -461,7 +461,9 @@ static cudaError_t launch_geometry_nt(const ReducedArgs &a, int mode, size_t sme
 }
 
 // CTA size by r: a small factor keeps few threads busy, and smaller CTAs let
-// more chains share an SM (the kernel's loops stride over blockDim).
+// more chains share an SM (the kernel's loops stride over blockDim); the
+// 128- and 256-thread kernels are held to 128 registers so that four and two
+// of them fit an SM.
 template <typename TJ, bool G>
 static cudaError_t launch_geometry_t(const ReducedArgs &a, int mode, size_t smem,
                                      cudaStream_t st) {
