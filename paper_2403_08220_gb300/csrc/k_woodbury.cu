@@ -644,7 +644,14 @@ __global__ void __launch_bounds__(NT, kWbMinBlocks) k_wb_propose(ReducedArgs a) 
   } else {
     rows_times<A, TJ>(J, dy, r, inv_sigma, x1E, x1E, false, Kxi, Kxi);  // K xi1
   }
-  for (size_t e = threadIdx.x; e < tri_size(dy); e += blockDim.x) Ms[e] = G[sl.R + e];
+  {  // the factor by 16-byte asynchronous copies (slots start on 16 bytes), all in flight
+    const size_t ne = tri_size(dy), npair = ne / 2;
+    for (size_t q = threadIdx.x; q < npair; q += blockDim.x)
+      cp_async16(Ms + 2 * q, G + sl.R + 2 * q, 16);
+    cp_async_commit();
+    if (threadIdx.x == 0 && (ne & 1)) Ms[ne - 1] = G[sl.R + ne - 1];
+    cp_async_wait<0>();
+  }
   for (int i = threadIdx.x; i < dy; i += blockDim.x) {
     yv[i] = (1.0 - s) * u[i] + cs * (xi2[i] - Kxi[i]);
     zE[i] = A::from(yv[i]);
