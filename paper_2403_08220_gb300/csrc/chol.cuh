@@ -176,6 +176,16 @@ struct DF {
     a.s = s;
     a.c = __fadd_rn(a.c, __fsub_rn(q, e));
   }
+  // the same for an FP32 x (a pair whose low part is 0: that term vanishes)
+  __device__ static void sub_f(Acc &a, float x, T y) {
+    const float p = __fmul_rn(x, y.x);
+    float e = __fmaf_rn(x, y.x, -p);
+    e = __fmaf_rn(x, y.y, e);
+    float s, q;
+    two_sum(a.s, -p, s, q);
+    a.s = s;
+    a.c = __fadd_rn(a.c, __fsub_rn(q, e));
+  }
   __device__ static T end(Acc a) {
     float h, l;
     two_sum(a.s, a.c, h, l);

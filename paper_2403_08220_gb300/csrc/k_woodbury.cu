@@ -689,12 +689,15 @@ __global__ void __launch_bounds__(NT, kWbMinBlocks) k_wb_propose(ReducedArgs a) 
 }
 
 // K b and K a from the FP32 Jacobian: eight lanes per row (c, i), four rows
-// per warp; lane q of a row takes columns q, q + 8, ... (each load
-// instruction covers four rows' whole 32-byte sectors), and the eight
-// double-float partial sums are combined by a three-level butterfly of
-// double-float additions.
+// per warp, and the eight double-float partial sums of a row combined by a
+// three-level butterfly of double-float additions.  kVec (r a multiple of
+// 4, so that rows of J and of b, a start on 16 bytes): lane q takes the
+// column quads q, q + 8, ... (one 16-byte load of J and two of each vector
+// per quad; a warp's load of J covers four rows' 128-byte segments); else
+// lane q takes the columns q, q + 8, ...
 constexpr int kRowLanes = 8;
 
+template <bool kVec>
 __global__ void k_rowprod(int rows, int r, int dy, const float *__restrict__ J,
                           const float2 *__restrict__ b, const float2 *__restrict__ a,
                           double kscale, double *__restrict__ Kb, double *__restrict__ Ka) {
@@ -710,11 +713,32 @@ __global__ void k_rowprod(int rows, int r, int dy, const float *__restrict__ J,
     const float2 *br = b + (size_t)c * r;
     const float2 *ar = a ? a + (size_t)c * r : nullptr;
     DF::Acc kb = DF::begin(float2{}), ka = DF::begin(float2{});
+    if constexpr (kVec) {
+      const int nq = r / 4;
+      for (int k = q; k < nq; k += kRowLanes) {
+        const float4 jq = reinterpret_cast<const float4 *>(Jr)[k];
+        const float4 b0 = reinterpret_cast<const float4 *>(br)[2 * k];
+        const float4 b1 = reinterpret_cast<const float4 *>(br)[2 * k + 1];
+        DF::sub_f(kb, jq.x, float2{-b0.x, -b0.y});
+        DF::sub_f(kb, jq.y, float2{-b0.z, -b0.w});
+        DF::sub_f(kb, jq.z, float2{-b1.x, -b1.y});
+        DF::sub_f(kb, jq.w, float2{-b1.z, -b1.w});
+        if (ar) {
+          const float4 a0 = reinterpret_cast<const float4 *>(ar)[2 * k];
+          const float4 a1 = reinterpret_cast<const float4 *>(ar)[2 * k + 1];
+          DF::sub_f(ka, jq.x, float2{-a0.x, -a0.y});
+          DF::sub_f(ka, jq.y, float2{-a0.z, -a0.w});
+          DF::sub_f(ka, jq.z, float2{-a1.x, -a1.y});
+          DF::sub_f(ka, jq.w, float2{-a1.z, -a1.w});
+        }
+      }
+    } else {
 #pragma unroll 5
-    for (int k = q; k < r; k += kRowLanes) {
-      const float2 jk = DF::from_j(Jr[k]);
-      DF::sub(kb, jk, DF::neg(br[k]));
-      if (ar) DF::sub(ka, jk, DF::neg(ar[k]));
+      for (int k = q; k < r; k += kRowLanes) {
+        const float jk = Jr[k];
+        DF::sub_f(kb, jk, DF::neg(br[k]));
+        if (ar) DF::sub_f(ka, jk, DF::neg(ar[k]));
+      }
     }
     float2 vb = DF::end(kb), va = DF::end(ka);
 #pragma unroll
@@ -817,7 +841,12 @@ cudaError_t launch_rowprod(int rows, int r, int d_y, const float *J, const float
   if (rows <= 0) return cudaSuccess;
   if (d_y < 1 || r < 1) return cudaErrorInvalidValue;
   const int grid = std::min((rows + 31) / 32, 152 * 16);  // 32 rows per 256-thread block
-  k_rowprod<<<grid, 256, 0, st>>>(rows, r, d_y, J, b, a, kscale, Kb, Ka);
+  const bool vec = r % 4 == 0 && ((uintptr_t)J & 15) == 0 && ((uintptr_t)b & 15) == 0 &&
+                   ((uintptr_t)a & 15) == 0;
+  if (vec)
+    k_rowprod<true><<<grid, 256, 0, st>>>(rows, r, d_y, J, b, a, kscale, Kb, Ka);
+  else
+    k_rowprod<false><<<grid, 256, 0, st>>>(rows, r, d_y, J, b, a, kscale, Kb, Ka);
   return cudaGetLastError();
 }
 

@@ -262,3 +262,37 @@ def test_host_field_read_in_place_matches_copy(dino):
     assert np.array_equal(out[0][0]["m_r"], out[1][0]["m_r"])
     for k in ("m_r", "phi", "accepts", "m"):
         assert np.array_equal(out[0][1][k], out[1][1][k]), k
+
+
+@pytest.mark.parametrize("r", [45, 264])
+def test_woodbury_bf16_under_caller_noise(dino, ctx, r):
+    """The tensor-core Woodbury path (d_y = 40 < r; K b and K a by k_rowprod
+    in double-float from the FP32 J, M from the tensor-core Gram matrices)
+    under the same caller-supplied noise as the oracle, with r below and above
+    one 256-column tile of the Jacobian product: the proposal within the mean
+    bar and log rho within 1e-3 of its scale."""
+    w = variant(CONFIGS["small_fp64"], r=r, widths=[r, 48, 48, 40], precision="bf16",
+                noise_frac=0.05)
+    sid = gpu_setup(dino, ctx, w)
+    sur, E, D = oracle_setup(w)
+    C, dt = 16, 1e-3
+    pool = dino.dino_chains_create(ctx, sid, C, dt, SEED_CHAINS)
+    och = oracle_chains(dino, ctx, sid, w, sur, E, D, C, dt)
+    assert och.noise == "perturbation"
+    rng = np.random.default_rng(11)
+    for _ in range(3):
+        nz = dict(xi=rng.standard_normal((C, w.r)), xi2=rng.standard_normal((C, w.d_y)),
+                  z=rng.standard_normal((C, w.N)), log_u=np.log(rng.uniform(size=C)))
+        dino.dino_chains_set_noise(ctx, pool, **nz)
+        st = dino.dino_chains_step(ctx, pool, 1)
+        och.step(noise=nz)
+        last = dino.dino_chains_read_last(ctx, pool, C, w.r)
+        assert st["nan_rejects"] == 0
+        assert rel_err(last["b"], och.last["b"]) <= 1e-3
+        scale = np.maximum(1.0, och.last["log_rho_scale"])
+        assert np.max(np.abs(last["log_rho"] - och.last["log_rho"]) / scale) <= 1e-3
+        # later steps start from the same state only where the decisions agree
+        if not np.array_equal(last["accepted"], och.last["accepted"]):
+            break
+    dino.dino_chains_destroy(ctx, pool)
+    dino.dino_unload_surrogate(ctx, sid)
