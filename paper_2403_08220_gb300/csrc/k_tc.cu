@@ -579,19 +579,35 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (epi == TC_EPI_STORE_F32 || epi == TC_EPI_BIAS_F32) {
           if (epi == TC_EPI_BIAS_F32)
             for (int j = 0; j < ncols; ++j) v[j] += p.bias[col0 + j];
+          // a ragged last group of 4, 8 or 12 columns (N = 200 leaves 8) in
+          // 16-byte stores as well: one per 4 FP32 values, one per 8 bf16s
           float *o = outf + (size_t)row * ldo + col0;
-          if (ncols == 16 && (ldo & 3) == 0) {
+          if ((ncols & 3) == 0 && (ldo & 3) == 0 && (reinterpret_cast<uintptr_t>(outf) & 15) == 0) {
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-              reinterpret_cast<float4 *>(o)[q] =
-                  make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+              if (4 * q < ncols)
+                reinterpret_cast<float4 *>(o)[q] =
+                    make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
           } else {
             for (int j = 0; j < ncols; ++j) o[j] = v[j];
           }
-          if (epi == TC_EPI_STORE_F32 && out_bf)
-            for (int j = 0; j < ncols; ++j)
-              store_slices(v[j], out_bf + (size_t)row * p.ldob + col0 + j, p.out_plane,
-                           p.out_slices);
+          if (epi == TC_EPI_STORE_F32 && out_bf) {
+            __nv_bfloat16 *ob = out_bf + (size_t)row * p.ldob + col0;
+            if ((ncols & 7) == 0 && (p.ldob & 7) == 0 && (p.out_plane & 7) == 0 &&
+                (reinterpret_cast<uintptr_t>(out_bf) & 15) == 0) {
+              for (int sl = 0; sl < p.out_slices; ++sl) {
+                uint32_t h[8];  // pack_bf16x2 leaves the remainders in v
+#pragma unroll
+                for (int j = 0; j < 8; ++j) h[j] = pack_bf16x2(v[2 * j], v[2 * j + 1]);
+                uint4 *os = reinterpret_cast<uint4 *>(ob + (size_t)sl * p.out_plane);
+                os[0] = make_uint4(h[0], h[1], h[2], h[3]);
+                if (ncols == 16) os[1] = make_uint4(h[4], h[5], h[6], h[7]);
+              }
+            } else {
+              for (int j = 0; j < ncols; ++j)
+                store_slices(v[j], ob + j, p.out_plane, p.out_slices);
+            }
+          }
         } else {
           float x[16];
           if (epi == TC_EPI_BIAS_ACT) {
