@@ -19,8 +19,10 @@
 //   warps 2-5  epilogue: tcgen05.ld of their 32 TMEM lanes, fused bias /
 //              activation / derivative / per-chain scaling, bf16 re-slicing,
 //              the complement's coefficient and field updates, stores of
-//              whole 128-byte row segments through swizzled staging tiles,
-//              overlapping the next tile's MMAs; then release the buffer.
+//              whole 128-byte row segments through swizzled staging tiles
+//              (bulk tensor stores, cp.async.bulk.tensor, where the epilogue
+//              stages only its output), overlapping the next tile's MMAs;
+//              then release the buffer.
 // Work items are output tiles, or (tile, K chunk) pairs when a projection of
 // a small pool splits K (FP32 partials, reduced by k_coef_finish).
 // Every mbarrier wait is bounded; on timeout the CTA raises a device error
@@ -29,6 +31,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "dino_internal.h"
 
@@ -41,6 +44,7 @@ constexpr int kThreads = 192;
 constexpr uint32_t kSpinLimit = 1u << 24;
 constexpr int kMaxStages = 4;
 constexpr int kStageTiles = 4 * 32 * 128;  // epilogue staging: 32 rows x 128 B per warp
+constexpr int kStageTilesTma = 2 * kStageTiles;  // two such tiles per warp (bulk stores)
 
 struct TcParams {
   int M, N, K, BN, nkb, npairs, stages;
@@ -66,6 +70,10 @@ struct TcParams {
   float *m;
   const float *Mf;
   int ldm;
+  // bulk tensor stores of the epilogue's 128-byte segments (tmO: FP32 output,
+  // tmS: bf16 slice planes); the staging region is stg_bytes (two tiles per
+  // epilogue warp with tma, else one)
+  int tma, stg_bytes;
   uint32_t tmem_cols;
   int *err;
 };
@@ -111,6 +119,32 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *tm,
       " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
       "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
       : "memory");
+}
+
+// Bulk tensor stores of the epilogue (shared -> global, 128-byte swizzle):
+// the issuing lane commits each store as a bulk group and, before a staging
+// tile is written again, waits until the stores that read it are done.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *tm, uint32_t src, int c0, int c1) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];"
+               ::"l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(src)
+               : "memory");
+}
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *tm, uint32_t src, int c0, int c1,
+                                             int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+          reinterpret_cast<uint64_t>(tm)),
+      "r"(c0), "r"(c1), "r"(c2), "r"(src)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read1() {
+  asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
@@ -227,6 +261,33 @@ __device__ __forceinline__ void store_rows_coalesced(uint4 *stg, const uint32_t 
   __syncwarp();
 }
 
+// The same 32 x 128-byte segment by one bulk tensor store: the lanes write
+// their rows into one of the warp's two staging tiles in the map's 128-byte
+// swizzle (chunk c of row r at c ^ (r & 7)), lane 0 stores the tile at
+// (x, y[, z]) of the map (rows past the tensor's end are not written) and
+// commits it.  Before a tile is written again, lane 0 waits until at most
+// one bulk group (the other tile's) is still reading shared memory.
+__device__ __forceinline__ void store_rows_tma(uint4 *stg2, int &buf, const uint32_t w[32],
+                                               const CUtensorMap *tm, bool three_d, int x, int y,
+                                               int z, int nrows, int lane) {
+  uint4 *stg = stg2 + buf * 256;
+  if (lane == 0) bulk_wait_read1();
+  __syncwarp();
+#pragma unroll
+  for (int c = 0; c < 8; ++c)
+    stg[lane * 8 + (c ^ (lane & 7))] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncwarp();
+  if (lane == 0 && nrows > 0) {  // a warp whose rows all lie past the end stores nothing
+    if (three_d)
+      tma_store_3d(tm, smem_u32(stg), x, y, z);
+    else
+      tma_store_2d(tm, smem_u32(stg), x, y);
+    bulk_commit();
+  }
+  buf ^= 1;
+}
+
 __device__ __forceinline__ uint32_t pack_bf16x2(float &a, float &b) {
   // bf16 of a and b (low half a), leaving the remainders a - bf16(a), b - bf16(b):
   // one paired round-to-nearest conversion; a bf16 widens to FP32 exactly by
@@ -272,6 +333,7 @@ __device__ __forceinline__ void store_slices(float x, __nv_bfloat16 *dst, size_t
 // warps drain the other buffer (acc_full / acc_empty mbarriers).
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtensorMap tmS,
               const TcParams p) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   // 1024-byte aligned stage ring, then barriers
@@ -283,9 +345,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   // B_0 .. B_{s-1}) and feeds all slice pairs; otherwise one pair per stage
   const uint32_t stage_bytes = p.grouped ? (a_bytes + b_bytes) * (uint32_t)p.nslice
                                          : a_bytes + b_bytes;
-  // after the ring: four 4 KB epilogue staging tiles, then the barriers
+  // after the ring: one or two 4 KB epilogue staging tiles per epilogue warp
+  // (1024-byte aligned, as the bulk stores' swizzle needs), then the barriers
   uint4 *stg_all = reinterpret_cast<uint4 *>(gbase + p.stages * stage_bytes);
-  uint64_t *bars = reinterpret_cast<uint64_t *>(gbase + p.stages * stage_bytes + kStageTiles);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(gbase + p.stages * stage_bytes + p.stg_bytes);
   // bars[0..S) full, [S..2S) empty, [2S, 2S+2) acc_full, [2S+2, 2S+4) acc_empty, [2S+4] drain
   const int S = p.stages;
   volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 2 * S + 5);
@@ -428,6 +491,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31
     const int quarter = warp & 3;
+    int sbuf = 0;  // staging tile of the next bulk store
     int j = 0;
     for (int t = blockIdx.x; t < nitems; t += gridDim.x, ++j) {
       const int b = j & 1;
@@ -455,7 +519,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t tacc = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * p.BN);
       const int nvalid = min(p.BN, p.N - n0);
       const int row0 = m0 + quarter * 32, nrows = min(32, p.M - row0);
-      uint4 *stg = stg_all + quarter * 256;
+      uint4 *stg = stg_all + quarter * (p.stg_bytes / 64);
       int c0 = 0;  // columns [0, c0) done by the coalesced groups below
       if (epi == TC_EPI_FIELD_T) {
         // lanes are consecutive field nodes of one chain per column: each
@@ -486,19 +550,26 @@ __global__ void __launch_bounds__(kThreads, 1)
               uint32_t w[32];
 #pragma unroll
               for (int j = 0; j < 32; ++j) w[j] = __float_as_uint(v[32 * h + j]);
-              store_rows_coalesced(
-                  stg, w, reinterpret_cast<char *>(outf + (size_t)row0 * ldo + n0 + c0 + 32 * h),
-                  (size_t)ldo * 4, nrows, lane);
+              if (p.tma)
+                store_rows_tma(stg, sbuf, w, &tmO, false, n0 + c0 + 32 * h, row0, 0, nrows,
+                               lane);
+              else
+                store_rows_coalesced(
+                    stg, w, reinterpret_cast<char *>(outf + (size_t)row0 * ldo + n0 + c0 + 32 * h),
+                    (size_t)ldo * 4, nrows, lane);
             }
             for (int sl = 0; sl < p.out_slices; ++sl) {
               uint32_t w[32];
 #pragma unroll
               for (int j = 0; j < 32; ++j) w[j] = pack_bf16x2(v[2 * j], v[2 * j + 1]);
-              store_rows_coalesced(
-                  stg, w,
-                  reinterpret_cast<char *>(out_bf + (size_t)row0 * p.ldob + n0 + c0 +
-                                           (size_t)sl * p.out_plane),
-                  (size_t)p.ldob * 2, nrows, lane);
+              if (p.tma)
+                store_rows_tma(stg, sbuf, w, &tmS, true, n0 + c0, row0, sl, nrows, lane);
+              else
+                store_rows_coalesced(
+                    stg, w,
+                    reinterpret_cast<char *>(out_bf + (size_t)row0 * p.ldob + n0 + c0 +
+                                             (size_t)sl * p.out_plane),
+                    (size_t)p.ldob * 2, nrows, lane);
             }
           }
         }
@@ -561,11 +632,14 @@ __global__ void __launch_bounds__(kThreads, 1)
               uint32_t w[32];
 #pragma unroll
               for (int j = 0; j < 32; ++j) w[j] = pack_bf16x2(v[2 * j], v[2 * j + 1]);
-              store_rows_coalesced(
-                  stg, w,
-                  reinterpret_cast<char *>(out_bf + (size_t)row0 * ldo + n0 + c0 +
-                                           (size_t)sl * p.out_plane),
-                  (size_t)ldo * 2, nrows, lane);
+              if (p.tma)
+                store_rows_tma(stg, sbuf, w, &tmS, true, n0 + c0, row0, sl, nrows, lane);
+              else
+                store_rows_coalesced(
+                    stg, w,
+                    reinterpret_cast<char *>(out_bf + (size_t)row0 * ldo + n0 + c0 +
+                                             (size_t)sl * p.out_plane),
+                    (size_t)ldo * 2, nrows, lane);
             }
           }
         }
@@ -671,6 +745,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bars[2 * S + 2 + b]))
                      : "memory");
     }
+    // the bulk stores have read their staging tiles and written global memory
+    if (p.tma && lane == 0) bulk_wait_all();
+    __syncwarp();
   }
   fence_before();
   __syncthreads();
@@ -973,6 +1050,20 @@ bool make_map(CUtensorMap *tm, const __nv_bfloat16 *ptr, int K, int rows, int ld
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 2D map over an FP32 matrix for the epilogue's bulk stores: dims (cols,
+// rows), box (32, 32): one 128-byte segment of 32 rows.
+bool make_map_f32(CUtensorMap *tm, const float *ptr, int cols, int rows, int ld) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  cuuint32_t box[2] = {32, 32};
+  cuuint32_t es[2] = {1, 1};
+  return fn(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)ptr, dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int *error_word() {
   static int *d = nullptr;
   if (!d && cudaMalloc(&d, sizeof(int)) == cudaSuccess) cudaMemset(d, 0, sizeof(int));
@@ -1048,10 +1139,6 @@ cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st) {
   if (!make_map(&tmA, a.A, a.K, a.M, a.lda, a.a_plane, a.nslice, kBlockM) ||
       !make_map(&tmB, a.B, a.K, a.N, a.ldb, a.b_plane, a.nslice, p.BN))
     return cudaErrorInvalidValue;
-  const size_t smem = 1024 + (size_t)p.stages * stage_bytes + kStageTiles + (2 * p.stages + 8) * 8;
-  cudaError_t e =
-      cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;  // persistent grid: one CTA per SM (its shared memory allows one)
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
@@ -1072,7 +1159,28 @@ cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st) {
       p.ws = a.ws;
     }
   }
-  k_tc_gemm<<<std::min(total * p.ksplit, sms), kThreads, smem, st>>>(tmA, tmB, p);
+  // bulk tensor stores for the epilogues that stage only their output's
+  // 128-byte segments (FP32 with slices, scaled or coefficient slices), when
+  // the maps encode and two staging tiles per warp fit
+  CUtensorMap tmO, tmS;
+  std::memset(&tmO, 0, sizeof(tmO));
+  std::memset(&tmS, 0, sizeof(tmS));
+  const size_t smem_base = 1024 + (size_t)p.stages * stage_bytes + (2 * p.stages + 8) * 8;
+  p.tma = 0;
+  p.stg_bytes = kStageTiles;
+  if (p.ksplit == 1 && a.out_bf && smem_base + kStageTilesTma <= 227 * 1024) {
+    if (a.epi == TC_EPI_STORE_F32 && a.outf)
+      p.tma = make_map_f32(&tmO, a.outf, a.N, a.M, a.ldo) &&
+              make_map(&tmS, a.out_bf, a.N, a.M, a.ldob, a.out_plane, a.out_slices, 32);
+    else if (a.epi == TC_EPI_SCALE_GROUP || a.epi == TC_EPI_COEF)
+      p.tma = make_map(&tmS, a.out_bf, a.N, a.M, a.ldo, a.out_plane, a.out_slices, 32);
+    if (p.tma) p.stg_bytes = kStageTilesTma;
+  }
+  const size_t smem = smem_base + p.stg_bytes;
+  cudaError_t e =
+      cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_tc_gemm<<<std::min(total * p.ksplit, sms), kThreads, smem, st>>>(tmA, tmB, tmO, tmS, p);
   cudaError_t e2 = cudaGetLastError();
   if (e2 != cudaSuccess || p.ksplit == 1) return e2;
   const size_t n = (size_t)a.M * a.N;
