@@ -621,9 +621,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 uint32_t w[32];
 #pragma unroll
                 for (int j = 0; j < 32; ++j) w[j] = __float_as_uint(act_deriv(p.act, v[32 * h + j]));
-                store_rows_coalesced(
-                    stg, w, reinterpret_cast<char *>(p.der + (size_t)row0 * p.N + n0 + c0 + 32 * h),
-                    (size_t)p.N * 4, nrows, lane);
+                if (p.tma)  // tmO maps the derivative here
+                  store_rows_tma(stg, sbuf, w, &tmO, false, n0 + c0 + 32 * h, row0, 0, nrows,
+                                 lane);
+                else
+                  store_rows_coalesced(
+                      stg, w,
+                      reinterpret_cast<char *>(p.der + (size_t)row0 * p.N + n0 + c0 + 32 * h),
+                      (size_t)p.N * 4, nrows, lane);
               }
 #pragma unroll
               for (int j = 0; j < 64; ++j) v[j] = act_fn(p.act, v[j]);
@@ -1090,7 +1095,12 @@ cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st) {
   p.M = a.M;
   p.N = a.N;
   p.K = a.K;
-  const int ntiles = (a.N + 255) / 256;
+  // the complement's three-slice products (long K, many tiles): at most 128
+  // columns, so that a stage with a k-block of every slice of A and B (at
+  // most 96 KB) fits twice and each slice is loaded once per k-block
+  const bool narrow = a.nslice == 3 && (a.epi == TC_EPI_COEF || a.epi == TC_EPI_FIELD_T);
+  const int bn_max = narrow ? 128 : 256;
+  const int ntiles = (a.N + bn_max - 1) / bn_max;
   p.BN = ((a.N + ntiles - 1) / ntiles + 15) / 16 * 16;
   p.nkb = (a.K + kBlockK - 1) / kBlockK;
   static const int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 2, 1, 0};
@@ -1174,6 +1184,9 @@ cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st) {
               make_map(&tmS, a.out_bf, a.N, a.M, a.ldob, a.out_plane, a.out_slices, 32);
     else if (a.epi == TC_EPI_SCALE_GROUP || a.epi == TC_EPI_COEF)
       p.tma = make_map(&tmS, a.out_bf, a.N, a.M, a.ldo, a.out_plane, a.out_slices, 32);
+    else if (a.epi == TC_EPI_BIAS_ACT && a.der)  // the derivative (pitch N) and the slices
+      p.tma = make_map_f32(&tmO, a.der, a.N, a.M, a.N) &&
+              make_map(&tmS, a.out_bf, a.N, a.M, a.ldo, a.out_plane, a.out_slices, 32);
     if (p.tma) p.stg_bytes = kStageTilesTma;
   }
   const size_t smem = smem_base + p.stg_bytes;
