@@ -160,6 +160,26 @@ constexpr int kPriorWide = 320;
 
 __host__ __device__ inline int prior_ld(int n) { return (n + 3) / 4 * 4; }
 
+// Four consecutive values of a padded shared-memory row (16-byte aligned: the
+// rows are multiples of 4 values and the arrays start on 16 bytes).
+template <typename T>
+__device__ __forceinline__ void load4(const T *p, T v[4]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 x = *reinterpret_cast<const float4 *>(p);
+    v[0] = x.x;
+    v[1] = x.y;
+    v[2] = x.z;
+    v[3] = x.w;
+  } else {
+    const double2 x = reinterpret_cast<const double2 *>(p)[0];
+    const double2 y = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = x.x;
+    v[1] = x.y;
+    v[2] = y.x;
+    v[3] = y.y;
+  }
+}
+
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT, NT == kPriorWide ? 4 : 1)
     k_prior_draw(int n, const T *__restrict__ sqrtlam, const T *__restrict__ S, uint64_t seed,
@@ -217,10 +237,8 @@ __global__ void __launch_bounds__(NT, NT == kPriorWide ? 4 : 1)
     T acc[4][4] = {};
     for (int k = 0; k < n; ++k) {
       T a[4], b[4];
-#pragma unroll
-      for (int p = 0; p < 4; ++p) a[p] = X[k * ld + r0 + p];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) b[q] = Ss[k * ld + c0 + q];
+      load4(X + k * ld + r0, a);
+      load4(Ss + k * ld + c0, b);
 #pragma unroll
       for (int p = 0; p < 4; ++p)
 #pragma unroll
@@ -232,17 +250,18 @@ __global__ void __launch_bounds__(NT, NT == kPriorWide ? 4 : 1)
       for (int q = 0; q < 4; ++q) Y[(r0 + p) * ld + c0 + q] = acc[p][q];
   }
   __syncthreads();
-  // M[j][i] = sum_ky S[ky][j] Y[ky][i]; node p = i + n j
-  T *o = out + (size_t)c * ldo;
+  // M[j][i] = sum_ky S[ky][j] Y[ky][i]; node p = i + n j.  The tiles land in
+  // shared memory (X's array, which the first product no longer reads: n^2
+  // nodes in order), and the CTA then writes M and its slices with
+  // consecutive threads on consecutive nodes.
+  T *Mo = X;
   for (int tt = threadIdx.x; tt < nt * nt; tt += blockDim.x) {
     const int r0 = 4 * (tt / nt), c0 = 4 * (tt % nt);
     T acc[4][4] = {};
     for (int k = 0; k < n; ++k) {
       T a[4], b[4];
-#pragma unroll
-      for (int p = 0; p < 4; ++p) a[p] = Ss[k * ld + r0 + p];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) b[q] = Y[k * ld + c0 + q];
+      load4(Ss + k * ld + r0, a);
+      load4(Y + k * ld + c0, b);
 #pragma unroll
       for (int p = 0; p < 4; ++p)
 #pragma unroll
@@ -252,21 +271,25 @@ __global__ void __launch_bounds__(NT, NT == kPriorWide ? 4 : 1)
     for (int p = 0; p < 4; ++p)
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        if (r0 + p < n && c0 + q < n) {
-          o[(r0 + p) * n + c0 + q] = acc[p][q];
-          if constexpr (sizeof(T) == 4) {
-            if (ms) {
-              __nv_bfloat16 *d = ms + (size_t)c * ldms + (r0 + p) * n + c0 + q;
-              float rem = acc[p][q];
-              for (int sl = 0; sl < ms_slices; ++sl) {
-                const __nv_bfloat16 hb = __float2bfloat16_rn(rem);
-                d[sl * ms_plane] = hb;
-                // exact widening: the bf16 bits in the upper half of an FP32 word
-                rem -= __uint_as_float((uint32_t)__bfloat16_as_ushort(hb) << 16);
-              }
-            }
-          }
+        if (r0 + p < n && c0 + q < n) Mo[(r0 + p) * n + c0 + q] = acc[p][q];
+  }
+  __syncthreads();
+  T *o = out + (size_t)c * ldo;
+  for (int e = threadIdx.x; e < N; e += blockDim.x) {
+    const T v = Mo[e];
+    o[e] = v;
+    if constexpr (sizeof(T) == 4) {
+      if (ms) {
+        __nv_bfloat16 *d = ms + (size_t)c * ldms + e;
+        float rem = v;
+        for (int sl = 0; sl < ms_slices; ++sl) {
+          const __nv_bfloat16 hb = __float2bfloat16_rn(rem);
+          d[sl * ms_plane] = hb;
+          // exact widening: the bf16 bits in the upper half of an FP32 word
+          rem -= __uint_as_float((uint32_t)__bfloat16_as_ushort(hb) << 16);
         }
+      }
+    }
   }
 }
 
