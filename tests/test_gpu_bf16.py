@@ -177,6 +177,19 @@ def test_bf16_small_config_mixing(dino, ctx):
     assert 0.05 < np.mean(out["acc"]) < 0.995
 
 
+def test_bf16_large_pool_sampled(dino, ctx):
+    """40000 chains of the small workload from the truth (3 steps at dt = 0.5,
+    most proposals accepted), 48 chains spread over the pool checked: the
+    complement's coefficient product then has enough 128-row tiles (313) to
+    run without splitting K, so its own epilogue writes the coefficients'
+    bf16 slices."""
+    C = 40000
+    sample = np.linspace(0, C - 1, 48).astype(int)
+    out = _precision_run(dino, ctx, SMALL, C, 0.5, 3, sample=sample, start="truth")
+    _check_bars(out)
+    assert np.mean(out["acc"]) > 0.5
+
+
 def test_bf16_full_size_sampled(dino, ctx):
     """16384 chains at r = 200 (the BF16 workload's launch shape), 10 chains
     checked: dt = 0.5 from prior draws (the configured step) and dt = 2e-5
