@@ -353,7 +353,7 @@ int dino_dis_from_surrogate(dino_ctx *ctx, int surrogate_id, int n_samples, uint
 /* ---- chain diagnostics (Sec. 6.2) ---------------------------------------- */
 
 /* A device trajectory of n_chains chains x n_dof degrees of freedom (at most
- * max_samples samples), and the diagnostics the paper uses to judge a pool
+ * max_samples samples), and the diagnostics the paper uses to assess a pool
  * of chains, computed on the device from it:
  *   ESS% per degree of freedom (eq:ess): 1 / (1 + 2 sum_{t=1}^{2n'+1} MACT(t)),
  *     MACT(t) = 1 - (w - mean_k AC(t, k)) / v with w, v the 1D covariance
