@@ -129,6 +129,35 @@ __device__ __forceinline__ float2 gram_entry(float x, float nh, float nl, bool d
   return make_float2(h, l);
 }
 
+// y = K x (= J x / sigma) from the chain's FP32 J with 16-byte rows (r a
+// multiple of 4), x as float pairs in shared memory: eight lanes per row,
+// four rows per warp and blockDim / 8 rows per pass, lane q taking the column
+// quads q, q + 8, ... straight from global memory; the eight double-float
+// partial sums of a row meet in a three-level butterfly.  Every lane runs the
+// same passes (rows past the end compute row d_y - 1 and store nothing).
+__device__ void rows_times_quads(const float *J, int dy, int r, double inv_sigma,
+                                 const float2 *x, double *y) {
+  const int q = threadIdx.x & 7, groups = blockDim.x >> 3, nq = r / 4;
+  const int passes = (dy + groups - 1) / groups;
+  for (int ps = 0; ps < passes; ++ps) {
+    const int row = ps * groups + (threadIdx.x >> 3), rr = min(row, dy - 1);
+    const float4 *J4 = reinterpret_cast<const float4 *>(J + (size_t)rr * r);
+    DF::Acc acc = DF::begin(float2{});
+    for (int k = q; k < nq; k += 8) {
+      const float4 j = J4[k];
+      const float2 *xk = x + 4 * k;
+      DF::sub_f(acc, j.x, DF::neg(xk[0]));
+      DF::sub_f(acc, j.y, DF::neg(xk[1]));
+      DF::sub_f(acc, j.z, DF::neg(xk[2]));
+      DF::sub_f(acc, j.w, DF::neg(xk[3]));
+    }
+    float2 v = DF::end(acc);
+#pragma unroll
+    for (int o = 4; o; o >>= 1) v = DF::add(v, shfl_xor_elt(v, o));
+    if (q == 0 && row < dy) y[row] = DF::to(v) * inv_sigma;
+  }
+}
+
 // Shared bytes of the two staging buffers of wb_gram_rows.
 __host__ __device__ inline size_t wb_stage2_bytes(int dy) {
   return 2 * (size_t)((dy + kHT - 1) / kHT * kHT) * kWbLd * sizeof(float);
@@ -629,8 +658,12 @@ __global__ void __launch_bounds__(NT, kWbMinBlocks) k_wb_propose(ReducedArgs a) 
       if (4 * blk + q < dy) xi2[4 * blk + q] = n4[q];
   }
   __syncthreads();
-  if constexpr (sizeof(TJ) == 4) {  // K xi1 from J staged through the (still empty) factor region
-    if (wb_ring4_fits(dy)) {
+  if constexpr (sizeof(TJ) == 4) {  // K xi1: by row quads, else J staged through the factor region
+    if ((r & 3) == 0 && (reinterpret_cast<uintptr_t>(J) & 15) == 0) {
+      rows_times_quads(reinterpret_cast<const float *>(J), dy, r, inv_sigma,
+                       reinterpret_cast<const float2 *>(x1E), Kxi);
+      __syncthreads();
+    } else if (wb_ring4_fits(dy)) {
       wb_gram_rows<A, false, 4>(reinterpret_cast<const float *>(J), dy, r, 0.0, inv_sigma,
                                 nullptr, reinterpret_cast<float *>(sm + lay.Ms),
                                 reinterpret_cast<const float2 *>(x1E), nullptr, false, Kxi, Kxi);
